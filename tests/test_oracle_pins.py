@@ -1,0 +1,299 @@
+"""Pins of the CPU oracle against closed forms, brute force, library
+routines and invariants (none of them re-type the oracle's formulas)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate
+
+import lattice_inputs as li
+from oracle import blocks, closed_forms as cf, dense, grid, sinc
+from tests import _cases
+
+
+# ---------------- Eq. 2.7: the R-term rule for 1/z ----------------
+
+def test_sinc_rule_converges_in_R():
+    errs = [sinc.sinc_table(R, 1e-3, 1e2)[2] for R in (12, 20, 28, 36)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < errs[0] / 100
+    # independent check of the reported error at off-grid points
+    t, c, e = sinc.sinc_table(32, 1e-3, 1e2)
+    z = np.exp(np.random.default_rng(1).uniform(np.log(1e-3), np.log(1e2), 500))
+    approx = np.exp(-(z[:, None] * t[None, :]) ** 2) @ c
+    assert np.max(np.abs(approx * z - 1)) < 2 * e + 1e-12
+
+
+# ---------------- closed-form cell integral of a Gaussian ----------------
+
+@pytest.mark.parametrize("t,lo,hi", [(0.3, -1.0, 0.5), (5.0, 2.0, 2.1), (5.0, -2.1, -2.0),
+                                     (40.0, -0.01, 0.02), (0.01, 100.0, 100.5), (3.0, 4.0, 4.2)])
+def test_gauss_cell_integral_vs_quad(t, lo, hi):
+    ref, _ = scipy.integrate.quad(lambda s: math.exp(-(t * s) ** 2), lo, hi, epsabs=0,
+                                  epsrel=1e-13)
+    got = float(grid.gauss_cell_integral(np.float64(t), np.float64(lo), np.float64(hi)))
+    assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-300
+
+
+def test_prism_formula_vs_quadrature():
+    # a cell away from the origin: plain adaptive cubature
+    lo, hi = (0.3, -0.2, 0.5), (0.7, 0.4, 0.9)
+    ref, _ = scipy.integrate.tplquad(lambda z, y, x: 1 / math.sqrt(x * x + y * y + z * z),
+                                     lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], epsabs=1e-12)
+    assert abs(cf.cell_integral_inv_r(lo, hi) - ref) < 1e-9
+    # a cube centred on the singularity: 8 corner cubes by symmetry, and
+    # int_{[0,1]^3} 1/r in spherical shells of the cube (1D quadrature)
+    full = cf.cell_integral_inv_r((-0.5,) * 3, (0.5,) * 3)
+    unit = cf.cell_integral_inv_r((0.0,) * 3, (1.0,) * 3)
+    assert abs(full - 8 * unit / 4.0) < 1e-12          # scaling: int over [0,a]^3 ~ a^2
+    ref, _ = scipy.integrate.tplquad(lambda z, y, x: 1 / math.sqrt(x * x + y * y + z * z + 1e-300),
+                                     0, 1, 0, 1, 0, 1, epsabs=1e-9)
+    assert abs(unit - ref) < 1e-6
+
+
+def test_projected_kernel_vs_exact_prism():
+    """Eqs. 2.6-2.7: the rank-R P0 tensor of one nucleus approaches the exact
+    cell integrals of 1/|x|, faster for larger R."""
+    errs = []
+    for R in (16, 32):
+        p = _cases.single_gaussian(alpha=1.0, n0=8, box=6.0, R=R)
+        so, slabs = grid.potential_slabs(p)
+        P = slabs[so]
+        x, X0, _ = grid.axis_nodes(p, 0)
+        a = X0 + 0.5 * p.b0
+        h = p.h
+        rng = np.random.default_rng(2)
+        idx = [tuple(rng.integers(0, p.N[0], 3)) for _ in range(40)]
+        idx += [tuple([int(np.argmin(abs(x - a)))] * 3)]   # the singular cell
+        e = 0.0
+        for i in idx:
+            lo = [x[i[d]] - h / 2 - a for d in range(3)]
+            hi = [x[i[d]] + h / 2 - a for d in range(3)]
+            ex = cf.cell_integral_inv_r(lo, hi)
+            e = max(e, abs(P[i] - ex) / ex)
+        errs.append(e)
+    assert errs[1] < errs[0] / 5
+    assert errs[1] < 5e-3
+
+
+def test_potential_product_of_window_sums_equals_3d_window():
+    """Eq. 2.13 (window sums inside each axis factor) equals the explicit sum
+    over the 3D window of lattice cells (brute force, tiny 3D lattice)."""
+    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    so, slabs = grid.potential_slabs(p)
+    P = grid.potential_full_window(p)
+    assert np.max(np.abs(slabs[so] - P)) <= 1e-13 * np.max(np.abs(P))
+
+
+# ---------------- Galerkin matrices vs brute force on the 3D grid ----------------
+
+def _phi3d(p):
+    Gs = [grid.basis_axis(p, a) for a in range(3)]
+    ks, mu = dense._index(p)
+    return np.stack([Gs[0][:, ks[0][a], mu[a]][:, None, None] *
+                     Gs[1][:, ks[1][a], mu[a]][None, :, None] *
+                     Gs[2][:, ks[2][a], mu[a]][None, None, :] for a in range(p.Nb)])
+
+
+def _stencil(u, ax, per, w_c, w_n):
+    """Apply w_c*u_i + w_n*(u_{i-1} + u_{i+1}) along ax (zero outside for Dirichlet)."""
+    out = w_c * u
+    for s in (-1, 1):
+        if per:
+            out = out + w_n * np.roll(u, s, axis=ax)
+        else:
+            sh = np.zeros_like(u)
+            src = [slice(None)] * 3
+            dst = [slice(None)] * 3
+            if s == 1:
+                src[ax], dst[ax] = slice(0, -1), slice(1, None)
+            else:
+                src[ax], dst[ax] = slice(1, None), slice(0, -1)
+            sh[tuple(dst)] = u[tuple(src)]
+            out = out + w_n * sh
+    return out
+
+
+@pytest.mark.parametrize("case", ["periodic", "box"])
+def test_mass_kinetic_potential_vs_3d_brute_force(case):
+    if case == "periodic":
+        p = _cases.periodic_3d_small(L=(2, 1, 2), n0=6, R=8)
+    else:
+        p = _cases.box_chain_small(L=3, n0=4, pad=3, n_perp=10, R=8)
+    H, S, A, V = dense.build(p, with_parts=True)
+    phi = _phi3d(p)
+    h = p.h
+    per = [bool(x) for x in p.periodic]
+    S3 = phi.copy()
+    for ax in range(3):
+        S3 = np.stack([_stencil(f, ax, per[ax], 4 * h / 6, h / 6) for f in S3])
+    Sb = np.einsum("aijk,bijk->ab", phi, S3)
+    Ab = 0
+    for pax in range(3):
+        T = phi.copy()
+        for ax in range(3):
+            if ax == pax:
+                T = np.stack([_stencil(f, ax, per[ax], 2 / h, -1 / h) for f in T])
+            else:
+                T = np.stack([_stencil(f, ax, per[ax], 4 * h / 6, h / 6) for f in T])
+        Ab = Ab + np.einsum("aijk,bijk->ab", phi, T)
+    so, slabs = grid.potential_slabs(p)
+    P = grid.potential_full_window(p)
+    Vb = np.einsum("aijk,bijk,ijk->ab", phi, phi, P)
+    for M, B in ((S, Sb), (A, Ab), (V, Vb)):
+        assert np.max(np.abs(M - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+# ---------------- grid quantities approach the continuum closed forms ----------------
+
+def test_overlap_kinetic_converge_to_closed_forms():
+    """s and p GTOs pairs, two centres on a periodic-free axis: the 1D P1
+    mass/stiffness forms approach the analytic integrals as O(h^2)."""
+    errs = []
+    for n0 in (8, 16, 32):
+        p = li.Problem(L=(2, 1, 1), periodic=(0, 0, 0), N=(2 * n0 + 2 * int(8 * n0 / 2), n0, n0),
+                       n0=n0, b0=2.0, Z=np.array([1.0]), frac=np.array([[0.3, 0.5, 0.5]]),
+                       exps=np.array([0.7, 1.3]), ang=np.array([0, 1]), centre=np.array([0, 0]),
+                       R=8)
+        forms = dense.axis_forms(p)
+        _, s, a = forms[0]
+        x, X0, _ = grid.axis_nodes(p, 0)
+        e = 0.0
+        for (k, mu), (m, nu) in [((0, 0), (1, 0)), ((0, 1), (1, 0)), ((0, 1), (1, 1)),
+                                 ((0, 0), (0, 0))]:
+            A = X0 + (k + 0.3) * p.b0
+            B = X0 + (m + 0.3) * p.b0
+            sref, tref = cf.overlap_and_stiffness_1d(p.exps[mu], A, p.ang[mu] == 1,
+                                                     p.exps[nu], B, p.ang[nu] == 1)
+            e = max(e, abs(s[k, mu, m, nu] - sref), abs(a[k, mu, m, nu] - tref) / 10)
+        errs.append(e)
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3
+    assert errs[2] < 2e-3
+
+
+def test_nuclear_attraction_converges():
+    """V entry of an s-Gaussian pair against the Boys-function closed form."""
+    errs = []
+    for n0 in (8, 16):
+        p = _cases.single_gaussian(alpha=0.8, n0=n0, box=10.0, R=40)
+        V = dense.potential_matrix(p)
+        x, X0, _ = grid.axis_nodes(p, 0)
+        C = [X0 + 0.5 * p.b0] * 3
+        ref = cf.nuclear_ss(0.8, C, 0.8, C, C)
+        errs.append(abs(V[0, 0] - ref) / ref)
+    assert errs[1] < errs[0] / 2.5
+    assert errs[1] < 1e-2
+
+
+def test_hydrogen_single_gaussian_energy():
+    """Textbook variational energy of one normalised s-Gaussian on a Z=1
+    nucleus: E(a) = 3a/2 - 2 sqrt(2a/pi), minimum -4/(3 pi)."""
+    alpha = 8 / (9 * math.pi)
+    exact = cf.hydrogen_single_gaussian(alpha)
+    assert abs(exact + 4 / (3 * math.pi)) < 1e-14
+    errs = []
+    for n0 in (8, 16):
+        p = _cases.single_gaussian(alpha=alpha, n0=n0, box=20.0, R=40)
+        ev = dense.solve(p)
+        errs.append(abs(ev[0] - exact))
+    assert errs[1] < errs[0] and errs[1] < 5e-3
+
+
+# ---------------- block-circulant structure (Lemma 3.1, Prop. A.1) ----------------
+
+@pytest.mark.parametrize("maker", ["chain_m0_4", "chain_m0_8", "lattice_3d"])
+def test_union_of_block_spectra_equals_dense_spectrum(maker):
+    if maker == "chain_m0_4":
+        p = _cases.periodic_chain_small(L=5, n0=8, n_perp=16, m0=4, R=16)
+    elif maker == "chain_m0_8":
+        p = _cases.periodic_chain_small(L=6, n0=6, n_perp=16, m0=8, R=16)
+    else:
+        p = _cases.periodic_3d_small(L=(3, 2, 2), n0=5, R=8)
+    H, S = dense.build(p)
+    ev = dense.eigvals(H, S)
+    evb, per_block = blocks.circulant_route(p, H, S)
+    assert np.max(np.abs(ev - evb)) <= _cases.eig_tol(S, ev, base=1e-11)
+    # circulant structure: block (r, c) depends on r - c only, and A_{L-k} = A_k^T
+    m0 = p.m0
+    if p.L[1] == p.L[2] == 1:
+        L = p.L[0]
+        for r in range(L):
+            for c in range(L):
+                blk = H[r * m0:(r + 1) * m0, c * m0:(c + 1) * m0]
+                ref = H[((r - c) % L) * m0:((r - c) % L + 1) * m0, :m0]
+                assert np.max(np.abs(blk - ref)) <= 1e-13 * np.max(np.abs(H))
+
+
+def test_m0_1_circulant_is_fft_of_first_column():
+    """m0 = 1: the pencil is diagonalised by the DFT, eigenvalues are
+    fft(H[:,0]) / fft(S[:,0]) (numpy.fft, Appendix A.1)."""
+    p = _cases.single_gaussian(alpha=0.4, n0=6, R=16, L=7, periodic=True)
+    p = li.Problem(L=(7, 1, 1), periodic=(1, 0, 0), N=(42, 18, 18), n0=6, b0=2.0,
+                   Z=p.Z, frac=p.frac, exps=p.exps, ang=p.ang, centre=p.centre, R=16,
+                   sinc_t=p.sinc_t, sinc_c=p.sinc_c)
+    H, S = dense.build(p)
+    lam = np.fft.fft(H[:, 0]) / np.fft.fft(S[:, 0])
+    assert np.max(np.abs(lam.imag)) < 1e-13
+    ev = dense.eigvals(H, S)
+    assert np.max(np.abs(np.sort(lam.real) - ev)) < 1e-12
+    # block j of the direct DFT is the j-th FFT coefficient (same sign convention)
+    Hb = blocks.fourier_blocks(p, blocks.generators_from_dense(p, H))[:, 0, 0]
+    Sb = blocks.fourier_blocks(p, blocks.generators_from_dense(p, S))[:, 0, 0]
+    assert np.max(np.abs(Hb - np.fft.fft(H[:, 0]))) < 1e-13 * np.max(np.abs(H))
+    assert np.max(np.abs(Sb - np.fft.fft(S[:, 0]))) < 1e-13 * np.max(np.abs(S))
+
+
+def test_fourier_blocks_hermitian_and_conjugate_pairs():
+    """Cor. A.2: symmetric generators give Hermitian blocks and
+    Abar_{L-j} = conj(Abar_j)."""
+    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    H, S = dense.build(p)
+    Hb = blocks.fourier_blocks(p, blocks.generators_from_dense(p, H))
+    L1, L2, L3 = p.L
+    Hb = Hb.reshape(L1, L2, L3, p.m0, p.m0)
+    assert np.max(np.abs(Hb - np.conj(np.swapaxes(Hb, -1, -2)))) < 1e-12
+    for j in np.ndindex(L1, L2, L3):
+        jm = tuple((-np.array(j)) % np.array(p.L))
+        assert np.max(np.abs(Hb[jm] - np.conj(Hb[j]))) < 1e-12
+
+
+# ---------------- box chains: Toeplitz interior, boundary defect ----------------
+
+def test_box_chain_toeplitz_interior_and_wall_defect():
+    """Sec. 2.3 (A)/(B): with the replicated potential the box matrix is block
+    Toeplitz away from the walls; the defect is confined to the blocks whose
+    supports reach the padding / walls."""
+    p = _cases.box_chain_small(L=24, n0=5, pad=8, n_perp=14, R=12)
+    H, S = dense.build(p)
+    m0, L = p.m0, p.L[0]
+    blk = lambda M, r, c: M[r * m0:(r + 1) * m0, c * m0:(c + 1) * m0]
+    kc = L // 2
+    scale = np.max(np.abs(H))
+    G = grid.basis_axis(p, 0)
+    nz = np.nonzero(np.any(G[:, kc, :] != 0, axis=1))[0]
+    x, X0, _ = grid.axis_nodes(p, 0)
+    reach = int(np.ceil(max(abs(x[nz[0]] - X0 - kc * p.b0), abs(x[nz[-1]] - X0 - (kc + 1) * p.b0))
+                        / p.b0)) + 1
+    for d in range(-3, 4):
+        T = blk(H, kc + d, kc)
+        for k in range(L):
+            if not (0 <= k + d < L):
+                continue
+            far = min(k, k + d) >= reach and max(k, k + d) <= L - 1 - reach
+            diff = np.max(np.abs(blk(H, k + d, k) - T))
+            if far:
+                assert diff <= 1e-13 * scale
+    # the end blocks differ from the interior ones (the defect exists)
+    assert np.max(np.abs(blk(H, 0, 0) - blk(H, kc, kc))) > 1e-8 * scale
+
+
+def test_defect_reduces_to_charge_change_single_molecule():
+    """A substitution Z -> Z' of the only nucleus of a single molecule equals
+    solving with charge Z' (the defect kernel is the molecule's kernel)."""
+    p = _cases.single_gaussian(alpha=0.9, n0=6, box=8.0, R=16)
+    import dataclasses
+    q = dataclasses.replace(p, defects=[li.Defect(cell=(0, 0, 0), nucleus=0, newZ=2.5)])
+    r = dataclasses.replace(p, Z=np.array([2.5]))
+    Hq, _ = dense.build(q)
+    Hr, _ = dense.build(r)
+    assert np.max(np.abs(Hq - Hr)) <= 1e-13 * np.max(np.abs(Hr))
