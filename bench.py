@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 lattice Fock eigensolver.
+
+One step = one pass of the whole hot path over one batch: B Dirichlet box
+chains shaped like the paper's hydrogen chains (64 x 1 x 1 cells of 2.0 bohr,
+n0 = 15 nodes per cell, 1024 x 256 x 256 nodes, m0 = 8 GTOs per cell from the
+8-function recipe with one seed per request, rank R = 32, lowest 16
+eigenpairs: assembly + circulant embedding + preconditioned block iteration)
+and, for every request, its periodic counterpart (the same chain made
+periodic, all 512 eigenvalues: assembly + FFT block diagonalisation + 64
+Fourier-block eigensolves) -- the box / periodic pairing of the paper's
+Table 1.  value = solves per second (2B solves per step), all inputs resident
+in HBM when the timed region starts; e2e = the same through fock_solve with
+host inputs and host outputs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lattice_inputs as li  # noqa: E402
+
+METRIC = "lattice Fock solves/s"
+UNIT = "solves/s"
+L_CHAIN, N0, PAD, NPERP, R_RANK, K_EIG = 64, 15, 32, 256, 32, 16
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) dense, nominal
+
+
+def workload(batch, rank):
+    """The step's problems: B box chains, then their periodic counterparts."""
+    box = [li.config2(rank * batch + r, L=L_CHAIN, n0=N0, pad=PAD, n_perp=NPERP, R=R_RANK)
+           for r in range(batch)]
+    for p in box:
+        p.k_eig = K_EIG
+    per = [p.as_periodic_chain() for p in box]
+    for p in per:
+        p.k_eig = 0
+    return box + per
+
+
+def config_dict(batch, world):
+    return {"workload": f"box chain {L_CHAIN}x1x1 (n0={N0}, grid {L_CHAIN * N0 + 2 * PAD}x{NPERP}x{NPERP}, "
+                        f"m0=8, R={R_RANK}, lowest {K_EIG}) + periodic counterpart (all eigenvalues); "
+                        f"batch {batch} requests/GPU",
+            "requests_per_gpu": batch, "solves_per_step_per_gpu": 2 * batch,
+            "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (512 MB write)"}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_sample(npairs, seed0=0):
+    """Time the CPU oracle on npairs (box, periodic) requests of the workload."""
+    from oracle import dense, sinc
+    ps = []
+    for r in range(npairs):
+        b = li.config2(seed0 + r, L=L_CHAIN, n0=N0, pad=PAD, n_perp=NPERP, R=R_RANK)
+        b.k_eig = K_EIG
+        ps += [b, b.as_periodic_chain()]
+    t0 = time.perf_counter()
+    for p in ps:
+        t, c, _ = sinc.table_for(p)
+        q = p.with_table(t, c)
+        q.k_eig = p.k_eig
+        dense.solve(q)
+    dt = time.perf_counter() - t0
+    return len(ps), dt
+
+
+def cpu_baseline(npairs):
+    n, dt = oracle_sample(npairs)
+    return {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{npairs} box + {npairs} periodic requests of the workload (dense FP64 Galerkin "
+                      f"matrices by 3D grid contraction + LAPACK eigh), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on bounded samples."""
+    if rank != 0:
+        return
+    npairs = max(1, args.ref_pairs)
+    for _ in range(args.warmup):
+        oracle_sample(npairs)
+    tot, n = 0.0, 0
+    for s in range(args.steps):
+        k, dt = oracle_sample(npairs, seed0=100 + s * npairs)
+        tot += dt
+        n += k
+    val = n / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(config_dict(npairs, 1), workload="CPU oracle on " + config_dict(npairs, 1)["workload"]),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{npairs} box + {npairs} periodic requests per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- work models
+def fp64_flops_per_step(problems, outs):
+    """Algorithmic FP64 operation counts of the kernels of one step (the
+    models stated in the design notes), keyed by kernel timer name."""
+    w = {}
+    for p, o in zip(problems, outs):
+        m0 = len(p.exps)
+        if p.is_box:
+            k = p.k_eig
+            n = p.L[0] * m0
+            it = max(o["iters"], 1)
+            # Rayleigh-Ritz of the 3k-column basis: two symmetric eigensolves
+            # (eigenvalues + vectors, ~9 n^3 each by tridiagonal QR) and the
+            # n^2 x r reduction products
+            nb = 3 * k
+            w["k_rr"] = w.get("k_rr", 0) + it * (2 * 9 * nb ** 3 + 4 * nb ** 3)
+            w["k_gemm_tn"] = w.get("k_gemm_tn", 0) + it * (2 * 2 * n * nb * nb + 2 * 2 * n * k * k)
+            w["k_gemm_nn"] = w.get("k_gemm_nn", 0) + it * (2 * n * nb * 2 * k + 6 * 2 * n * k * k)
+        else:
+            ncell = int(np.prod(p.L))
+            T = len(p.Z) * p.R
+            # per Fourier block: Hadamard combine over T+3 factor terms on the
+            # upper triangle (complex, 3 products + accumulate ~ 20 flops),
+            # Cholesky (4/3 m^3), reduction (8 m^3), Householder tridiagonal
+            # (16/3 m^3), bisection (m eigenvalues x 55 steps x 4 m)
+            per = (T + 3) * m0 * (m0 + 1) // 2 * 20 + (4 / 3 + 8 + 16 / 3) * m0 ** 3 + 55 * 4 * m0 * m0
+            w["k_fblocks_eig"] = w.get("k_fblocks_eig", 0) + ncell * per
+    return w
+
+
+# --------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--cpu-pairs", type=int, default=8)
+    ap.add_argument("--ref-pairs", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-json", default="")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1702_00339_gb300 import build, fock
+    build.build()
+    torch.cuda.set_device(local)
+    dev = local
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fock.Context(dev, stream=stream.cuda_stream)
+    problems = workload(args.batch, rank)
+    nsolve = len(problems)
+
+    # ---- device-resident timing ----
+    plan = ctx.plan(problems)
+    for _ in range(args.warmup):
+        plan.execute()
+    outs = plan.outputs(check=False)
+    bad = [o["status"] for o in outs if o["status"] != 0]
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
+    ctx.profile(True)
+    ctx.profile_reset()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.execute()
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = nsolve * world * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through fock_solve (host inputs and outputs) ----
+    e2e_steps = max(2, min(args.steps, 3))
+    ctx.solve(problems, check=False)   # grows the context arena once, outside the timed loop
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = ctx.solve(problems, check=False)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e_val = nsolve * world * e2e_steps / float(te_t.item())
+    d2h = sum(8 * r["n_evals"] + (4 * r["n_evals"] if r["block_of"] is not None else 0) for r in res)
+
+    # ---- roofline of the dominant kernel (live CUDA-event timers) ----
+    launches = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    flops = fp64_flops_per_step(problems, outs)
+    peak = FP64_NOMINAL_TFLOPS
+    if dom[0] in flops:
+        nl, dms = dom[1]
+        per_launch = flops[dom[0]] * args.steps / nl
+        achieved = per_launch / (dms / nl / 1e3) / 1e12
+        roof = {"kernel": dom[0], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz), derived",
+                "share_of_step": dms / ms}
+    else:
+        roof = {"kernel": dom[0], "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "share_of_step": dom[1][1] / ms}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_dict(args.batch, world),
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(plan.upload_bytes),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
+                "box_iters": [int(o["iters"]) for o in outs[:args.batch]][:8],
+                "statuses_nonzero": len(bad)}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
+        print(json.dumps(line), flush=True)
+        if args.profile_json:
+            with open(args.profile_json, "w") as f:
+                json.dump({k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}, f, indent=1)
+    plan.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * libfock -- lattice core-Hamiltonian eigensolver on one GB300 (sm_103a).
+ *
+ * C ABI.  Plain pointers and sizes only; no exceptions cross it; every
+ * function returns a fock_status (0 = success).  All host pointers are
+ * owned by the caller and read (or written) only during the call.  Device
+ * memory used by a context is owned by the context and released by
+ * fock_destroy.
+ *
+ * The problem (struct fock_problem) follows the paper's statement of the
+ * method (Sec. 2.1-2.3, Sec. 3.3): an L1 x L2 x L3 lattice of unit cells
+ * of size b0, each holding M0 nuclei (charges Z, positions as cell
+ * fractions) and m0 separable Gaussian (GTO) basis functions; a uniform
+ * grid of step h = b0/n0 with N_l nodes per axis; a rank-R Gaussian-sum
+ * quadrature of the Newton kernel (Eqs. 2.6-2.7).  The discrete operator is
+ * H = A/2 - V (Eqs. 2.4-2.5) with A, S the Galerkin Laplacian and mass
+ * matrices of the P1-interpolated GTOs (Eqs. 2.15-2.17) and V the Galerkin
+ * matrix of the lattice-summed P0 potential (Lemma 2.1, Eq. 2.13, Eq. 3.6);
+ * the eigenproblem is H C = S C Lambda.
+ *
+ * Grid conventions (identical in the oracle and the kernels):
+ *   periodic axis:  N = L*n0 nodes at x_i = (i + 1/2) h, period N h;
+ *   Dirichlet axis: N nodes at x_i = (i + 1) h, walls at 0 and (N+1) h,
+ *                   lattice origin X0 = (pad + 1/2) h, pad = (N - L n0) / 2
+ *                   (integer division), N >= L n0.
+ * Basis index a = kbar*m0 + mu, kbar = (k1*L2 + k2)*L3 + k3.
+ */
+#ifndef FOCK_H
+#define FOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FOCK_OK = 0,
+  FOCK_EINVAL = -1,    /* malformed problem or argument */
+  FOCK_ENOMEM = -2,    /* the request does not fit the context's HBM budget */
+  FOCK_ENOCONV = -3,   /* iterative solve hit maxit; best estimates returned */
+  FOCK_ETIMEOUT = -4,  /* a bounded wait ran out */
+  FOCK_EAGAIN = -5,    /* result not ready yet (serving poll) */
+  FOCK_ECUDA = -6      /* a CUDA call failed; see fock_last_error */
+} fock_status;
+
+enum { FOCK_FP64 = 0, FOCK_MIXED = 1 };
+enum { FOCK_ANG_S = 0, FOCK_ANG_PX = 1, FOCK_ANG_PY = 2, FOCK_ANG_PZ = 3 };
+enum { FOCK_OP_H = 0, FOCK_OP_S = 1 };
+
+/* Substitution of nucleus `nucleus` of lattice cell `cell` by charge newZ
+ * (newZ = 0: vacancy; the basis functions stay).  Only the defect's own
+ * rank-R kernel is added (no lattice window, no replication).  The paper
+ * only motivates defects (Sec. 1, Sec. 2.3 item (B)); supported on chains
+ * (at most one axis with L > 1). */
+typedef struct {
+  int cell[3];
+  int nucleus;
+  double newZ;
+} fock_defect;
+
+typedef struct {
+  int L[3];              /* lattice cells per axis, >= 1 */
+  int periodic[3];       /* 1 periodic, 0 Dirichlet */
+  int N[3];              /* grid nodes per axis (periodic: L*n0) */
+  int n0;                /* nodes per cell, h = b0 / n0 */
+  double b0;             /* cell size (bohr) */
+  int M0;                /* nuclei per cell */
+  const double* Z;       /* [M0] charges */
+  const double* frac;    /* [M0][3] positions as fractions of the cell */
+  int m0;                /* GTOs per cell, 1..32 */
+  const double* exps;    /* [m0] exponents alpha > 0 */
+  const int* ang;        /* [m0] FOCK_ANG_* */
+  const int* centre;     /* [m0] nucleus index of each GTO */
+  int R;                 /* quadrature rank, 3..64 */
+  const double* sinc_t;  /* [R] Gaussian parameters t_q, or NULL: default rule */
+  const double* sinc_c;  /* [R] weights c_q, or NULL: default rule */
+  double eps_support;    /* GTO support cut-off (<= 0: 1e-14) */
+  int ndef;              /* number of defects */
+  const fock_defect* defects;
+  int k_eig;             /* box / defect solves: eigenpairs wanted (0: 16) */
+  int precision;         /* FOCK_FP64 (FOCK_MIXED reserved) */
+} fock_problem;
+
+/* Output slot of one problem in a batched solve. */
+typedef struct {
+  double* evals;    /* [n_evals]: periodic: all |L|*m0 eigenvalues; box/defect:
+                       the k_eig lowest; ascending.  Host or device memory
+                       (see `outputs_on_device`). */
+  int* block_of;    /* optional [n_evals] (periodic only): linear Fourier index
+                       jbar = (j1*L2 + j2)*L3 + j3 of each eigenvalue, else NULL */
+  int n_evals;      /* out: number written */
+  int iters;        /* out: iterations of the box eigensolver (0 periodic) */
+  double resid;     /* out: max relative residual |Hx - lSx| / (|l| |Sx|) */
+  int status;       /* out: fock_status of this problem */
+} fock_output;
+
+typedef struct fock_ctx fock_ctx;
+typedef struct fock_blocks fock_blocks;
+
+/* Context: owns device memory (a growable arena) and one CUDA stream.
+ * device: CUDA ordinal.  hbm_budget_bytes: cap on the arena (0: 90% of the
+ * free memory at creation).  stream: a cudaStream_t to run on, or NULL to
+ * create a private one.  Errors: FOCK_EINVAL, FOCK_ECUDA. */
+int fock_create(fock_ctx** ctx, int device, size_t hbm_budget_bytes, void* stream);
+/* Frees the context; every fock_blocks / fock_plan made from it must be
+ * freed first (they use its stream). */
+void fock_destroy(fock_ctx* ctx);
+const char* fock_last_error(const fock_ctx* ctx);
+int fock_synchronize(fock_ctx* ctx);
+
+/* Default quadrature rule (Eq. 2.7 read as a sinc rule in u = log t with a
+ * tail node, (u_lo, u_hi) tuned on [zmin, zmax]); writes t[R], c[R] and the
+ * measured maximum relative error.  Host only. */
+int fock_sinc_table(int R, double zmin, double zmax, double* t, double* c, double* err);
+/* The default z-range of a problem (zmin = h/100, zmax = twice a bound on
+ * the nucleus-node distance over the lattice window). */
+int fock_default_range(const fock_problem* p, double* zmin, double* zmax);
+
+/* Batched solve (stages (a)+(b) for periodic problems, (a)+(c) for box
+ * chains and problems with defects).  nprob problems, outs[nprob].
+ * Evals pointers are device pointers when outputs_on_device != 0.
+ * Returns the first non-zero per-problem status, or FOCK_OK. */
+int fock_solve(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_output* outs,
+               int outputs_on_device);
+
+/* Stage (a) for one problem: separable rank-R assembly of the generator
+ * blocks (Lemma 2.1, Prop. 2.2, Lemma 3.4).  The handle keeps the per-axis
+ * factor tensors and (box) the Toeplitz generators, the embedding Fourier
+ * blocks and the boundary perturbation resident on the device. */
+int fock_assemble(fock_ctx* ctx, const fock_problem* p, fock_blocks** out);
+void fock_blocks_free(fock_blocks* b);
+
+/* Sizes of an assembled handle: N_b, the number of generator blocks
+ * written by fock_blocks_copy_generators, of boundary blocks, and the
+ * circulant size used by the matvec (|L| periodic; M >= L + D box). */
+int fock_blocks_info(const fock_blocks* b, int* Nb, int* ngen, int* nbound, int* mcirc);
+
+/* Copies generators to host memory, layout [g][mu][nu] row-major.
+ * Periodic: the |L| generators A_k = block (row cell k, column cell 0) in
+ * kbar order (ngen = |L|).  Box chain: T_d = block (k+d, k) of an interior
+ * cell for d = -D..D (ngen = 2D+1, d = g - D), and the boundary blocks E
+ * with their (row cell, column cell) in bound_rc[2*nbound] such that
+ * H = BToepl(T) + E.  Any output pointer may be NULL. */
+int fock_blocks_copy_generators(const fock_blocks* b, double* H, double* S, double* EH,
+                                double* ES, int* bound_rc);
+
+/* Periodic eigenvalues by FFT block-diagonalisation (Lemma 3.1, Thm 3.3,
+ * Eqs. 3.11-3.12): evals[|L|*m0] ascending (host), block_of optional. */
+int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of);
+
+/* y = H x or y = S x (which = FOCK_OP_H / FOCK_OP_S) for an assembled box
+ * chain or periodic problem, by the block-circulant embedding FFT matvec
+ * plus the boundary/defect blocks (Remark 3.2, Sec. 2.3).  x, y: N_b x nvec,
+ * column-major; device pointers when on_device != 0, else host. */
+int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
+                         double* y, int nvec, int on_device);
+
+/* Lowest k eigenpairs of (H, S) by preconditioned block iteration
+ * (Sec. 2.3, "structured iteration on subspace"; LOBPCG with the embedding's
+ * shifted inverse as preconditioner).  evals[k] host; evecs[N_b x k]
+ * (host, column-major, S-orthonormal) or NULL; iters out.  Returns
+ * FOCK_ENOCONV (with the best estimates written) when maxit is reached. */
+int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int maxit,
+                 double* evals, double* evecs, int* iters);
+
+/* ---- device-resident batched execution ----
+ * fock_plan_create validates and plans nprob problems, allocates their device
+ * memory and uploads every input (parameters, index maps, descriptors) once.
+ * fock_plan_execute runs the whole hot path -- stage (a) for all, (b) for
+ * periodic problems, (c) for box chains -- on the context's stream; results
+ * stay on the device until fock_plan_outputs copies them (host or device
+ * destinations).  A plan may be executed any number of times. */
+typedef struct fock_plan fock_plan;
+int fock_plan_create(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_plan** out);
+int fock_plan_execute(fock_plan* plan, double tol, int maxit);
+int fock_plan_outputs(fock_plan* plan, fock_output* outs, int outputs_on_device);
+/* bytes uploaded by fock_plan_create, bytes of device memory held, and the
+ * number of eigenvalues the plan returns in total */
+int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_bytes, size_t* n_evals);
+void fock_plan_free(fock_plan* plan);
+
+/* ---- kernel timers (CUDA events recorded on the context's stream) ----
+ * While enabled, every kernel launch of the library is bracketed by events;
+ * fock_profile_read synchronizes and returns, per kernel name, the number of
+ * launches and the summed device time.  names: buffer of `cap` entries of
+ * 32 chars.  Returns the number of distinct kernels written. */
+int fock_profile_enable(fock_ctx* ctx, int on);
+int fock_profile_reset(fock_ctx* ctx);
+int fock_profile_read(fock_ctx* ctx, int cap, char* names, int* launches, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOCK_H */

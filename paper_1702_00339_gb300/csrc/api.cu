@@ -1,0 +1,1433 @@
+// libfock host layer: problem validation, geometry and index maps, the
+// device memory plan of a batch of problems, the stage drivers and the C ABI.
+//
+// A batch is planned twice with the same deterministic code: once to size
+// the device slab, once with the real base address to fill the descriptors.
+// Every array of the path lives in that slab; all arithmetic of the method
+// runs in the kernels (k_assemble.cu, k_eig.cu, k_matvec.cu, k_lobpcg.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fock.h"
+#include "common.cuh"
+
+namespace fock {
+
+
+
+
+
+
+
+
+
+
+
+
+
+
+
+// launchers (defined in the .cu files)
+void launch_vec1d(const ProbDev*, const SegDesc*, int, const SegDesc*, int, const DefTab*, int, cudaStream_t);
+void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream_t);
+void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
+void launch_axis_dft(const ProbDev*, const DftTask*, int, cudaStream_t);
+void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
+void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
+void launch_sort_small(const SortTask*, int, int, cudaStream_t);
+void launch_sort_global(double*, int*, int, double*, int*, cudaStream_t);
+void launch_twiddles(CircDev*, int, cudaStream_t);
+void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t);
+void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
+void launch_eapply(const EApplyTask*, int, cudaStream_t);
+void launch_band_factor(const BandTask*, int, cudaStream_t);
+void launch_band_solve(const BandTask*, int, cudaStream_t);
+__global__ void k_init_x(const InitTask*);
+__global__ void k_gemm_tn(const GemmTask*);
+__global__ void k_gemm_nn(const GemmTask*);
+__global__ void k_resid(const ResidTask*, double);
+__global__ void k_rr(const RRTask*, int);
+__global__ void k_copy_cols(const CopyTask*);
+}  // namespace fock
+
+using namespace fock;
+
+struct fock_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  char* arena = nullptr;
+  size_t arena_cap = 0;
+  std::string err;
+  // kernel timers: events recorded around launches while enabled
+  bool prof = false;
+  struct Rec { const char* name; int nlaunch; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+thread_local fock_ctx* g_prof = nullptr;   // context whose launches are being timed
+
+cudaEvent_t prof_event(fock_ctx* c) {
+  if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets the launches issued in its scope with two events on the stream.
+struct ProfScope {
+  fock_ctx* c = nullptr;
+  size_t idx = 0;
+  ProfScope(const char* name, int nlaunch) {
+    if (!g_prof || !g_prof->prof) return;
+    c = g_prof;
+    fock_ctx::Rec r{name, nlaunch, prof_event(c), prof_event(c)};
+    cudaEventRecord(r.a, c->stream);
+    idx = c->recs.size();
+    c->recs.push_back(r);
+  }
+  ~ProfScope() {
+    if (c) cudaEventRecord(c->recs[idx].b, c->stream);
+  }
+};
+struct ProfBind {   // sets the context being timed for the duration of an API call
+  fock_ctx* prev;
+  explicit ProfBind(fock_ctx* c) : prev(g_prof) { g_prof = c; }
+  ~ProfBind() { g_prof = prev; }
+};
+}  // namespace
+#define PROF_CAT2(a, b) a##b
+#define PROF_CAT(a, b) PROF_CAT2(a, b)
+#define PROF(name, n) ProfScope PROF_CAT(prof_scope_, __LINE__)(name, n)
+
+namespace {
+
+const int kSmallSort = 4096;
+const double kPrecShift = 2e-3;   // sigma = min_j lambda_min(Chat_j) - kPrecShift (1 + |.|)
+
+int set_err(fock_ctx* c, int code, const std::string& m) {
+  if (c) c->err = m;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_err(ctx, FOCK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- host copy of one problem, with its quadrature table ----
+struct HostProb {
+  int L[3], per[3], N[3], n0;
+  double b0, h, eps;
+  int M0, m0, R, T, nF;
+  std::vector<double> Z, frac, alpha, tq, cq;
+  std::vector<int> ang, centre;
+  int k_eig;
+  int kind;            // 0 periodic (circulant eigensolve), 1 structured iteration
+};
+
+int validate(const fock_problem& p, HostProb& H, std::string& why) {
+  if (p.n0 <= 0 || !(p.b0 > 0.0)) { why = "n0 > 0 and b0 > 0 required"; return FOCK_EINVAL; }
+  if (p.M0 < 1 || p.M0 > 8 || !p.Z || !p.frac) { why = "1 <= M0 <= 8 with Z and frac"; return FOCK_EINVAL; }
+  if (p.m0 < 1 || p.m0 > MAXM0 || !p.exps || !p.ang || !p.centre) { why = "1 <= m0 <= 32 with exps/ang/centre"; return FOCK_EINVAL; }
+  if (p.R < 3 || p.R > MAXR) { why = "3 <= R <= 64"; return FOCK_EINVAL; }
+  if (p.ndef != 0) { why = "defects are not supported by this build"; return FOCK_EINVAL; }
+  H.n0 = p.n0; H.b0 = p.b0; H.h = p.b0 / p.n0;
+  H.eps = (p.eps_support > 0.0) ? p.eps_support : 1e-14;
+  int nlong = 0;
+  bool dir_long = false;
+  for (int a = 0; a < 3; ++a) {
+    H.L[a] = p.L[a]; H.per[a] = p.periodic[a] ? 1 : 0; H.N[a] = p.N[a];
+    if (p.L[a] < 1) { why = "L >= 1"; return FOCK_EINVAL; }
+    if (H.per[a] && p.N[a] != p.L[a] * p.n0) { why = "periodic axis needs N = L*n0"; return FOCK_EINVAL; }
+    if (!H.per[a] && p.N[a] < p.L[a] * p.n0) { why = "Dirichlet axis needs N >= L*n0"; return FOCK_EINVAL; }
+    if (p.L[a] > 1) { ++nlong; if (!H.per[a]) dir_long = true; }
+  }
+  H.kind = dir_long ? 1 : 0;
+  if (H.kind == 1 && (nlong > 1 || p.L[0] == 1)) {
+    why = "box problems must be chains along axis 0 (L2 = L3 = 1)";
+    return FOCK_EINVAL;
+  }
+  H.M0 = p.M0; H.m0 = p.m0; H.R = p.R; H.T = p.M0 * p.R; H.nF = H.T + 2;
+  H.Z.assign(p.Z, p.Z + p.M0);
+  H.frac.assign(p.frac, p.frac + 3 * p.M0);
+  H.alpha.assign(p.exps, p.exps + p.m0);
+  H.ang.assign(p.ang, p.ang + p.m0);
+  H.centre.assign(p.centre, p.centre + p.m0);
+  for (int mu = 0; mu < p.m0; ++mu) {
+    if (!(H.alpha[mu] > 0.0)) { why = "exponents must be positive"; return FOCK_EINVAL; }
+    if (H.ang[mu] < 0 || H.ang[mu] > 3) { why = "ang in 0..3"; return FOCK_EINVAL; }
+    if (H.centre[mu] < 0 || H.centre[mu] >= p.M0) { why = "centre out of range"; return FOCK_EINVAL; }
+  }
+  H.tq.resize(p.R);
+  H.cq.resize(p.R);
+  if (p.sinc_t && p.sinc_c) {
+    for (int q = 0; q < p.R; ++q) {
+      H.tq[q] = p.sinc_t[q]; H.cq[q] = p.sinc_c[q];
+      if (!(H.tq[q] > 0.0)) { why = "sinc_t must be positive"; return FOCK_EINVAL; }
+    }
+  } else {
+    double zmin, zmax;
+    fock_default_range(&p, &zmin, &zmax);
+    if (fock_sinc_table(p.R, zmin, zmax, H.tq.data(), H.cq.data(), nullptr) != FOCK_OK) {
+      why = "default quadrature rule failed"; return FOCK_EINVAL;
+    }
+  }
+  H.k_eig = (p.k_eig > 0) ? p.k_eig : 16;
+  if (H.kind == 1) {
+    int Nb = H.L[0] * H.m0;
+    if (H.k_eig > Nb / 3 || 3 * H.k_eig > 192) { why = "k_eig must satisfy 3k <= min(N_b, 192)"; return FOCK_EINVAL; }
+  }
+  return FOCK_OK;
+}
+
+// FNV-1a hash of the problem's parameters: the LOBPCG start of a problem is
+// the same whatever batch it is solved in.
+uint64_t problem_seed(const HostProb& H) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  };
+  mix(H.L, sizeof(H.L)); mix(H.per, sizeof(H.per)); mix(H.N, sizeof(H.N)); mix(&H.n0, sizeof(H.n0));
+  mix(&H.b0, sizeof(H.b0)); mix(&H.k_eig, sizeof(H.k_eig));
+  mix(H.alpha.data(), H.alpha.size() * 8); mix(H.Z.data(), H.Z.size() * 8);
+  mix(H.frac.data(), H.frac.size() * 8); mix(H.ang.data(), H.ang.size() * 4);
+  mix(H.centre.data(), H.centre.size() * 4); mix(H.tq.data(), H.tq.size() * 8);
+  return h;
+}
+
+// smallest 2^a 3^b 5^c >= n
+int smooth_at_least(int n) {
+  for (int m = std::max(n, 1);; ++m) {
+    int r = m;
+    for (int f : {2, 3, 5}) while (r % f == 0) r /= f;
+    if (r == 1) return m;
+  }
+}
+
+std::vector<int> radix_factors(int M) {
+  std::vector<int> f;
+  int r = M;
+  while (r % 4 == 0) { f.push_back(4); r /= 4; }
+  for (int p : {2, 3, 5}) while (r % p == 0) { f.push_back(p); r /= p; }
+  for (int p = 7; r > 1; p += 2) while (r % p == 0) { f.push_back(p); r /= p; }
+  return f;
+}
+
+// ---- slab allocators used by the two planning passes ----
+struct Slab {
+  char* base = nullptr;  // null during the sizing pass
+  size_t off = 0;
+  std::vector<char>* stage = nullptr;   // upload slab: host staging copy
+  template <class T> T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+  template <class T> T* put(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    size_t at = (off + 255) & ~(size_t)255;
+    T* p = take<T>(v.size());
+    if (stage) {
+      if (stage->size() < off) stage->resize(off);
+      std::memcpy(stage->data() + at, v.data(), v.size() * sizeof(T));
+    }
+    return p;
+  }
+};
+
+// per-axis geometry of one problem (host side)
+struct AxisPlan {
+  int jmin, jmax;      // support of the reference-cell functions (virtual node index)
+  int jlo, W, rlo, nr, pad;
+  std::vector<int> offs;   // periodic: lattice offsets d with possibly non-zero forms
+};
+
+void axis_plan(const HostProb& H, int a, AxisPlan& A) {
+  int N = H.N[a], L = H.L[a], n0 = H.n0;
+  A.pad = H.per[a] ? 0 : (N - L * n0) / 2;
+  int jmin = 1 << 30, jmax = -(1 << 30);
+  for (int mu = 0; mu < H.m0; ++mu) {
+    double cj = H.frac[H.centre[mu] * 3 + a] * n0 - 0.5;
+    double r = std::sqrt(std::log(1.0 / H.eps) / H.alpha[mu]) / H.h;
+    jmin = std::min(jmin, (int)std::floor(cj - r) - 1);
+    jmax = std::max(jmax, (int)std::ceil(cj + r) + 1);
+  }
+  A.jmin = jmin; A.jmax = jmax;
+  if (H.per[a]) {
+    A.jlo = 0; A.W = N; A.rlo = 0; A.nr = n0;
+    A.offs.clear();
+    int span = jmax - jmin + 2;
+    for (int d = 0; d < L; ++d) {
+      int s = (d * n0) % N;
+      int dist = std::min(s, N - s);
+      if (span >= N || dist <= span) A.offs.push_back(d);
+    }
+  } else {
+    A.jlo = jmin; A.W = jmax - jmin + 1;
+    A.rlo = -A.pad; A.nr = N - (L - 1) * n0;
+  }
+}
+
+// ---- one planned batch ----
+struct Batch {
+  int nprob = 0;
+  std::vector<HostProb> hp;
+  std::vector<AxisPlan> ap;          // [nprob*3]
+  size_t bytes = 0;
+  char* base = nullptr;
+  bool own = false;                  // slab owned by the batch (fock_blocks)
+  // device descriptors
+  ProbDev* d_probs = nullptr;
+  std::vector<ProbDev> probs;
+  std::vector<SegDesc> gsegs, psegs;
+  SegDesc *d_gsegs = nullptr, *d_psegs = nullptr;
+  std::vector<GramTask> gram; GramTask* d_gram = nullptr;
+  std::vector<CombineTask> combT, combE; CombineTask *d_combT = nullptr, *d_combE = nullptr;
+  std::vector<DftTask> dft; DftTask* d_dft = nullptr;
+  std::vector<FBlockTask> fbp, fbs; FBlockTask *d_fbp = nullptr, *d_fbs = nullptr;
+  int maxnj_p = 0, maxnj_s = 0, maxm0 = 1;
+  std::vector<PrecTask> prec; PrecTask* d_prec = nullptr; int maxM = 0;
+  std::vector<SortTask> sorts; SortTask* d_sorts = nullptr; int maxsort = 0;
+  std::vector<int> bigsort;          // problems whose eigenvalues need the global sort
+  double* sort_pv = nullptr; int* sort_pi = nullptr;
+  std::vector<CircDev> circs; CircDev* d_circs = nullptr;
+  // per-problem outputs / structured operators
+  struct PerProb {
+    double* ev = nullptr; int* blk = nullptr; int nev = 0;
+    // periodic factors
+    double* X[3] = {nullptr, nullptr, nullptr};  // first task's X of each axis (periodic offsets contiguous)
+    int ntask_axis[3] = {0, 0, 0};
+    cplx* Xh[3] = {nullptr, nullptr, nullptr};
+    // structured
+    int Lc = 0, M = 0, D = 0, circ = -1;
+    double *TH = nullptr, *TS = nullptr;
+    int nE = 0;
+    std::vector<int> Ek, Em;          // (row cell, column cell) of each boundary block
+    double *EH = nullptr, *ES = nullptr;
+    int *Erows = nullptr, *Erowptr = nullptr, *Ecols = nullptr; int nErows = 0;
+    cplx *CH = nullptr, *CS = nullptr, *K = nullptr;
+    double *emin = nullptr, *sigma = nullptr;
+    bool use_band = false;            // preconditioner: banded Cholesky (else circulant inverse)
+    double *band = nullptr, *sigma_band = nullptr;
+    int *band_fail = nullptr;
+    int* fail = nullptr;
+  };
+  std::vector<PerProb> pp;
+  // LOBPCG state (structured problems)
+  struct Lob {
+    int n, k, ld3;
+    double *Y, *HY, *SY, *T1, *R, *GH, *GS, *work, *Cc, *Cx, *lam, *res;
+    int *active, *fail;
+  };
+  std::vector<Lob> lob;              // index = structured problem order
+  std::vector<int> sidx;             // problem index of each structured problem
+  int kmax = 0;
+  cplx *mvX = nullptr, *mvY1 = nullptr, *mvY2 = nullptr;   // FFT work (shared by all structured)
+  std::vector<size_t> mv_off;        // per structured problem: offset (cplx) into mv buffers
+  struct TL { void* d = nullptr; int n = 0; int ga = 1, gb = 1; };
+  // basis layout Y = [X | P | W] (k columns each)
+  TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
+  TL eHXP, eSXP, eHW, eSW;
+  TL bandF, bandS;
+  TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid;
+  int fft_cc = 1, fft_chunks = 1;
+  int* d_ones = nullptr;
+  int* d_active = nullptr;
+  int* d_fail = nullptr;
+  double* d_res = nullptr;
+  double* d_lam = nullptr;
+  // upload slab: parameters and descriptors, staged on the host, one copy
+  size_t ubytes = 0;
+  char* ubase = nullptr;
+  std::vector<char> stage;
+};
+
+// Plan everything.  With S.base == nullptr only sizes are computed.
+void plan(Batch& B, Slab& S, Slab& U) {
+  const int np = B.nprob;
+  B.probs.assign(np, ProbDev());
+  B.pp.assign(np, Batch::PerProb());
+  B.gsegs.clear(); B.psegs.clear(); B.gram.clear(); B.combT.clear(); B.combE.clear();
+  B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.sorts.clear(); B.bigsort.clear();
+  B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
+  B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0;
+  size_t zs_total = 0;
+  // ---- parameters, vectors, gram tasks ----
+  for (int i = 0; i < np; ++i) {
+    const HostProb& H = B.hp[i];
+    ProbDev& P = B.probs[i];
+    Batch::PerProb& Q = B.pp[i];
+    P.m0 = H.m0; P.M0 = H.M0; P.R = H.R; P.T = H.T; P.nF = H.nF; P.n0 = H.n0;
+    P.b0 = H.b0; P.h = H.h; P.eps = H.eps;
+    B.maxm0 = std::max(B.maxm0, H.m0);
+    std::vector<double> hpar;
+    hpar.insert(hpar.end(), H.alpha.begin(), H.alpha.end());
+    hpar.insert(hpar.end(), H.Z.begin(), H.Z.end());
+    hpar.insert(hpar.end(), H.frac.begin(), H.frac.end());
+    hpar.insert(hpar.end(), H.tq.begin(), H.tq.end());
+    hpar.insert(hpar.end(), H.cq.begin(), H.cq.end());
+    std::vector<int> hipar(H.ang.begin(), H.ang.end());
+    hipar.insert(hipar.end(), H.centre.begin(), H.centre.end());
+    const double* par = U.put(hpar);
+    const int* ipar = U.put(hipar);
+    P.alpha = par; P.Z = par + H.m0; P.frac = P.Z + H.M0; P.tq = P.frac + 3 * H.M0; P.cq = P.tq + H.R;
+    P.ang = ipar; P.centre = ipar + H.m0;
+    const int m2 = H.m0 * H.m0;
+    for (int a = 0; a < 3; ++a) {
+      AxisPlan& A = B.ap[i * 3 + a];
+      AxisDev& D = P.ax[a];
+      D.N = H.N[a]; D.L = H.L[a]; D.per = H.per[a]; D.pad = A.pad;
+      D.jlo = A.jlo; D.W = A.W; D.rlo = A.rlo; D.nr = A.nr;
+      D.g = S.take<double>((size_t)H.m0 * A.W);
+      D.p = S.take<double>((size_t)H.T * A.nr);
+      B.gsegs.push_back({i, a, H.m0 * A.W});
+      B.psegs.push_back({i, a, H.T * A.nr});
+    }
+    // gram tasks
+    for (int a = 0; a < 3; ++a) {
+      AxisPlan& A = B.ap[i * 3 + a];
+      const int N = H.N[a], n0 = H.n0, L = H.L[a];
+      double* xblock = nullptr;   // periodic axis: factors of all offsets contiguous
+      if (H.per[a]) xblock = S.take<double>(A.offs.size() * (size_t)H.nF * m2);
+      int nadded = 0;
+      auto add = [&](int mode, int ca, int cb, int r0, int r1, int nfold, int foldlo) {
+        GramTask t;
+        t.prob = i; t.axis = a; t.mode = mode; t.a = ca; t.b = cb; t.rho0 = r0; t.rho1 = r1;
+        t.ptab = -1; t.nfold = nfold; t.foldlo = foldlo;
+        t.X = xblock ? xblock + (size_t)(nadded++) * H.nF * m2 : S.take<double>((size_t)H.nF * m2);
+        zs_total += (size_t)nfold * m2;
+        t.Zs = nullptr;
+        B.gram.push_back(t);
+        return (int)B.gram.size() - 1;
+      };
+      if (H.per[a]) {
+        Q.ntask_axis[a] = (int)A.offs.size();
+        for (size_t o = 0; o < A.offs.size(); ++o) {
+          int ti = add(RING, A.offs[o], 0, 0, N, n0, 0);
+          if (o == 0) Q.X[a] = B.gram[ti].X;
+        }
+      } else if (L == 1) {
+        int r0 = std::max(-A.pad, A.jlo - 1), r1 = std::min(N - A.pad, A.jlo + A.W + 1);
+        int ti = add(WALL, 0, 0, r0, r1, A.nr, A.rlo);
+        Q.X[a] = B.gram[ti].X;
+        Q.ntask_axis[a] = 1;
+      } else {
+        // box chain axis (a == 0): Toeplitz generators d = 0..D, then boundary pairs
+        int span = A.jmax - A.jmin + 2;
+        int D = std::min(span / n0, L - 1);
+        Q.Lc = L; Q.D = D;
+        for (int d = 0; d <= D; ++d) {
+          int lo = std::max(A.jlo, A.jlo + d * n0) - 1, hi = std::min(A.jlo + A.W, A.jlo + A.W + d * n0) + 1;
+          int ti = add(VIRT, d, 0, lo, hi, n0, 0);
+          if (d == 0) Q.X[a] = B.gram[ti].X;
+        }
+        Q.ntask_axis[a] = D + 1;
+        std::vector<char> aff(L, 0);
+        for (int k = 0; k < L; ++k)
+          aff[k] = (k * n0 + A.jmin - 2 < 0) || (k * n0 + A.jmax + 2 > L * n0 - 1);
+        Q.Ek.clear(); Q.Em.clear();
+        for (int k = 0; k < L; ++k)
+          for (int m = std::max(0, k - D); m <= std::min(L - 1, k + D); ++m)
+            if (aff[k] && aff[m]) { Q.Ek.push_back(k); Q.Em.push_back(m); }
+        Q.nE = (int)Q.Ek.size();
+        for (int e = 0; e < Q.nE; ++e) {
+          int k = Q.Ek[e], m = Q.Em[e];
+          int lo = std::max(A.jlo + k * n0, A.jlo + m * n0) - 1;
+          int hi = std::min(A.jlo + A.W + k * n0, A.jlo + A.W + m * n0) + 1;
+          lo = std::max(lo, -A.pad); hi = std::min(hi, N - A.pad);
+          add(WALL, k, m, lo, hi, A.nr, A.rlo);
+        }
+      }
+    }
+  }
+  // fold scratch (shared by all tasks of the batch)
+  double* zs = S.take<double>(std::max<size_t>(zs_total, 1));
+  {
+    size_t o = 0;
+    for (auto& t : B.gram) {
+      t.Zs = zs + o;
+      o += (size_t)t.nfold * B.probs[t.prob].m0 * B.probs[t.prob].m0;
+    }
+  }
+  // ---- combine, DFT, Fourier blocks, structured operators ----
+  for (int i = 0; i < np; ++i) {
+    const HostProb& H = B.hp[i];
+    Batch::PerProb& Q = B.pp[i];
+    const int m2 = H.m0 * H.m0;
+    const size_t xs = (size_t)H.nF * m2;
+    if (H.kind == 0) {
+      int ncell = H.L[0] * H.L[1] * H.L[2];
+      for (int a = 0; a < 3; ++a) {
+        AxisPlan& A = B.ap[i * 3 + a];
+        Q.Xh[a] = S.take<cplx>((size_t)H.L[a] * xs);
+        DftTask t;
+        t.prob = i; t.L = H.L[a];
+        std::vector<int> offs = H.per[a] ? A.offs : std::vector<int>{0};
+        t.noff = (int)offs.size();
+        t.offs = U.put(offs);
+        t.X = Q.X[a]; t.Xh = Q.Xh[a];
+        B.dft.push_back(t);
+      }
+      Q.nev = ncell * H.m0;
+      Q.ev = S.take<double>(Q.nev);
+      Q.blk = S.take<int>(Q.nev);
+      Q.fail = S.take<int>(1);
+      FBlockTask f;
+      std::memset(&f, 0, sizeof(f));
+      f.prob = i; f.source = 0; f.nj = ncell;
+      for (int a = 0; a < 3; ++a) { f.L[a] = H.L[a]; f.Xh[a] = Q.Xh[a]; }
+      f.want = 1; f.ev = Q.ev; f.blk = Q.blk; f.fail = Q.fail;
+      B.fbp.push_back(f);
+      B.maxnj_p = std::max(B.maxnj_p, ncell);
+      if (Q.nev <= kSmallSort) {
+        B.sorts.push_back({Q.nev, Q.ev, Q.blk});
+        B.maxsort = std::max(B.maxsort, Q.nev);
+      } else {
+        B.bigsort.push_back(i);
+      }
+    } else {
+      // Toeplitz generators and boundary blocks
+      Q.TH = S.take<double>((size_t)(Q.D + 1) * m2);
+      Q.TS = S.take<double>((size_t)(Q.D + 1) * m2);
+      int g0 = -1;
+      for (size_t t = 0; t < B.gram.size(); ++t)
+        if (B.gram[t].prob == i && B.gram[t].axis == 0) { g0 = (int)t; break; }
+      const double* X1 = Q.X[1];
+      const double* X2 = Q.X[2];
+      for (int d = 0; d <= Q.D; ++d) {
+        CombineTask c;
+        std::memset(&c, 0, sizeof(c));
+        c.prob = i; c.X0 = B.gram[g0 + d].X; c.X1 = X1; c.X2 = X2;
+        c.outH = Q.TH + (size_t)d * m2; c.outS = Q.TS + (size_t)d * m2;
+        B.combT.push_back(c);
+      }
+      Q.EH = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
+      Q.ES = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
+      for (int e = 0; e < Q.nE; ++e) {
+        int k = Q.Ek[e], m = Q.Em[e], d = std::abs(k - m);
+        CombineTask c;
+        std::memset(&c, 0, sizeof(c));
+        c.prob = i; c.X0 = B.gram[g0 + Q.D + 1 + e].X; c.X1 = X1; c.X2 = X2;
+        c.subH = Q.TH + (size_t)d * m2; c.subS = Q.TS + (size_t)d * m2; c.subT = (k < m);
+        c.outH = Q.EH + (size_t)e * m2; c.outS = Q.ES + (size_t)e * m2;
+        B.combE.push_back(c);
+      }
+      // CSR over block rows (the entries are already grouped by row k ascending)
+      std::vector<int> rows, rowptr, cols;
+      for (int e = 0; e < Q.nE; ++e) {
+        if (rows.empty() || rows.back() != Q.Ek[e]) { rows.push_back(Q.Ek[e]); rowptr.push_back(e); }
+        cols.push_back(Q.Em[e]);
+      }
+      rowptr.push_back(Q.nE);
+      Q.nErows = (int)rows.size();
+      Q.Erows = U.put(rows);
+      Q.Erowptr = U.put(rowptr);
+      Q.Ecols = U.put(cols);
+      // circulant embedding
+      Q.M = smooth_at_least(Q.Lc + Q.D);
+      CircDev cd;
+      std::memset(&cd, 0, sizeof(cd));
+      cd.M = Q.M;
+      std::vector<int> f = radix_factors(Q.M);
+      cd.nfac = (int)f.size();
+      for (int q = 0; q < cd.nfac; ++q) cd.fac[q] = f[q];
+      cd.tw = S.take<cplx>(Q.M);
+      Q.circ = (int)B.circs.size();
+      B.circs.push_back(cd);
+      B.maxM = std::max(B.maxM, Q.M);
+      Q.CH = S.take<cplx>((size_t)Q.M * m2);
+      Q.CS = S.take<cplx>((size_t)Q.M * m2);
+      Q.K = S.take<cplx>((size_t)Q.M * m2);
+      Q.emin = S.take<double>(Q.M);
+      Q.sigma = S.take<double>(1);
+      // banded Cholesky of H - sigma S when its one-CTA setup stays small
+      Q.use_band = 2.0 * Q.Lc * (double)Q.D * Q.D * (double)H.m0 * H.m0 * H.m0 <= 5e8;
+      if (Q.use_band) {
+        Q.band = S.take<double>((size_t)Q.Lc * (Q.D + 1) * m2);
+        Q.sigma_band = S.take<double>(1);
+        Q.band_fail = S.take<int>(1);
+      }
+      Q.fail = S.take<int>(1);
+      FBlockTask fb;
+      std::memset(&fb, 0, sizeof(fb));
+      fb.prob = i; fb.source = 1; fb.nj = Q.M; fb.M = Q.M; fb.D = Q.D; fb.TH = Q.TH; fb.TS = Q.TS;
+      fb.outH = Q.CH; fb.outS = Q.CS; fb.want = 2; fb.ev = Q.emin; fb.fail = Q.fail;
+      B.fbs.push_back(fb);
+      B.maxnj_s = std::max(B.maxnj_s, Q.M);
+      PrecTask pt;
+      pt.prob = i; pt.M = Q.M; pt.emin = Q.emin; pt.sigma = Q.sigma; pt.CH = Q.CH; pt.CS = Q.CS; pt.K = Q.K;
+      pt.rel_shift = kPrecShift;
+      B.prec.push_back(pt);
+      Q.nev = H.k_eig;
+      Q.ev = S.take<double>(Q.nev);
+      B.sidx.push_back(i);
+      B.kmax = std::max(B.kmax, H.k_eig);
+    }
+  }
+  // ---- LOBPCG state ----
+  size_t mv_total = 0;
+  for (size_t s = 0; s < B.sidx.size(); ++s) {
+    int i = B.sidx[s];
+    const HostProb& H = B.hp[i];
+    Batch::PerProb& Q = B.pp[i];
+    Batch::Lob l;
+    l.n = Q.Lc * H.m0; l.k = H.k_eig; l.ld3 = 3 * l.k + 1;   // +1: Jacobi pads odd sizes
+    size_t nk = (size_t)l.n * l.k;
+    l.Y = S.take<double>(3 * nk); l.HY = S.take<double>(3 * nk); l.SY = S.take<double>(3 * nk);
+    l.T1 = S.take<double>(2 * nk);
+    l.R = S.take<double>(nk);
+    l.GH = S.take<double>((size_t)l.ld3 * l.ld3); l.GS = S.take<double>((size_t)l.ld3 * l.ld3);
+    l.work = S.take<double>((size_t)3 * l.ld3 * l.ld3);
+    l.Cc = S.take<double>((size_t)l.ld3 * 2 * l.k);
+    l.Cx = S.take<double>((size_t)l.k * l.k);
+    B.lob.push_back(l);
+    B.mv_off.push_back(mv_total);
+    mv_total += (size_t)Q.M * H.m0 * 2 * l.k;   // matvecs of up to 2k columns
+  }
+  if (!B.sidx.empty()) {
+    const int ns = (int)B.sidx.size();
+    B.d_active = S.take<int>(ns);
+    B.d_fail = S.take<int>(ns);
+    B.d_res = S.take<double>((size_t)ns * B.kmax);
+    B.d_lam = S.take<double>((size_t)ns * B.kmax);
+    for (int s = 0; s < ns; ++s) {
+      B.lob[s].active = B.d_active + s;
+      B.lob[s].fail = B.d_fail + s;
+      B.lob[s].res = B.d_res + (size_t)s * B.kmax;
+      B.lob[s].lam = B.d_lam + (size_t)s * B.kmax;
+    }
+    B.mvX = S.take<cplx>(mv_total);
+    B.mvY1 = S.take<cplx>(mv_total);
+    B.mvY2 = S.take<cplx>(mv_total);
+  }
+  if (!B.bigsort.empty()) {
+    int mx = 0;
+    for (int i : B.bigsort) mx = std::max(mx, B.pp[i].nev);
+    int n2 = 1;
+    while (n2 < mx) n2 <<= 1;
+    B.sort_pv = S.take<double>(n2);
+    B.sort_pi = S.take<int>(n2);
+  }
+  B.d_circs = U.put(B.circs);
+  // ---- LOBPCG task lists (fixed addresses, built once) ----
+  if (!B.sidx.empty()) {
+    const int ns = (int)B.sidx.size();
+    B.fft_cc = std::max(1, std::min(16, 98304 / (32 * std::max(B.maxM, 1))));
+    int maxcols = 1;
+    std::vector<FftTask> fXP, fW, fR, iHXP, iSXP, iHW, iSW, iPW;
+    std::vector<BmulTask> bHS2, bHS1, bK;
+    std::vector<EApplyTask> ehxp, esxp, ehw, esw;
+    std::vector<InitTask> ini;
+    std::vector<GemmTask> tcx, nw, tcp, npp, gg1, gg3, uu1, uu3;
+    std::vector<RRTask> r1, r3;
+    std::vector<CopyTask> c2k;
+    std::vector<ResidTask> rs;
+    std::vector<BandTask> bnd;
+    std::vector<int> ones(ns, 1);
+    B.d_ones = U.put(ones);
+    for (int s2 = 0; s2 < ns; ++s2) {
+      const int i = B.sidx[s2];
+      const HostProb& H = B.hp[i];
+      Batch::PerProb& Q = B.pp[i];
+      Batch::Lob& l = B.lob[s2];
+      const int n = l.n, k = l.k, m0 = H.m0, ld3 = l.ld3;
+      const size_t nk = (size_t)n * k;
+      maxcols = std::max(maxcols, 2 * m0 * k);
+      cplx* X = B.mvX + B.mv_off[s2];
+      cplx* Y1 = B.mvY1 + B.mv_off[s2];
+      cplx* Y2 = B.mvY2 + B.mv_off[s2];
+      const CircDev* cd = B.d_circs + Q.circ;
+      auto fwd = [&](const double* src, int ncol) {
+        FftTask t; std::memset(&t, 0, sizeof(t));
+        t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.x = src; t.ldx = n; t.X = X;
+        t.cc = B.fft_cc;
+        return t;
+      };
+      auto inv = [&](cplx* from, double* dst, int ncol) {
+        FftTask t; std::memset(&t, 0, sizeof(t));
+        t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.X = from; t.y = dst; t.ldy = n;
+        t.beta = 0.0; t.cc = B.fft_cc;
+        return t;
+      };
+      double* Yx = l.Y;            // X: columns [0, k)
+      double* Yw = l.Y + 2 * nk;   // W: columns [2k, 3k)
+      fXP.push_back(fwd(Yx, 2 * k)); fW.push_back(fwd(Yw, k));
+      iHXP.push_back(inv(Y1, l.HY, 2 * k)); iSXP.push_back(inv(Y2, l.SY, 2 * k));
+      iHW.push_back(inv(Y1, l.HY + 2 * nk, k)); iSW.push_back(inv(Y2, l.SY + 2 * nk, k));
+      bHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2});
+      bHS1.push_back({i, Q.M, m0, k, Q.CH, Q.CS, X, Y1, Y2});
+      if (Q.use_band) {
+        BandTask bt;
+        std::memset(&bt, 0, sizeof(bt));
+        bt.m0 = m0; bt.L = Q.Lc; bt.D = Q.D; bt.k = k; bt.n = n;
+        bt.TH = Q.TH; bt.TS = Q.TS; bt.nE = Q.nE; bt.Ek = U.put(Q.Ek); bt.Em = U.put(Q.Em);
+        bt.EH = Q.EH; bt.ES = Q.ES; bt.sigma0 = Q.sigma; bt.band = Q.band; bt.sigma_used = Q.sigma_band;
+        bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
+        bnd.push_back(bt);
+      } else {
+        fR.push_back(fwd(l.R, k));
+        iPW.push_back(inv(Y1, Yw, k));
+        bK.push_back({i, Q.M, m0, k, Q.K, nullptr, X, Y1, nullptr});
+      }
+      auto ea = [&](const double* vals, const double* x, double* y, int ncol) {
+        EApplyTask t;
+        t.prob = i; t.m0 = m0; t.ncol = ncol; t.nrows = Q.nErows; t.rows = Q.Erows; t.rowptr = Q.Erowptr;
+        t.cols = Q.Ecols; t.vals = vals; t.x = x; t.ldx = n; t.y = y; t.ldy = n;
+        return t;
+      };
+      if (Q.nE) {
+        ehxp.push_back(ea(Q.EH, Yx, l.HY, 2 * k)); esxp.push_back(ea(Q.ES, Yx, l.SY, 2 * k));
+        ehw.push_back(ea(Q.EH, Yw, l.HY + 2 * nk, k)); esw.push_back(ea(Q.ES, Yw, l.SY + 2 * nk, k));
+      }
+      ini.push_back({n, k, n, problem_seed(H), l.Y});   // start depends on the problem only
+      auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
+                    double alpha, double beta) {
+        GemmTask g; g.active = l.active; g.n = n; g.a = a; g.b = b; g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb;
+        g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+        return g;
+      };
+      // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C  (same for HW, SW)
+      tcx.push_back(gt(k, k, l.SY, n, Yw, n, l.Cx, k, 1.0, 0.0));
+      tcp.push_back(gt(k, k, l.SY, n, l.Y + nk, n, l.Cx, k, 1.0, 0.0));
+      for (int w = 0; w < 3; ++w) {
+        double* base = w == 0 ? l.Y : (w == 1 ? l.HY : l.SY);
+        nw.push_back(gt(k, k, base, n, l.Cx, k, base + 2 * nk, n, -1.0, 1.0));
+        npp.push_back(gt(k, k, base, n, l.Cx, k, base + nk, n, -1.0, 1.0));
+      }
+      gg1.push_back(gt(k, k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0));
+      gg1.push_back(gt(k, k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
+      gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0));
+      gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
+      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail});
+      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail});
+      // [X' | P'] = Y[:, :nb] Cc, then copied over [X | P]; images recomputed by a matvec
+      uu1.push_back(gt(k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
+      uu3.push_back(gt(3 * k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
+      c2k.push_back({l.active, n, 2 * k, l.T1, n, l.Y, n});
+      rs.push_back({l.active, n, k, n, l.Y, l.HY, l.SY, l.lam, l.R, l.res});
+    }
+    B.fft_chunks = (maxcols + B.fft_cc - 1) / B.fft_cc;
+    auto TLp = [&](auto& v, Batch::TL& tl, int ga = 1, int gb = 1) {
+      tl.d = (void*)U.put(v); tl.n = (int)v.size(); tl.ga = ga; tl.gb = gb;
+    };
+    const int kk = B.kmax;
+    int maxld3 = 0;
+    for (auto& l : B.lob) maxld3 = std::max(maxld3, l.ld3);
+    TLp(fXP, B.fwdXP); TLp(fW, B.fwdW); TLp(fR, B.fwdR);
+    TLp(iHXP, B.invHXP); TLp(iSXP, B.invSXP); TLp(iHW, B.invHW); TLp(iSW, B.invSW); TLp(iPW, B.invPW);
+    TLp(bHS2, B.bmulHS2); TLp(bHS1, B.bmulHS1); TLp(bK, B.bmulK);
+    TLp(ehxp, B.eHXP); TLp(esxp, B.eSXP); TLp(ehw, B.eHW); TLp(esw, B.eSW);
+    TLp(ini, B.init);
+    TLp(tcx, B.tnCx, (kk + 15) / 16, (kk + 15) / 16); TLp(tcp, B.tnCp, (kk + 15) / 16, (kk + 15) / 16);
+    TLp(nw, B.nnW); TLp(npp, B.nnP);
+    TLp(gg1, B.g1, (kk + 15) / 16, (kk + 15) / 16);
+    TLp(gg3, B.g3, (3 * kk + 15) / 16, (3 * kk + 15) / 16);
+    TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
+    TLp(uu1, B.u1); TLp(uu3, B.u3);
+    TLp(c2k, B.cp2k);
+    TLp(bnd, B.bandF);
+    B.bandS = B.bandF;
+    TLp(rs, B.resid, kk);
+  }
+  // ---- descriptor arrays (uploaded in one copy with the parameters) ----
+  B.d_probs = U.put(B.probs);
+  B.d_gsegs = U.put(B.gsegs);
+  B.d_psegs = U.put(B.psegs);
+  B.d_gram = U.put(B.gram);
+  B.d_combT = U.put(B.combT);
+  B.d_combE = U.put(B.combE);
+  B.d_dft = U.put(B.dft);
+  B.d_fbp = U.put(B.fbp);
+  B.d_fbs = U.put(B.fbs);
+  B.d_prec = U.put(B.prec);
+  B.d_sorts = U.put(B.sorts);
+  B.bytes = S.off;
+  B.ubytes = U.off;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ drivers
+namespace {
+
+int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
+  Slab S0, U0;
+  plan(B, S0, U0);
+  size_t need = S0.off + 256, uneed = U0.off + 256;
+  if (ctx->budget && need + uneed > ctx->budget)
+    return set_err(ctx, FOCK_ENOMEM, "batch needs " + std::to_string(need + uneed) + " bytes, budget " +
+                                         std::to_string(ctx->budget));
+  char *mb = nullptr, *ub = nullptr;
+  if (own) {
+    CUDA_TRY(ctx, cudaMalloc(&mb, need));
+    CUDA_TRY(ctx, cudaMalloc(&ub, uneed));
+    B.own = true;
+  } else {
+    if (ctx->arena_cap < need + uneed) {
+      if (ctx->arena) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->arena); ctx->arena = nullptr; ctx->arena_cap = 0; }
+      size_t cap = (need + uneed) + (need + uneed) / 4;
+      CUDA_TRY(ctx, cudaMalloc(&ctx->arena, cap));
+      ctx->arena_cap = cap;
+    }
+    mb = ctx->arena;
+    ub = ctx->arena + ((need + 255) & ~(size_t)255);
+  }
+  B.base = mb;
+  B.ubase = ub;
+  Slab S, U;
+  S.base = mb;
+  U.base = ub;
+  B.stage.assign(U0.off + 16, 0);
+  U.stage = &B.stage;
+  plan(B, S, U);
+  CUDA_TRY(ctx, cudaMemcpyAsync(ub, B.stage.data(), U.off, cudaMemcpyHostToDevice, ctx->stream));
+  return FOCK_OK;
+}
+
+void free_batch(Batch& B) {
+  if (B.own) {
+    cudaFree(B.base);
+    cudaFree(B.ubase);
+  }
+  B.base = B.ubase = nullptr;
+}
+
+int build_batch(fock_ctx* ctx, int nprob, const fock_problem* probs, Batch& B, bool own) {
+  if (nprob <= 0 || !probs) return set_err(ctx, FOCK_EINVAL, "no problems");
+  B.nprob = nprob;
+  B.hp.assign(nprob, HostProb());
+  B.ap.assign((size_t)nprob * 3, AxisPlan());
+  for (int i = 0; i < nprob; ++i) {
+    std::string why;
+    int rc = validate(probs[i], B.hp[i], why);
+    if (rc) return set_err(ctx, rc, "problem " + std::to_string(i) + ": " + why);
+    for (int a = 0; a < 3; ++a) axis_plan(B.hp[i], a, B.ap[i * 3 + a]);
+  }
+  return alloc_and_plan(ctx, B, own);
+}
+
+void run_assemble(fock_ctx* ctx, Batch& B) {
+  cudaStream_t st = ctx->stream;
+  { PROF("k_vec1d", 2); launch_vec1d(B.d_probs, B.d_gsegs, (int)B.gsegs.size(), B.d_psegs, (int)B.psegs.size(), nullptr, 0, st); }
+  { PROF("k_gram", 2); launch_gram(B.d_probs, B.d_gram, (int)B.gram.size(), nullptr, st); }
+  if (!B.combT.empty()) { PROF("k_combine", 2);
+    launch_combine(B.d_probs, B.d_combT, (int)B.combT.size(), st);
+    launch_combine(B.d_probs, B.d_combE, (int)B.combE.size(), st); }
+}
+
+void zero_fail_flags(Batch& B, int kind, cudaStream_t st) {
+  for (int i = 0; i < B.nprob; ++i)
+    if (B.hp[i].kind == kind && B.pp[i].fail) cudaMemsetAsync(B.pp[i].fail, 0, sizeof(int), st);
+}
+
+void run_periodic(fock_ctx* ctx, Batch& B) {
+  cudaStream_t st = ctx->stream;
+  if (B.fbp.empty()) return;
+  zero_fail_flags(B, 0, st);
+  { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), st); }
+  { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st); }
+  if (!B.sorts.empty()) { PROF("k_sort", 1); launch_sort_small(B.d_sorts, (int)B.sorts.size(), B.maxsort, st); }
+  for (int i : B.bigsort) { PROF("k_sort_global", 1);
+    launch_sort_global(B.pp[i].ev, B.pp[i].blk, B.pp[i].nev, B.sort_pv, B.sort_pi, st); }
+}
+
+void run_struct_setup(fock_ctx* ctx, Batch& B) {
+  cudaStream_t st = ctx->stream;
+  if (B.fbs.empty()) return;
+  zero_fail_flags(B, 1, st);
+  { PROF("k_twiddle", 1); launch_twiddles(B.d_circs, (int)B.circs.size(), st); }
+  { PROF("k_fblocks_embed", 1); launch_fblocks(B.d_probs, B.d_fbs, (int)B.fbs.size(), B.maxnj_s, B.maxm0, st); }
+  { PROF("k_precond", 2); launch_precond(B.d_probs, B.d_prec, (int)B.prec.size(), B.maxM, B.maxm0, st); }
+  for (auto& Q : B.pp)
+    if (Q.band_fail) cudaMemsetAsync(Q.band_fail, 0, sizeof(int), st);
+  if (B.bandF.n) { PROF("k_band_factor", 1);
+    launch_band_factor(reinterpret_cast<const BandTask*>(B.bandF.d), B.bandF.n, st); }
+}
+
+template <class T> const T* tl(const Batch::TL& t) { return reinterpret_cast<const T*>(t.d); }
+
+void mv_fwd(Batch& B, const Batch::TL& t, cudaStream_t st) {
+  PROF("k_fft", 1);
+  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, +1, st);
+}
+void mv_inv(Batch& B, const Batch::TL& t, cudaStream_t st) {
+  PROF("k_fft", 1);
+  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, -1, st);
+}
+void gemm_tn(const Batch::TL& t, cudaStream_t st) {
+  PROF("k_gemm_tn", 1);
+  if (t.n) k_gemm_tn<<<dim3(t.ga, t.gb, t.n), 256, 0, st>>>(tl<GemmTask>(t));
+}
+void gemm_nn(const Batch::TL& t, cudaStream_t st) {
+  PROF("k_gemm_nn", 1);
+  if (t.n) k_gemm_nn<<<dim3(64, t.n), 256, 0, st>>>(tl<GemmTask>(t));
+}
+void rr(const Batch::TL& t, cudaStream_t st) {
+  PROF("k_rr", 1);
+  if (!t.n) return;
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; }
+  size_t sm = (size_t)3 * t.ga * t.ga * sizeof(double);
+  if (sm > 160 * 1024) sm = 0;
+  k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm);
+}
+void copies(const Batch::TL& t, cudaStream_t st) {
+  PROF("k_copy_cols", 1);
+  if (t.n) k_copy_cols<<<dim3(32, t.n), 256, 0, st>>>(tl<CopyTask>(t));
+}
+
+// H and S images of the [X | P] columns (2k) or of the W columns (k) of every structured problem
+void mv_HS(Batch& B, bool xp, cudaStream_t st) {
+  mv_fwd(B, xp ? B.fwdXP : B.fwdW, st);
+  const Batch::TL& bm = xp ? B.bmulHS2 : B.bmulHS1;
+  { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(bm), bm.n, B.maxM, B.maxm0, st); }
+  mv_inv(B, xp ? B.invHXP : B.invHW, st);
+  mv_inv(B, xp ? B.invSXP : B.invSW, st);
+  const Batch::TL& eh = xp ? B.eHXP : B.eHW;
+  const Batch::TL& es = xp ? B.eSXP : B.eSW;
+  if (eh.n) { PROF("k_eapply", 2);
+    launch_eapply(tl<EApplyTask>(eh), eh.n, st);
+    launch_eapply(tl<EApplyTask>(es), es.n, st); }
+}
+
+int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
+               std::vector<double>& resid, std::vector<int>& conv) {
+  cudaStream_t st = ctx->stream;
+  const int ns = (int)B.sidx.size();
+  iters.assign(ns, 0);
+  resid.assign(ns, 0.0);
+  conv.assign(ns, 0);
+  if (!ns) return FOCK_OK;
+  CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, B.d_ones, ns * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(ctx, cudaMemsetAsync(B.d_fail, 0, ns * sizeof(int), st));
+  const bool dbg = getenv("FOCK_DEBUG") != nullptr;
+  auto dump = [&](const char* stage, int it) {
+    if (!dbg) return;
+    cudaStreamSynchronize(st);
+    const Batch::Lob& l = B.lob[0];
+    size_t nk = (size_t)l.n * l.k;
+    std::vector<double> h(9 * nk);
+    cudaMemcpy(h.data(), l.Y, 3 * nk * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(h.data() + 3 * nk, l.HY, 3 * nk * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(h.data() + 6 * nk, l.SY, 3 * nk * 8, cudaMemcpyDeviceToHost);
+    std::vector<double> g(2 * (size_t)l.ld3 * l.ld3), lm(l.k);
+    cudaMemcpy(g.data(), l.GH, g.size() / 2 * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(g.data() + g.size() / 2, l.GS, g.size() / 2 * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(lm.data(), l.lam, l.k * 8, cudaMemcpyDeviceToHost);
+    auto st3 = [&](const double* p, size_t n, double& mx, int& nan) {
+      mx = 0; nan = 0;
+      for (size_t i = 0; i < n; ++i) { if (!(p[i] == p[i])) ++nan; else mx = std::max(mx, std::fabs(p[i])); }
+    };
+    double m[6]; int nn[6];
+    for (int q = 0; q < 3; ++q) st3(h.data() + q * 3 * nk, 3 * nk, m[q], nn[q]);
+    st3(g.data(), g.size() / 2, m[3], nn[3]);
+    st3(g.data() + g.size() / 2, g.size() / 2, m[4], nn[4]);
+    st3(lm.data(), lm.size(), m[5], nn[5]);
+    if (const char* dd = getenv("FOCK_DEBUG_DIR")) {
+      auto wr = [&](const char* nm, const void* p, size_t bytes) {
+        std::string f = std::string(dd) + "/" + stage + "_" + std::to_string(it) + "_" + nm + ".bin";
+        FILE* fp = fopen(f.c_str(), "wb");
+        if (fp) { fwrite(p, 1, bytes, fp); fclose(fp); }
+      };
+      std::vector<double> cc((size_t)l.ld3 * 2 * l.k);
+      cudaMemcpy(cc.data(), l.Cc, cc.size() * 8, cudaMemcpyDeviceToHost);
+      wr("G", g.data(), g.size() * 8);
+      wr("lam", lm.data(), lm.size() * 8);
+      wr("Cc", cc.data(), cc.size() * 8);
+      wr("Y", h.data(), h.size() * 8);
+    }
+    fprintf(stderr, "[fock dbg] it %d %-6s Y %.3e/%d HY %.3e/%d SY %.3e/%d GH %.3e/%d GS %.3e/%d lam0 %.12g nan %d err %s\n",
+            it, stage, m[0], nn[0], m[1], nn[1], m[2], nn[2], m[3], nn[3], m[4], nn[4], lm[0], nn[5],
+            cudaGetErrorString(cudaGetLastError()));
+  };
+  // X random, P = W = 0; Rayleigh-Ritz on X alone, then fresh images of [X | P]
+  { PROF("k_init_x", 1); k_init_x<<<dim3(32, B.init.n), 256, 0, st>>>(tl<InitTask>(B.init)); }
+  mv_HS(B, true, st);
+  gemm_tn(B.g1, st);
+  rr(B.rr1, st);
+  gemm_nn(B.u1, st);
+  copies(B.cp2k, st);
+  mv_HS(B, true, st);
+  dump("init", -1);
+  std::vector<double> hres((size_t)ns * B.kmax);
+  std::vector<int> active(ns, 1);
+  // a residual that stops improving below kFloorTol is at the rounding floor
+  // of the pencil (it scales with kappa(S)); Rayleigh quotients are then
+  // accurate to about the square of the residual, so the problem is done
+  const double kFloorTol = 1e-8;
+  const int kStagnation = 8;
+  std::vector<double> best(ns, INFINITY);
+  std::vector<int> best_it(ns, 0);
+  int it = 0;
+  for (;; ++it) {
+    { PROF("k_resid", 1); k_resid<<<dim3(B.kmax, B.resid.n), 256, 0, st>>>(tl<ResidTask>(B.resid), tol); }
+    CUDA_TRY(ctx, cudaMemcpyAsync(hres.data(), B.d_res, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    bool any = false, changed = false;
+    for (int s2 = 0; s2 < ns; ++s2) {
+      if (!active[s2]) continue;
+      double mx = 0.0;
+      bool bad = false;
+      for (int c = 0; c < B.lob[s2].k; ++c) {
+        double r = hres[(size_t)s2 * B.kmax + c];
+        if (!(r == r) || std::isinf(r)) bad = true; else mx = std::max(mx, r);
+      }
+      resid[s2] = bad ? INFINITY : mx;
+      iters[s2] = it;
+      if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
+      if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
+      else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
+      else if (best[s2] <= kFloorTol && it - best_it[s2] >= kStagnation) {
+        active[s2] = 0; conv[s2] = 1; changed = true;
+      }
+      else any = true;
+    }
+    if (dbg) {
+      fprintf(stderr, "[fock dbg] it %d res", it);
+      for (int s2 = 0; s2 < std::min(ns, 2); ++s2) fprintf(stderr, " %.3e", resid[s2]);
+      std::vector<double> lm(B.kmax);
+      cudaMemcpy(lm.data(), B.lob[0].lam, B.lob[0].k * 8, cudaMemcpyDeviceToHost);
+      fprintf(stderr, " lam %.14g %.14g %.14g\n", lm[0], lm[1], lm[B.lob[0].k - 1]);
+    }
+    if (!any || it >= maxit) break;
+    if (changed) CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, active.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
+    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, st); }
+    if (B.fwdR.n) {
+      mv_fwd(B, B.fwdR, st);
+      { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st); }
+      mv_inv(B, B.invPW, st);
+    }
+    mv_HS(B, false, st);
+    gemm_tn(B.tnCx, st);
+    gemm_nn(B.nnW, st);
+    // Rayleigh-Ritz on [X | P | W]
+    gemm_tn(B.g3, st);
+    rr(B.rr3, st);
+    if (it < 3) dump("rr", it);
+    // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
+    gemm_nn(B.u3, st);
+    copies(B.cp2k, st);
+    mv_HS(B, true, st);
+    gemm_tn(B.tnCp, st);
+    gemm_nn(B.nnP, st);
+  }
+  CUDA_TRY(ctx, cudaGetLastError());
+  return FOCK_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+struct fock_plan {
+  fock_ctx* ctx = nullptr;
+  Batch B;
+  std::vector<int> iters, conv;
+  std::vector<double> resid;
+};
+
+namespace {
+
+int plan_execute(fock_plan& P, double tol, int maxit) {
+  fock_ctx* ctx = P.ctx;
+  Batch& B = P.B;
+  run_assemble(ctx, B);
+  run_periodic(ctx, B);
+  run_struct_setup(ctx, B);
+  int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv);
+  if (rc) return rc;
+  CUDA_TRY(ctx, cudaGetLastError());
+  return FOCK_OK;
+}
+
+int plan_outputs(fock_plan& P, fock_output* outs, int on_device) {
+  fock_ctx* ctx = P.ctx;
+  Batch& B = P.B;
+  const int nprob = B.nprob;
+  const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  std::vector<int> pfail(nprob, 0);
+  for (int i = 0; i < nprob; ++i) {
+    Batch::PerProb& Q = B.pp[i];
+    outs[i].n_evals = Q.nev;
+    outs[i].iters = 0;
+    outs[i].resid = 0.0;
+    outs[i].status = FOCK_OK;
+    if (B.hp[i].kind == 0) {
+      if (outs[i].evals) CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, Q.ev, Q.nev * sizeof(double), kd, ctx->stream));
+      if (outs[i].block_of) CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].block_of, Q.blk, Q.nev * sizeof(int), kd, ctx->stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(&pfail[i], Q.fail, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  for (size_t s2 = 0; s2 < B.sidx.size(); ++s2) {
+    int i = B.sidx[s2];
+    if (outs[i].evals)
+      CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, B.lob[s2].lam, B.pp[i].nev * sizeof(double), kd, ctx->stream));
+    if (s2 < P.iters.size()) {
+      outs[i].iters = P.iters[s2];
+      outs[i].resid = P.resid[s2];
+      if (!P.conv[s2]) outs[i].status = FOCK_ENOCONV;
+    }
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  int first = FOCK_OK;
+  for (int i = 0; i < nprob; ++i) {
+    if (pfail[i]) outs[i].status = FOCK_EINVAL;
+    if (outs[i].status && !first) first = outs[i].status;
+  }
+  if (first == FOCK_EINVAL) set_err(ctx, first, "a Fourier-block mass matrix was not positive definite");
+  if (first == FOCK_ENOCONV) set_err(ctx, first, "box eigensolver reached maxit");
+  return first;
+}
+
+}  // namespace
+
+struct fock_blocks {
+  fock_ctx* ctx;
+  Batch B;
+};
+
+extern "C" {
+
+int fock_create(fock_ctx** out, int device, size_t hbm_budget_bytes, void* stream) {
+  if (!out) return FOCK_EINVAL;
+  *out = nullptr;
+  fock_ctx* c = new fock_ctx();
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return FOCK_ECUDA; }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return FOCK_ECUDA; }
+    c->own_stream = true;
+  }
+  if (hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    hbm_budget_bytes = (size_t)(0.9 * (double)fr);
+  }
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return FOCK_OK;
+}
+
+void fock_destroy(fock_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->arena) cudaFree(c->arena);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* fock_last_error(const fock_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int fock_synchronize(fock_ctx* c) {
+  if (!c) return FOCK_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FOCK_OK;
+}
+
+int fock_solve(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_output* outs, int on_device) {
+  if (!ctx || !outs) return FOCK_EINVAL;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ProfBind pb(ctx);
+  fock_plan P;
+  P.ctx = ctx;
+  int rc = build_batch(ctx, nprob, probs, P.B, false);
+  if (rc) return rc;
+  rc = plan_execute(P, 1e-10, 400);
+  if (rc) return rc;
+  return plan_outputs(P, outs, on_device);
+}
+
+int fock_plan_create(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_plan** out) {
+  if (!ctx || !out) return FOCK_EINVAL;
+  *out = nullptr;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  fock_plan* P = new fock_plan();
+  P->ctx = ctx;
+  int rc = build_batch(ctx, nprob, probs, P->B, true);
+  if (rc) { free_batch(P->B); delete P; return rc; }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { free_batch(P->B); delete P; return set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e)); }
+  *out = P;
+  return FOCK_OK;
+}
+
+int fock_plan_execute(fock_plan* P, double tol, int maxit) {
+  if (!P) return FOCK_EINVAL;
+  ProfBind pb(P->ctx);
+  return plan_execute(*P, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : 400);
+}
+
+int fock_plan_outputs(fock_plan* P, fock_output* outs, int on_device) {
+  if (!P || !outs) return FOCK_EINVAL;
+  return plan_outputs(*P, outs, on_device);
+}
+
+int fock_plan_info(const fock_plan* P, size_t* upload_bytes, size_t* device_bytes, size_t* n_evals) {
+  if (!P) return FOCK_EINVAL;
+  if (upload_bytes) *upload_bytes = P->B.ubytes;
+  if (device_bytes) *device_bytes = P->B.bytes + P->B.ubytes;
+  if (n_evals) {
+    size_t n = 0;
+    for (const auto& Q : P->B.pp) n += Q.nev;
+    *n_evals = n;
+  }
+  return FOCK_OK;
+}
+
+void fock_plan_free(fock_plan* P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->ctx->stream);
+  free_batch(P->B);
+  delete P;
+}
+
+int fock_profile_enable(fock_ctx* c, int on) {
+  if (!c) return FOCK_EINVAL;
+  c->prof = on != 0;
+  return FOCK_OK;
+}
+
+int fock_profile_reset(fock_ctx* c) {
+  if (!c) return FOCK_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (auto& r : c->recs) { c->pool.push_back(r.a); c->pool.push_back(r.b); }
+  c->recs.clear();
+  return FOCK_OK;
+}
+
+int fock_profile_read(fock_ctx* c, int cap, char* names, int* launches, double* ms) {
+  if (!c) return FOCK_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<std::string> nm;
+  std::vector<int> cnt;
+  std::vector<double> tot;
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    size_t i = 0;
+    while (i < nm.size() && nm[i] != r.name) ++i;
+    if (i == nm.size()) { nm.push_back(r.name); cnt.push_back(0); tot.push_back(0.0); }
+    cnt[i] += r.nlaunch;
+    tot[i] += t;
+  }
+  int n = (int)std::min<size_t>(nm.size(), (size_t)std::max(cap, 0));
+  for (int i = 0; i < n; ++i) {
+    if (names) { std::memset(names + 32 * i, 0, 32); std::strncpy(names + 32 * i, nm[i].c_str(), 31); }
+    if (launches) launches[i] = cnt[i];
+    if (ms) ms[i] = tot[i];
+  }
+  return n;
+}
+
+int fock_assemble(fock_ctx* ctx, const fock_problem* p, fock_blocks** out) {
+  if (!ctx || !p || !out) return FOCK_EINVAL;
+  *out = nullptr;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ProfBind pb(ctx);
+  fock_blocks* b = new fock_blocks();
+  b->ctx = ctx;
+  int rc = build_batch(ctx, 1, p, b->B, true);
+  if (rc) { free_batch(b->B); delete b; return rc; }
+  run_assemble(ctx, b->B);
+  run_struct_setup(ctx, b->B);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { free_batch(b->B); delete b; return set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e)); }
+  *out = b;
+  return FOCK_OK;
+}
+
+void fock_blocks_free(fock_blocks* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->ctx->stream);
+  free_batch(b->B);
+  delete b;
+}
+
+int fock_blocks_info(const fock_blocks* b, int* Nb, int* ngen, int* nbound, int* mcirc) {
+  if (!b) return FOCK_EINVAL;
+  const HostProb& H = b->B.hp[0];
+  const Batch::PerProb& Q = b->B.pp[0];
+  int ncell = H.L[0] * H.L[1] * H.L[2];
+  if (Nb) *Nb = ncell * H.m0;
+  if (H.kind == 0) {
+    if (ngen) *ngen = ncell;
+    if (nbound) *nbound = 0;
+    if (mcirc) *mcirc = ncell;
+  } else {
+    if (ngen) *ngen = 2 * Q.D + 1;
+    if (nbound) *nbound = Q.nE;
+    if (mcirc) *mcirc = Q.M;
+  }
+  return FOCK_OK;
+}
+
+int fock_blocks_copy_generators(const fock_blocks* b, double* Hout, double* Sout, double* EH, double* ES,
+                                int* bound_rc) {
+  if (!b) return FOCK_EINVAL;
+  fock_ctx* ctx = b->ctx;
+  const Batch& B = b->B;
+  const HostProb& H = B.hp[0];
+  const Batch::PerProb& Q = B.pp[0];
+  const int m2 = H.m0 * H.m0;
+  cudaStream_t st = ctx->stream;
+  if (H.kind == 1) {
+    std::vector<double> th((size_t)(Q.D + 1) * m2), ts((size_t)(Q.D + 1) * m2);
+    CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), Q.TH, th.size() * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ts.data(), Q.TS, ts.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (EH && Q.nE) CUDA_TRY(ctx, cudaMemcpyAsync(EH, Q.EH, (size_t)Q.nE * m2 * 8, cudaMemcpyDeviceToHost, st));
+    if (ES && Q.nE) CUDA_TRY(ctx, cudaMemcpyAsync(ES, Q.ES, (size_t)Q.nE * m2 * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    for (int g = 0; g < 2 * Q.D + 1; ++g) {
+      int d = g - Q.D, ad = std::abs(d);
+      for (int mu = 0; mu < H.m0; ++mu)
+        for (int nu = 0; nu < H.m0; ++nu) {
+          int src = (d >= 0) ? (mu * H.m0 + nu) : (nu * H.m0 + mu);
+          if (Hout) Hout[(size_t)g * m2 + mu * H.m0 + nu] = th[(size_t)ad * m2 + src];
+          if (Sout) Sout[(size_t)g * m2 + mu * H.m0 + nu] = ts[(size_t)ad * m2 + src];
+        }
+    }
+    if (bound_rc)
+      for (int e = 0; e < Q.nE; ++e) { bound_rc[2 * e] = Q.Ek[e]; bound_rc[2 * e + 1] = Q.Em[e]; }
+    return FOCK_OK;
+  }
+  // periodic: A_k = combine of the per-axis factors at offsets (k1, k2, k3)
+  const int ncell = H.L[0] * H.L[1] * H.L[2];
+  const size_t xs = (size_t)H.nF * m2;
+  double *zero = nullptr, *gh = nullptr, *gs = nullptr;
+  CombineTask* dt = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&zero, xs * 8));
+  CUDA_TRY(ctx, cudaMalloc(&gh, (size_t)ncell * m2 * 8));
+  CUDA_TRY(ctx, cudaMalloc(&gs, (size_t)ncell * m2 * 8));
+  CUDA_TRY(ctx, cudaMalloc(&dt, (size_t)ncell * sizeof(CombineTask)));
+  CUDA_TRY(ctx, cudaMemsetAsync(zero, 0, xs * 8, st));
+  std::vector<const double*> fx[3];
+  for (int a = 0; a < 3; ++a) {
+    fx[a].assign(H.L[a], zero);
+    const AxisPlan& A = B.ap[a];
+    if (H.per[a]) {
+      for (size_t o = 0; o < A.offs.size(); ++o) fx[a][A.offs[o]] = Q.X[a] + o * xs;
+    } else {
+      fx[a][0] = Q.X[a];
+    }
+  }
+  std::vector<CombineTask> ct(ncell);
+  for (int kb = 0; kb < ncell; ++kb) {
+    int k3 = kb % H.L[2], k2 = (kb / H.L[2]) % H.L[1], k1 = kb / (H.L[1] * H.L[2]);
+    CombineTask& c = ct[kb];
+    std::memset(&c, 0, sizeof(c));
+    c.prob = 0; c.X0 = fx[0][k1]; c.X1 = fx[1][k2]; c.X2 = fx[2][k3];
+    c.outH = gh + (size_t)kb * m2; c.outS = gs + (size_t)kb * m2;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(dt, ct.data(), ct.size() * sizeof(CombineTask), cudaMemcpyHostToDevice, st));
+  launch_combine(B.d_probs, dt, ncell, st);
+  if (Hout) CUDA_TRY(ctx, cudaMemcpyAsync(Hout, gh, (size_t)ncell * m2 * 8, cudaMemcpyDeviceToHost, st));
+  if (Sout) CUDA_TRY(ctx, cudaMemcpyAsync(Sout, gs, (size_t)ncell * m2 * 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  cudaFree(zero); cudaFree(gh); cudaFree(gs); cudaFree(dt);
+  return FOCK_OK;
+}
+
+int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of) {
+  if (!ctx || !b || !evals) return FOCK_EINVAL;
+  Batch& B = const_cast<Batch&>(b->B);
+  if (B.hp[0].kind != 0) return set_err(ctx, FOCK_EINVAL, "not a periodic problem");
+  ProfBind pb(ctx);
+  run_periodic(ctx, B);
+  const Batch::PerProb& Q = B.pp[0];
+  int fail = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(evals, Q.ev, Q.nev * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (block_of) CUDA_TRY(ctx, cudaMemcpyAsync(block_of, Q.blk, Q.nev * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(&fail, Q.fail, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (fail) return set_err(ctx, FOCK_EINVAL, "a Fourier-block mass matrix was not positive definite");
+  return FOCK_OK;
+}
+
+int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x, double* y,
+                         int nvec, int on_device) {
+  if (!ctx || !b || !x || !y || nvec <= 0) return FOCK_EINVAL;
+  const Batch& B = b->B;
+  const HostProb& H = B.hp[0];
+  if (H.kind != 1) return set_err(ctx, FOCK_EINVAL, "matvec needs a box chain");
+  const Batch::PerProb& Q = B.pp[0];
+  cudaStream_t st = ctx->stream;
+  const int n = Q.Lc * H.m0;
+  const size_t nbytes = (size_t)n * nvec * 8;
+  double *dx = nullptr, *dy = nullptr;
+  cplx *X = nullptr, *Y = nullptr;
+  char* tasks = nullptr;
+  if (on_device) { dx = const_cast<double*>(x); dy = y; }
+  else {
+    CUDA_TRY(ctx, cudaMalloc(&dx, nbytes));
+    CUDA_TRY(ctx, cudaMalloc(&dy, nbytes));
+    CUDA_TRY(ctx, cudaMemcpyAsync(dx, x, nbytes, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(ctx, cudaMalloc(&X, (size_t)Q.M * H.m0 * nvec * sizeof(cplx)));
+  CUDA_TRY(ctx, cudaMalloc(&Y, (size_t)Q.M * H.m0 * nvec * sizeof(cplx)));
+  CUDA_TRY(ctx, cudaMalloc(&tasks, 4096));
+  int cc = std::max(1, std::min(16, 98304 / (32 * Q.M)));
+  FftTask tf; std::memset(&tf, 0, sizeof(tf));
+  tf.prob = 0; tf.L = Q.Lc; tf.m0 = H.m0; tf.ncol = nvec; tf.circ = B.d_circs + Q.circ; tf.x = dx; tf.ldx = n;
+  tf.X = X; tf.cc = cc;
+  FftTask ti = tf; ti.x = nullptr; ti.X = Y; ti.y = dy; ti.ldy = n; ti.beta = 0.0;
+  BmulTask bm = {0, Q.M, H.m0, nvec, which == FOCK_OP_H ? Q.CH : Q.CS, nullptr, X, Y, nullptr};
+  EApplyTask ea;
+  ea.prob = 0; ea.m0 = H.m0; ea.ncol = nvec; ea.nrows = Q.nErows; ea.rows = Q.Erows; ea.rowptr = Q.Erowptr;
+  ea.cols = Q.Ecols; ea.vals = which == FOCK_OP_H ? Q.EH : Q.ES; ea.x = dx; ea.ldx = n; ea.y = dy; ea.ldy = n;
+  char hbuf[4096];
+  std::memcpy(hbuf, &tf, sizeof(tf));
+  std::memcpy(hbuf + 512, &ti, sizeof(ti));
+  std::memcpy(hbuf + 1024, &bm, sizeof(bm));
+  std::memcpy(hbuf + 1536, &ea, sizeof(ea));
+  CUDA_TRY(ctx, cudaMemcpyAsync(tasks, hbuf, 2048, cudaMemcpyHostToDevice, st));
+  int chunks = (H.m0 * nvec + cc - 1) / cc;
+  launch_fft((const FftTask*)tasks, 1, chunks, Q.M, cc, +1, st);
+  launch_blockmul((const BmulTask*)(tasks + 1024), 1, Q.M, H.m0, st);
+  launch_fft((const FftTask*)(tasks + 512), 1, chunks, Q.M, cc, -1, st);
+  if (Q.nE) launch_eapply((const EApplyTask*)(tasks + 1536), 1, st);
+  if (!on_device) CUDA_TRY(ctx, cudaMemcpyAsync(y, dy, nbytes, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, cudaGetLastError());
+  if (!on_device) { cudaFree(dx); cudaFree(dy); }
+  cudaFree(X); cudaFree(Y); cudaFree(tasks);
+  return FOCK_OK;
+}
+
+int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int maxit, double* evals,
+                 double* evecs, int* iters) {
+  if (!ctx || !b || !evals) return FOCK_EINVAL;
+  Batch& B = const_cast<Batch&>(b->B);
+  if (B.hp[0].kind != 1) return set_err(ctx, FOCK_EINVAL, "not a box problem");
+  if (k <= 0 || k > B.lob[0].k) return set_err(ctx, FOCK_EINVAL, "k exceeds the planned k_eig");
+  ProfBind pb(ctx);
+  std::vector<int> it, conv;
+  std::vector<double> res;
+  int rc = run_lobpcg(ctx, B, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : 400, it, res, conv);
+  if (rc) return rc;
+  const Batch::Lob& l = B.lob[0];
+  CUDA_TRY(ctx, cudaMemcpyAsync(evals, l.lam, (size_t)k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (evecs) CUDA_TRY(ctx, cudaMemcpyAsync(evecs, l.Y, (size_t)l.n * k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (iters) *iters = it[0];
+  if (!conv[0]) return set_err(ctx, FOCK_ENOCONV, "maxit reached");
+  return FOCK_OK;
+}
+
+}  // extern "C"

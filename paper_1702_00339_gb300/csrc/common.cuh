@@ -1,0 +1,208 @@
+// Internal descriptors and device helpers of libfock (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fock {
+
+constexpr int MAXM0 = 32;
+constexpr int MAXR = 64;
+constexpr int MAXRADIX = 16;   // radix factors of a circulant size
+
+// Modes of a 1D Galerkin form along one axis (gram task):
+//   RING - periodic axis: nodes 0..N-1 with wrap-around, potential tiled;
+//   VIRT - Toeplitz generator of a chain axis: unbounded node line, no walls,
+//          potential tiled with period n0 (what an interior cell sees);
+//   WALL - Dirichlet axis as it is: nodes -pad..N-pad-1, zero outside,
+//          potential replicated with the cell index clamped to 0..L-1.
+enum GramMode { RING = 0, VIRT = 1, WALL = 2 };
+
+struct AxisDev {
+  int N, L, per, pad;
+  int jlo, W;           // reference-cell function window: j in [jlo, jlo + W)
+  int rlo, nr;          // potential table: reduced node r in [rlo, rlo + nr)
+  double* g;            // [m0][W]   nodal GTO factors of the reference cell
+  double* p;            // [T][nr]   window-summed P0 Gaussian integrals
+};
+
+struct ProbDev {
+  int m0, M0, R, T, nF; // T = M0*R potential terms, nF = T + 2 factors
+  int n0;
+  double b0, h, eps;
+  AxisDev ax[3];
+  const double* alpha;  // [m0]
+  const int* ang;       // [m0]
+  const int* centre;    // [m0]
+  const double* Z;      // [M0]
+  const double* frac;   // [M0*3]
+  const double* tq;     // [R]
+  const double* cq;     // [R]
+};
+
+// One 1D Galerkin form: X[f][mu][nu] = sum_rho g_{a,mu}(rho) [W_f g_{b,nu}](rho)
+// for f = 0 (mass S1), 1 (stiffness A1), 2 + t (potential term t).
+struct GramTask {
+  int prob, axis, mode;
+  int a, b;             // cells of the row / column function
+  int rho0, rho1;       // node range [rho0, rho1) (RING: 0..N)
+  int ptab;             // -1: the lattice potential table of the axis; >= 0: a
+                        //     defect table index (no replication, direct nodes)
+  double* X;            // out [nF][m0*m0]
+  double* Zs;           // scratch [nfold][m0*m0] (folded pair products)
+  int nfold;            // number of reduced nodes of the fold
+  int foldlo;           // first reduced node
+};
+
+// A defect table: single-nucleus Gaussian integrals e[q][i] on the grid of
+// one axis (no window, no replication), scaled into the defect term.
+struct DefTab {
+  int prob, axis, N, pad;
+  double pos;           // nucleus coordinate in lattice units relative to X0 (h units)
+  double* e;            // [R][N]
+};
+
+struct __align__(16) cplx { double x, y; };
+
+__host__ __device__ inline cplx cmk(double a, double b) { cplx r; r.x = a; r.y = b; return r; }
+__host__ __device__ inline cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cplx csub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline cplx cmul(cplx a, cplx b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline cplx cmulc(cplx a, cplx b) {  // a * conj(b)
+  return cmk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ inline cplx cconj(cplx a) { return cmk(a.x, -a.y); }
+__host__ __device__ inline cplx cscale(cplx a, double s) { return cmk(a.x * s, a.y * s); }
+__host__ __device__ inline double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+
+__device__ inline int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+__device__ inline int posmod(int a, int b) { int r = a % b; return r < 0 ? r + b : r; }
+
+// Circulant (FFT) plan of one problem's block lattice index.
+struct CircDev {
+  int M;                // circulant size
+  int nfac;             // radix factors of M
+  int fac[MAXRADIX];
+  cplx* tw;             // [M] exp(-2 pi i t / M)
+};
+
+// ---- task descriptors shared by the host planner and the kernels ----
+struct SegDesc { int prob, axis, count; };
+
+struct CombineTask {
+  int prob;
+  const double* X0; const double* X1; const double* X2;   // [nF][m0*m0]
+  const double* subH; const double* subS; int subT;        // generator to subtract (transposed?)
+  const double* D0; const double* D1; const double* D2;    // defect forms [R][m0*m0] or null
+  double dZ;
+  double* outH; double* outS;
+};
+
+struct DftTask {
+  int prob, L, noff;
+  const int* offs;        // [noff] lattice offsets d
+  const double* X;        // [noff][nF][m0*m0]
+  cplx* Xh;               // [L][nF][m0*m0]
+};
+
+struct FBlockTask {
+  int prob, source, nj;          // Fourier indices handled: j in [0, nj)
+  int L[3];                      // lattice (FACTORS)
+  const cplx* Xh[3];             // per-axis DFT'd factors [L_l][nF][m0*m0] (FACTORS)
+  int M, D;                      // circulant size and generator reach (TOEPLITZ)
+  const double* TH;              // [D+1][m0*m0] generators T_d of H (TOEPLITZ)
+  const double* TS;              // [D+1][m0*m0] of S
+  cplx* outH;                    // optional [nj][m0*m0]: store Hbar_j
+  cplx* outS;                    // optional [nj][m0*m0]: store Sbar_j
+  int want;                      // 0: no eigenvalues, 1: all, 2: only the lowest
+  double* ev;                    // [nj*m0] (want 1) or [nj] (want 2)
+  int* blk;                      // optional [nj*m0] Fourier index of each eigenvalue
+  int* fail;                     // set to 1 if a block's Sbar is not positive definite
+};
+
+struct PrecTask {
+  int prob, M;
+  const double* emin;    // [M] lowest eigenvalue of each embedding block
+  double* sigma;         // out
+  const cplx* CH; const cplx* CS;   // [M][m0*m0]
+  cplx* K;               // out [M][m0*m0]
+  double rel_shift;
+};
+
+struct SortTask { int n; double* v; int* idx; };
+
+struct FftTask {
+  int prob, L, m0, ncol;          // block rows L, block size m0, vectors ncol
+  const CircDev* circ;
+  const double* x; int ldx;       // forward input (real, N_b x ncol, col-major)
+  cplx* X;                        // [M][m0*ncol]
+  double* y; int ldy;             // inverse output
+  double beta;                    // y = beta*y + Re(.)/M
+  int cc;                         // columns per CTA
+};
+
+struct BmulTask {
+  int prob, M, m0, ncol;
+  const cplx* B1; const cplx* B2;  // [M][m0*m0] (B2 optional)
+  const cplx* X;                   // [M][m0*ncol]
+  cplx* Y1; cplx* Y2;
+};
+
+struct EApplyTask {
+  int prob, m0, ncol, nrows;
+  const int* rows;      // [nrows] block-row ids
+  const int* rowptr;    // [nrows+1] into cols/vals
+  const int* cols;      // block-column ids
+  const double* vals;   // [nnz][m0*m0]
+  const double* x; int ldx;
+  double* y; int ldy;
+};
+
+struct InitTask { int n, k, ld; uint64_t seed; double* X; };
+
+struct GemmTask {
+  const int* active;           // skip when *active == 0
+  int n, a, b;                 // TN: G[a x b] = A[n x a]^T B[n x b];  NN: C[n x b] = A[n x a] B[a x b]
+  const double* A; int lda;
+  const double* B; int ldb;
+  double* C; int ldc;
+  double alpha, beta;
+};
+
+struct ResidTask {
+  const int* active;
+  int n, k, ld;
+  const double* X; const double* HX; const double* SX;
+  double* lam;        // Rayleigh quotients (recomputed from X, HX, SX)
+  double* R;          // [n x k]
+  double* res;        // [k] relative residual
+};
+
+struct RRTask {
+  const int* active;
+  int nb, k, ld;          // current basis size, wanted pairs, leading dim of G / C
+  double* GH; double* GS; // [nb x nb] (ld), destroyed
+  double* work;           // [3 * ld * ld] scratch: C, V, Z
+  double* lam;            // out [k]
+  double* Cc;             // out [nb x 2k] (ld): [C | C with the first k rows zeroed]
+  int* fail;              // out: 1 if Y^T S Y was not numerically positive definite
+};
+
+struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };
+
+struct BandTask {
+  int m0, L, D, k, n;
+  const double* TH; const double* TS;      // [D+1][m0*m0]
+  int nE;
+  const int* Ek; const int* Em;            // boundary block positions
+  const double* EH; const double* ES;      // [nE][m0*m0]
+  const double* sigma0;                    // shift from the embedding
+  double* band;                            // [L][D+1][m0*m0]
+  double* sigma_used;                      // out
+  int* fail;                               // out: 1 if every attempt broke down
+  const double* R; double* W; int ld;      // solve: W = A^-1 R (n x k, ld)
+  const int* active;
+};
+
+}  // namespace fock

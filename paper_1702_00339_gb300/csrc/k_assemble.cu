@@ -1,0 +1,275 @@
+// Stage (a): separable rank-R assembly (Lemma 2.1, Prop. 2.2, Lemma 3.4).
+//
+//  k_gref     nodal 1D GTO factors of the reference cell      (Sec. 2.4)
+//  k_ptab     window-summed P0 Gaussian integrals per axis    (Eq. 2.13, Eq. 3.6)
+//  k_deftab   one nucleus' P0 Gaussian integrals per axis     (defects)
+//  k_gram_fold / k_gram_pot
+//             1D Galerkin forms  X_f[mu][nu] = <g_{a,mu}, W_f g_{b,nu}>  with
+//             W_f = S1, A1 or diag(p_t) (Lemma 2.1 display, Eqs. 2.16-2.17).
+//             The potential of an interior node depends only on its node
+//             modulo n0 (replicated cell), so the node sum folds first into
+//             per-residue pair products Z[r][mu nu] and then contracts with
+//             the n0-long potential rows: X_t = P_t . Z.
+//  k_combine  Hadamard combine over the axes into m0 x m0 blocks
+//             H = A/2 - V, S (Lemma 3.4, Eqs. 2.16-2.17).
+//  k_axis_dft sparse DFT of the per-axis factors over the lattice offset
+//             (Thm. 3.3: only 1D transforms of the factors are needed).
+#include "common.cuh"
+
+namespace fock {
+
+// ---------------------------------------------------------------- K1 ----
+// Segment = (problem, axis).  Items = m0*W (gref) or T*nr (ptab).
+
+
+__global__ void k_gref(const ProbDev* __restrict__ probs, const SegDesc* __restrict__ segs) {
+  const SegDesc sg = segs[blockIdx.y];
+  const ProbDev& P = probs[sg.prob];
+  const AxisDev& A = P.ax[sg.axis];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < sg.count; it += gridDim.x * blockDim.x) {
+    int mu = it / A.W, jj = it % A.W;
+    int j = A.jlo + jj;
+    double al = P.alpha[mu];
+    int isp = (P.ang[mu] == sg.axis + 1);
+    double f = P.frac[P.centre[mu] * 3 + sg.axis];
+    double d = ((double)j + 0.5 - f * (double)P.n0) * P.h;
+    if (A.per) {
+      double period = (double)A.N * P.h;
+      d = d - period * floor(d / period + 0.5);
+    }
+    double rcut = sqrt(log(1.0 / P.eps) / al);
+    double v = 0.0;
+    if (fabs(d) <= rcut) {
+      double nrm = sqrt(sqrt(2.0 * al / 3.14159265358979323846));
+      if (isp) nrm *= 2.0 * sqrt(al);
+      v = nrm * exp(-al * d * d);
+      if (isp) v *= d;
+    }
+    A.g[it] = v;
+  }
+}
+
+// int_lo^hi exp(-t^2 s^2) ds, erfc in the tails.
+__device__ inline double gauss_cell(double t, double lo, double hi) {
+  double a = t * lo, b = t * hi, v;
+  if (a >= 0.0) v = erfc(a) - erfc(b);
+  else if (b <= 0.0) v = erfc(-b) - erfc(-a);
+  else v = erf(b) - erf(a);
+  return v * (0.88622692545275801365 / t);   // sqrt(pi)/2
+}
+
+__global__ void k_ptab(const ProbDev* __restrict__ probs, const SegDesc* __restrict__ segs) {
+  const SegDesc sg = segs[blockIdx.y];
+  const ProbDev& P = probs[sg.prob];
+  const AxisDev& A = P.ax[sg.axis];
+  const int L = A.L;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < sg.count; it += gridDim.x * blockDim.x) {
+    int t = it / A.nr, rr = it % A.nr;
+    int nu = t / P.R, q = t % P.R;
+    double r = (double)(A.rlo + rr);
+    double f = P.frac[nu * 3 + sg.axis];
+    double tq = P.tq[q];
+    double acc = 0.0;
+    int hw = (L == 1) ? 0 : L / 2;
+    for (int k = -hw; k <= hw; ++k) {
+      double w = (L > 1 && (L % 2 == 0) && (k == -hw || k == hw)) ? 0.5 : 1.0;
+      double u = (r - ((double)k + f) * (double)P.n0) * P.h;   // lo - a, h units -> bohr
+      acc += w * gauss_cell(tq, u, u + P.h);
+    }
+    A.p[it] = acc;
+  }
+}
+
+__global__ void k_deftab(const ProbDev* __restrict__ probs, const DefTab* __restrict__ tabs) {
+  const DefTab D = tabs[blockIdx.y];
+  const ProbDev& P = probs[D.prob];
+  const int per = P.ax[D.axis].per;
+  const int cnt = P.R * D.N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < cnt; it += gridDim.x * blockDim.x) {
+    int q = it / D.N, i = it % D.N;
+    double rho = (double)(i - D.pad);
+    double dc = (rho + 0.5 - D.pos) * P.h;      // node centre - nucleus
+    if (per) {
+      double period = (double)D.N * P.h;
+      dc = dc - period * floor(dc / period + 0.5);
+    }
+    D.e[it] = gauss_cell(P.tq[q], dc - 0.5 * P.h, dc + 0.5 * P.h);
+  }
+}
+
+// ---------------------------------------------------------------- K2 ----
+__device__ inline double gval(const AxisDev& A, int mode, int n0, int mu, int cell, int rho) {
+  if (mode == RING) {
+    int j = posmod(rho - cell * n0, A.N);
+    return A.g[mu * A.W + j];
+  }
+  if (mode == WALL && (rho < -A.pad || rho >= A.N - A.pad)) return 0.0;
+  int j = rho - cell * n0 - A.jlo;
+  if (j < 0 || j >= A.W) return 0.0;
+  return A.g[mu * A.W + j];
+}
+
+// One CTA per task: folded pair products Z[r][mu nu] and the S1 / A1 forms.
+__global__ void k_gram_fold(const ProbDev* __restrict__ probs, const GramTask* __restrict__ tasks) {
+  const GramTask T = tasks[blockIdx.x];
+  const ProbDev& P = probs[T.prob];
+  const AxisDev& A = P.ax[T.axis];
+  const int m0 = P.m0, n0 = P.n0, np = m0 * m0;
+  const bool direct = (T.ptab >= 0);      // defect tables: no replication
+  const int tot = T.nfold * np;
+  for (int it = threadIdx.x; it < tot; it += blockDim.x) {
+    int rr = it / np, pr = it % np, mu = pr / m0, nu = pr % m0;
+    int r = T.foldlo + rr;
+    double acc = 0.0;
+    if (direct) {
+      if (r >= T.rho0 && r < T.rho1)
+        acc = gval(A, T.mode, n0, mu, T.a, r) * gval(A, T.mode, n0, nu, T.b, r);
+    } else if (T.mode == RING) {
+      for (int c = 0; c < A.L; ++c) {
+        int rho = r + c * n0;
+        acc += gval(A, RING, n0, mu, T.a, rho) * gval(A, RING, n0, nu, T.b, rho);
+      }
+    } else if (T.mode == VIRT || (r >= 0 && r < n0)) {
+      // all nodes rho = r (mod n0) in the window (WALL: interior cells 0..L-1)
+      int c0 = floordiv(T.rho0 - r + n0 - 1, n0), c1 = floordiv(T.rho1 - 1 - r, n0);
+      if (T.mode == WALL) { c0 = max(c0, 0); c1 = min(c1, A.L - 1); }
+      for (int c = c0; c <= c1; ++c) {
+        int rho = r + c * n0;
+        acc += gval(A, T.mode, n0, mu, T.a, rho) * gval(A, T.mode, n0, nu, T.b, rho);
+      }
+    } else {
+      // WALL padding node: replicated from the end cell (clamped cell index)
+      int rho = (r < 0) ? r : r + (A.L - 1) * n0;
+      if (rho >= T.rho0 && rho < T.rho1)
+        acc = gval(A, WALL, n0, mu, T.a, rho) * gval(A, WALL, n0, nu, T.b, rho);
+    }
+    T.Zs[it] = acc;
+  }
+  if (direct) return;   // defect forms carry no mass / stiffness part
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    int mu = pr / m0, nu = pr % m0;
+    double s = 0.0, a = 0.0;
+    for (int rho = T.rho0; rho < T.rho1; ++rho) {
+      double ga = gval(A, T.mode, n0, mu, T.a, rho);
+      if (ga == 0.0) continue;
+      double b0 = gval(A, T.mode, n0, nu, T.b, rho);
+      double bm = gval(A, T.mode, n0, nu, T.b, rho - 1);
+      double bp = gval(A, T.mode, n0, nu, T.b, rho + 1);
+      s += ga * (4.0 * b0 + bm + bp);
+      a += ga * (2.0 * b0 - bm - bp);
+    }
+    T.X[0 * np + pr] = s * (P.h / 6.0);
+    T.X[1 * np + pr] = a / P.h;
+  }
+}
+
+// One CTA per task: X_t[mu nu] = sum_r P_t[r] Z[r][mu nu].
+__global__ void k_gram_pot(const ProbDev* __restrict__ probs, const GramTask* __restrict__ tasks,
+                           const DefTab* __restrict__ dtabs) {
+  const GramTask T = tasks[blockIdx.x];
+  const ProbDev& P = probs[T.prob];
+  const AxisDev& A = P.ax[T.axis];
+  const int np = P.m0 * P.m0;
+  const bool direct = (T.ptab >= 0);
+  const int nt = direct ? P.R : P.T;
+  const double* tab = direct ? dtabs[T.ptab].e : A.p;
+  const int ld = direct ? dtabs[T.ptab].N : A.nr;
+  const int off = direct ? (T.foldlo + dtabs[T.ptab].pad) : (T.foldlo - A.rlo);
+  double* out = T.X + (direct ? 0 : 2 * np);
+  for (int it = threadIdx.x; it < nt * np; it += blockDim.x) {
+    int t = it / np, pr = it % np;
+    const double* pt = tab + (size_t)t * ld + off;
+    double acc = 0.0;
+    for (int rr = 0; rr < T.nfold; ++rr) acc += pt[rr] * T.Zs[(size_t)rr * np + pr];
+    out[(size_t)t * np + pr] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- K3 ----
+// H/S block from three per-axis factor sets (Lemma 3.4):
+//   H = 1/2 (A0 S1 S2 + S0 A1 S2 + S0 S1 A2) - sum_t w_t M0_t M1_t M2_t,  S = S0 S1 S2
+// (products elementwise in mu nu), w_t = Z_nu c_q for t = nu*R + q.  Optional
+// subtraction of a Toeplitz generator (boundary blocks E = block - T_{k-m}),
+// optional defect term (-dZ c_q Y0_q Y1_q Y2_q).
+
+
+__global__ void k_combine(const ProbDev* __restrict__ probs, const CombineTask* __restrict__ tasks) {
+  const CombineTask C = tasks[blockIdx.x];
+  const ProbDev& P = probs[C.prob];
+  const int m0 = P.m0, np = m0 * m0;
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    double h = 0.0, s = 0.0, v = 0.0;
+    if (C.X0) {   // lattice part (absent for a defect-only block)
+      double s0 = C.X0[pr], s1 = C.X1[pr], s2 = C.X2[pr];
+      double a0 = C.X0[np + pr], a1 = C.X1[np + pr], a2 = C.X2[np + pr];
+      h = 0.5 * (a0 * s1 * s2 + s0 * a1 * s2 + s0 * s1 * a2);
+      for (int t = 0; t < P.T; ++t) {
+        double w = P.Z[t / P.R] * P.cq[t % P.R];
+        v += w * C.X0[(2 + t) * np + pr] * C.X1[(2 + t) * np + pr] * C.X2[(2 + t) * np + pr];
+      }
+      s = s0 * s1 * s2;
+    }
+    if (C.D0) {
+      double dv = 0.0;
+      for (int q = 0; q < P.R; ++q)
+        dv += P.cq[q] * C.D0[q * np + pr] * C.D1[q * np + pr] * C.D2[q * np + pr];
+      v += C.dZ * dv;
+    }
+    h -= v;
+    if (C.subH) {
+      int ps = C.subT ? ((pr % m0) * m0 + pr / m0) : pr;
+      h -= C.subH[ps];
+      s -= C.subS[ps];
+    }
+    if (C.outH) C.outH[pr] = h;
+    if (C.outS) C.outS[pr] = s;
+  }
+}
+
+// ---------------------------------------------------------------- K4 ----
+
+
+__global__ void k_axis_dft(const ProbDev* __restrict__ probs, const DftTask* __restrict__ tasks) {
+  const DftTask D = tasks[blockIdx.y];
+  const ProbDev& P = probs[D.prob];
+  const int per = P.nF * P.m0 * P.m0;
+  const int tot = D.L * per;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
+    int j = it / per, e = it % per;
+    double re = 0.0, im = 0.0;
+    for (int o = 0; o < D.noff; ++o) {
+      int jd = (int)(((long long)j * D.offs[o]) % D.L);
+      double s, c;
+      sincospi(-2.0 * (double)jd / (double)D.L, &s, &c);
+      double x = D.X[(size_t)o * per + e];
+      re += c * x;
+      im += s * x;
+    }
+    D.Xh[it] = cmk(re, im);
+  }
+}
+
+// ------------------------------------------------------------ launchers ----
+void launch_vec1d(const ProbDev* probs, const SegDesc* gsegs, int ngseg, const SegDesc* psegs,
+                  int npseg, const DefTab* dtabs, int ndtab, cudaStream_t st) {
+  if (ngseg) k_gref<<<dim3(8, ngseg), 256, 0, st>>>(probs, gsegs);
+  if (npseg) k_ptab<<<dim3(16, npseg), 256, 0, st>>>(probs, psegs);
+  if (ndtab) k_deftab<<<dim3(8, ndtab), 256, 0, st>>>(probs, dtabs);
+}
+
+void launch_gram(const ProbDev* probs, const GramTask* tasks, int ntask, const DefTab* dtabs,
+                 cudaStream_t st) {
+  if (!ntask) return;
+  k_gram_fold<<<ntask, 256, 0, st>>>(probs, tasks);
+  k_gram_pot<<<ntask, 256, 0, st>>>(probs, tasks, dtabs);
+}
+
+void launch_combine(const ProbDev* probs, const CombineTask* tasks, int n, cudaStream_t st) {
+  if (n) k_combine<<<n, 256, 0, st>>>(probs, tasks);
+}
+
+void launch_axis_dft(const ProbDev* probs, const DftTask* tasks, int n, cudaStream_t st) {
+  if (n) k_axis_dft<<<dim3(32, n), 256, 0, st>>>(probs, tasks);
+}
+
+}  // namespace fock

@@ -1,0 +1,432 @@
+// Stage (b) and the Fourier side of stage (c).
+//
+//  k_fblocks   one CTA per Fourier index j: forms the m0 x m0 Hermitian pair
+//              (Hbar_j, Sbar_j) and, on request, stores it and/or solves the
+//              generalized eigenproblem Hbar u = l Sbar u in FP64.
+//     source FACTORS (periodic lattice, Thm. 3.3 with the CP rank of the
+//       potential, Remark 3.5): Hbar_j = 1/2 sum_p (prod_{l!=p} Shat_l) Ahat_p
+//       - sum_t w_t prod_l Mhat_{l,t}, Sbar_j = prod_l Shat_l, elementwise in
+//       (mu, nu), each factor picked at the axis component j_l;
+//     source TOEPLITZ (box chain, Remark 3.2): the size-M block circulant
+//       that embeds the symmetric block Toeplitz matrix with generators
+//       T_d = block (k+d, k), |d| <= D: Chat_j = T_0 + sum_d (w^{jd} T_d +
+//       w^{-jd} T_d^T), w = exp(-2 pi i / M) (Eq. A.3 convention).
+//     eigensolver: Cholesky Sbar = L L^H, C = L^-1 Hbar L^-H, Householder
+//       reduction of C to a real tridiagonal, Sturm-sequence bisection per
+//       eigenvalue (ascending, so the block spectrum comes out sorted).
+//  k_sigma      shift of the preconditioner: min_j lambda_min(Chat_j) - delta.
+//  k_precond    K_j = (Chat_H,j - sigma Chat_S,j)^-1 per Fourier index.
+//  k_sort_*     ascending sort of (eigenvalue, Fourier index) pairs.
+#include <float.h>
+#include "common.cuh"
+
+namespace fock {
+
+enum FSource { FROM_FACTORS = 0, FROM_TOEPLITZ = 1 };
+
+
+
+// ---- dense Hermitian helpers (shared memory, whole CTA) ----
+
+// In-place lower Cholesky of a Hermitian positive definite m x m (row-major).
+__device__ bool cta_cholesky(cplx* a, int m) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      double d = a[k * m + k].x;
+      if (!(d > 0.0)) { bad = 1; d = 1.0; }
+      a[k * m + k] = cmk(sqrt(d), 0.0);
+    }
+    __syncthreads();
+    double dk = a[k * m + k].x;
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) a[i * m + k] = cscale(a[i * m + k], 1.0 / dk);
+    __syncthreads();
+    int nt = m - k - 1;
+    for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
+      int i = k + 1 + it / nt, j = k + 1 + it % nt;
+      if (j <= i) a[i * m + j] = csub(a[i * m + j], cmulc(a[i * m + k], a[j * m + k]));
+    }
+    __syncthreads();
+  }
+  return bad == 0;
+}
+
+// h <- L^-1 h L^-H (h Hermitian full storage, L lower in l).
+__device__ void cta_reduce(cplx* h, const cplx* l, int m) {
+  // Y = L^-1 H: thread per column
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      cplx s = h[i * m + j];
+      for (int q = 0; q < i; ++q) s = csub(s, cmul(l[i * m + q], h[q * m + j]));
+      h[i * m + j] = cscale(s, 1.0 / l[i * m + i].x);
+    }
+  }
+  __syncthreads();
+  // C = Y L^-H: thread per row, C[i][j] = (Y[i][j] - sum_{q<j} C[i][q] conj(L[j][q])) / L[j][j]
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int j = 0; j < m; ++j) {
+      cplx s = h[i * m + j];
+      for (int q = 0; q < j; ++q) s = csub(s, cmulc(h[i * m + q], l[j * m + q]));
+      h[i * m + j] = cscale(s, 1.0 / l[j * m + j].x);
+    }
+  }
+  __syncthreads();
+}
+
+// Householder reduction of Hermitian c (full storage, destroyed) to a real
+// symmetric tridiagonal (d, e) with e_k = |c'_{k+1,k}| (a diagonal unitary
+// scaling removes the phases).
+__device__ void cta_tridiag(cplx* c, int m, double* d, double* e, cplx* v, cplx* p) {
+  __shared__ double red[32];
+  __shared__ double s_tau, s_K, s_norm;
+  for (int k = 0; k < m - 2; ++k) {
+    // ||x||^2, x = c[k+1:, k]
+    double part = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) part += cabs2(c[i * m + k]);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+      double xn = sqrt(s);
+      cplx x0 = c[(k + 1) * m + k];
+      double ax0 = sqrt(cabs2(x0));
+      cplx ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
+      cplx alpha = cscale(ph, -xn);
+      d[k] = c[k * m + k].x;
+      e[k] = xn;
+      double vn2 = 2.0 * (s + xn * ax0);
+      s_tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+      s_norm = xn;
+      v[k + 1] = csub(x0, alpha);
+    }
+    __syncthreads();
+    for (int i = k + 2 + threadIdx.x; i < m; i += blockDim.x) v[i] = c[i * m + k];
+    __syncthreads();
+    const double tau = s_tau;
+    if (tau != 0.0) {
+      for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        cplx s = cmk(0.0, 0.0);
+        for (int j = k + 1; j < m; ++j) s = cadd(s, cmul(c[i * m + j], v[j]));
+        p[i] = cscale(s, tau);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double K = 0.0;   // (tau/2) v^H p, real for Hermitian c
+        for (int i = k + 1; i < m; ++i) K += v[i].x * p[i].x + v[i].y * p[i].y;
+        s_K = 0.5 * tau * K;
+      }
+      __syncthreads();
+      const double K = s_K;
+      for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) p[i] = csub(p[i], cscale(v[i], K));
+      __syncthreads();
+      const int nt = m - k - 1;
+      for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
+        int i = k + 1 + it / nt, j = k + 1 + it % nt;
+        // c -= v w^H + w v^H   (w stored in p)
+        cplx u = cadd(cmulc(v[i], p[j]), cmulc(p[i], v[j]));
+        c[i * m + j] = csub(c[i * m + j], u);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (m >= 2) {
+      d[m - 2] = c[(m - 2) * m + (m - 2)].x;
+      d[m - 1] = c[(m - 1) * m + (m - 1)].x;
+      e[m - 2] = sqrt(cabs2(c[(m - 1) * m + (m - 2)]));
+    } else {
+      d[0] = c[0].x;
+    }
+  }
+  __syncthreads();
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
+__device__ inline int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += (q < 0.0);
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0);
+  }
+  return cnt;
+}
+
+// idx-th (0-based, ascending) eigenvalue by bisection.
+__device__ double tridiag_eig_bisect(const double* d, const double* e, int m, int idx) {
+  double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? e[i - 1] : 0.0) + (i < m - 1 ? e[i] : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < m - 1) emax = fmax(emax, e[i]);
+  }
+  double tnorm = fmax(fabs(lo), fabs(hi));
+  double pivmin = DBL_MIN * fmax(1.0, emax * emax);
+  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
+  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__device__ inline cplx twiddle(long long num, int M) {   // exp(-2 pi i num / M)
+  double s, c;
+  sincospi(-2.0 * (double)(num % M) / (double)M, &s, &c);
+  return cmk(c, s);
+}
+
+__global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* __restrict__ tasks) {
+  extern __shared__ cplx sm[];
+  const FBlockTask F = tasks[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= F.nj) return;
+  const ProbDev& P = probs[F.prob];
+  const int m0 = P.m0, np = m0 * m0;
+  cplx* H = sm;
+  cplx* S = sm + np;
+  cplx* v = S + np;
+  cplx* pv = v + MAXM0;
+  double* dd = (double*)(pv + MAXM0);
+  double* ee = dd + MAXM0;
+
+  if (F.source == FROM_FACTORS) {
+    const int j3 = j % F.L[2], j2 = (j / F.L[2]) % F.L[1], j1 = j / (F.L[1] * F.L[2]);
+    const int nfe = P.nF * np;
+    const cplx* x0 = F.Xh[0] + (size_t)j1 * nfe;
+    const cplx* x1 = F.Xh[1] + (size_t)j2 * nfe;
+    const cplx* x2 = F.Xh[2] + (size_t)j3 * nfe;
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      cplx s0 = x0[pr], s1 = x1[pr], s2 = x2[pr];
+      cplx a0 = x0[np + pr], a1 = x1[np + pr], a2 = x2[np + pr];
+      cplx s12 = cmul(s1, s2);
+      cplx hk = cadd(cmul(a0, s12), cmul(s0, cadd(cmul(a1, s2), cmul(s1, a2))));
+      hk = cscale(hk, 0.5);
+      cplx vv = cmk(0.0, 0.0);
+      for (int t = 0; t < P.T; ++t) {
+        double w = P.Z[t / P.R] * P.cq[t % P.R];
+        cplx pr3 = cmul(cmul(x0[(2 + t) * np + pr], x1[(2 + t) * np + pr]), x2[(2 + t) * np + pr]);
+        vv = cadd(vv, cscale(pr3, w));
+      }
+      H[pr] = csub(hk, vv);
+      S[pr] = cmul(s0, s12);
+    }
+  } else {
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      int mu = pr / m0, nu = pr % m0, tr = nu * m0 + mu;
+      cplx h = cmk(F.TH[pr], 0.0), s = cmk(F.TS[pr], 0.0);
+      for (int dd2 = 1; dd2 <= F.D; ++dd2) {
+        cplx w = twiddle((long long)j * dd2, F.M);
+        const double* th = F.TH + (size_t)dd2 * np;
+        const double* ts = F.TS + (size_t)dd2 * np;
+        // w T_d[mu][nu] + conj(w) T_d[nu][mu]
+        h = cadd(h, cmk(w.x * (th[pr] + th[tr]), w.y * (th[pr] - th[tr])));
+        s = cadd(s, cmk(w.x * (ts[pr] + ts[tr]), w.y * (ts[pr] - ts[tr])));
+      }
+      H[pr] = h;
+      S[pr] = s;
+    }
+  }
+  __syncthreads();
+  // exact Hermitian symmetrisation of the formed pair (removes rounding asymmetry)
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    int mu = pr / m0, nu = pr % m0;
+    if (mu < nu) {
+      cplx h1 = H[pr], h2 = H[nu * m0 + mu], s1 = S[pr], s2 = S[nu * m0 + mu];
+      cplx hm = cscale(cadd(h1, cconj(h2)), 0.5), sm2 = cscale(cadd(s1, cconj(s2)), 0.5);
+      H[pr] = hm; H[nu * m0 + mu] = cconj(hm);
+      S[pr] = sm2; S[nu * m0 + mu] = cconj(sm2);
+    } else if (mu == nu) {
+      H[pr].y = 0.0; S[pr].y = 0.0;
+    }
+  }
+  __syncthreads();
+  if (F.outH)
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      F.outH[(size_t)j * np + pr] = H[pr];
+      F.outS[(size_t)j * np + pr] = S[pr];
+    }
+  if (F.want == 0) return;
+  __syncthreads();
+  bool ok = cta_cholesky(S, m0);
+  if (!ok && threadIdx.x == 0 && F.fail) *F.fail = 1;
+  cta_reduce(H, S, m0);
+  cta_tridiag(H, m0, dd, ee, v, pv);
+  if (F.want == 1) {
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+      F.ev[(size_t)j * m0 + i] = tridiag_eig_bisect(dd, ee, m0, i);
+      if (F.blk) F.blk[(size_t)j * m0 + i] = j;
+    }
+  } else if (threadIdx.x == 0) {
+    F.ev[j] = tridiag_eig_bisect(dd, ee, m0, 0);
+  }
+}
+
+// ---- preconditioner ----
+
+
+__global__ void k_sigma(const PrecTask* __restrict__ tasks) {
+  const PrecTask T = tasks[blockIdx.x];
+  __shared__ double red[256];
+  double mn = DBL_MAX;
+  for (int j = threadIdx.x; j < T.M; j += blockDim.x) mn = fmin(mn, T.emin[j]);
+  red[threadIdx.x] = mn;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *T.sigma = red[0] - T.rel_shift * (1.0 + fabs(red[0]));
+}
+
+__global__ void k_precond(const ProbDev* __restrict__ probs, const PrecTask* __restrict__ tasks) {
+  extern __shared__ cplx sm[];
+  const PrecTask T = tasks[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= T.M) return;
+  const int m0 = probs[T.prob].m0, np = m0 * m0;
+  const double sg = *T.sigma;
+  cplx* A = sm;
+  cplx* Li = sm + np;
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    cplx h = T.CH[(size_t)j * np + pr], s = T.CS[(size_t)j * np + pr];
+    A[pr] = csub(h, cscale(s, sg));
+  }
+  __syncthreads();
+  cta_cholesky(A, m0);
+  // Li = L^-1 (lower), thread per column
+  for (int c = threadIdx.x; c < m0; c += blockDim.x) {
+    for (int i = 0; i < m0; ++i) {
+      cplx s = cmk(i == c ? 1.0 : 0.0, 0.0);
+      for (int q = c; q < i; ++q) s = csub(s, cmul(A[i * m0 + q], Li[q * m0 + c]));
+      Li[i * m0 + c] = (i < c) ? cmk(0.0, 0.0) : cscale(s, 1.0 / A[i * m0 + i].x);
+    }
+  }
+  __syncthreads();
+  // K = L^-H L^-1 : K[a][b] = sum_i conj(Li[i][a]) Li[i][b]
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    int a = pr / m0, b = pr % m0;
+    cplx s = cmk(0.0, 0.0);
+    for (int i = max(a, b); i < m0; ++i) s = cadd(s, cmulc(Li[i * m0 + b], Li[i * m0 + a]));
+    T.K[(size_t)j * np + pr] = s;
+  }
+}
+
+// ---- sorting of (value, index) pairs ----
+
+
+__global__ void k_sort_small(const SortTask* __restrict__ tasks) {
+  extern __shared__ double ssv[];
+  const SortTask T = tasks[blockIdx.x];
+  int n2 = 1;
+  while (n2 < T.n) n2 <<= 1;
+  double* sv = ssv;
+  int* si = (int*)(ssv + n2);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    sv[i] = (i < T.n) ? T.v[i] : DBL_MAX;
+    si[i] = (i < T.n && T.idx) ? T.idx[i] : i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        int ij = i ^ jj;
+        if (ij > i) {
+          bool up = ((i & k) == 0);
+          if ((sv[i] > sv[ij]) == up) {
+            double tv = sv[i]; sv[i] = sv[ij]; sv[ij] = tv;
+            int ti = si[i]; si[i] = si[ij]; si[ij] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < T.n; i += blockDim.x) {
+    T.v[i] = sv[i];
+    if (T.idx) T.idx[i] = si[i];
+  }
+}
+
+// one compare-exchange pass of a global bitonic network (n2 a power of 2;
+// v/idx padded to n2 with +inf)
+__global__ void k_bitonic_pass(double* v, int* idx, int n2, int k, int jj) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+    int ij = i ^ jj;
+    if (ij > i) {
+      bool up = ((i & k) == 0);
+      if ((v[i] > v[ij]) == up) {
+        double tv = v[i]; v[i] = v[ij]; v[ij] = tv;
+        int ti = idx[i]; idx[i] = idx[ij]; idx[ij] = ti;
+      }
+    }
+  }
+}
+
+__global__ void k_pad_copy(const double* v, const int* idx, int n, double* pv, int* pidx, int n2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+    pv[i] = (i < n) ? v[i] : DBL_MAX;
+    pidx[i] = (i < n) ? (idx ? idx[i] : i) : 0x7fffffff;
+  }
+}
+
+__global__ void k_unpad_copy(const double* pv, const int* pidx, int n, double* v, int* idx) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    v[i] = pv[i];
+    if (idx) idx[i] = pidx[i];
+  }
+}
+
+// ---- launchers ----
+size_t fblocks_smem(int m0) {
+  return (size_t)(2 * m0 * m0 + 2 * MAXM0) * sizeof(cplx) + 2 * MAXM0 * sizeof(double);
+}
+
+void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,
+                    cudaStream_t st) {
+  if (!ntask || !maxnj) return;
+  size_t sm = fblocks_smem(maxm0);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_fblocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_fblocks<<<dim3(maxnj, ntask), 128, sm, st>>>(probs, tasks);
+}
+
+void launch_precond(const ProbDev* probs, const PrecTask* tasks, int ntask, int maxM, int maxm0,
+                    cudaStream_t st) {
+  if (!ntask) return;
+  k_sigma<<<ntask, 256, 0, st>>>(tasks);
+  size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_precond, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_precond<<<dim3(maxM, ntask), 128, sm, st>>>(probs, tasks);
+}
+
+void launch_sort_small(const SortTask* tasks, int ntask, int maxn, cudaStream_t st) {
+  if (!ntask) return;
+  int n2 = 1;
+  while (n2 < maxn) n2 <<= 1;
+  size_t sm = (size_t)n2 * (sizeof(double) + sizeof(int));
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_sort_small<<<ntask, 512, sm, st>>>(tasks);
+}
+
+// sort n pairs in place with scratch (pv, pidx of length n2 = next pow2)
+void launch_sort_global(double* v, int* idx, int n, double* pv, int* pidx, cudaStream_t st) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  int grid = (n2 + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_pad_copy<<<grid, 256, 0, st>>>(v, idx, n, pv, pidx, n2);
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) k_bitonic_pass<<<grid, 256, 0, st>>>(pv, pidx, n2, k, jj);
+  k_unpad_copy<<<grid, 256, 0, st>>>(pv, pidx, n, v, idx);
+}
+
+}  // namespace fock

@@ -1,0 +1,185 @@
+// Stage (c): the block-Toeplitz / block-circulant matvec by FFT over the
+// lattice (block) index (Remark 3.2, Prop. A.1), plus the block-sparse
+// boundary / defect perturbation E (Sec. 2.3 items (A), (B)).
+//
+//   y = C x (first L blocks) + E x,  C = sum_c pi^c (x) C_c of size M >= L + D,
+//   xt_j = sum_{k<L} w^{jk} x_k,  yt_j = Chat_j xt_j,  y_k = (1/M) sum_j w^{-jk} yt_j,
+//   w = exp(-2 pi i / M).
+//
+//  k_twiddle  table exp(-2 pi i t / M)
+//  k_fft      batched mixed-radix Stockham FFT of the columns (one CTA holds
+//             a chunk of columns of one problem in shared memory)
+//  k_blockmul per Fourier index: m0 x m0 complex block times m0 x nvec
+//  k_eapply   y += E x over the block rows that carry boundary/defect blocks
+#include "common.cuh"
+
+namespace fock {
+
+__global__ void k_twiddle(CircDev* circs, int n) {
+  const CircDev c = circs[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < c.M; t += gridDim.x * blockDim.x) {
+    double s, co;
+    sincospi(-2.0 * (double)t / (double)c.M, &s, &co);
+    c.tw[t] = cmk(co, s);
+  }
+}
+
+
+
+// dir = +1 forward (w), -1 inverse (conj w).
+template <int DIR>
+__global__ void k_fft(const FftTask* __restrict__ tasks) {
+  extern __shared__ cplx sm[];
+  const FftTask T = tasks[blockIdx.y];
+  const CircDev C = *T.circ;
+  const int M = C.M, CC = T.cc;
+  const int ncols = T.m0 * T.ncol;
+  const int c0 = blockIdx.x * CC;
+  if (c0 >= ncols) return;
+  const int ncc = min(CC, ncols - c0);
+  cplx* A = sm;
+  cplx* B = sm + (size_t)M * CC;
+  // load
+  for (int it = threadIdx.x; it < M * CC; it += blockDim.x) {
+    int k = it / CC, cc = it % CC;
+    cplx val = cmk(0.0, 0.0);
+    if (cc < ncc) {
+      int c = c0 + cc;
+      if (DIR > 0) {
+        if (k < T.L) {
+          int mu = c % T.m0, v = c / T.m0;
+          val = cmk(T.x[(size_t)(k * T.m0 + mu) + (size_t)T.ldx * v], 0.0);
+        }
+      } else {
+        val = T.X[(size_t)k * ncols + c];
+      }
+    }
+    A[it] = val;
+  }
+  __syncthreads();
+  int Ps = 1;
+  for (int s = 0; s < C.nfac; ++s) {
+    const int r = C.fac[s];
+    const int Pn = Ps * r, m = M / Pn;
+    const int nb = M / r;
+    for (int it = threadIdx.x; it < nb * CC; it += blockDim.x) {
+      int b = it / CC, cc = it % CC;
+      int kp = b / Ps, j = b % Ps;
+      for (int p = 0; p < r; ++p) {
+        cplx acc = cmk(0.0, 0.0);
+        for (int q = 0; q < r; ++q) {
+          cplx a = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
+          long long e1 = ((long long)q * j * m) % M;           // w_{Pn}^{q j}
+          long long e2 = ((long long)q * p * (M / r)) % M;     // w_r^{q p}
+          cplx w = C.tw[(e1 + e2) % M];
+          if (DIR < 0) w.y = -w.y;
+          acc = cadd(acc, cmul(w, a));
+        }
+        B[(size_t)(kp * Pn + j + Ps * p) * CC + cc] = acc;
+      }
+    }
+    __syncthreads();
+    cplx* t = A; A = B; B = t;
+    Ps = Pn;
+  }
+  // store
+  if (DIR > 0) {
+    for (int it = threadIdx.x; it < M * CC; it += blockDim.x) {
+      int k = it / CC, cc = it % CC;
+      if (cc < ncc) T.X[(size_t)k * ncols + c0 + cc] = A[it];
+    }
+  } else {
+    const double inv = 1.0 / (double)M;
+    for (int it = threadIdx.x; it < T.L * CC; it += blockDim.x) {
+      int k = it / CC, cc = it % CC;
+      if (cc < ncc) {
+        int c = c0 + cc, mu = c % T.m0, v = c / T.m0;
+        size_t o = (size_t)(k * T.m0 + mu) + (size_t)T.ldy * v;
+        double val = A[it].x * inv;
+        T.y[o] = (T.beta == 0.0) ? val : T.beta * T.y[o] + val;
+      }
+    }
+  }
+}
+
+
+
+__global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
+  extern __shared__ cplx sb[];
+  const BmulTask T = tasks[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= T.M) return;
+  const int m0 = T.m0, np = m0 * m0, nc = m0 * T.ncol;
+  cplx* b1 = sb;
+  cplx* b2 = sb + np;
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    b1[pr] = T.B1[(size_t)j * np + pr];
+    if (T.B2) b2[pr] = T.B2[(size_t)j * np + pr];
+  }
+  __syncthreads();
+  const cplx* xj = T.X + (size_t)j * nc;
+  for (int it = threadIdx.x; it < nc; it += blockDim.x) {
+    int mu = it % m0, v = it / m0;
+    cplx a1 = cmk(0.0, 0.0), a2 = cmk(0.0, 0.0);
+    for (int nu = 0; nu < m0; ++nu) {
+      cplx xv = xj[v * m0 + nu];
+      a1 = cadd(a1, cmul(b1[mu * m0 + nu], xv));
+      if (T.B2) a2 = cadd(a2, cmul(b2[mu * m0 + nu], xv));
+    }
+    T.Y1[(size_t)j * nc + it] = a1;
+    if (T.B2) T.Y2[(size_t)j * nc + it] = a2;
+  }
+}
+
+
+
+__global__ void k_eapply(const EApplyTask* __restrict__ tasks) {
+  const EApplyTask T = tasks[blockIdx.y];
+  const int m0 = T.m0, np = m0 * m0;
+  const int tot = T.nrows * m0 * T.ncol;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
+    int mu = it % m0, rest = it / m0;
+    int ri = rest % T.nrows, v = rest / T.nrows;
+    int row = T.rows[ri];
+    double acc = 0.0;
+    for (int e = T.rowptr[ri]; e < T.rowptr[ri + 1]; ++e) {
+      const double* Eb = T.vals + (size_t)e * np + mu * m0;
+      const double* xv = T.x + (size_t)T.cols[e] * m0 + (size_t)T.ldx * v;
+      for (int nu = 0; nu < m0; ++nu) acc += Eb[nu] * xv[nu];
+    }
+    T.y[(size_t)row * m0 + mu + (size_t)T.ldy * v] += acc;
+  }
+}
+
+// ---- launchers ----
+void launch_twiddles(CircDev* circs, int n, cudaStream_t st) {
+  if (n) k_twiddle<<<dim3(4, n), 256, 0, st>>>(circs, n);
+}
+
+size_t fft_smem(int M, int cc) { return (size_t)2 * M * cc * sizeof(cplx); }
+
+void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
+                cudaStream_t st) {
+  if (!ntask) return;
+  size_t sm = fft_smem(maxM, cc);
+  if (dir > 0) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft<1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+  } else {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft<-1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+  }
+}
+
+void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st) {
+  if (!ntask) return;
+  size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_blockmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_blockmul<<<dim3(maxM, ntask), 256, sm, st>>>(tasks);
+}
+
+void launch_eapply(const EApplyTask* tasks, int ntask, cudaStream_t st) {
+  if (ntask) k_eapply<<<dim3(16, ntask), 256, 0, st>>>(tasks);
+}
+
+}  // namespace fock

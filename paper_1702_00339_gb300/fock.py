@@ -1,0 +1,375 @@
+"""Python binding of libfock (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels behind the C ABI declared
+in include/fock.h; this module converts lattice_inputs.Problem objects and
+numpy / torch buffers to the ABI's plain structs and pointers.  It fails
+loudly when the library is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_PKG, "libfock.so")
+
+FOCK_OK, FOCK_EINVAL, FOCK_ENOMEM, FOCK_ENOCONV = 0, -1, -2, -3
+FOCK_ETIMEOUT, FOCK_EAGAIN, FOCK_ECUDA = -4, -5, -6
+FOCK_OP_H, FOCK_OP_S = 0, 1
+_NAMES = {0: "FOCK_OK", -1: "FOCK_EINVAL", -2: "FOCK_ENOMEM", -3: "FOCK_ENOCONV",
+          -4: "FOCK_ETIMEOUT", -5: "FOCK_EAGAIN", -6: "FOCK_ECUDA"}
+
+
+class FockError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class c_defect(C.Structure):
+    _fields_ = [("cell", C.c_int * 3), ("nucleus", C.c_int), ("newZ", C.c_double)]
+
+
+class c_problem(C.Structure):
+    _fields_ = [("L", C.c_int * 3), ("periodic", C.c_int * 3), ("N", C.c_int * 3), ("n0", C.c_int),
+                ("b0", C.c_double), ("M0", C.c_int), ("Z", C.POINTER(C.c_double)),
+                ("frac", C.POINTER(C.c_double)), ("m0", C.c_int), ("exps", C.POINTER(C.c_double)),
+                ("ang", C.POINTER(C.c_int)), ("centre", C.POINTER(C.c_int)), ("R", C.c_int),
+                ("sinc_t", C.POINTER(C.c_double)), ("sinc_c", C.POINTER(C.c_double)),
+                ("eps_support", C.c_double), ("ndef", C.c_int),
+                ("defects", C.POINTER(c_defect)), ("k_eig", C.c_int), ("precision", C.c_int)]
+
+
+class c_output(C.Structure):
+    _fields_ = [("evals", C.c_void_p), ("block_of", C.c_void_p), ("n_evals", C.c_int),
+                ("iters", C.c_int), ("resid", C.c_double), ("status", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfock.so (built in-tree by paper_1702_00339_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIBPATH):
+            raise ImportError(f"libfock.so not built at {_LIBPATH}; run paper_1702_00339_gb300.build.build()")
+        L = C.CDLL(_LIBPATH)
+        P = C.POINTER
+        L.fock_create.argtypes = [P(C.c_void_p), C.c_int, C.c_size_t, C.c_void_p]
+        L.fock_destroy.argtypes = [C.c_void_p]
+        L.fock_destroy.restype = None
+        L.fock_last_error.argtypes = [C.c_void_p]
+        L.fock_last_error.restype = C.c_char_p
+        L.fock_synchronize.argtypes = [C.c_void_p]
+        L.fock_sinc_table.argtypes = [C.c_int, C.c_double, C.c_double, P(C.c_double), P(C.c_double),
+                                      P(C.c_double)]
+        L.fock_default_range.argtypes = [P(c_problem), P(C.c_double), P(C.c_double)]
+        L.fock_solve.argtypes = [C.c_void_p, C.c_int, P(c_problem), P(c_output), C.c_int]
+        L.fock_assemble.argtypes = [C.c_void_p, P(c_problem), P(C.c_void_p)]
+        L.fock_blocks_free.argtypes = [C.c_void_p]
+        L.fock_blocks_free.restype = None
+        L.fock_blocks_info.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int)]
+        L.fock_blocks_copy_generators.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double),
+                                                  P(C.c_double), P(C.c_double), P(C.c_int)]
+        L.fock_circulant_eig.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_int)]
+        L.fock_toeplitz_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_int, C.c_int]
+        L.fock_box_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, P(C.c_double),
+                                   P(C.c_double), P(C.c_int)]
+        L.fock_plan_create.argtypes = [C.c_void_p, C.c_int, P(c_problem), P(C.c_void_p)]
+        L.fock_plan_execute.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.fock_plan_outputs.argtypes = [C.c_void_p, P(c_output), C.c_int]
+        L.fock_plan_info.argtypes = [C.c_void_p, P(C.c_size_t), P(C.c_size_t), P(C.c_size_t)]
+        L.fock_plan_free.argtypes = [C.c_void_p]
+        L.fock_plan_free.restype = None
+        L.fock_profile_enable.argtypes = [C.c_void_p, C.c_int]
+        L.fock_profile_reset.argtypes = [C.c_void_p]
+        L.fock_profile_read.argtypes = [C.c_void_p, C.c_int, C.c_char_p, P(C.c_int), P(C.c_double)]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class _Marshal:
+    """Keeps the numpy arrays behind one c_problem alive."""
+
+    def __init__(self, p):
+        self.keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            self.keep.append(a)
+            return a
+
+        s = c_problem()
+        s.L[:] = [int(v) for v in p.L]
+        s.periodic[:] = [int(v) for v in p.periodic]
+        s.N[:] = [int(v) for v in p.N]
+        s.n0 = int(p.n0)
+        s.b0 = float(p.b0)
+        s.M0 = int(len(p.Z))
+        s.Z = _dp(arr(p.Z, np.float64))
+        s.frac = _dp(arr(np.asarray(p.frac, float).reshape(-1), np.float64))
+        s.m0 = int(len(p.exps))
+        s.exps = _dp(arr(p.exps, np.float64))
+        s.ang = _ip(arr(p.ang, np.int32))
+        s.centre = _ip(arr(p.centre, np.int32))
+        s.R = int(p.R)
+        if p.sinc_t is not None:
+            s.sinc_t = _dp(arr(p.sinc_t, np.float64))
+            s.sinc_c = _dp(arr(p.sinc_c, np.float64))
+        s.eps_support = float(p.eps_support)
+        s.ndef = len(p.defects)
+        if p.defects:
+            d = (c_defect * len(p.defects))()
+            for i, x in enumerate(p.defects):
+                d[i].cell[:] = [int(v) for v in x.cell]
+                d[i].nucleus = int(x.nucleus)
+                d[i].newZ = float(x.newZ)
+            self.keep.append(d)
+            s.defects = C.cast(d, C.POINTER(c_defect))
+        s.k_eig = int(p.k_eig)
+        s.precision = 0
+        self.s = s
+
+
+def n_evals(p):
+    ncell = int(np.prod(p.L))
+    if p.is_box:
+        return int(p.k_eig or 16)
+    return ncell * len(p.exps)
+
+
+def sinc_table(R, zmin, zmax):
+    t = np.zeros(R)
+    c = np.zeros(R)
+    e = C.c_double()
+    rc = lib().fock_sinc_table(int(R), float(zmin), float(zmax), _dp(t), _dp(c), C.byref(e))
+    if rc:
+        raise FockError(rc, "fock_sinc_table")
+    return t, c, e.value
+
+
+def default_range(p):
+    m = _Marshal(p)
+    a, b = C.c_double(), C.c_double()
+    rc = lib().fock_default_range(C.byref(m.s), C.byref(a), C.byref(b))
+    if rc:
+        raise FockError(rc, "fock_default_range")
+    return a.value, b.value
+
+
+class Context:
+    """A libfock context on one CUDA device (owns device memory and a stream)."""
+
+    def __init__(self, device=0, budget_bytes=0, stream=None):
+        import weakref
+        self._children = weakref.WeakSet()   # handles freed before the context
+        self.h = C.c_void_p()
+        rc = lib().fock_create(C.byref(self.h), int(device), C.c_size_t(budget_bytes),
+                               C.c_void_p(stream) if stream else None)
+        if rc:
+            raise FockError(rc, "fock_create")
+
+    def close(self):
+        if self.h:
+            for c in list(self._children):
+                c.close()
+            lib().fock_destroy(self.h)
+            self.h = C.c_void_p()
+
+    __del__ = close
+
+    def _check(self, rc, what):
+        if rc:
+            raise FockError(rc, f"{what}: {lib().fock_last_error(self.h).decode()}")
+
+    def synchronize(self):
+        self._check(lib().fock_synchronize(self.h), "fock_synchronize")
+
+    def solve(self, problems, outputs=None, check=True):
+        """Batched solve.  Host outputs (numpy) unless `outputs` gives, per
+        problem, (evals_ptr, block_of_ptr_or_0) device pointers."""
+        n = len(problems)
+        ms = [_Marshal(p) for p in problems]
+        arr = (c_problem * n)(*[m.s for m in ms])
+        outs = (c_output * n)()
+        host = []
+        for i, p in enumerate(problems):
+            if outputs is None:
+                ev = np.zeros(n_evals(p))
+                blk = np.zeros(n_evals(p), np.int32)
+                outs[i].evals = ev.ctypes.data
+                outs[i].block_of = blk.ctypes.data if not p.is_box else None
+                host.append((ev, blk))
+            else:
+                outs[i].evals, outs[i].block_of = outputs[i]
+        rc = lib().fock_solve(self.h, n, arr, outs, 0 if outputs is None else 1)
+        if rc and check:
+            self._check(rc, "fock_solve")
+        res = []
+        for i, p in enumerate(problems):
+            r = {"n_evals": outs[i].n_evals, "iters": outs[i].iters, "resid": outs[i].resid,
+                 "status": outs[i].status}
+            if outputs is None:
+                r["evals"] = host[i][0]
+                r["block_of"] = None if p.is_box else host[i][1]
+            res.append(r)
+        return res
+
+    def assemble(self, p):
+        return Blocks(self, p)
+
+    def plan(self, problems):
+        return Plan(self, problems)
+
+    # ---- kernel timers ----
+    def profile(self, on=True):
+        self._check(lib().fock_profile_enable(self.h, 1 if on else 0), "fock_profile_enable")
+
+    def profile_reset(self):
+        self._check(lib().fock_profile_reset(self.h), "fock_profile_reset")
+
+    def profile_read(self, cap=64):
+        names = C.create_string_buffer(32 * cap)
+        nl = (C.c_int * cap)()
+        ms = (C.c_double * cap)()
+        n = lib().fock_profile_read(self.h, cap, names, nl, ms)
+        if n < 0:
+            self._check(n, "fock_profile_read")
+        out = {}
+        for i in range(n):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(nl[i]), float(ms[i]))
+        return out
+
+
+class Blocks:
+    """Device-resident assembled operator of one problem (fock_assemble)."""
+
+    def __init__(self, ctx, p):
+        self.ctx = ctx
+        self.p = p
+        self.h = C.c_void_p()
+        m = _Marshal(p)
+        ctx._check(lib().fock_assemble(ctx.h, C.byref(m.s), C.byref(self.h)), "fock_assemble")
+        ctx._children.add(self)
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib().fock_blocks_info(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d))
+        self.Nb, self.ngen, self.nbound, self.mcirc = a.value, b.value, c.value, d.value
+
+    def close(self):
+        if self.h and self.ctx.h:
+            lib().fock_blocks_free(self.h)
+        self.h = C.c_void_p()
+
+    __del__ = close
+
+    def generators(self):
+        m0 = len(self.p.exps)
+        H = np.zeros((self.ngen, m0, m0))
+        S = np.zeros((self.ngen, m0, m0))
+        nb = max(self.nbound, 1)
+        EH = np.zeros((nb, m0, m0))
+        ES = np.zeros((nb, m0, m0))
+        rc_ = np.zeros((nb, 2), np.int32)
+        self.ctx._check(lib().fock_blocks_copy_generators(self.h, _dp(H), _dp(S), _dp(EH), _dp(ES),
+                                                          _ip(rc_)), "fock_blocks_copy_generators")
+        return H, S, EH[:self.nbound], ES[:self.nbound], rc_[:self.nbound]
+
+    def circulant_eig(self):
+        n = self.Nb
+        ev = np.zeros(n)
+        blk = np.zeros(n, np.int32)
+        self.ctx._check(lib().fock_circulant_eig(self.ctx.h, self.h, _dp(ev), _ip(blk)),
+                        "fock_circulant_eig")
+        return ev, blk
+
+    def matvec(self, x, which=FOCK_OP_H):
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.Nb, -1))
+        y = np.zeros_like(x, order="F")
+        self.ctx._check(lib().fock_toeplitz_matvec(self.ctx.h, self.h, int(which), x.ctypes.data,
+                                                   y.ctypes.data, x.shape[1], 0),
+                        "fock_toeplitz_matvec")
+        return y
+
+    def matvec_device(self, x_ptr, y_ptr, nvec, which=FOCK_OP_H):
+        self.ctx._check(lib().fock_toeplitz_matvec(self.ctx.h, self.h, int(which), x_ptr, y_ptr,
+                                                   int(nvec), 1), "fock_toeplitz_matvec")
+
+    def box_eig(self, k, tol=1e-10, maxit=400, vectors=False):
+        ev = np.zeros(k)
+        V = np.zeros((self.Nb, k), order="F") if vectors else None
+        it = C.c_int()
+        rc = lib().fock_box_eig(self.ctx.h, self.h, int(k), float(tol), int(maxit), _dp(ev),
+                                _dp(V) if vectors else None, C.byref(it))
+        if rc and rc != FOCK_ENOCONV:
+            self.ctx._check(rc, "fock_box_eig")
+        return ev, V, it.value, rc
+
+
+class Plan:
+    """Device-resident batch (fock_plan_*): inputs uploaded once, executed
+    any number of times; results copied out on request."""
+
+    def __init__(self, ctx, problems):
+        self.ctx = ctx
+        self.problems = list(problems)
+        self.h = C.c_void_p()
+        ms = [_Marshal(p) for p in self.problems]
+        arr = (c_problem * len(ms))(*[m.s for m in ms])
+        ctx._check(lib().fock_plan_create(ctx.h, len(ms), arr, C.byref(self.h)), "fock_plan_create")
+        ctx._children.add(self)
+        a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        lib().fock_plan_info(self.h, C.byref(a), C.byref(b), C.byref(c))
+        self.upload_bytes, self.device_bytes, self.n_evals = a.value, b.value, c.value
+
+    def execute(self, tol=1e-10, maxit=400):
+        rc = lib().fock_plan_execute(self.h, float(tol), int(maxit))
+        if rc:
+            self.ctx._check(rc, "fock_plan_execute")
+
+    def outputs(self, device_ptrs=None, check=True):
+        """Host copies (list of dicts) or, with device_ptrs = [(evals_ptr,
+        block_of_ptr_or_0), ...], device-to-device copies."""
+        n = len(self.problems)
+        outs = (c_output * n)()
+        host = []
+        for i, p in enumerate(self.problems):
+            if device_ptrs is None:
+                ev = np.zeros(n_evals(p))
+                blk = np.zeros(n_evals(p), np.int32)
+                outs[i].evals = ev.ctypes.data
+                outs[i].block_of = blk.ctypes.data if not p.is_box else None
+                host.append((ev, blk))
+            else:
+                outs[i].evals, outs[i].block_of = device_ptrs[i]
+        rc = lib().fock_plan_outputs(self.h, outs, 0 if device_ptrs is None else 1)
+        if rc and check:
+            self.ctx._check(rc, "fock_plan_outputs")
+        res = []
+        for i, p in enumerate(self.problems):
+            r = {"n_evals": outs[i].n_evals, "iters": outs[i].iters, "resid": outs[i].resid,
+                 "status": outs[i].status}
+            if device_ptrs is None:
+                r["evals"] = host[i][0]
+                r["block_of"] = None if p.is_box else host[i][1]
+            res.append(r)
+        return res
+
+    def close(self):
+        if self.h and self.ctx.h:
+            lib().fock_plan_free(self.h)
+        self.h = C.c_void_p()
+
+    __del__ = close
