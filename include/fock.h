@@ -157,6 +157,23 @@ int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* 
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
                          double* y, int nvec, int on_device);
 
+/* Same product as fock_toeplitz_matvec (device x, y only), for callers that
+ * cannot allocate device memory: code being captured into a CUDA graph,
+ * real-time loops that forbid allocator calls after start-up, hosts whose
+ * own allocator owns the device.  The paper has no counterpart; it is a
+ * deployment variant.  All work arrays and launch descriptors live in one
+ * fixed device array of FOCK_NOALLOC_SCRATCH_BYTES per device, held until
+ * the process exits; requires 2*M*m0*nvec*16 + 4096 <= that size (M =
+ * circulant size from fock_blocks_info), else FOCK_EINVAL with a message.
+ * The first call on a device looks the array's address up (call it before
+ * any stream capture).  Calls share the array: two calls whose work
+ * overlaps on the GPU race; the array keeps the last call's contents and
+ * every part a call reads is written earlier in the same call.  Synchronous
+ * on the context's stream. */
+#define FOCK_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fock_toeplitz_matvec_noalloc(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
+                                 double* y, int nvec);
+
 /* Lowest k eigenpairs of (H, S) by preconditioned block iteration
  * (Sec. 2.3, "structured iteration on subspace"; LOBPCG with the embedding's
  * shifted inverse as preconditioner).  evals[k] host; evecs[N_b x k]

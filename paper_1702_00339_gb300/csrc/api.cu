@@ -1099,6 +1099,26 @@ struct fock_blocks {
   Batch B;
 };
 
+namespace fock {
+
+int blocks_matvec_view(const fock_blocks* b, MatvecView* v) {
+  if (!b || !v) return FOCK_EINVAL;
+  const Batch& B = b->B;
+  if (B.hp[0].kind != 1) return FOCK_EINVAL;
+  const Batch::PerProb& Q = B.pp[0];
+  v->Lc = Q.Lc; v->m0 = B.hp[0].m0; v->M = Q.M; v->nE = Q.nE; v->nErows = Q.nErows;
+  v->circ = B.d_circs + Q.circ;
+  v->CH = Q.CH; v->CS = Q.CS;
+  v->Erows = Q.Erows; v->Erowptr = Q.Erowptr; v->Ecols = Q.Ecols;
+  v->EH = Q.EH; v->ES = Q.ES;
+  v->stream = b->ctx->stream;
+  v->device = b->ctx->device;
+  return FOCK_OK;
+}
+
+void set_ctx_error(fock_ctx* c, const char* msg) { if (c) c->err = msg; }
+}  // namespace fock
+
 extern "C" {
 
 int fock_create(fock_ctx** out, int device, size_t hbm_budget_bytes, void* stream) {

@@ -205,4 +205,15 @@ struct BandTask {
   const int* active;
 };
 
+// Device pointers and sizes the matvec of an assembled box chain needs.
+struct MatvecView {
+  int Lc, m0, M, nE, nErows;
+  const CircDev* circ;
+  const cplx *CH, *CS;
+  const int *Erows, *Erowptr, *Ecols;
+  const double *EH, *ES;
+  cudaStream_t stream;
+  int device;
+};
+
 }  // namespace fock

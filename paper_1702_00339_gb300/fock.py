@@ -77,6 +77,8 @@ def lib():
         L.fock_circulant_eig.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_int)]
         L.fock_toeplitz_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_int, C.c_int]
+        L.fock_toeplitz_matvec_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                                   C.c_void_p, C.c_int]
         L.fock_box_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, P(C.c_double),
                                    P(C.c_double), P(C.c_int)]
         L.fock_plan_create.argtypes = [C.c_void_p, C.c_int, P(c_problem), P(C.c_void_p)]
@@ -306,6 +308,12 @@ class Blocks:
     def matvec_device(self, x_ptr, y_ptr, nvec, which=FOCK_OP_H):
         self.ctx._check(lib().fock_toeplitz_matvec(self.ctx.h, self.h, int(which), x_ptr, y_ptr,
                                                    int(nvec), 1), "fock_toeplitz_matvec")
+
+    def matvec_noalloc(self, x_ptr, y_ptr, nvec, which=FOCK_OP_H):
+        """Device x, y; no device allocation (fixed per-device scratch)."""
+        self.ctx._check(lib().fock_toeplitz_matvec_noalloc(self.ctx.h, self.h, int(which), x_ptr,
+                                                           y_ptr, int(nvec)),
+                        "fock_toeplitz_matvec_noalloc")
 
     def box_eig(self, k, tol=1e-10, maxit=400, vectors=False):
         ev = np.zeros(k)
