@@ -176,6 +176,12 @@ def fp64_flops_per_step(problems, outs):
             w["k_rr"] = w.get("k_rr", 0) + it * (2 * 9 * nb ** 3 + 4 * nb ** 3)
             w["k_gemm_tn"] = w.get("k_gemm_tn", 0) + it * (2 * 2 * n * nb * nb + 2 * 2 * n * k * k)
             w["k_gemm_nn"] = w.get("k_gemm_nn", 0) + it * (2 * n * nb * 2 * k + 6 * 2 * n * k * k)
+            # circulant-embedding FFTs: per iteration 9 k m0 column transforms (forward of W
+            # and [X|P], inverse of their H and S images), 12 k m0 at start; conventional
+            # 5 M log2 M flops per complex transform of length M
+            M = o.get("M")
+            if M:
+                w["k_fft"] = w.get("k_fft", 0) + (it * 9 + 12) * k * m0 * 5 * M * math.log2(M)
         else:
             ncell = int(np.prod(p.L))
             T = len(p.Z) * p.R
@@ -195,7 +201,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--cpu-pairs", type=int, default=8)
     ap.add_argument("--ref-pairs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -226,6 +232,8 @@ def main():
     for _ in range(args.warmup):
         plan.execute()
     outs = plan.outputs(check=False)
+    for i, o in enumerate(outs):
+        o["M"] = plan.sizes(i)[1]
     bad = [o["status"] for o in outs if o["status"] != 0]
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
     ctx.profile(True)

@@ -196,6 +196,9 @@ int fock_plan_outputs(fock_plan* plan, fock_output* outs, int outputs_on_device)
 /* bytes uploaded by fock_plan_create, bytes of device memory held, and the
  * number of eigenvalues the plan returns in total */
 int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_bytes, size_t* n_evals);
+/* Sizes of problem i of a plan: N_b, circulant size M (box: M >= L + D;
+ * periodic: |L|), generator reach D in cells (box) and boundary blocks. */
+int fock_plan_problem_sizes(const fock_plan* plan, int i, int* Nb, int* mcirc, int* D, int* nbound);
 void fock_plan_free(fock_plan* plan);
 
 /* ---- kernel timers (CUDA events recorded on the context's stream) ----

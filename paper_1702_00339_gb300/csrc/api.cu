@@ -36,7 +36,7 @@ namespace fock {
 void launch_vec1d(const ProbDev*, const SegDesc*, int, const SegDesc*, int, const DefTab*, int, cudaStream_t);
 void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream_t);
 void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
-void launch_axis_dft(const ProbDev*, const DftTask*, int, cudaStream_t);
+void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
 void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
 void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
 void launch_sort_small(const SortTask*, int, int, cudaStream_t);
@@ -296,7 +296,7 @@ struct Batch {
   SegDesc *d_gsegs = nullptr, *d_psegs = nullptr;
   std::vector<GramTask> gram; GramTask* d_gram = nullptr;
   std::vector<CombineTask> combT, combE; CombineTask *d_combT = nullptr, *d_combE = nullptr;
-  std::vector<DftTask> dft; DftTask* d_dft = nullptr;
+  std::vector<DftTask> dft; DftTask* d_dft = nullptr; int maxLdft = 1;
   std::vector<FBlockTask> fbp, fbs; FBlockTask *d_fbp = nullptr, *d_fbs = nullptr;
   int maxnj_p = 0, maxnj_s = 0, maxm0 = 1;
   std::vector<PrecTask> prec; PrecTask* d_prec = nullptr; int maxM = 0;
@@ -363,7 +363,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.gsegs.clear(); B.psegs.clear(); B.gram.clear(); B.combT.clear(); B.combE.clear();
   B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
-  B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0;
+  B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
   for (int i = 0; i < np; ++i) {
@@ -480,6 +480,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         t.offs = U.put(offs);
         t.X = Q.X[a]; t.Xh = Q.Xh[a];
         B.dft.push_back(t);
+        B.maxLdft = std::max(B.maxLdft, t.L);
       }
       Q.nev = ncell * H.m0;
       Q.ev = S.take<double>(Q.nev);
@@ -837,7 +838,7 @@ void run_periodic(fock_ctx* ctx, Batch& B) {
   cudaStream_t st = ctx->stream;
   if (B.fbp.empty()) return;
   zero_fail_flags(B, 0, st);
-  { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), st); }
+  { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
   { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st); }
   if (!B.sorts.empty()) { PROF("k_sort", 1); launch_sort_small(B.d_sorts, (int)B.sorts.size(), B.maxsort, st); }
   for (int i : B.bigsort) { PROF("k_sort_global", 1);
@@ -1208,6 +1209,18 @@ int fock_plan_info(const fock_plan* P, size_t* upload_bytes, size_t* device_byte
     for (const auto& Q : P->B.pp) n += Q.nev;
     *n_evals = n;
   }
+  return FOCK_OK;
+}
+
+int fock_plan_problem_sizes(const fock_plan* P, int i, int* Nb, int* mcirc, int* D, int* nbound) {
+  if (!P || i < 0 || i >= P->B.nprob) return FOCK_EINVAL;
+  const HostProb& H = P->B.hp[i];
+  const Batch::PerProb& Q = P->B.pp[i];
+  const int ncell = H.L[0] * H.L[1] * H.L[2];
+  if (Nb) *Nb = ncell * H.m0;
+  if (mcirc) *mcirc = H.kind == 1 ? Q.M : ncell;
+  if (D) *D = H.kind == 1 ? Q.D : 0;
+  if (nbound) *nbound = H.kind == 1 ? Q.nE : 0;
   return FOCK_OK;
 }
 

@@ -230,20 +230,25 @@ __global__ void k_combine(const ProbDev* __restrict__ probs, const CombineTask* 
 
 
 __global__ void k_axis_dft(const ProbDev* __restrict__ probs, const DftTask* __restrict__ tasks) {
+  extern __shared__ cplx tw[];   // exp(-2 pi i t / L), t < L
   const DftTask D = tasks[blockIdx.y];
   const ProbDev& P = probs[D.prob];
+  for (int t = threadIdx.x; t < D.L; t += blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)D.L, &s, &c);
+    tw[t] = cmk(c, s);
+  }
+  __syncthreads();
   const int per = P.nF * P.m0 * P.m0;
   const int tot = D.L * per;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
     int j = it / per, e = it % per;
     double re = 0.0, im = 0.0;
     for (int o = 0; o < D.noff; ++o) {
-      int jd = (int)(((long long)j * D.offs[o]) % D.L);
-      double s, c;
-      sincospi(-2.0 * (double)jd / (double)D.L, &s, &c);
+      cplx w = tw[(int)(((long long)j * D.offs[o]) % D.L)];
       double x = D.X[(size_t)o * per + e];
-      re += c * x;
-      im += s * x;
+      re += w.x * x;
+      im += w.y * x;
     }
     D.Xh[it] = cmk(re, im);
   }
@@ -268,8 +273,11 @@ void launch_combine(const ProbDev* probs, const CombineTask* tasks, int n, cudaS
   if (n) k_combine<<<n, 256, 0, st>>>(probs, tasks);
 }
 
-void launch_axis_dft(const ProbDev* probs, const DftTask* tasks, int n, cudaStream_t st) {
-  if (n) k_axis_dft<<<dim3(32, n), 256, 0, st>>>(probs, tasks);
+void launch_axis_dft(const ProbDev* probs, const DftTask* tasks, int n, int maxL, cudaStream_t st) {
+  if (!n) return;
+  size_t sm = (size_t)maxL * sizeof(cplx);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_axis_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_axis_dft<<<dim3(32, n), 256, sm, st>>>(probs, tasks);
 }
 
 }  // namespace fock

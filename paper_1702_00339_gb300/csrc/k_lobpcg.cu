@@ -226,29 +226,31 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
 }
 
 // Rayleigh-Ritz on the basis Y (Gram matrices GH = Y^T H Y, GS = Y^T S Y):
-// scale by D = diag(GS)^-1/2, eigendecompose D GS D = Q diag(s) Q^T and keep
-// the directions with s > kDropRel * max(s) (a numerically dependent basis
-// loses its dependent directions instead of amplifying rounding), reduce
-// B^T (D GH D) B with B = Q_kept diag(s)^-1/2, eigendecompose, keep the k
-// lowest.  Coefficients in the Y basis: D B w.
+// scale by D = diag(GS)^-1/2; Cholesky of D GS D with diagonal pivoting,
+// stopping when the largest remaining pivot falls below kDropRel (the
+// remaining columns are numerically in the span of the kept ones and are
+// dropped, as are zero columns); with the kept set K and G_KK = L L^T,
+// eigendecompose C = L^-1 (D GH D)_KK L^-T by Jacobi and keep the k lowest.
+// Coefficients in the Y basis: D P [L^-T w; 0].
 __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   const RRTask T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
-  const double kDropRel = 1e-10;
   extern __shared__ double rr_smem[];
+  const double kDropRel = 1e-10;
   const int ld = T.ld, k = T.k, nb = T.nb;
   // working matrices in shared memory when 3 ld^2 doubles fit, else global
   const bool in_smem = (3 * ld * ld * (int)sizeof(double) <= smem_bytes);
   double* base = in_smem ? rr_smem : T.work;
-  double* C = base;                          // scaled H-Gram / reduced matrix
-  double* V = base + (size_t)ld * ld;        // eigenvectors / scratch
-  double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram, then B
-  __shared__ double dsc[256], sv[256];
-  __shared__ int keep[256], order[256];
-  __shared__ int s_r;
+  double* C = base;                          // scaled H-Gram, then the reduced matrix
+  double* V = base + (size_t)ld * ld;        // Jacobi eigenvectors
+  double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram, then its pivoted factor
+  __shared__ double dsc[256], dg[256], red[256];
+  __shared__ int perm[256], order[256], rid[256];
+  __shared__ int s_r, s_piv;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     double g = T.GS[(size_t)i * ld + i];
     dsc[i] = (g > 0.0) ? 1.0 / sqrt(g) : 0.0;
+    perm[i] = i;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < nb * nb; it += blockDim.x) {
@@ -259,51 +261,98 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
     C[i * ld + j] = gh * dsc[i] * dsc[j];
   }
   __syncthreads();
-  cta_jacobi(G, V, nb, ld);
-  if (threadIdx.x == 0) {
-    double smax = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      double si = G[i * ld + i];
-      if (si == si) smax = fmax(smax, si);
-    }
-    int r = 0;
-    for (int i = 0; i < nb; ++i) {
-      double si = G[i * ld + i];
-      if (si == si && si > kDropRel * smax) { keep[r] = i; sv[r] = si; ++r; }
-    }
-    s_r = r;
-    if (r < k && T.fail) *T.fail = 1;
-  }
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) dg[i] = G[i * ld + i];
   __syncthreads();
+  // pivoted Cholesky: L is kept in V (row j = j-th pivot position, column q),
+  // G is read through perm
+  if (threadIdx.x == 0) s_r = nb;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    // argmax of the remaining diagonal over positions j..nb-1
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + threadIdx.x; i < nb; i += blockDim.x) {
+      double d = dg[perm[i]];
+      if (d > best) { best = d; bi = i; }
+    }
+    red[threadIdx.x] = best;
+    rid[threadIdx.x] = bi;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        double o = red[threadIdx.x + st];
+        int oi = rid[threadIdx.x + st];
+        if (o > red[threadIdx.x] || (o == red[threadIdx.x] && oi < rid[threadIdx.x])) {
+          red[threadIdx.x] = o; rid[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      s_piv = rid[0];
+      if (!(red[0] > kDropRel)) s_r = j;       // the diagonal scale is 1: drop below kDropRel
+      else { int t = perm[j]; perm[j] = perm[s_piv]; perm[s_piv] = t; }
+    }
+    __syncthreads();
+    if (s_r == j) break;
+    if (s_piv != j)   // the computed part of the two rows of L moves with the pivot
+      for (int q = threadIdx.x; q < j; q += blockDim.x) {
+        double t = V[j * ld + q];
+        V[j * ld + q] = V[s_piv * ld + q];
+        V[s_piv * ld + q] = t;
+      }
+    __syncthreads();
+    const int pj = perm[j];
+    const double ljj = sqrt(dg[pj]);
+    // column j of L (rows i > j in permuted order), L[j][j] = ljj
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      const int pi = perm[i];
+      double acc = G[pi * ld + pj];
+      for (int q = 0; q < j; ++q) acc -= V[i * ld + q] * V[j * ld + q];
+      V[i * ld + j] = acc / ljj;
+    }
+    if (threadIdx.x == 0) V[j * ld + j] = ljj;
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      double l = V[i * ld + j];
+      dg[perm[i]] -= l * l;
+    }
+    __syncthreads();
+  }
   const int r = s_r;
-  // B[i][c] = Q[i][keep c] / sqrt(s_c)  (into G)
-  for (int it = threadIdx.x; it < nb * r; it += blockDim.x) {
-    int i = it / r, c = it % r;
-    G[i * ld + c] = V[i * ld + keep[c]] / sqrt(sv[c]);
-  }
-  __syncthreads();
-  // V <- C B  (nb x r)
-  for (int it = threadIdx.x; it < nb * r; it += blockDim.x) {
-    int i = it / r, c = it % r;
-    double acc = 0.0;
-    for (int q = 0; q < nb; ++q) acc += C[i * ld + q] * G[q * ld + c];
-    V[i * ld + c] = acc;
-  }
-  __syncthreads();
-  // C <- B^T V  (r x r), symmetrised
+  if (r < k && threadIdx.x == 0 && T.fail) *T.fail = 1;
+  // L (r x r) into G, then C <- L^-1 Hpp L^-T with Hpp[a][b] = C[perm a][perm b]
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
-    int a = it / r, c = it % r;
-    double acc = 0.0;
-    for (int q = 0; q < nb; ++q) acc += G[q * ld + a] * V[q * ld + c];
-    C[a * ld + c] = acc;
+    int aa = it / r, bb = it % r;
+    G[aa * ld + bb] = (bb <= aa) ? V[aa * ld + bb] : 0.0;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
-    int a = it / r, c = it % r;
-    if (a < c) {
-      double m = 0.5 * (C[a * ld + c] + C[c * ld + a]);
-      C[a * ld + c] = m;
-      C[c * ld + a] = m;
+    int aa = it / r, bb = it % r;
+    V[aa * ld + bb] = C[perm[aa] * ld + perm[bb]];
+  }
+  __syncthreads();
+  // V <- L^-1 V (thread per column), then C <- V L^-T (thread per row)
+  for (int j = threadIdx.x; j < r; j += blockDim.x)
+    for (int i = 0; i < r; ++i) {
+      double acc = V[i * ld + j];
+      for (int q = 0; q < i; ++q) acc -= G[i * ld + q] * V[q * ld + j];
+      V[i * ld + j] = acc / G[i * ld + i];
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
+    for (int j = 0; j < r; ++j) {
+      double acc = V[i * ld + j];
+      for (int q = 0; q < j; ++q) acc -= C[i * ld + q] * G[j * ld + q];
+      C[i * ld + j] = acc / G[j * ld + j];
+    }
+  __syncthreads();
+  for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
+    int aa = it / r, bb = it % r;
+    if (aa < bb) {
+      double mm = 0.5 * (C[aa * ld + bb] + C[bb * ld + aa]);
+      C[aa * ld + bb] = mm;
+      C[bb * ld + aa] = mm;
     }
   }
   __syncthreads();
@@ -325,17 +374,21 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   __syncthreads();
   const int kk = min(k, r);
   for (int c = threadIdx.x; c < k; c += blockDim.x) T.lam[c] = (c < kk) ? C[order[c] * ld + order[c]] : NAN;
-  // coefficients in the Y basis: D B w, and the P-update copy without the X rows
-  for (int it = threadIdx.x; it < nb * k; it += blockDim.x) {
-    int i = it % nb, c = it / nb;
-    double acc = 0.0;
+  // coefficients: w = L^-T v (back substitution in permuted order), z[perm a] = D w[a]
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double* z = T.Cc + (size_t)ld * c;
+    double* zp = T.Cc + (size_t)ld * (k + c);
+    for (int i = 0; i < nb; ++i) z[i] = 0.0;
     if (c < kk) {
-      int oc = order[c];
-      for (int q = 0; q < r; ++q) acc += G[i * ld + q] * V[q * ld + oc];
-      acc *= dsc[i];
+      const int oc = order[c];
+      for (int aa = r - 1; aa >= 0; --aa) {
+        double acc = V[aa * ld + oc];
+        for (int q = aa + 1; q < r; ++q) acc -= G[q * ld + aa] * z[perm[q]];
+        z[perm[aa]] = acc / G[aa * ld + aa];
+      }
+      for (int i = 0; i < nb; ++i) z[i] *= dsc[i];
     }
-    T.Cc[(size_t)i + (size_t)ld * c] = acc;
-    T.Cc[(size_t)i + (size_t)ld * (k + c)] = (i < k) ? 0.0 : acc;
+    for (int i = 0; i < nb; ++i) zp[i] = (i < k) ? 0.0 : z[i];
   }
 }
 

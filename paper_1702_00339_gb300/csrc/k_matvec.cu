@@ -62,21 +62,47 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
     const int r = C.fac[s];
     const int Pn = Ps * r, m = M / Pn;
     const int nb = M / r;
+    const int stepr = M / r;                 // w_r = tw[stepr]
     for (int it = threadIdx.x; it < nb * CC; it += blockDim.x) {
-      int b = it / CC, cc = it % CC;
-      int kp = b / Ps, j = b % Ps;
-      for (int p = 0; p < r; ++p) {
-        cplx acc = cmk(0.0, 0.0);
-        for (int q = 0; q < r; ++q) {
-          cplx a = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
-          long long e1 = ((long long)q * j * m) % M;           // w_{Pn}^{q j}
-          long long e2 = ((long long)q * p * (M / r)) % M;     // w_r^{q p}
-          cplx w = C.tw[(e1 + e2) % M];
+      const int b = it / CC, cc = it % CC;
+      const int kp = b / Ps, j = b % Ps;
+      // inputs times the stage twiddles w_{Pn}^{q j} = tw[q j m]
+      cplx a[5];
+      const int jm = j * m;
+      for (int q = 0; q < r; ++q) {
+        cplx x = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
+        if (q) {
+          cplx w = C.tw[(q * jm) % M];
           if (DIR < 0) w.y = -w.y;
-          acc = cadd(acc, cmul(w, a));
+          x = cmul(w, x);
         }
-        B[(size_t)(kp * Pn + j + Ps * p) * CC + cc] = acc;
+        a[q] = x;
       }
+      cplx o[5];
+      if (r == 2) {
+        o[0] = cadd(a[0], a[1]);
+        o[1] = csub(a[0], a[1]);
+      } else if (r == 4) {
+        cplx t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        cplx t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+        // multiply t3 by -i (forward) or +i (inverse)
+        cplx t3r = (DIR > 0) ? cmk(t3.y, -t3.x) : cmk(-t3.y, t3.x);
+        o[0] = cadd(t0, t2);
+        o[2] = csub(t0, t2);
+        o[1] = cadd(t1, t3r);
+        o[3] = csub(t1, t3r);
+      } else {   // r = 3 or 5: direct small DFT with the table's r-th roots
+        for (int p = 0; p < r; ++p) {
+          cplx acc = a[0];
+          for (int q = 1; q < r; ++q) {
+            cplx w = C.tw[((q * p) % r) * stepr];
+            if (DIR < 0) w.y = -w.y;
+            acc = cadd(acc, cmul(w, a[q]));
+          }
+          o[p] = acc;
+        }
+      }
+      for (int p = 0; p < r; ++p) B[(size_t)(kp * Pn + j + Ps * p) * CC + cc] = o[p];
     }
     __syncthreads();
     cplx* t = A; A = B; B = t;

@@ -85,6 +85,8 @@ def lib():
         L.fock_plan_execute.argtypes = [C.c_void_p, C.c_double, C.c_int]
         L.fock_plan_outputs.argtypes = [C.c_void_p, P(c_output), C.c_int]
         L.fock_plan_info.argtypes = [C.c_void_p, P(C.c_size_t), P(C.c_size_t), P(C.c_size_t)]
+        L.fock_plan_problem_sizes.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int),
+                                              P(C.c_int)]
         L.fock_plan_free.argtypes = [C.c_void_p]
         L.fock_plan_free.restype = None
         L.fock_profile_enable.argtypes = [C.c_void_p, C.c_int]
@@ -341,6 +343,13 @@ class Plan:
         a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
         lib().fock_plan_info(self.h, C.byref(a), C.byref(b), C.byref(c))
         self.upload_bytes, self.device_bytes, self.n_evals = a.value, b.value, c.value
+
+    def sizes(self, i):
+        """(N_b, circulant size M, generator reach D, boundary blocks) of problem i."""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self.ctx._check(lib().fock_plan_problem_sizes(self.h, int(i), C.byref(a), C.byref(b), C.byref(c),
+                                                      C.byref(d)), "fock_plan_problem_sizes")
+        return a.value, b.value, c.value, d.value
 
     def execute(self, tol=1e-10, maxit=400):
         rc = lib().fock_plan_execute(self.h, float(tol), int(maxit))
