@@ -60,7 +60,7 @@ def config_dict(batch, world):
 # --------------------------------------------------------------- CPU oracle
 def oracle_sample(npairs, seed0=0):
     """Time the CPU oracle on npairs (box, periodic) requests of the workload."""
-    from oracle import dense, sinc
+    from oracle import blocks, sinc
     ps = []
     for r in range(npairs):
         b = li.config2(seed0 + r, L=L_CHAIN, n0=N0, pad=PAD, n_perp=NPERP, R=R_RANK)
@@ -71,7 +71,7 @@ def oracle_sample(npairs, seed0=0):
         t, c, _ = sinc.table_for(p)
         q = p.with_table(t, c)
         q.k_eig = p.k_eig
-        dense.solve(q)
+        blocks.solve(q)
     dt = time.perf_counter() - t0
     return len(ps), dt
 

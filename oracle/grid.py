@@ -56,25 +56,27 @@ def gto_norm_1d(alpha, is_p):
     return n * 2.0 * np.sqrt(alpha) if is_p else n
 
 
-def basis_axis(p, ax):
-    """G[i, k, mu] = 1D factor along `ax` of GTO mu of cell k at node i."""
+def basis_axis(p, ax, cells=None):
+    """G[i, c, mu] = 1D factor along `ax` of GTO mu of cell k at node i, for
+    all cells k (c = k) or for the listed cells (c = position in `cells`)."""
     x, X0, period = axis_nodes(p, ax)
     N, L, m0 = p.N[ax], p.L[ax], p.m0
-    G = np.zeros((N, L, m0))
+    cells = list(range(L)) if cells is None else list(cells)
+    G = np.zeros((N, len(cells), m0))
     for mu in range(m0):
         alpha = float(p.exps[mu])
         is_p = int(p.ang[mu]) == ax + 1
         rcut = np.sqrt(np.log(1.0 / p.eps_support) / alpha)
         nrm = gto_norm_1d(alpha, is_p)
         f = float(p.frac[int(p.centre[mu]), ax])
-        for k in range(L):
+        for c, k in enumerate(cells):
             A = X0 + (k + f) * p.b0
             d = min_image(x - A, period)
             v = nrm * np.exp(-alpha * d * d)
             if is_p:
                 v = v * d
             v[np.abs(d) > rcut] = 0.0
-            G[:, k, mu] = v
+            G[:, c, mu] = v
     return G
 
 

@@ -47,6 +47,8 @@ void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
 void launch_eapply(const EApplyTask*, int, cudaStream_t);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
 void launch_band_solve(const BandTask*, int, cudaStream_t);
+void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
+void launch_cell_back(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 __global__ void k_init_x(const InitTask*);
 __global__ void k_gemm_tn(const GemmTask*);
 __global__ void k_gemm_nn(const GemmTask*);
@@ -136,6 +138,11 @@ struct HostProb {
   int kind;            // 0 periodic (circulant eigensolve), 1 structured iteration
 };
 
+// Guard vectors of the block iteration: k + g columns are iterated and the k
+// lowest must converge; the guards move the convergence rate of the k-th
+// eigenpair from lambda_{k+1} to lambda_{k+g+1} (clustered band edges).
+int lobpcg_guard(int k) { return std::max(2, k / 4); }
+
 int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (p.n0 <= 0 || !(p.b0 > 0.0)) { why = "n0 > 0 and b0 > 0 required"; return FOCK_EINVAL; }
   if (p.M0 < 1 || p.M0 > 8 || !p.Z || !p.frac) { why = "1 <= M0 <= 8 with Z and frac"; return FOCK_EINVAL; }
@@ -186,7 +193,10 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   H.k_eig = (p.k_eig > 0) ? p.k_eig : 16;
   if (H.kind == 1) {
     int Nb = H.L[0] * H.m0;
-    if (H.k_eig > Nb / 3 || 3 * H.k_eig > 192) { why = "k_eig must satisfy 3k <= min(N_b, 192)"; return FOCK_EINVAL; }
+    int kb = H.k_eig + lobpcg_guard(H.k_eig);
+    if (3 * kb > Nb || 3 * kb > 255) {
+      why = "k_eig too large: 3 (k + guard) must not exceed min(N_b, 255)"; return FOCK_EINVAL;
+    }
   }
   return FOCK_OK;
 }
@@ -300,6 +310,8 @@ struct Batch {
   std::vector<FBlockTask> fbp, fbs; FBlockTask *d_fbp = nullptr, *d_fbs = nullptr;
   int maxnj_p = 0, maxnj_s = 0, maxm0 = 1;
   std::vector<PrecTask> prec; PrecTask* d_prec = nullptr; int maxM = 0;
+  std::vector<CanonTask> canon; CanonTask* d_canon = nullptr; int maxcblk = 0;
+  std::vector<FBlockTask> fbo; FBlockTask* d_fbo = nullptr;
   std::vector<SortTask> sorts; SortTask* d_sorts = nullptr; int maxsort = 0;
   std::vector<int> bigsort;          // problems whose eigenvalues need the global sort
   double* sort_pv = nullptr; int* sort_pi = nullptr;
@@ -321,6 +333,10 @@ struct Batch {
     cplx *CH = nullptr, *CS = nullptr, *K = nullptr;
     double *emin = nullptr, *sigma = nullptr;
     bool use_band = false;            // preconditioner: banded Cholesky (else circulant inverse)
+    // cell canonical orthogonalisation: transformed operator used by the solver
+    double *Xc = nullptr, *THc = nullptr, *TSc = nullptr, *EHc = nullptr, *ESc = nullptr;
+    int* kept = nullptr;
+    cplx *CHo = nullptr, *CSo = nullptr;   // Fourier blocks of the original operator (matvec API)
     double *band = nullptr, *sigma_band = nullptr;
     int *band_fail = nullptr;
     int* fail = nullptr;
@@ -328,7 +344,7 @@ struct Batch {
   std::vector<PerProb> pp;
   // LOBPCG state (structured problems)
   struct Lob {
-    int n, k, ld3;
+    int n, k, kw, ld3;   // k: block size (wanted kw + guards)
     double *Y, *HY, *SY, *T1, *R, *GH, *GS, *work, *Cc, *Cx, *lam, *res;
     int *active, *fail;
   };
@@ -361,7 +377,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.probs.assign(np, ProbDev());
   B.pp.assign(np, Batch::PerProb());
   B.gsegs.clear(); B.psegs.clear(); B.gram.clear(); B.combT.clear(); B.combE.clear();
-  B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.sorts.clear(); B.bigsort.clear();
+  B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   size_t zs_total = 0;
@@ -517,6 +533,19 @@ void plan(Batch& B, Slab& S, Slab& U) {
       }
       Q.EH = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
       Q.ES = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
+      Q.Xc = S.take<double>(m2);
+      Q.kept = S.take<int>(1);
+      Q.THc = S.take<double>((size_t)(Q.D + 1) * m2);
+      Q.TSc = S.take<double>((size_t)(Q.D + 1) * m2);
+      Q.EHc = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
+      Q.ESc = S.take<double>((size_t)std::max(Q.nE, 1) * m2);
+      {
+        CanonTask ct;
+        ct.m0 = H.m0; ct.D = Q.D; ct.nE = Q.nE; ct.TH = Q.TH; ct.TS = Q.TS; ct.EH = Q.EH; ct.ES = Q.ES;
+        ct.Xc = Q.Xc; ct.kept = Q.kept; ct.THc = Q.THc; ct.TSc = Q.TSc; ct.EHc = Q.EHc; ct.ESc = Q.ESc;
+        B.canon.push_back(ct);
+        B.maxcblk = std::max(B.maxcblk, 2 * (Q.D + 1) + 2 * Q.nE);
+      }
       for (int e = 0; e < Q.nE; ++e) {
         int k = Q.Ek[e], m = Q.Em[e], d = std::abs(k - m);
         CombineTask c;
@@ -551,6 +580,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
       B.maxM = std::max(B.maxM, Q.M);
       Q.CH = S.take<cplx>((size_t)Q.M * m2);
       Q.CS = S.take<cplx>((size_t)Q.M * m2);
+      Q.CHo = S.take<cplx>((size_t)Q.M * m2);
+      Q.CSo = S.take<cplx>((size_t)Q.M * m2);
       Q.K = S.take<cplx>((size_t)Q.M * m2);
       Q.emin = S.take<double>(Q.M);
       Q.sigma = S.take<double>(1);
@@ -564,9 +595,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Q.fail = S.take<int>(1);
       FBlockTask fb;
       std::memset(&fb, 0, sizeof(fb));
-      fb.prob = i; fb.source = 1; fb.nj = Q.M; fb.M = Q.M; fb.D = Q.D; fb.TH = Q.TH; fb.TS = Q.TS;
+      fb.prob = i; fb.source = 1; fb.nj = Q.M; fb.M = Q.M; fb.D = Q.D; fb.TH = Q.THc; fb.TS = Q.TSc;
       fb.outH = Q.CH; fb.outS = Q.CS; fb.want = 2; fb.ev = Q.emin; fb.fail = Q.fail;
       B.fbs.push_back(fb);
+      FBlockTask fo = fb;   // the original operator's blocks, for the matvec entry points
+      fo.TH = Q.TH; fo.TS = Q.TS; fo.outH = Q.CHo; fo.outS = Q.CSo; fo.want = 0; fo.ev = nullptr;
+      B.fbo.push_back(fo);
       B.maxnj_s = std::max(B.maxnj_s, Q.M);
       PrecTask pt;
       pt.prob = i; pt.M = Q.M; pt.emin = Q.emin; pt.sigma = Q.sigma; pt.CH = Q.CH; pt.CS = Q.CS; pt.K = Q.K;
@@ -575,7 +609,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Q.nev = H.k_eig;
       Q.ev = S.take<double>(Q.nev);
       B.sidx.push_back(i);
-      B.kmax = std::max(B.kmax, H.k_eig);
+      B.kmax = std::max(B.kmax, H.k_eig + lobpcg_guard(H.k_eig));
     }
   }
   // ---- LOBPCG state ----
@@ -585,7 +619,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
     const HostProb& H = B.hp[i];
     Batch::PerProb& Q = B.pp[i];
     Batch::Lob l;
-    l.n = Q.Lc * H.m0; l.k = H.k_eig; l.ld3 = 3 * l.k + 1;   // +1: Jacobi pads odd sizes
+    l.n = Q.Lc * H.m0; l.kw = H.k_eig; l.k = H.k_eig + lobpcg_guard(H.k_eig);
+    l.ld3 = 3 * l.k + 1;   // +1: Jacobi pads odd sizes
     size_t nk = (size_t)l.n * l.k;
     l.Y = S.take<double>(3 * nk); l.HY = S.take<double>(3 * nk); l.SY = S.take<double>(3 * nk);
     l.T1 = S.take<double>(2 * nk);
@@ -674,8 +709,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
         BandTask bt;
         std::memset(&bt, 0, sizeof(bt));
         bt.m0 = m0; bt.L = Q.Lc; bt.D = Q.D; bt.k = k; bt.n = n;
-        bt.TH = Q.TH; bt.TS = Q.TS; bt.nE = Q.nE; bt.Ek = U.put(Q.Ek); bt.Em = U.put(Q.Em);
-        bt.EH = Q.EH; bt.ES = Q.ES; bt.sigma0 = Q.sigma; bt.band = Q.band; bt.sigma_used = Q.sigma_band;
+        bt.TH = Q.THc; bt.TS = Q.TSc; bt.nE = Q.nE; bt.Ek = U.put(Q.Ek); bt.Em = U.put(Q.Em);
+        bt.EH = Q.EHc; bt.ES = Q.ESc; bt.sigma0 = Q.sigma; bt.band = Q.band; bt.sigma_used = Q.sigma_band;
         bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
         bnd.push_back(bt);
       } else {
@@ -690,8 +725,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
         return t;
       };
       if (Q.nE) {
-        ehxp.push_back(ea(Q.EH, Yx, l.HY, 2 * k)); esxp.push_back(ea(Q.ES, Yx, l.SY, 2 * k));
-        ehw.push_back(ea(Q.EH, Yw, l.HY + 2 * nk, k)); esw.push_back(ea(Q.ES, Yw, l.SY + 2 * nk, k));
+        ehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k)); esxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k));
+        ehw.push_back(ea(Q.EHc, Yw, l.HY + 2 * nk, k)); esw.push_back(ea(Q.ESc, Yw, l.SY + 2 * nk, k));
       }
       ini.push_back({n, k, n, problem_seed(H), l.Y});   // start depends on the problem only
       auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
@@ -754,6 +789,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.d_fbp = U.put(B.fbp);
   B.d_fbs = U.put(B.fbs);
   B.d_prec = U.put(B.prec);
+  B.d_canon = U.put(B.canon);
+  B.d_fbo = U.put(B.fbo);
   B.d_sorts = U.put(B.sorts);
   B.bytes = S.off;
   B.ubytes = U.off;
@@ -849,6 +886,7 @@ void run_struct_setup(fock_ctx* ctx, Batch& B) {
   cudaStream_t st = ctx->stream;
   if (B.fbs.empty()) return;
   zero_fail_flags(B, 1, st);
+  { PROF("k_cell_canon", 2); launch_cell_canon(B.d_canon, (int)B.canon.size(), B.maxm0, B.maxcblk, st); }
   { PROF("k_twiddle", 1); launch_twiddles(B.d_circs, (int)B.circs.size(), st); }
   { PROF("k_fblocks_embed", 1); launch_fblocks(B.d_probs, B.d_fbs, (int)B.fbs.size(), B.maxnj_s, B.maxm0, st); }
   { PROF("k_precond", 2); launch_precond(B.d_probs, B.d_prec, (int)B.prec.size(), B.maxM, B.maxm0, st); }
@@ -982,7 +1020,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       if (!active[s2]) continue;
       double mx = 0.0;
       bool bad = false;
-      for (int c = 0; c < B.lob[s2].k; ++c) {
+      for (int c = 0; c < B.lob[s2].kw; ++c) {   // the wanted pairs decide convergence
         double r = hres[(size_t)s2 * B.kmax + c];
         if (!(r == r) || std::isinf(r)) bad = true; else mx = std::max(mx, r);
       }
@@ -1109,7 +1147,7 @@ int blocks_matvec_view(const fock_blocks* b, MatvecView* v) {
   const Batch::PerProb& Q = B.pp[0];
   v->Lc = Q.Lc; v->m0 = B.hp[0].m0; v->M = Q.M; v->nE = Q.nE; v->nErows = Q.nErows;
   v->circ = B.d_circs + Q.circ;
-  v->CH = Q.CH; v->CS = Q.CS;
+  v->CH = Q.CHo; v->CS = Q.CSo;
   v->Erows = Q.Erows; v->Erowptr = Q.Erowptr; v->Ecols = Q.Ecols;
   v->EH = Q.EH; v->ES = Q.ES;
   v->stream = b->ctx->stream;
@@ -1280,6 +1318,10 @@ int fock_assemble(fock_ctx* ctx, const fock_problem* p, fock_blocks** out) {
   if (rc) { free_batch(b->B); delete b; return rc; }
   run_assemble(ctx, b->B);
   run_struct_setup(ctx, b->B);
+  if (!b->B.fbo.empty()) {   // Fourier blocks of the original operator for the matvec entry points
+    PROF("k_fblocks_embed", 1);
+    launch_fblocks(b->B.d_probs, b->B.d_fbo, (int)b->B.fbo.size(), b->B.maxnj_s, b->B.maxm0, ctx->stream);
+  }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) { free_batch(b->B); delete b; return set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e)); }
   *out = b;
@@ -1420,7 +1462,7 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   tf.prob = 0; tf.L = Q.Lc; tf.m0 = H.m0; tf.ncol = nvec; tf.circ = B.d_circs + Q.circ; tf.x = dx; tf.ldx = n;
   tf.X = X; tf.cc = cc;
   FftTask ti = tf; ti.x = nullptr; ti.X = Y; ti.y = dy; ti.ldy = n; ti.beta = 0.0;
-  BmulTask bm = {0, Q.M, H.m0, nvec, which == FOCK_OP_H ? Q.CH : Q.CS, nullptr, X, Y, nullptr};
+  BmulTask bm = {0, Q.M, H.m0, nvec, which == FOCK_OP_H ? Q.CHo : Q.CSo, nullptr, X, Y, nullptr};
   EApplyTask ea;
   ea.prob = 0; ea.m0 = H.m0; ea.ncol = nvec; ea.nrows = Q.nErows; ea.rows = Q.Erows; ea.rowptr = Q.Erowptr;
   ea.cols = Q.Ecols; ea.vals = which == FOCK_OP_H ? Q.EH : Q.ES; ea.x = dx; ea.ldx = n; ea.y = dy; ea.ldy = n;
@@ -1448,7 +1490,7 @@ int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int max
   if (!ctx || !b || !evals) return FOCK_EINVAL;
   Batch& B = const_cast<Batch&>(b->B);
   if (B.hp[0].kind != 1) return set_err(ctx, FOCK_EINVAL, "not a box problem");
-  if (k <= 0 || k > B.lob[0].k) return set_err(ctx, FOCK_EINVAL, "k exceeds the planned k_eig");
+  if (k <= 0 || k > B.lob[0].kw) return set_err(ctx, FOCK_EINVAL, "k exceeds the planned k_eig");
   ProfBind pb(ctx);
   std::vector<int> it, conv;
   std::vector<double> res;
@@ -1456,7 +1498,11 @@ int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int max
   if (rc) return rc;
   const Batch::Lob& l = B.lob[0];
   CUDA_TRY(ctx, cudaMemcpyAsync(evals, l.lam, (size_t)k * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  if (evecs) CUDA_TRY(ctx, cudaMemcpyAsync(evecs, l.Y, (size_t)l.n * k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (evecs) {   // back to the original basis: (I_L (x) Xc) V'
+    const Batch::PerProb& Q = B.pp[0];
+    launch_cell_back(Q.Xc, B.hp[0].m0, Q.Lc, k, l.Y, l.T1, l.n, ctx->stream);
+    CUDA_TRY(ctx, cudaMemcpyAsync(evecs, l.T1, (size_t)l.n * k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  }
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (iters) *iters = it[0];
   if (!conv[0]) return set_err(ctx, FOCK_ENOCONV, "maxit reached");

@@ -9,6 +9,12 @@ constexpr int MAXM0 = 32;
 constexpr int MAXR = 64;
 constexpr int MAXRADIX = 16;   // radix factors of a circulant size
 
+// Canonical (Loewdin) orthogonalisation threshold: an eigen-direction of an
+// overlap matrix (a Fourier block's Sbar_j, or a box chain's cell overlap
+// T_S[0]) whose eigenvalue is at most kCanonTau times that matrix's largest
+// eigenvalue is removed from the variational space.
+constexpr double kCanonTau = 1e-8;
+
 // Modes of a 1D Galerkin form along one axis (gram task):
 //   RING - periodic axis: nodes 0..N-1 with wrap-around, potential tiled;
 //   VIRT - Toeplitz generator of a chain axis: unbounded node line, no walls,
@@ -203,6 +209,19 @@ struct BandTask {
   int* fail;                               // out: 1 if every attempt broke down
   const double* R; double* W; int ld;      // solve: W = A^-1 R (n x k, ld)
   const int* active;
+};
+
+// Canonical orthogonalisation of a box chain's cell basis: Xc (m0 x m0,
+// row-major Xc[mu][j]) from the cell overlap block T_S[0]; columns j >= the
+// kept count are zero.  Then every block B becomes Xc^T B Xc.
+struct CanonTask {
+  int m0, D, nE;
+  const double* TH; const double* TS;     // original generators [D+1][m0*m0]
+  const double* EH; const double* ES;     // original boundary blocks [nE][m0*m0]
+  double* Xc;                             // out [m0*m0]
+  int* kept;                              // out: kept directions
+  double* THc; double* TSc;               // out transformed generators
+  double* EHc; double* ESc;               // out transformed boundary blocks
 };
 
 // Device pointers and sizes the matvec of an assembled box chain needs.

@@ -11,9 +11,12 @@
 //       that embeds the symmetric block Toeplitz matrix with generators
 //       T_d = block (k+d, k), |d| <= D: Chat_j = T_0 + sum_d (w^{jd} T_d +
 //       w^{-jd} T_d^T), w = exp(-2 pi i / M) (Eq. A.3 convention).
-//     eigensolver: Cholesky Sbar = L L^H, C = L^-1 Hbar L^-H, Householder
-//       reduction of C to a real tridiagonal, Sturm-sequence bisection per
-//       eigenvalue (ascending, so the block spectrum comes out sorted).
+//     eigensolver: canonical (Loewdin) orthogonalisation -- Jacobi
+//       eigendecomposition Sbar = Q diag(s) Q^H, X = Q_K diag(s_K)^-1/2 over
+//       the kept directions K = {s > kCanonTau max s}, C = X^H Hbar X --
+//       then Householder reduction of C to a real tridiagonal and
+//       Sturm-sequence bisection per eigenvalue (ascending, so the block
+//       spectrum comes out sorted); the removed directions report +inf.
 //  k_sigma      shift of the preconditioner: min_j lambda_min(Chat_j) - delta.
 //  k_precond    K_j = (Chat_H,j - sigma Chat_S,j)^-1 per Fourier index.
 //  k_sort_*     ascending sort of (eigenvalue, Fourier index) pairs.
@@ -23,8 +26,6 @@
 namespace fock {
 
 enum FSource { FROM_FACTORS = 0, FROM_TOEPLITZ = 1 };
-
-
 
 // ---- dense Hermitian helpers (shared memory, whole CTA) ----
 
@@ -53,26 +54,152 @@ __device__ bool cta_cholesky(cplx* a, int m) {
   return bad == 0;
 }
 
-// h <- L^-1 h L^-H (h Hermitian full storage, L lower in l).
-__device__ void cta_reduce(cplx* h, const cplx* l, int m) {
-  // Y = L^-1 H: thread per column
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      cplx s = h[i * m + j];
-      for (int q = 0; q < i; ++q) s = csub(s, cmul(l[i * m + q], h[q * m + j]));
-      h[i * m + j] = cscale(s, 1.0 / l[i * m + i].x);
+// Cyclic Jacobi eigendecomposition of a Hermitian n x n matrix a (row-major,
+// stride ld >= n + (n & 1)), whole CTA.  Each step rotates n/2 disjoint
+// index pairs (round-robin ordering, an odd n gets a zero pad index).  For a
+// pair (p, q) with a_pq = r e^{i phi} the unitary U = diag(1, e^{-i phi}) J,
+// J the real rotation that annihilates the real pair (a_pp, r, a_qq), gives
+// a <- U^H a U and v <- v U.  On return the diagonal of a holds the
+// eigenvalues (real parts) and the columns of v the eigenvectors.  A pair is
+// skipped once |a_pq| <= 1e-15 ||a||_F; at most 30 sweeps.
+__device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
+  __shared__ double rc[MAXM0 / 2 + 1], rs[MAXM0 / 2 + 1];
+  __shared__ cplx rph[MAXM0 / 2 + 1];
+  __shared__ int rp[MAXM0 / 2 + 1], rq[MAXM0 / 2 + 1];
+  __shared__ int nrot;
+  __shared__ double red[32], s_thr;
+  const int ne = n + (n & 1);
+  double part = 0.0;
+  for (int it = threadIdx.x; it < n * n; it += blockDim.x) part += cabs2(a[(it / n) * ld + (it % n)]);
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    s_thr = 1e-15 * sqrt(t);
+  }
+  for (int it = threadIdx.x; it < ne * ne; it += blockDim.x) {
+    int i = it / ne, j = it % ne;
+    v[i * ld + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
+    if (i == n || j == n) a[i * ld + j] = cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  const double thr = s_thr;
+  const int np2 = ne / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < ne - 1; ++rnd) {
+      for (int pi = threadIdx.x; pi < np2; pi += blockDim.x) {
+        int x = (pi == 0) ? 0 : ((pi - 1 + rnd) % (ne - 1)) + 1;
+        int y = ((ne - 2 - pi + rnd) % (ne - 1)) + 1;
+        int p = min(x, y), q = max(x, y);
+        cplx apq = a[p * ld + q];
+        double r = sqrt(cabs2(apq)), app = a[p * ld + p].x, aqq = a[q * ld + q].x;
+        double c = 1.0, s = 0.0;
+        cplx ph = cmk(1.0, 0.0);
+        if (r > thr && r > 1e-17 * sqrt(fabs(app * aqq))) {
+          ph = cscale(apq, 1.0 / r);
+          double th = (aqq - app) / (2.0 * r);
+          double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+          atomicAdd(&nrot, 1);
+        }
+        rp[pi] = p; rq[pi] = q; rc[pi] = c; rs[pi] = s; rph[pi] = ph;
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < np2 * ne; it += blockDim.x) {   // rows: U^H a
+        int pi = it / ne, jj = it % ne;
+        double s = rs[pi];
+        if (s == 0.0) continue;
+        int p = rp[pi], q = rq[pi];
+        double c = rc[pi];
+        cplx ap = a[p * ld + jj], aq = cmul(rph[pi], a[q * ld + jj]);
+        a[p * ld + jj] = csub(cscale(ap, c), cscale(aq, s));
+        a[q * ld + jj] = cadd(cscale(ap, s), cscale(aq, c));
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < np2 * ne; it += blockDim.x) {   // columns: a U, v U
+        int pi = it / ne, ii = it % ne;
+        double s = rs[pi];
+        if (s == 0.0) continue;
+        int p = rp[pi], q = rq[pi];
+        double c = rc[pi];
+        cplx phc = cconj(rph[pi]);
+        cplx ap = a[ii * ld + p], aq = cmul(phc, a[ii * ld + q]);
+        a[ii * ld + p] = csub(cscale(ap, c), cscale(aq, s));
+        a[ii * ld + q] = cadd(cscale(ap, s), cscale(aq, c));
+        cplx vp = v[ii * ld + p], vq = cmul(phc, v[ii * ld + q]);
+        v[ii * ld + p] = csub(cscale(vp, c), cscale(vq, s));
+        v[ii * ld + q] = cadd(cscale(vp, s), cscale(vq, c));
+      }
+      __syncthreads();
+    }
+    int done = (nrot == 0);
+    __syncthreads();
+    if (done) break;
+  }
+}
+
+// Canonical (Loewdin) orthogonalisation of a Hermitian pencil block (h, s),
+// both m x m with stride m: Jacobi eigendecomposition s = Q diag(w) Q^H (in
+// a, q: scratch of ld x ld, ld = m + (m & 1)), kept set K = {w_i > tau max
+// w} in ascending Jacobi index, X = Q_K diag(w_K)^-1/2, and h <- X^H h X
+// (r x r, stride r, exactly Hermitian).  Returns r = |K|.  sv and keep are
+// shared arrays of MAXM0 entries.
+__device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m, double tau,
+                                 double* sv, int* keep) {
+  __shared__ int s_r;
+  const int ld = m + (m & 1);
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
+  __syncthreads();
+  cta_jacobi_herm(a, q, m, ld);
+  if (threadIdx.x == 0) {
+    double wmax = 0.0;
+    for (int i = 0; i < m; ++i) wmax = fmax(wmax, a[i * ld + i].x);
+    int r = 0;
+    if (wmax > 0.0)
+      for (int i = 0; i < m; ++i)
+        if (a[i * ld + i].x > tau * wmax) { keep[r] = i; sv[r] = a[i * ld + i].x; ++r; }
+    s_r = r;
+  }
+  __syncthreads();
+  const int r = s_r;
+  cplx* X = a;   // m x r
+  for (int it = threadIdx.x; it < m * r; it += blockDim.x) {
+    int mu = it / r, c = it % r;
+    X[it] = cscale(q[mu * ld + keep[c]], 1.0 / sqrt(sv[c]));
+  }
+  __syncthreads();
+  cplx* Y = q;   // m x r, Y = h X
+  for (int it = threadIdx.x; it < m * r; it += blockDim.x) {
+    int mu = it / r, c = it % r;
+    cplx acc = cmk(0.0, 0.0);
+    for (int nu = 0; nu < m; ++nu) acc = cadd(acc, cmul(h[mu * m + nu], X[nu * r + c]));
+    Y[it] = acc;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < r * r; it += blockDim.x) {   // h = X^H Y
+    int ia = it / r, ib = it % r;
+    cplx acc = cmk(0.0, 0.0);
+    for (int mu = 0; mu < m; ++mu) acc = cadd(acc, cmulc(Y[mu * r + ib], X[mu * r + ia]));
+    h[it] = acc;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
+    int ia = it / r, ib = it % r;
+    if (ia < ib) {
+      cplx hm = cscale(cadd(h[it], cconj(h[ib * r + ia])), 0.5);
+      h[it] = hm;
+      h[ib * r + ia] = cconj(hm);
+    } else if (ia == ib) {
+      h[it].y = 0.0;
     }
   }
   __syncthreads();
-  // C = Y L^-H: thread per row, C[i][j] = (Y[i][j] - sum_{q<j} C[i][q] conj(L[j][q])) / L[j][j]
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    for (int j = 0; j < m; ++j) {
-      cplx s = h[i * m + j];
-      for (int q = 0; q < j; ++q) s = csub(s, cmulc(h[i * m + q], l[j * m + q]));
-      h[i * m + j] = cscale(s, 1.0 / l[j * m + j].x);
-    }
-  }
-  __syncthreads();
+  return r;
 }
 
 // Householder reduction of Hermitian c (full storage, destroyed) to a real
@@ -193,9 +320,12 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   if (j >= F.nj) return;
   const ProbDev& P = probs[F.prob];
   const int m0 = P.m0, np = m0 * m0;
+  const int ldj = m0 + (m0 & 1);
   cplx* H = sm;
   cplx* S = sm + np;
-  cplx* v = S + np;
+  cplx* Aj = S + np;            // Jacobi work, ldj x ldj
+  cplx* Qj = Aj + ldj * ldj;    // Jacobi eigenvectors, ldj x ldj
+  cplx* v = Qj + ldj * ldj;
   cplx* pv = v + MAXM0;
   double* dd = (double*)(pv + MAXM0);
   double* ee = dd + MAXM0;
@@ -258,17 +388,18 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     }
   if (F.want == 0) return;
   __syncthreads();
-  bool ok = cta_cholesky(S, m0);
-  if (!ok && threadIdx.x == 0 && F.fail) *F.fail = 1;
-  cta_reduce(H, S, m0);
-  cta_tridiag(H, m0, dd, ee, v, pv);
+  // canonical orthogonalisation (removes numerically dependent Bloch combinations)
+  __shared__ int keep[MAXM0];
+  __shared__ double sv[MAXM0];
+  const int r = cta_lowdin_reduce(H, S, Aj, Qj, m0, kCanonTau, sv, keep);
+  if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
   if (F.want == 1) {
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-      F.ev[(size_t)j * m0 + i] = tridiag_eig_bisect(dd, ee, m0, i);
+      F.ev[(size_t)j * m0 + i] = (i < r) ? tridiag_eig_bisect(dd, ee, r, i) : INFINITY;
       if (F.blk) F.blk[(size_t)j * m0 + i] = j;
     }
   } else if (threadIdx.x == 0) {
-    F.ev[j] = tridiag_eig_bisect(dd, ee, m0, 0);
+    F.ev[j] = (r > 0) ? tridiag_eig_bisect(dd, ee, r, 0) : INFINITY;
   }
 }
 
@@ -323,7 +454,13 @@ __global__ void k_precond(const ProbDev* __restrict__ probs, const PrecTask* __r
 }
 
 // ---- sorting of (value, index) pairs ----
+// Order: ascending value, ties by ascending index.  Pads carry +inf and an
+// index above every real one, so they sort after the removed directions'
+// +inf entries and the result is deterministic.
 
+__device__ inline bool pair_gt(double va, int ia, double vb, int ib) {
+  return va > vb || (va == vb && ia > ib);
+}
 
 __global__ void k_sort_small(const SortTask* __restrict__ tasks) {
   extern __shared__ double ssv[];
@@ -333,8 +470,8 @@ __global__ void k_sort_small(const SortTask* __restrict__ tasks) {
   double* sv = ssv;
   int* si = (int*)(ssv + n2);
   for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    sv[i] = (i < T.n) ? T.v[i] : DBL_MAX;
-    si[i] = (i < T.n && T.idx) ? T.idx[i] : i;
+    sv[i] = (i < T.n) ? T.v[i] : INFINITY;
+    si[i] = (i < T.n) ? (T.idx ? T.idx[i] : i) : 0x7fffffff;
   }
   __syncthreads();
   for (int k = 2; k <= n2; k <<= 1)
@@ -343,7 +480,7 @@ __global__ void k_sort_small(const SortTask* __restrict__ tasks) {
         int ij = i ^ jj;
         if (ij > i) {
           bool up = ((i & k) == 0);
-          if ((sv[i] > sv[ij]) == up) {
+          if (pair_gt(sv[i], si[i], sv[ij], si[ij]) == up) {
             double tv = sv[i]; sv[i] = sv[ij]; sv[ij] = tv;
             int ti = si[i]; si[i] = si[ij]; si[ij] = ti;
           }
@@ -364,7 +501,7 @@ __global__ void k_bitonic_pass(double* v, int* idx, int n2, int k, int jj) {
     int ij = i ^ jj;
     if (ij > i) {
       bool up = ((i & k) == 0);
-      if ((v[i] > v[ij]) == up) {
+      if (pair_gt(v[i], idx[i], v[ij], idx[ij]) == up) {
         double tv = v[i]; v[i] = v[ij]; v[ij] = tv;
         int ti = idx[i]; idx[i] = idx[ij]; idx[ij] = ti;
       }
@@ -374,7 +511,7 @@ __global__ void k_bitonic_pass(double* v, int* idx, int n2, int k, int jj) {
 
 __global__ void k_pad_copy(const double* v, const int* idx, int n, double* pv, int* pidx, int n2) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-    pv[i] = (i < n) ? v[i] : DBL_MAX;
+    pv[i] = (i < n) ? v[i] : INFINITY;
     pidx[i] = (i < n) ? (idx ? idx[i] : i) : 0x7fffffff;
   }
 }
@@ -388,7 +525,8 @@ __global__ void k_unpad_copy(const double* pv, const int* pidx, int n, double* v
 
 // ---- launchers ----
 size_t fblocks_smem(int m0) {
-  return (size_t)(2 * m0 * m0 + 2 * MAXM0) * sizeof(cplx) + 2 * MAXM0 * sizeof(double);
+  const int ldj = m0 + (m0 & 1);
+  return (size_t)(2 * m0 * m0 + 2 * ldj * ldj + 2 * MAXM0) * sizeof(cplx) + 2 * MAXM0 * sizeof(double);
 }
 
 void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,

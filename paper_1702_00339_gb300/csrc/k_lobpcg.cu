@@ -16,6 +16,10 @@
 
 namespace fock {
 
+// eigenvalue given to the cell directions dropped by the canonical transform
+constexpr double kDecoupledEig = 1e6;
+
+
 
 __device__ inline uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -400,6 +404,107 @@ __global__ void k_copy_cols(const CopyTask* __restrict__ tasks) {
     int i = it % T.n, c = it / T.n;
     T.dst[(size_t)i + (size_t)T.ldd * c] = T.src[(size_t)i + (size_t)T.lds * c];
   }
+}
+
+}  // namespace fock
+
+namespace fock {
+
+// One CTA per box problem: canonical (Loewdin) orthogonalisation of the
+// cell basis.  Jacobi eigendecomposition T_S[0] = Q diag(s) Q^T of the cell
+// overlap, kept set K = {s > kCanonTau max s} in ascending Jacobi index,
+// Xc = Q_K diag(s_K)^-1/2 (m0 x m0, the columns past |K| zero).
+__global__ void k_cell_canon(const CanonTask* __restrict__ tasks) {
+  extern __shared__ double cs[];
+  const CanonTask T = tasks[blockIdx.x];
+  const int m0 = T.m0, ld = m0 + 1;
+  double* G = cs;                 // ld x ld
+  double* Q = cs + ld * ld;       // ld x ld
+  __shared__ double sv[MAXM0 + 1];
+  __shared__ int keep[MAXM0 + 1], s_r;
+  for (int it = threadIdx.x; it < m0 * m0; it += blockDim.x) {
+    int i = it / m0, j = it % m0;
+    G[i * ld + j] = 0.5 * (T.TS[i * m0 + j] + T.TS[j * m0 + i]);
+  }
+  __syncthreads();
+  cta_jacobi(G, Q, m0, ld);
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int i = 0; i < m0; ++i) smax = fmax(smax, G[i * ld + i]);
+    int r = 0;
+    if (smax > 0.0)
+      for (int i = 0; i < m0; ++i)
+        if (G[i * ld + i] > kCanonTau * smax) { keep[r] = i; sv[r] = G[i * ld + i]; ++r; }
+    s_r = r;
+    *T.kept = r;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < m0 * m0; it += blockDim.x) {
+    int mu = it / m0, j = it % m0;
+    T.Xc[it] = (j < s_r) ? Q[mu * ld + keep[j]] / sqrt(sv[j]) : 0.0;
+  }
+}
+
+// One CTA per block: B' = Xc^T B Xc.  Blocks: [0, D] generators (H then S),
+// then the boundary blocks (H then S).  The dropped directions of the cell
+// (zero columns of Xc) get a decoupled diagonal in T_H[0], T_S[0]: H = big,
+// S = 1, so their eigenvalue `big` stays above every wanted one.
+__global__ void k_cell_transform(const CanonTask* __restrict__ tasks) {
+  extern __shared__ double ts[];
+  const CanonTask T = tasks[blockIdx.y];
+  const int m0 = T.m0, m2 = m0 * m0;
+  const int nblk = 2 * (T.D + 1) + 2 * T.nE;
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const double* src; double* dst;
+  const int g = T.D + 1;
+  if (b < g) { src = T.TH + (size_t)b * m2; dst = T.THc + (size_t)b * m2; }
+  else if (b < 2 * g) { src = T.TS + (size_t)(b - g) * m2; dst = T.TSc + (size_t)(b - g) * m2; }
+  else if (b < 2 * g + T.nE) { src = T.EH + (size_t)(b - 2 * g) * m2; dst = T.EHc + (size_t)(b - 2 * g) * m2; }
+  else { src = T.ES + (size_t)(b - 2 * g - T.nE) * m2; dst = T.ESc + (size_t)(b - 2 * g - T.nE) * m2; }
+  double* X = ts;
+  double* Y = ts + m2;
+  for (int it = threadIdx.x; it < m2; it += blockDim.x) X[it] = T.Xc[it];
+  __syncthreads();
+  for (int it = threadIdx.x; it < m2; it += blockDim.x) {   // Y = B Xc
+    int mu = it / m0, j = it % m0;
+    double acc = 0.0;
+    for (int nu = 0; nu < m0; ++nu) acc += src[mu * m0 + nu] * X[nu * m0 + j];
+    Y[it] = acc;
+  }
+  __syncthreads();
+  const int r = *T.kept;
+  for (int it = threadIdx.x; it < m2; it += blockDim.x) {   // dst = Xc^T Y
+    int i = it / m0, j = it % m0;
+    double acc = 0.0;
+    for (int mu = 0; mu < m0; ++mu) acc += X[mu * m0 + i] * Y[mu * m0 + j];
+    if ((b == 0 || b == g) && i == j && i >= r) acc = (b == 0) ? kDecoupledEig : 1.0;
+    dst[it] = acc;
+  }
+}
+
+// V (original basis) = (I_L (x) Xc) V' for n = L m0 rows, ncol columns.
+__global__ void k_cell_back(const double* __restrict__ Xc, int m0, int L, int ncol, const double* Vr,
+                            double* V, int ld) {
+  const int tot = L * m0 * ncol;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
+    int mu = it % m0, rest = it / m0, cell = rest % L, c = rest / L;
+    double acc = 0.0;
+    for (int j = 0; j < m0; ++j) acc += Xc[mu * m0 + j] * Vr[(size_t)(cell * m0 + j) + (size_t)ld * c];
+    V[(size_t)(cell * m0 + mu) + (size_t)ld * c] = acc;
+  }
+}
+
+void launch_cell_canon(const CanonTask* t, int n, int maxm0, int maxblk, cudaStream_t st) {
+  if (!n) return;
+  size_t sm = (size_t)2 * (maxm0 + 1) * (maxm0 + 1) * sizeof(double);
+  k_cell_canon<<<n, 256, sm, st>>>(t);
+  k_cell_transform<<<dim3(maxblk, n), 256, (size_t)2 * maxm0 * maxm0 * sizeof(double), st>>>(t);
+}
+
+void launch_cell_back(const double* Xc, int m0, int L, int ncol, const double* Vr, double* V, int ld,
+                      cudaStream_t st) {
+  k_cell_back<<<64, 256, 0, st>>>(Xc, m0, L, ncol, Vr, V, ld);
 }
 
 }  // namespace fock

@@ -8,7 +8,7 @@ ragged tail.  The quadrature table always comes from the oracle's rule.
 import numpy as np
 
 import lattice_inputs as li
-from oracle import sinc
+from oracle import blocks, sinc
 
 
 def with_table(p):
@@ -63,3 +63,38 @@ def eig_tol(S, ev_ref, base=1e-10):
     w = np.linalg.eigvalsh(S)
     kappa = float(w.max() / w.min())
     return max(base, 4.0 * U64 * kappa) * float(np.max(np.abs(ev_ref)))
+
+
+def canon_tol(ev_ref, kappa, base=1e-10):
+    """Eigenvalue tolerance after canonical orthogonalisation:
+    max(base, 16 u kappa_K) * max|lambda| with kappa_K the condition number of
+    the kept part of the overlap (at most 1/CANON_TAU): a backward-stable
+    solve of the reduced pencil perturbs eigenvalues by about
+    u kappa_K |lambda|; the factor 16 covers the rounding of the Fourier sums
+    that form the blocks (sums over up to 32768 lattice terms whose Bloch
+    combinations cancel)."""
+    fin = np.isfinite(ev_ref)
+    return max(base, 16.0 * U64 * float(np.max(kappa))) * float(np.max(np.abs(ev_ref[fin])))
+
+
+def reference(p, H, S):
+    """The oracle's answer under the canonical-orthogonalisation reading and
+    its tolerance: periodic -> (sorted spectrum with +inf, tol, per-block
+    spectra); box -> (lowest k_eig, tol, (eigenvectors, reduced overlap,
+    block-diagonal cell basis))."""
+    if p.is_box:
+        ev, V, Sr = blocks.box_eigs(p, H, S, vectors=True)
+        Xb, _ = blocks.box_basis(p)
+        return ev, eig_tol(Sr, ev), (V, Sr, Xb)
+    ev, per, kap = blocks.periodic_eigs(p, H, S)
+    return ev, canon_tol(ev, kap), per
+
+
+def assert_spectra_match(got, ref, tol):
+    """Same removed directions (+inf in the same places) and finite
+    eigenvalues within tol."""
+    got = np.asarray(got)
+    assert np.array_equal(np.isfinite(got), np.isfinite(ref))
+    f = np.isfinite(ref)
+    if f.any():
+        assert np.max(np.abs(got[f] - ref[f])) <= tol

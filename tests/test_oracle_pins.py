@@ -297,3 +297,122 @@ def test_defect_reduces_to_charge_change_single_molecule():
     Hq, _ = dense.build(q)
     Hr, _ = dense.build(r)
     assert np.max(np.abs(Hq - Hr)) <= 1e-13 * np.max(np.abs(Hr))
+
+
+def test_single_block_contraction_equals_dense_route():
+    """The one-block 3D contraction used for large problems reproduces the
+    dense matrices' blocks (periodic generators and a box chain's blocks)."""
+    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    H, S = dense.build(p)
+    m0 = p.m0
+    for kc in [(0, 0, 0), (1, 1, 3), (2, 0, 1)]:
+        kb = (kc[0] * p.L[1] + kc[1]) * p.L[2] + kc[2]
+        h, s = blocks.generator_block(p, kc)
+        assert np.max(np.abs(h - H[kb * m0:(kb + 1) * m0, :m0])) <= 1e-14 * np.max(np.abs(H))
+        assert np.max(np.abs(s - S[kb * m0:(kb + 1) * m0, :m0])) <= 1e-14 * np.max(np.abs(S))
+    q = _cases.box_chain_small(L=9, n0=4, pad=5, n_perp=12, R=8)
+    H, S = dense.build(q)
+    m0 = q.m0
+    for k, m in [(0, 0), (3, 1), (8, 6), (4, 4)]:
+        h, s = blocks.generator_block(q, (k, 0, 0), mcell=(m, 0, 0))
+        h2, _ = blocks.generator_block(q, (k, 0, 0), forms=dense.axis_forms(q), mcell=(m, 0, 0))
+        assert np.max(np.abs(h - h2)) <= 1e-14 * np.max(np.abs(H))
+        assert np.max(np.abs(h - H[k * m0:(k + 1) * m0, m * m0:(m + 1) * m0])) <= 1e-14 * np.max(np.abs(H))
+        assert np.max(np.abs(s - S[k * m0:(k + 1) * m0, m * m0:(m + 1) * m0])) <= 1e-14 * np.max(np.abs(S))
+
+
+def test_canonical_orthogonalisation_reduces_to_range_of_S():
+    """Dependent basis functions: with m functions spanning an r-dimensional
+    space (S = F^H F, H = F^H H0 F, F of rank r), the finite eigenvalues are
+    those of H0 on that space, the other m - r are dropped (+inf); full rank:
+    LAPACK's generalized eigenvalues."""
+    rng = np.random.default_rng(5)
+    m, r = 7, 4
+    Hh = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    Hh = Hh + Hh.conj().T
+    A = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    S = A @ A.conj().T + 0.1 * np.eye(m)
+    assert np.max(np.abs(blocks.canonical_eigs(Hh, S) - scipy.linalg.eigh(Hh, S, eigvals_only=True))) < 1e-11
+    F = rng.standard_normal((r, m)) + 1j * rng.standard_normal((r, m))
+    H0 = rng.standard_normal((r, r)) + 1j * rng.standard_normal((r, r))
+    H0 = H0 + H0.conj().T
+    got = blocks.canonical_eigs(F.conj().T @ H0 @ F, F.conj().T @ F)
+    assert np.sum(np.isinf(got)) == m - r
+    ref = np.linalg.eigvalsh(H0)
+    assert np.max(np.abs(got[:r] - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def _with_duplicate(p, mu):
+    """The same problem with basis function mu listed twice (an exactly
+    dependent basis: the overlap gets an exact null vector e_mu - e_m0)."""
+    q = li.Problem(L=p.L, periodic=p.periodic, N=p.N, n0=p.n0, b0=p.b0, Z=p.Z, frac=p.frac,
+                   exps=np.append(p.exps, p.exps[mu]), ang=np.append(p.ang, p.ang[mu]),
+                   centre=np.append(p.centre, p.centre[mu]), R=p.R, sinc_t=p.sinc_t,
+                   sinc_c=p.sinc_c)
+    q.k_eig = p.k_eig
+    return q
+
+
+def test_lowdin_basis_orthonormalises_the_kept_directions():
+    """X^H S X = I on the kept directions; the removed ones are exactly the
+    eigenvalues at or below tau * max."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((9, 6)) + 1j * rng.standard_normal((9, 6))
+    S = A @ A.conj().T + 1e-12 * np.eye(9)         # rank 6 up to a tiny ridge
+    X, s = blocks.lowdin_basis(S)
+    assert X.shape == (9, 6)
+    assert np.max(np.abs(X.conj().T @ S @ X - np.eye(6))) < 1e-10
+    assert np.sum(s <= blocks.CANON_TAU * s.max()) == 3
+
+
+def test_canonical_route_with_duplicated_function_periodic():
+    """Periodic chain whose basis lists one GTO twice: every Fourier block
+    loses exactly one direction (+inf) and the kept spectrum equals the
+    original problem's, which itself has nothing removed and equals the
+    dense LAPACK spectrum (Prop. A.1)."""
+    p = _cases.periodic_chain_small(L=5, n0=6, n_perp=16, m0=4, R=12)
+    H, S = dense.build(p)
+    ev0, per0, kap0 = blocks.periodic_eigs(p, H, S)
+    assert np.all(np.isfinite(ev0))
+    assert np.max(np.abs(ev0 - dense.eigvals(H, S))) <= _cases.canon_tol(ev0, kap0)
+    q = _with_duplicate(p, 1)
+    ev1, per1, kap1 = blocks.periodic_eigs(q)
+    assert np.all(np.sum(np.isinf(per1), axis=1) == 1)
+    assert np.max(np.abs(np.sort(ev1[np.isfinite(ev1)]) - ev0)) <= _cases.canon_tol(ev0, kap0)
+
+
+def test_canonical_cell_basis_with_duplicated_function_box():
+    """Box chain whose basis lists one GTO twice: the cell basis loses one
+    direction and the lowest eigenvalues equal the original problem's
+    (nothing removed there, so also the dense LAPACK ones)."""
+    p = _cases.box_chain_small(L=6, n0=4, pad=4, n_perp=12, R=8, k=4, seed=3)
+    H, S = dense.build(p)
+    ev0, _, Sr0 = blocks.box_eigs(p, H, S)
+    assert blocks.box_basis(p)[1].shape[1] == p.m0
+    assert np.max(np.abs(ev0 - dense.eigvals(H, S, p.k_eig))) <= _cases.eig_tol(S, ev0)
+    q = _with_duplicate(p, 2)
+    assert blocks.box_basis(q)[1].shape[1] == p.m0
+    ev1, _, _ = blocks.box_eigs(q)
+    assert np.max(np.abs(ev1 - ev0)) <= _cases.eig_tol(Sr0, ev0)
+
+
+def test_cell_overlap_is_the_interior_diagonal_block():
+    """The cell overlap (Toeplitz generator T_S[0]) equals the dense overlap's
+    diagonal block of a cell whose functions reach neither wall."""
+    p = _cases.box_chain_small(L=5, n0=4, pad=80, n_perp=12, R=8, k=4, seed=1)
+    m0 = p.m0
+    S = dense.mass_kinetic(p)[0]
+    T0 = blocks.cell_overlap(p)
+    for k in range(p.L[0]):
+        assert np.max(np.abs(S[k * m0:(k + 1) * m0, k * m0:(k + 1) * m0] - T0)) <= 1e-14 * np.max(np.abs(S))
+
+
+def test_cell_reduction_is_variational():
+    """Removing cell directions restricts the trial space, so every reduced
+    eigenvalue lies at or above the full problem's (Courant-Fischer)."""
+    p = _cases.box_chain_small(L=8, n0=5, pad=6, n_perp=14, seed=2, R=12, k=6)
+    H, S = dense.build(p)
+    assert blocks.box_basis(p)[1].shape[1] < p.m0
+    full = dense.eigvals(H, S, p.k_eig)
+    red, _, _ = blocks.box_eigs(p, H, S)
+    assert np.all(red >= full - _cases.eig_tol(S, full))
