@@ -57,6 +57,65 @@ def config_dict(batch, world):
             "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (512 MB write)"}
 
 
+# --------------------------------------------------------------- serving
+def serving_requests(n, seed):
+    """Requests shaped like the serving mix (chains 4..256 cells and cubes
+    8..24^3, m0 in {4, 8, 16}, periodic or box); the library's default
+    quadrature rule."""
+    ps = li.serving_stream(n, seed=seed)
+    for p in ps:
+        p.defects = []
+    return ps
+
+
+def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plain_s=4.0):
+    """Continuous-batching leg: capacity from a burst of n_warm requests, then
+    n_stream requests with Poisson arrivals at 80 % of that capacity; latency
+    = done - submit per request (server clock).  Also the plain per-lattice
+    FP64 path (one fock_solve per request, sequential) on the same mix."""
+    srv = fock.Server(dev, slots=slots, max_batch=max_batch)
+    warm = serving_requests(n_warm, seed=3100)
+    t0 = time.perf_counter()
+    tk = [srv.submit(p) for p in warm]
+    rw = [srv.poll(t, timeout_ms=600000) for t in tk]
+    cap = n_warm / (time.perf_counter() - t0)
+    stream = serving_requests(n_stream, seed=3000)
+    rate = 0.8 * cap
+    gaps = np.random.default_rng(7).exponential(1.0 / rate, size=n_stream)
+    tickets = []
+    t0 = time.perf_counter()
+    nxt = t0
+    for p, g in zip(stream, gaps):
+        nxt += g
+        d = nxt - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(p))
+    res = [srv.poll(t, timeout_ms=600000) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.stop()
+    lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res])
+    ok = sum(r["status"] == 0 for r in res + rw)
+    # plain per-lattice FP64 path on the same mix, bounded by time
+    ctx = fock.Context(dev)
+    ctx.solve([stream[0]], check=False)
+    n_plain, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < plain_s and n_plain < len(stream):
+        ctx.solve([stream[n_plain]], check=False)
+        n_plain += 1
+    plain = n_plain / (time.perf_counter() - t1)
+    ctx.close()
+    return {"requests": n_stream, "arrival": f"Poisson at 80% of the burst capacity ({rate:.1f}/s)",
+            "throughput": n_stream / wall, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "burst_capacity": cap,
+            "plain_per_lattice_fp64": plain, "plain_sample": n_plain, "slots": slots,
+            "max_batch": max_batch, "batches": int(st["batches"]), "max_inflight": int(st["max_inflight"]),
+            "peak_reserved_bytes": int(st["peak_reserved_bytes"]), "status_ok": int(ok),
+            "mix": "chains 4..256 cells x1x1 (box or periodic) and periodic cubes 8,12,16,24^3; m0 4/8/16; "
+                   "n0 16, N_perp 256, R 32; no defects"}
+
+
 # --------------------------------------------------------------- CPU oracle
 def oracle_sample(npairs, seed0=0):
     """Time the CPU oracle on npairs (box, periodic) requests of the workload."""
@@ -206,6 +265,8 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default="")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -310,6 +371,8 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
                 "box_iters": [int(o["iters"]) for o in outs[:args.batch]][:8],
                 "statuses_nonzero": len(bad)}
+        if not args.no_serve:
+            line["serving"] = serving_run(fock, dev, n_stream=args.serve_requests)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
         print(json.dumps(line), flush=True)

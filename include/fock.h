@@ -210,6 +210,68 @@ int fock_profile_enable(fock_ctx* ctx, int on);
 int fock_profile_reset(fock_ctx* ctx);
 int fock_profile_read(fock_ctx* ctx, int cap, char* names, int* launches, double* ms);
 
+/* ---- serving: continuous batching of lattice problems on one GPU ----
+ *
+ * The paper solves one lattice at a time; this layer serves a stream of
+ * problems (different L, m0, periodic or box chains).  A server owns
+ * `slots` worker threads, each with a private CUDA stream, and one
+ * stream-ordered device memory pool.  Submitted problems are deep-copied,
+ * validated and sized, and queued in arrival order; a free worker admits
+ * the queue's head problems while the device bytes of the batches already
+ * in flight plus theirs stay within hbm_budget_bytes (and at most
+ * max_batch of them), solves them as one batch (fock_solve's path) and
+ * publishes one result per ticket.  Problems that arrive while batches
+ * run are admitted by the next free worker, so their kernels overlap with
+ * the batches in flight.  Each result equals the result of solving that
+ * problem alone (per-problem reduction orders and start vectors are fixed).
+ */
+typedef struct fock_server fock_server;
+typedef struct {
+  int slots;                /* concurrent batches (worker threads/streams); 0: 2, at most 16 */
+  int max_batch;            /* problems per batch; 0: 256 */
+  size_t hbm_budget_bytes;  /* device bytes for all batches in flight; 0: 80% of free memory */
+  double tol;               /* box eigensolver relative residual; <= 0: 1e-10 */
+  int maxit;                /* box eigensolver iteration cap; <= 0: 400 */
+} fock_serve_config;
+/* One request's result.  evals/block_of point into library-owned host
+ * memory that stays valid until fock_result_release(ticket) or
+ * fock_serve_stop.  Times are nanoseconds since fock_serve_start. */
+typedef struct {
+  const double* evals;      /* [n_evals] ascending (periodic: all |L| m0, +inf for removed
+                               directions; box: the k_eig lowest) */
+  const int* block_of;      /* [n_evals] Fourier index of each eigenvalue (periodic), else NULL */
+  int n_evals;
+  int status;               /* fock_status of this problem */
+  int iters;                /* box eigensolver iterations (0 periodic) */
+  double resid;             /* box: max relative residual */
+  int64_t t_submit_ns, t_admit_ns, t_done_ns;
+  int batch_id, batch_size; /* the batch the request was solved in */
+} fock_result;
+typedef struct {
+  uint64_t completed, pending, batches;
+  int inflight, max_inflight;            /* batches on the device now / at most so far */
+  size_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+} fock_serve_stats_t;
+/* Starts the workers on CUDA device `device`.  cfg may be NULL (defaults).
+ * Errors: FOCK_EINVAL, FOCK_ECUDA. */
+int fock_serve_start(int device, const fock_serve_config* cfg, fock_server** out);
+/* Queues a copy of *p (the caller may free p at once) and returns its ticket.
+ * Errors: FOCK_EINVAL (malformed problem, server stopping; message in
+ * fock_serve_last_error), FOCK_ENOMEM (the problem alone exceeds the budget).
+ * Thread-safe. */
+int fock_serve_submit(fock_server* s, const fock_problem* p, uint64_t* ticket);
+/* Waits up to timeout_ms (< 0: no limit, 0: no wait) for the ticket's result.
+ * FOCK_OK: *out filled (the problem's own status in out->status);
+ * FOCK_EAGAIN: not finished yet; FOCK_EINVAL: unknown ticket.  Thread-safe. */
+int fock_serve_poll(fock_server* s, uint64_t ticket, fock_result* out, int timeout_ms);
+/* Frees a finished ticket's result (FOCK_EAGAIN if it is still running). */
+int fock_result_release(fock_server* s, uint64_t ticket);
+int fock_serve_stats(fock_server* s, fock_serve_stats_t* out);
+const char* fock_serve_last_error(const fock_server* s);
+/* Finishes every queued problem, joins the workers, frees all device memory
+ * and every unreleased result. */
+int fock_serve_stop(fock_server* s);
+
 #ifdef __cplusplus
 }
 #endif

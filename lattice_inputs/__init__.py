@@ -218,13 +218,17 @@ def serving_stream(n_requests: int = 512, seed: int = 3000, n0: int = 16, n_perp
             Lv = (L, L, L)
             per = (1, 1, 1)
             N = (L * n0,) * 3
+        # lowest 16 eigenpairs, fewer on chains too short for 16 (the block
+        # iteration needs 3 (k + guard) <= L m0)
+        nb = Lv[0] * m0
+        k = 16 if nb >= 60 else max(1, nb // 5)
         p = Problem(L=Lv, periodic=per, N=N, n0=n0, b0=2.0, Z=np.array([1.0]),
                     frac=np.array([[0.5, 0.5, 0.5]]), exps=np.array(exps), ang=np.array(ang),
-                    centre=np.array(cen), R=R, k_eig=16 if box else 0)
+                    centre=np.array(cen), R=R, k_eig=k if box else 0)
         if chain:
             nd = int(rng.integers(0, 5))
             p.defects = random_defects(rng, Lv, 1, nd)
             if nd:
-                p.k_eig = 16
+                p.k_eig = k
         out.append(p)
     return out

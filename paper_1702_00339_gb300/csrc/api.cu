@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,7 @@ struct fock_ctx {
   size_t budget = 0;
   char* arena = nullptr;
   size_t arena_cap = 0;
+  cudaMemPool_t mempool = nullptr;   // serving workers: batches allocated stream-ordered from this pool
   std::string err;
   // kernel timers: events recorded around launches while enabled
   bool prof = false;
@@ -299,6 +301,7 @@ struct Batch {
   size_t bytes = 0;
   char* base = nullptr;
   bool own = false;                  // slab owned by the batch (fock_blocks)
+  cudaStream_t pooled = nullptr;     // slab allocated from a memory pool on this stream
   // device descriptors
   ProbDev* d_probs = nullptr;
   std::vector<ProbDev> probs;
@@ -585,8 +588,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Q.K = S.take<cplx>((size_t)Q.M * m2);
       Q.emin = S.take<double>(Q.M);
       Q.sigma = S.take<double>(1);
-      // banded Cholesky of H - sigma S when its one-CTA setup stays small
-      Q.use_band = 2.0 * Q.Lc * (double)Q.D * Q.D * (double)H.m0 * H.m0 * H.m0 <= 5e8;
+      // banded Cholesky of H - sigma S when its one-CTA factorisation stays
+      // within ~4 GFLOP (tens of ms); above that the circulant inverse
+      Q.use_band = 2.0 * Q.Lc * (double)Q.D * Q.D * (double)H.m0 * H.m0 * H.m0 <= 4e9;
       if (Q.use_band) {
         Q.band = S.take<double>((size_t)Q.Lc * (Q.D + 1) * m2);
         Q.sigma_band = S.take<double>(1);
@@ -809,7 +813,11 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
     return set_err(ctx, FOCK_ENOMEM, "batch needs " + std::to_string(need + uneed) + " bytes, budget " +
                                          std::to_string(ctx->budget));
   char *mb = nullptr, *ub = nullptr;
-  if (own) {
+  if (ctx->mempool) {
+    CUDA_TRY(ctx, cudaMallocFromPoolAsync((void**)&mb, need, ctx->mempool, ctx->stream));
+    CUDA_TRY(ctx, cudaMallocFromPoolAsync((void**)&ub, uneed, ctx->mempool, ctx->stream));
+    B.pooled = ctx->stream;
+  } else if (own) {
     CUDA_TRY(ctx, cudaMalloc(&mb, need));
     CUDA_TRY(ctx, cudaMalloc(&ub, uneed));
     B.own = true;
@@ -836,7 +844,10 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
 }
 
 void free_batch(Batch& B) {
-  if (B.own) {
+  if (B.pooled) {
+    cudaFreeAsync(B.base, B.pooled);
+    cudaFreeAsync(B.ubase, B.pooled);
+  } else if (B.own) {
     cudaFree(B.base);
     cudaFree(B.ubase);
   }
@@ -917,8 +928,8 @@ void gemm_nn(const Batch::TL& t, cudaStream_t st) {
 void rr(const Batch::TL& t, cudaStream_t st) {
   PROF("k_rr", 1);
   if (!t.n) return;
-  static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; }
+  static std::once_flag attr;
+  std::call_once(attr, [] { cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); });
   size_t sm = (size_t)3 * t.ga * t.ga * sizeof(double);
   if (sm > 160 * 1024) sm = 0;
   k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm);
@@ -1156,6 +1167,54 @@ int blocks_matvec_view(const fock_blocks* b, MatvecView* v) {
 }
 
 void set_ctx_error(fock_ctx* c, const char* msg) { if (c) c->err = msg; }
+}  // namespace fock
+
+// ------------------------------------------------------------------ serving hooks
+// Used by the serving loop (serve.cu): size estimate of one request, private
+// worker contexts that allocate from a shared pool, and one batched solve
+// with host outputs.
+namespace fock {
+
+int detail_estimate(const fock_problem& p, size_t* bytes, int* n_evals, std::string& why) {
+  Batch B;
+  B.nprob = 1;
+  B.hp.assign(1, HostProb());
+  B.ap.assign(3, AxisPlan());
+  int rc = validate(p, B.hp[0], why);
+  if (rc) return rc;
+  for (int a = 0; a < 3; ++a) axis_plan(B.hp[0], a, B.ap[a]);
+  Slab S0, U0;
+  plan(B, S0, U0);
+  *bytes = S0.off + U0.off + 512;
+  *n_evals = B.pp[0].nev;
+  return FOCK_OK;
+}
+
+fock_ctx* detail_worker_ctx(int device, cudaMemPool_t pool, size_t budget) {
+  if (cudaSetDevice(device) != cudaSuccess) return nullptr;
+  fock_ctx* c = new fock_ctx();
+  c->device = device;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return nullptr; }
+  c->own_stream = true;
+  c->mempool = pool;
+  c->budget = budget;
+  return c;
+}
+
+const char* detail_ctx_error(const fock_ctx* c) { return c->err.c_str(); }
+cudaStream_t detail_ctx_stream(const fock_ctx* c) { return c->stream; }
+
+int detail_solve(fock_ctx* w, int n, const fock_problem* probs, fock_output* outs, double tol, int maxit) {
+  fock_plan P;
+  P.ctx = w;
+  int rc = build_batch(w, n, probs, P.B, false);
+  if (rc == FOCK_OK) rc = plan_execute(P, tol, maxit);
+  if (rc == FOCK_OK || rc == FOCK_ENOCONV) rc = plan_outputs(P, outs, 0);
+  free_batch(P.B);
+  cudaStreamSynchronize(w->stream);
+  return rc;
+}
+
 }  // namespace fock
 
 extern "C" {

@@ -42,6 +42,24 @@ class c_problem(C.Structure):
                 ("defects", C.POINTER(c_defect)), ("k_eig", C.c_int), ("precision", C.c_int)]
 
 
+class c_serve_config(C.Structure):
+    _fields_ = [("slots", C.c_int), ("max_batch", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("tol", C.c_double), ("maxit", C.c_int)]
+
+
+class c_result(C.Structure):
+    _fields_ = [("evals", C.POINTER(C.c_double)), ("block_of", C.POINTER(C.c_int)),
+                ("n_evals", C.c_int), ("status", C.c_int), ("iters", C.c_int), ("resid", C.c_double),
+                ("t_submit_ns", C.c_int64), ("t_admit_ns", C.c_int64), ("t_done_ns", C.c_int64),
+                ("batch_id", C.c_int), ("batch_size", C.c_int)]
+
+
+class c_serve_stats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("pending", C.c_uint64), ("batches", C.c_uint64),
+                ("inflight", C.c_int), ("max_inflight", C.c_int), ("reserved_bytes", C.c_size_t),
+                ("peak_reserved_bytes", C.c_size_t), ("budget_bytes", C.c_size_t)]
+
+
 class c_output(C.Structure):
     _fields_ = [("evals", C.c_void_p), ("block_of", C.c_void_p), ("n_evals", C.c_int),
                 ("iters", C.c_int), ("resid", C.c_double), ("status", C.c_int)]
@@ -92,6 +110,14 @@ def lib():
         L.fock_profile_enable.argtypes = [C.c_void_p, C.c_int]
         L.fock_profile_reset.argtypes = [C.c_void_p]
         L.fock_profile_read.argtypes = [C.c_void_p, C.c_int, C.c_char_p, P(C.c_int), P(C.c_double)]
+        L.fock_serve_start.argtypes = [C.c_int, P(c_serve_config), P(C.c_void_p)]
+        L.fock_serve_submit.argtypes = [C.c_void_p, P(c_problem), P(C.c_uint64)]
+        L.fock_serve_poll.argtypes = [C.c_void_p, C.c_uint64, P(c_result), C.c_int]
+        L.fock_result_release.argtypes = [C.c_void_p, C.c_uint64]
+        L.fock_serve_stats.argtypes = [C.c_void_p, P(c_serve_stats)]
+        L.fock_serve_last_error.argtypes = [C.c_void_p]
+        L.fock_serve_last_error.restype = C.c_char_p
+        L.fock_serve_stop.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -390,3 +416,68 @@ class Plan:
         self.h = C.c_void_p()
 
     __del__ = close
+
+
+class Server:
+    """Continuous-batching server (fock_serve_*): submit problems from any
+    thread, poll tickets for results."""
+
+    def __init__(self, device=0, slots=2, max_batch=256, budget_bytes=0, tol=1e-10, maxit=400):
+        cfg = c_serve_config(int(slots), int(max_batch), C.c_size_t(budget_bytes), float(tol), int(maxit))
+        self.h = C.c_void_p()
+        rc = lib().fock_serve_start(int(device), C.byref(cfg), C.byref(self.h))
+        if rc:
+            raise FockError(rc, "fock_serve_start")
+
+    def _err(self):
+        return lib().fock_serve_last_error(self.h).decode()
+
+    def submit(self, p):
+        m = _Marshal(p)
+        t = C.c_uint64()
+        rc = lib().fock_serve_submit(self.h, C.byref(m.s), C.byref(t))
+        if rc:
+            raise FockError(rc, f"fock_serve_submit: {self._err()}")
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1, release=True):
+        """The ticket's result as a dict, or None if not finished within
+        timeout_ms.  Copies the eigenvalues out and (by default) releases the
+        library's buffers."""
+        r = c_result()
+        rc = lib().fock_serve_poll(self.h, C.c_uint64(ticket), C.byref(r), int(timeout_ms))
+        if rc == FOCK_EAGAIN:
+            return None
+        if rc:
+            raise FockError(rc, f"fock_serve_poll: {self._err()}")
+        n = r.n_evals
+        out = {"evals": np.ctypeslib.as_array(r.evals, (n,)).copy() if n else np.zeros(0),
+               "block_of": (np.ctypeslib.as_array(r.block_of, (n,)).copy() if r.block_of else None),
+               "status": r.status, "iters": r.iters, "resid": r.resid,
+               "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns,
+               "batch_id": r.batch_id, "batch_size": r.batch_size}
+        if release:
+            lib().fock_result_release(self.h, C.c_uint64(ticket))
+        return out
+
+    def stats(self):
+        s = c_serve_stats()
+        rc = lib().fock_serve_stats(self.h, C.byref(s))
+        if rc:
+            raise FockError(rc, "fock_serve_stats")
+        return {f: getattr(s, f) for f, _ in c_serve_stats._fields_}
+
+    def stop(self):
+        if self.h:
+            rc = lib().fock_serve_stop(self.h)
+            self.h = C.c_void_p()
+            if rc:
+                raise FockError(rc, "fock_serve_stop")
+
+    close = stop
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

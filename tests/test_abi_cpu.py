@@ -65,3 +65,16 @@ def test_sinc_table_rejects_bad_arguments(libpath):
         fock.sinc_table(2, 1e-3, 1.0)
     with pytest.raises(fock.FockError):
         fock.sinc_table(16, 1.0, 0.5)
+
+
+def test_serve_start_without_a_device_fails_cleanly(libpath):
+    """Host-only: with no usable CUDA device the server refuses to start
+    (FOCK_ECUDA) instead of crashing."""
+    import ctypes as C
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1702_00339_gb300 import fock
+    h = C.c_void_p()
+    rc = fock.lib().fock_serve_start(0, None, C.byref(h))
+    assert rc == fock.FOCK_ECUDA and not h.value
