@@ -47,7 +47,7 @@ void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t);
 void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
 void launch_eapply(const EApplyTask*, int, cudaStream_t);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
-void launch_band_solve(const BandTask*, int, cudaStream_t);
+void launch_band_solve(const BandTask*, int, int, cudaStream_t);
 void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
 void launch_cell_back(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 __global__ void k_init_x(const InitTask*);
@@ -1055,7 +1055,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     if (!any || it >= maxit) break;
     if (changed) CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, active.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
     // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
-    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, st); }
+    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, st); }
     if (B.fwdR.n) {
       mv_fwd(B, B.fwdR, st);
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st); }

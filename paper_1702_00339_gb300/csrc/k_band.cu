@@ -11,8 +11,11 @@
 //  k_band_factor  one CTA per problem: fill the band from T and E, factor it
 //                 block column by block column; on a non-positive pivot lower
 //                 sigma and start again (at most 4 attempts)
-//  k_band_solve   one CTA per problem: forward and back substitution for the
-//                 k columns of R
+//                 (the diagonal slots then hold L_JJ^-1, which the solve
+//                 applies as a mat-vec)
+//  k_band_solve   forward and back substitution for the k columns of R;
+//                 the columns of a problem are spread over several CTAs
+//                 (they are independent), the D-term sums over threads
 #include "common.cuh"
 
 namespace fock {
@@ -26,6 +29,7 @@ __device__ inline double* bblk(double* band, int D, int m2, int J, int d) {
 __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
   const BandTask T = tasks[blockIdx.x];
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L;
+  __shared__ double inv[MAXM0 * MAXM0];
   __shared__ int bad;
   __shared__ double s_sigma;
   if (threadIdx.x == 0) s_sigma = *T.sigma0;
@@ -82,6 +86,17 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
         }
       }
       __syncthreads();
+      // L_JJ^-1 (lower) into the diagonal slot: column c by forward substitution
+      for (int c = threadIdx.x; c < m0; c += blockDim.x) {
+        for (int i = 0; i < m0; ++i) {
+          double s = (i == c) ? 1.0 : 0.0;
+          if (i >= c)
+            for (int q = c; q < i; ++q) s -= Ajj[i * m0 + q] * inv[q * m0 + c];
+          inv[i * m0 + c] = (i >= c) ? s / Ajj[i * m0 + i] : 0.0;
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < m2; e += blockDim.x) Ajj[e] = inv[e];
       // trailing update: block (J+d1, J+d2) -= L[J+d1][J] L[J+d2][J]^T, 1 <= d2 <= d1 <= dmax
       const int npair = dmax * (dmax + 1) / 2;
       for (int it = threadIdx.x; it < npair * m2; it += blockDim.x) {
@@ -111,59 +126,83 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
   }
 }
 
-// W = (L L^T)^-1 R for the k columns (thread per (row in block, column)).
+// W = (L L^T)^-1 R.  blockIdx.y picks a group of kBandCols columns; a work
+// item is (row mu of the block, column), and the nsplit threads of an item
+// share its sum over the D off-diagonal blocks (partial sums reduced in
+// shared memory).  The diagonal slots hold L_JJ^-1.
+constexpr int kBandCols = 4;
+
 __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
   const BandTask T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
-  const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L, k = T.k, ld = T.ld;
-  double* band = const_cast<double*>(T.band);
+  const int c0 = blockIdx.y * kBandCols;
+  if (c0 >= T.k) return;
+  const int nc = min(kBandCols, T.k - c0);
+  const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L, ld = T.ld;
+  const double* band = T.band;
+  __shared__ double part[256];
+  __shared__ double tv[MAXM0 * kBandCols];
+  const int items = m0 * nc;
+  const int nsplit = max(1, min((int)blockDim.x / items, 8));
+  const int tid = threadIdx.x;
+  const int item = tid % items, sp = tid / items;
+  const bool on = sp < nsplit;
+  const int mu = item % m0, c = c0 + item / m0;
+  double* Wc = T.W + (size_t)ld * c;
+  const double* Rc = T.R + (size_t)ld * c;
   // forward: y_J = L_JJ^-1 (r_J - sum_d L[J][J-d] y_{J-d})
   for (int J = 0; J < L; ++J) {
-    for (int it = threadIdx.x; it < m0 * k; it += blockDim.x) {
-      int mu = it % m0, c = it / m0;
-      double s = T.R[(size_t)(J * m0 + mu) + (size_t)ld * c];
+    double s = 0.0;
+    if (on) {
       const int dmax = min(D, J);
-      for (int d = 1; d <= dmax; ++d) {
-        const double* l = bblk(band, D, m2, J - d, d) + mu * m0;   // block (J, J-d)
-        const double* y = T.W + (size_t)((J - d) * m0) + (size_t)ld * c;
-        for (int q = 0; q < m0; ++q) s += -l[q] * y[q];
+      for (int d = 1 + sp; d <= dmax; d += nsplit) {
+        const double* l = bblk(const_cast<double*>(band), D, m2, J - d, d) + mu * m0;   // block (J, J-d)
+        const double* y = Wc + (size_t)((J - d) * m0);
+        for (int q = 0; q < m0; ++q) s -= l[q] * y[q];
       }
-      T.W[(size_t)(J * m0 + mu) + (size_t)ld * c] = s;
+      part[tid] = s;
     }
     __syncthreads();
-    const double* Ljj = bblk(band, D, m2, J, 0);
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      double* y = T.W + (size_t)(J * m0) + (size_t)ld * c;
-      for (int mu = 0; mu < m0; ++mu) {
-        double s = y[mu];
-        for (int q = 0; q < mu; ++q) s -= Ljj[mu * m0 + q] * y[q];
-        y[mu] = s / Ljj[mu * m0 + mu];
-      }
+    if (on && sp == 0) {
+      double r = Rc[(size_t)(J * m0 + mu)];
+      for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
+      tv[item] = r;
+    }
+    __syncthreads();
+    if (on && sp == 0) {
+      const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0) + mu * m0;
+      const int cb = (item / m0) * m0;
+      double y = 0.0;
+      for (int q = 0; q <= mu; ++q) y += iv[q] * tv[cb + q];
+      Wc[(size_t)(J * m0 + mu)] = y;
     }
     __syncthreads();
   }
   // backward: x_J = L_JJ^-T (y_J - sum_d L[J+d][J]^T x_{J+d})
   for (int J = L - 1; J >= 0; --J) {
-    for (int it = threadIdx.x; it < m0 * k; it += blockDim.x) {
-      int mu = it % m0, c = it / m0;
-      double s = T.W[(size_t)(J * m0 + mu) + (size_t)ld * c];
+    double s = 0.0;
+    if (on) {
       const int dmax = min(D, L - 1 - J);
-      for (int d = 1; d <= dmax; ++d) {
-        const double* l = bblk(band, D, m2, J, d);   // block (J+d, J): column mu
-        const double* x = T.W + (size_t)((J + d) * m0) + (size_t)ld * c;
+      for (int d = 1 + sp; d <= dmax; d += nsplit) {
+        const double* l = bblk(const_cast<double*>(band), D, m2, J, d);   // block (J+d, J): column mu
+        const double* x = Wc + (size_t)((J + d) * m0);
         for (int q = 0; q < m0; ++q) s -= l[q * m0 + mu] * x[q];
       }
-      T.W[(size_t)(J * m0 + mu) + (size_t)ld * c] = s;
+      part[tid] = s;
     }
     __syncthreads();
-    const double* Ljj = bblk(band, D, m2, J, 0);
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      double* x = T.W + (size_t)(J * m0) + (size_t)ld * c;
-      for (int mu = m0 - 1; mu >= 0; --mu) {
-        double s = x[mu];
-        for (int q = mu + 1; q < m0; ++q) s -= Ljj[q * m0 + mu] * x[q];
-        x[mu] = s / Ljj[mu * m0 + mu];
-      }
+    if (on && sp == 0) {
+      double r = Wc[(size_t)(J * m0 + mu)];
+      for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
+      tv[item] = r;
+    }
+    __syncthreads();
+    if (on && sp == 0) {
+      const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0);
+      const int cb = (item / m0) * m0;
+      double x = 0.0;
+      for (int q = mu; q < m0; ++q) x += iv[q * m0 + mu] * tv[cb + q];
+      Wc[(size_t)(J * m0 + mu)] = x;
     }
     __syncthreads();
   }
@@ -172,8 +211,8 @@ __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
 void launch_band_factor(const BandTask* t, int n, cudaStream_t st) {
   if (n) k_band_factor<<<n, 256, 0, st>>>(t);
 }
-void launch_band_solve(const BandTask* t, int n, cudaStream_t st) {
-  if (n) k_band_solve<<<n, 256, 0, st>>>(t);
+void launch_band_solve(const BandTask* t, int n, int kmax, cudaStream_t st) {
+  if (n) k_band_solve<<<dim3(n, (kmax + kBandCols - 1) / kBandCols), 256, 0, st>>>(t);
 }
 
 }  // namespace fock
