@@ -59,13 +59,10 @@ def config_dict(batch, world):
 
 # --------------------------------------------------------------- serving
 def serving_requests(n, seed):
-    """Requests shaped like the serving mix (chains 4..256 cells and cubes
-    8..24^3, m0 in {4, 8, 16}, periodic or box); the library's default
-    quadrature rule."""
-    ps = li.serving_stream(n, seed=seed)
-    for p in ps:
-        p.defects = []
-    return ps
+    """Requests shaped like the serving mix (chains 4..256 cells with 0-4
+    vacancy / substitution defects, cubes 8..24^3, m0 in {4, 8, 16}, periodic
+    or box); the library's default quadrature rule."""
+    return li.serving_stream(n, seed=seed)
 
 
 def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plain_s=4.0):
@@ -97,6 +94,11 @@ def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plai
     srv.stop()
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res])
     ok = sum(r["status"] == 0 for r in res + rw)
+    fails = [{"stream": nm, "i": i, "status": r["status"], "L": list(p.L), "periodic": list(p.periodic),
+              "m0": len(p.exps), "k": p.k_eig, "iters": r["iters"], "resid": r["resid"],
+              "batch_size": r["batch_size"]}
+             for nm, ps_, rs_ in (("warm", warm, rw), ("stream", stream, res))
+             for i, (p, r) in enumerate(zip(ps_, rs_)) if r["status"] != 0][:8]
     # plain per-lattice FP64 path on the same mix, bounded by time
     ctx = fock.Context(dev)
     ctx.solve([stream[0]], check=False)
@@ -112,8 +114,9 @@ def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plai
             "plain_per_lattice_fp64": plain, "plain_sample": n_plain, "slots": slots,
             "max_batch": max_batch, "batches": int(st["batches"]), "max_inflight": int(st["max_inflight"]),
             "peak_reserved_bytes": int(st["peak_reserved_bytes"]), "status_ok": int(ok),
+            "failures": fails,
             "mix": "chains 4..256 cells x1x1 (box or periodic) and periodic cubes 8,12,16,24^3; m0 4/8/16; "
-                   "n0 16, N_perp 256, R 32; no defects"}
+                   "n0 16, N_perp 256, R 32; 0-4 defects per chain"}
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -224,7 +227,7 @@ def fp64_flops_per_step(problems, outs):
     w = {}
     for p, o in zip(problems, outs):
         m0 = len(p.exps)
-        if p.is_box:
+        if p.is_box or p.defects:
             k = p.k_eig
             n = p.L[0] * m0
             it = max(o["iters"], 1)

@@ -192,28 +192,35 @@ def periodic_eigs(p, H=None, S=None, tau=CANON_TAU):
 
 
 def cell_overlap(p):
-    """Overlap of one cell's basis with itself as an interior cell of a box
-    chain sees it (the Toeplitz generator T_S[0], Remark 3.2): axis 0 on a
-    node line long enough that no wall reaches the cell's functions, the
-    single-cell transverse axes as they are.  Product of the 1D mass forms."""
-    rmax = np.sqrt(np.log(1.0 / p.eps_support) / np.min(p.exps))
-    pe = int(np.ceil(rmax / p.h)) + 2
-    q = type(p)(L=(1, p.L[1], p.L[2]), periodic=(0, p.periodic[1], p.periodic[2]),
-                N=(p.n0 + 2 * pe, p.N[1], p.N[2]), n0=p.n0, b0=p.b0, Z=p.Z, frac=p.frac,
-                exps=p.exps, ang=p.ang, centre=p.centre, R=p.R, eps_support=p.eps_support)
+    """Overlap of one cell's basis with itself as the structured (chain)
+    solve sees it: for a box chain the interior cell of the Toeplitz
+    generator T_S[0] (Remark 3.2) -- axis 0 on a node line long enough that no
+    wall reaches the cell's functions; for a periodic chain the periodic
+    diagonal block A_0 of S on its own ring.  The single-cell transverse axes
+    as they are.  Product of the 1D mass forms."""
+    if p.periodic[0]:
+        q = p
+    else:
+        rmax = np.sqrt(np.log(1.0 / p.eps_support) / np.min(p.exps))
+        pe = int(np.ceil(rmax / p.h)) + 2
+        q = type(p)(L=(1, p.L[1], p.L[2]), periodic=(0, p.periodic[1], p.periodic[2]),
+                    N=(p.n0 + 2 * pe, p.N[1], p.N[2]), n0=p.n0, b0=p.b0, Z=p.Z, frac=p.frac,
+                    exps=p.exps, ang=p.ang, centre=p.centre, R=p.R, eps_support=p.eps_support)
     (_, s0, _), (_, s1, _), (_, s2, _) = dense.axis_forms(q)
     return s0[0, :, 0, :] * s1[0, :, 0, :] * s2[0, :, 0, :]
 
 
 def box_basis(p, tau=CANON_TAU):
-    """Block-diagonal change of basis of a box chain: the canonical cell
-    basis Xc = lowdin_basis(cell_overlap) on every cell, I_L (x) Xc."""
+    """Block-diagonal change of basis of a chain on the structured path: the
+    canonical cell basis Xc = lowdin_basis(cell_overlap) on every cell,
+    I_L (x) Xc."""
     Xc, _ = lowdin_basis(cell_overlap(p), tau)
     return np.kron(np.eye(p.L[0]), Xc), Xc
 
 
 def box_eigs(p, H=None, S=None, k=None, tau=CANON_TAU, vectors=False):
-    """Lowest k eigenpairs of a box chain in the canonical cell basis:
+    """Lowest k eigenpairs of a chain on the structured path (box, or with
+    defects) in the canonical cell basis:
     (Xb^T H Xb) y = lambda (Xb^T S Xb) y by LAPACK, eigenvectors Xb y in the
     original coordinates.  Returns (eigenvalues, vectors or None, reduced S)."""
     if H is None:
@@ -226,11 +233,17 @@ def box_eigs(p, H=None, S=None, k=None, tau=CANON_TAU, vectors=False):
     return ev, (Xb @ Y if vectors else None), Sr
 
 
+def structured(p):
+    """Box chains and problems with defects take the lowest-k structured
+    solve; defect-free periodic lattices the Fourier-block route."""
+    return bool(p.is_box or p.defects)
+
+
 def solve(p):
     """The problem's answer under the canonical-orthogonalisation reading:
     a periodic problem's whole spectrum (+inf for removed directions), a box
-    chain's lowest k_eig eigenvalues."""
+    chain's or a defect problem's lowest k_eig eigenvalues."""
     H, S = dense.build(p)
-    if p.is_box:
+    if structured(p):
         return box_eigs(p, H, S)[0]
     return periodic_eigs(p, H, S)[0]

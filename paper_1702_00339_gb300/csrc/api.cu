@@ -37,6 +37,7 @@ namespace fock {
 void launch_vec1d(const ProbDev*, const SegDesc*, int, const SegDesc*, int, const DefTab*, int, cudaStream_t);
 void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream_t);
 void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
+void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
 void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
 void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
@@ -45,7 +46,8 @@ void launch_sort_global(double*, int*, int, double*, int*, cudaStream_t);
 void launch_twiddles(CircDev*, int, cudaStream_t);
 void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t);
 void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
-void launch_eapply(const EApplyTask*, int, cudaStream_t);
+void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
+int eapply_grid(long long items);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
 void launch_band_solve(const BandTask*, int, int, cudaStream_t);
 void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
@@ -138,6 +140,8 @@ struct HostProb {
   std::vector<int> ang, centre;
   int k_eig;
   int kind;            // 0 periodic (circulant eigensolve), 1 structured iteration
+  int pchain = 0;      // structured path of a periodic chain (defects on a periodic axis 0)
+  std::vector<fock_defect> defs;
 };
 
 // Guard vectors of the block iteration: k + g columns are iterated and the k
@@ -150,7 +154,7 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (p.M0 < 1 || p.M0 > 8 || !p.Z || !p.frac) { why = "1 <= M0 <= 8 with Z and frac"; return FOCK_EINVAL; }
   if (p.m0 < 1 || p.m0 > MAXM0 || !p.exps || !p.ang || !p.centre) { why = "1 <= m0 <= 32 with exps/ang/centre"; return FOCK_EINVAL; }
   if (p.R < 3 || p.R > MAXR) { why = "3 <= R <= 64"; return FOCK_EINVAL; }
-  if (p.ndef != 0) { why = "defects are not supported by this build"; return FOCK_EINVAL; }
+  if (p.ndef < 0 || (p.ndef > 0 && !p.defects)) { why = "ndef >= 0 with a defects array"; return FOCK_EINVAL; }
   H.n0 = p.n0; H.b0 = p.b0; H.h = p.b0 / p.n0;
   H.eps = (p.eps_support > 0.0) ? p.eps_support : 1e-14;
   int nlong = 0;
@@ -162,10 +166,22 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
     if (!H.per[a] && p.N[a] < p.L[a] * p.n0) { why = "Dirichlet axis needs N >= L*n0"; return FOCK_EINVAL; }
     if (p.L[a] > 1) { ++nlong; if (!H.per[a]) dir_long = true; }
   }
-  H.kind = dir_long ? 1 : 0;
+  H.kind = (dir_long || p.ndef > 0) ? 1 : 0;
   if (H.kind == 1 && (nlong > 1 || p.L[0] == 1)) {
-    why = "box problems must be chains along axis 0 (L2 = L3 = 1)";
+    why = "box problems and problems with defects must be chains along axis 0 (L1 >= 2, L2 = L3 = 1)";
     return FOCK_EINVAL;
+  }
+  H.pchain = (H.kind == 1 && H.per[0]) ? 1 : 0;
+  if (p.ndef > 0) {
+    if (p.periodic[1] || p.periodic[2]) { why = "defects need Dirichlet transverse axes"; return FOCK_EINVAL; }
+    if (p.ndef > 64) { why = "at most 64 defects"; return FOCK_EINVAL; }
+    H.defs.assign(p.defects, p.defects + p.ndef);
+    for (const fock_defect& d : H.defs) {
+      if (d.cell[0] < 0 || d.cell[0] >= p.L[0] || d.cell[1] != 0 || d.cell[2] != 0 ||
+          d.nucleus < 0 || d.nucleus >= p.M0 || !std::isfinite(d.newZ)) {
+        why = "defect cell / nucleus out of range or newZ not finite"; return FOCK_EINVAL;
+      }
+    }
   }
   H.M0 = p.M0; H.m0 = p.m0; H.R = p.R; H.T = p.M0 * p.R; H.nF = H.T + 2;
   H.Z.assign(p.Z, p.Z + p.M0);
@@ -216,8 +232,11 @@ uint64_t problem_seed(const HostProb& H) {
   mix(H.alpha.data(), H.alpha.size() * 8); mix(H.Z.data(), H.Z.size() * 8);
   mix(H.frac.data(), H.frac.size() * 8); mix(H.ang.data(), H.ang.size() * 4);
   mix(H.centre.data(), H.centre.size() * 4); mix(H.tq.data(), H.tq.size() * 8);
+  for (const fock_defect& d : H.defs) { mix(d.cell, sizeof(d.cell)); mix(&d.nucleus, 4); mix(&d.newZ, 8); }
   return h;
 }
+
+inline int posmod_h(int a, int b) { int r = a % b; return r < 0 ? r + b : r; }
 
 // smallest 2^a 3^b 5^c >= n
 int smooth_at_least(int n) {
@@ -309,6 +328,9 @@ struct Batch {
   SegDesc *d_gsegs = nullptr, *d_psegs = nullptr;
   std::vector<GramTask> gram; GramTask* d_gram = nullptr;
   std::vector<CombineTask> combT, combE; CombineTask *d_combT = nullptr, *d_combE = nullptr;
+  std::vector<DefTab> dtabs; DefTab* d_dtabs = nullptr;
+  std::vector<DefField> dfields; DefField* d_dfields = nullptr;
+  std::vector<DefBlock> dblocks; DefBlock* d_dblocks = nullptr;
   std::vector<DftTask> dft; DftTask* d_dft = nullptr; int maxLdft = 1;
   std::vector<FBlockTask> fbp, fbs; FBlockTask *d_fbp = nullptr, *d_fbs = nullptr;
   int maxnj_p = 0, maxnj_s = 0, maxm0 = 1;
@@ -331,6 +353,11 @@ struct Batch {
     double *TH = nullptr, *TS = nullptr;
     int nE = 0;
     std::vector<int> Ek, Em;          // (row cell, column cell) of each boundary block
+    // source of each E entry: 0 wall block (gram index Esrc), 1 periodic wrap
+    // block (ring offset Esrc), 2 defect block
+    std::vector<int> Ekind, Esrc;
+    std::vector<double*> ringX;       // periodic chain: forms of each ring offset (or null)
+    std::vector<double*> defD1, defD2; // per defect: transverse forms [R][m0^2]
     double *EH = nullptr, *ES = nullptr;
     int *Erows = nullptr, *Erowptr = nullptr, *Ecols = nullptr; int nErows = 0;
     cplx *CH = nullptr, *CS = nullptr, *K = nullptr;
@@ -363,6 +390,7 @@ struct Batch {
   TL bandF, bandS;
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid;
   int fft_cc = 1, fft_chunks = 1;
+  int eapply_gx = 16;
   int* d_ones = nullptr;
   int* d_active = nullptr;
   int* d_fail = nullptr;
@@ -380,6 +408,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.probs.assign(np, ProbDev());
   B.pp.assign(np, Batch::PerProb());
   B.gsegs.clear(); B.psegs.clear(); B.gram.clear(); B.combT.clear(); B.combE.clear();
+  B.dtabs.clear(); B.dfields.clear(); B.dblocks.clear();
   B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
@@ -434,9 +463,29 @@ void plan(Batch& B, Slab& S, Slab& U) {
       };
       if (H.per[a]) {
         Q.ntask_axis[a] = (int)A.offs.size();
+        if (a == 0 && H.pchain) Q.ringX.assign(L, nullptr);
         for (size_t o = 0; o < A.offs.size(); ++o) {
           int ti = add(RING, A.offs[o], 0, 0, N, n0, 0);
           if (o == 0) Q.X[a] = B.gram[ti].X;
+          if (a == 0 && H.pchain) Q.ringX[A.offs[o]] = B.gram[ti].X;
+        }
+        if (a == 0 && H.pchain) {
+          // periodic chain on the structured path: generators A_d, d <= Dp, as
+          // a Toeplitz band plus the wrap-around corner blocks; a chain too
+          // short for the two to separate is its whole circulant as Toeplitz
+          int Dp = 0;
+          for (int d : A.offs) if (2 * d <= L) Dp = std::max(Dp, d);
+          Q.Lc = L;
+          Q.D = (L > 2 * Dp + 1) ? Dp : L - 1;
+          Q.Ek.clear(); Q.Em.clear(); Q.Ekind.clear(); Q.Esrc.clear();
+          if (Q.D < L - 1)
+            for (int k = 0; k < L; ++k)
+              for (int m = 0; m < L; ++m) {
+                int dd = posmod_h(k - m, L);
+                if (std::abs(k - m) > Q.D && Q.ringX[dd]) {
+                  Q.Ek.push_back(k); Q.Em.push_back(m); Q.Ekind.push_back(1); Q.Esrc.push_back(dd);
+                }
+              }
         }
       } else if (L == 1) {
         int r0 = std::max(-A.pad, A.jlo - 1), r1 = std::min(N - A.pad, A.jlo + A.W + 1);
@@ -457,20 +506,97 @@ void plan(Batch& B, Slab& S, Slab& U) {
         std::vector<char> aff(L, 0);
         for (int k = 0; k < L; ++k)
           aff[k] = (k * n0 + A.jmin - 2 < 0) || (k * n0 + A.jmax + 2 > L * n0 - 1);
-        Q.Ek.clear(); Q.Em.clear();
+        Q.Ek.clear(); Q.Em.clear(); Q.Ekind.clear(); Q.Esrc.clear();
         for (int k = 0; k < L; ++k)
           for (int m = std::max(0, k - D); m <= std::min(L - 1, k + D); ++m)
-            if (aff[k] && aff[m]) { Q.Ek.push_back(k); Q.Em.push_back(m); }
-        Q.nE = (int)Q.Ek.size();
-        for (int e = 0; e < Q.nE; ++e) {
-          int k = Q.Ek[e], m = Q.Em[e];
-          int lo = std::max(A.jlo + k * n0, A.jlo + m * n0) - 1;
-          int hi = std::min(A.jlo + A.W + k * n0, A.jlo + A.W + m * n0) + 1;
-          lo = std::max(lo, -A.pad); hi = std::min(hi, N - A.pad);
-          add(WALL, k, m, lo, hi, A.nr, A.rlo);
-        }
+            if (aff[k] && aff[m]) {
+              int lo = std::max(A.jlo + k * n0, A.jlo + m * n0) - 1;
+              int hi = std::min(A.jlo + A.W + k * n0, A.jlo + A.W + m * n0) + 1;
+              lo = std::max(lo, -A.pad); hi = std::min(hi, N - A.pad);
+              int ti = add(WALL, k, m, lo, hi, A.nr, A.rlo);
+              Q.Ek.push_back(k); Q.Em.push_back(m); Q.Ekind.push_back(0); Q.Esrc.push_back(ti);
+            }
       }
     }
+  }
+  // ---- defects (reading R-DEF): tables, transverse forms, E entries ----
+  for (int i = 0; i < np; ++i) {
+    const HostProb& H = B.hp[i];
+    Batch::PerProb& Q = B.pp[i];
+    if (H.defs.empty()) continue;
+    const int m2 = H.m0 * H.m0, n0 = H.n0, L = H.L[0];
+    const AxisPlan& A0 = B.ap[i * 3 + 0];
+    Q.defD1.clear(); Q.defD2.clear();
+    std::vector<DefRef> refs;
+    for (const fock_defect& d : H.defs) {
+      DefRef rf;
+      DefTab t0;
+      t0.prob = i; t0.axis = 0; t0.N = H.N[0]; t0.pad = A0.pad;
+      t0.pos = ((double)d.cell[0] + H.frac[d.nucleus * 3 + 0]) * n0;
+      t0.e = S.take<double>((size_t)H.R * H.N[0]);
+      B.dtabs.push_back(t0);
+      rf.e = t0.e;
+      rf.dz = d.newZ - H.Z[d.nucleus];
+      for (int a = 1; a <= 2; ++a) {
+        const AxisPlan& A = B.ap[i * 3 + a];
+        DefTab ta;
+        ta.prob = i; ta.axis = a; ta.N = H.N[a]; ta.pad = A.pad;
+        ta.pos = H.frac[d.nucleus * 3 + a] * n0;
+        ta.e = S.take<double>((size_t)H.R * H.N[a]);
+        B.dtabs.push_back(ta);
+        GramTask g;
+        g.prob = i; g.axis = a; g.mode = WALL; g.a = 0; g.b = 0;
+        g.rho0 = std::max(-A.pad, A.jlo - 1); g.rho1 = std::min(H.N[a] - A.pad, A.jlo + A.W + 1);
+        g.ptab = (int)B.dtabs.size() - 1;
+        g.nfold = g.rho1 - g.rho0; g.foldlo = g.rho0;
+        g.X = S.take<double>((size_t)H.R * m2);
+        g.Zs = nullptr;
+        zs_total += (size_t)g.nfold * m2;
+        B.gram.push_back(g);
+        (a == 1 ? rf.D1 : rf.D2) = g.X;
+      }
+      refs.push_back(rf);
+    }
+    DefField f;
+    f.prob = i; f.N = H.N[0]; f.ndef = (int)refs.size(); f.refs = U.put(refs);
+    f.F = S.take<double>((size_t)H.N[0] * m2);
+    B.dfields.push_back(f);
+    // a defect block on every pair of cells whose functions overlap
+    const bool ring = H.pchain;
+    const int span = A0.jmax - A0.jmin + 1;
+    for (int k = 0; k < L; ++k)
+      for (int m = 0; m < L; ++m) {
+        bool pair = ring ? (Q.ringX[posmod_h(k - m, L)] != nullptr) : (std::abs(k - m) <= Q.D);
+        if (!pair) continue;
+        DefBlock b;
+        b.prob = i; b.mode = ring ? RING : WALL; b.a = k; b.b = m; b.F = f.F;
+        if (ring) {
+          b.pad = 0;
+          if (span >= H.N[0]) { b.rho0 = 0; b.rho1 = H.N[0]; }
+          else { b.rho0 = k * n0 + A0.jmin; b.rho1 = k * n0 + A0.jmax + 1; }
+        } else {
+          b.pad = A0.pad;
+          b.rho0 = std::max(std::max(A0.jlo + k * n0, A0.jlo + m * n0), -A0.pad);
+          b.rho1 = std::min(std::min(A0.jlo + A0.W + k * n0, A0.jlo + A0.W + m * n0), H.N[0] - A0.pad);
+        }
+        b.outH = b.outS = nullptr;   // set once the E storage exists
+        Q.Ek.push_back(k); Q.Em.push_back(m); Q.Ekind.push_back(2); Q.Esrc.push_back((int)B.dblocks.size());
+        B.dblocks.push_back(b);
+      }
+  }
+  // E entries grouped by block row (stable: the boundary/wrap block of a position precedes its defect block)
+  for (int i = 0; i < np; ++i) {
+    Batch::PerProb& Q = B.pp[i];
+    const size_t n = Q.Ek.size();
+    std::vector<size_t> ord(n);
+    for (size_t e = 0; e < n; ++e) ord[e] = e;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+      return Q.Ek[x] != Q.Ek[y] ? Q.Ek[x] < Q.Ek[y] : Q.Em[x] < Q.Em[y];
+    });
+    std::vector<int> k2(n), m2v(n), kd(n), sr(n);
+    for (size_t e = 0; e < n; ++e) { k2[e] = Q.Ek[ord[e]]; m2v[e] = Q.Em[ord[e]]; kd[e] = Q.Ekind[ord[e]]; sr[e] = Q.Esrc[ord[e]]; }
+    Q.Ek = k2; Q.Em = m2v; Q.Ekind = kd; Q.Esrc = sr;
+    Q.nE = (int)n;
   }
   // fold scratch (shared by all tasks of the batch)
   double* zs = S.take<double>(std::max<size_t>(zs_total, 1));
@@ -530,7 +656,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       for (int d = 0; d <= Q.D; ++d) {
         CombineTask c;
         std::memset(&c, 0, sizeof(c));
-        c.prob = i; c.X0 = B.gram[g0 + d].X; c.X1 = X1; c.X2 = X2;
+        c.prob = i; c.X0 = H.pchain ? Q.ringX[d] : B.gram[g0 + d].X; c.X1 = X1; c.X2 = X2;
         c.outH = Q.TH + (size_t)d * m2; c.outS = Q.TS + (size_t)d * m2;
         B.combT.push_back(c);
       }
@@ -551,10 +677,20 @@ void plan(Batch& B, Slab& S, Slab& U) {
       }
       for (int e = 0; e < Q.nE; ++e) {
         int k = Q.Ek[e], m = Q.Em[e], d = std::abs(k - m);
+        if (Q.Ekind[e] == 2) {   // defect block: written by k_defect_blocks
+          B.dblocks[Q.Esrc[e]].outH = Q.EH + (size_t)e * m2;
+          B.dblocks[Q.Esrc[e]].outS = Q.ES + (size_t)e * m2;
+          continue;
+        }
         CombineTask c;
         std::memset(&c, 0, sizeof(c));
-        c.prob = i; c.X0 = B.gram[g0 + Q.D + 1 + e].X; c.X1 = X1; c.X2 = X2;
-        c.subH = Q.TH + (size_t)d * m2; c.subS = Q.TS + (size_t)d * m2; c.subT = (k < m);
+        c.prob = i; c.X1 = X1; c.X2 = X2;
+        if (Q.Ekind[e] == 0) {   // wall block: the block minus its Toeplitz generator
+          c.X0 = B.gram[Q.Esrc[e]].X;
+          c.subH = Q.TH + (size_t)d * m2; c.subS = Q.TS + (size_t)d * m2; c.subT = (k < m);
+        } else {                 // wrap-around block of a periodic chain: A_{(k-m) mod L}
+          c.X0 = Q.ringX[Q.Esrc[e]];
+        }
         c.outH = Q.EH + (size_t)e * m2; c.outS = Q.ES + (size_t)e * m2;
         B.combE.push_back(c);
       }
@@ -686,6 +822,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       const int n = l.n, k = l.k, m0 = H.m0, ld3 = l.ld3;
       const size_t nk = (size_t)n * k;
       maxcols = std::max(maxcols, 2 * m0 * k);
+      B.eapply_gx = std::max(B.eapply_gx, eapply_grid((long long)Q.nErows * m0 * 2 * k));
       cplx* X = B.mvX + B.mv_off[s2];
       cplx* Y1 = B.mvY1 + B.mv_off[s2];
       cplx* Y2 = B.mvY2 + B.mv_off[s2];
@@ -789,6 +926,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.d_gram = U.put(B.gram);
   B.d_combT = U.put(B.combT);
   B.d_combE = U.put(B.combE);
+  B.d_dtabs = U.put(B.dtabs);
+  B.d_dfields = U.put(B.dfields);
+  B.d_dblocks = U.put(B.dblocks);
   B.d_dft = U.put(B.dft);
   B.d_fbp = U.put(B.fbp);
   B.d_fbs = U.put(B.fbs);
@@ -870,11 +1010,14 @@ int build_batch(fock_ctx* ctx, int nprob, const fock_problem* probs, Batch& B, b
 
 void run_assemble(fock_ctx* ctx, Batch& B) {
   cudaStream_t st = ctx->stream;
-  { PROF("k_vec1d", 2); launch_vec1d(B.d_probs, B.d_gsegs, (int)B.gsegs.size(), B.d_psegs, (int)B.psegs.size(), nullptr, 0, st); }
-  { PROF("k_gram", 2); launch_gram(B.d_probs, B.d_gram, (int)B.gram.size(), nullptr, st); }
+  { PROF("k_vec1d", 2); launch_vec1d(B.d_probs, B.d_gsegs, (int)B.gsegs.size(), B.d_psegs, (int)B.psegs.size(),
+                                     B.d_dtabs, (int)B.dtabs.size(), st); }
+  { PROF("k_gram", 2); launch_gram(B.d_probs, B.d_gram, (int)B.gram.size(), B.d_dtabs, st); }
   if (!B.combT.empty()) { PROF("k_combine", 2);
     launch_combine(B.d_probs, B.d_combT, (int)B.combT.size(), st);
     launch_combine(B.d_probs, B.d_combE, (int)B.combE.size(), st); }
+  if (!B.dfields.empty()) { PROF("k_defects", 2);
+    launch_defects(B.d_probs, B.d_dfields, (int)B.dfields.size(), B.d_dblocks, (int)B.dblocks.size(), st); }
 }
 
 void zero_fail_flags(Batch& B, int kind, cudaStream_t st) {
@@ -928,8 +1071,7 @@ void gemm_nn(const Batch::TL& t, cudaStream_t st) {
 void rr(const Batch::TL& t, cudaStream_t st) {
   PROF("k_rr", 1);
   if (!t.n) return;
-  static std::once_flag attr;
-  std::call_once(attr, [] { cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); });
+  FOCK_SMEM_OPTIN(k_rr);
   size_t sm = (size_t)3 * t.ga * t.ga * sizeof(double);
   if (sm > 160 * 1024) sm = 0;
   k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm);
@@ -949,8 +1091,8 @@ void mv_HS(Batch& B, bool xp, cudaStream_t st) {
   const Batch::TL& eh = xp ? B.eHXP : B.eHW;
   const Batch::TL& es = xp ? B.eSXP : B.eSW;
   if (eh.n) { PROF("k_eapply", 2);
-    launch_eapply(tl<EApplyTask>(eh), eh.n, st);
-    launch_eapply(tl<EApplyTask>(es), es.n, st); }
+    launch_eapply(tl<EApplyTask>(eh), eh.n, B.eapply_gx, st);
+    launch_eapply(tl<EApplyTask>(es), es.n, B.eapply_gx, st); }
 }
 
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
@@ -1535,7 +1677,7 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   launch_fft((const FftTask*)tasks, 1, chunks, Q.M, cc, +1, st);
   launch_blockmul((const BmulTask*)(tasks + 1024), 1, Q.M, H.m0, st);
   launch_fft((const FftTask*)(tasks + 512), 1, chunks, Q.M, cc, -1, st);
-  if (Q.nE) launch_eapply((const EApplyTask*)(tasks + 1536), 1, st);
+  if (Q.nE) launch_eapply((const EApplyTask*)(tasks + 1536), 1, eapply_grid((long long)Q.nErows * H.m0 * nvec), st);
   if (!on_device) CUDA_TRY(ctx, cudaMemcpyAsync(y, dy, nbytes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
   CUDA_TRY(ctx, cudaGetLastError());

@@ -3,6 +3,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+// Raises a kernel's dynamic shared memory limit, once per process, to the
+// device's opt-in maximum minus the kernel's static shared memory.  The
+// attribute is a per-function upper bound (a launch still occupies only the
+// bytes it asks for); setting it per batch instead would let concurrent
+// batches on other streams lower it under a launch in flight.
+#define FOCK_SMEM_OPTIN(kernel)                                                       \
+  do {                                                                                \
+    static std::once_flag fock_optin_flag_;                                           \
+    std::call_once(fock_optin_flag_, [] {                                             \
+      int dev = 0, mx = 0;                                                            \
+      cudaGetDevice(&dev);                                                            \
+      cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);      \
+      cudaFuncAttributes fa;                                                          \
+      if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) mx -= (int)fa.sharedSizeBytes; \
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);  \
+    });                                                                               \
+  } while (0)
+
 namespace fock {
 
 constexpr int MAXM0 = 32;
@@ -65,6 +85,30 @@ struct DefTab {
   int prob, axis, N, pad;
   double pos;           // nucleus coordinate in lattice units relative to X0 (h units)
   double* e;            // [R][N]
+};
+
+// Defect field of a chain (reading R-DEF): F[rho][mu nu] = sum over defects d
+// and quadrature terms q of dZ_d c_q D1_d[q][mu nu] D2_d[q][mu nu] e_d[q][rho],
+// with e_d the defect's axis-0 single-nucleus table and D1_d, D2_d its
+// transverse forms (the chain's transverse axes hold one cell, so these do
+// not depend on the block pair).
+struct DefRef {
+  const double* e;      // [R][N0] axis-0 table
+  const double* D1;     // [R][m0*m0] transverse forms (axis 1)
+  const double* D2;     // [R][m0*m0] transverse forms (axis 2)
+  double dz;            // newZ - Z
+};
+struct DefField {
+  int prob, N, ndef;
+  const DefRef* refs;   // [ndef]
+  double* F;            // [N][m0*m0]
+};
+// One defect block: out_H[mu nu] = -sum_rho g_{a mu}(rho) g_{b nu}(rho) F[rho][mu nu]
+// over the pair's node range (axis 0, WALL or RING), out_S = 0.
+struct DefBlock {
+  int prob, mode, a, b, rho0, rho1, pad;
+  const double* F;
+  double* outH; double* outS;
 };
 
 struct __align__(16) cplx { double x, y; };

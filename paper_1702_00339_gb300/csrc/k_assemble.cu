@@ -71,7 +71,13 @@ __global__ void k_ptab(const ProbDev* __restrict__ probs, const SegDesc* __restr
     double tq = P.tq[q];
     double acc = 0.0;
     int hw = (L == 1) ? 0 : L / 2;
-    for (int k = -hw; k <= hw; ++k) {
+    // only window cells whose P0 integral exceeds the erfc(7) ~ 4e-23 tail:
+    // the cell [u, u + h] must meet (-7/t, 7/t), u = (r - (k + f) n0) h
+    const double reach = 7.0 / tq;
+    const double cn = (double)P.n0 * P.h;
+    const int klo = (int)fmax((double)-hw, floor((r * P.h - reach) / cn - f) - 1.0);
+    const int khi = (int)fmin((double)hw, ceil((r * P.h + reach + P.h) / cn - f) + 1.0);
+    for (int k = klo; k <= khi; ++k) {
       double w = (L > 1 && (L % 2 == 0) && (k == -hw || k == hw)) ? 0.5 : 1.0;
       double u = (r - ((double)k + f) * (double)P.n0) * P.h;   // lo - a, h units -> bohr
       acc += w * gauss_cell(tq, u, u + P.h);
@@ -226,6 +232,54 @@ __global__ void k_combine(const ProbDev* __restrict__ probs, const CombineTask* 
   }
 }
 
+// ------------------------------------------------------------ defects ----
+// Field of the chain's defects on the axis-0 nodes (reading R-DEF).
+__global__ void k_defect_field(const ProbDev* __restrict__ probs, const DefField* __restrict__ tasks) {
+  const DefField T = tasks[blockIdx.y];
+  const ProbDev& P = probs[T.prob];
+  const int np = P.m0 * P.m0, R = P.R;
+  const int tot = T.N * np;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
+    const int rho = it / np, pr = it % np;
+    double acc = 0.0;
+    for (int d = 0; d < T.ndef; ++d) {
+      const DefRef& Rf = T.refs[d];
+      double s = 0.0;
+      for (int q = 0; q < R; ++q)
+        s += P.cq[q] * Rf.D1[q * np + pr] * Rf.D2[q * np + pr] * Rf.e[(size_t)q * T.N + rho];
+      acc += Rf.dz * s;
+    }
+    T.F[it] = acc;
+  }
+}
+
+// One CTA per defect block.
+__global__ void k_defect_blocks(const ProbDev* __restrict__ probs, const DefBlock* __restrict__ tasks) {
+  const DefBlock T = tasks[blockIdx.x];
+  const ProbDev& P = probs[T.prob];
+  const AxisDev& A = P.ax[0];
+  const int m0 = P.m0, np = m0 * m0, n0 = P.n0;
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    const int mu = pr / m0, nu = pr % m0;
+    double acc = 0.0;
+    for (int rho = T.rho0; rho < T.rho1; ++rho) {
+      double ga = gval(A, T.mode, n0, mu, T.a, rho);
+      if (ga == 0.0) continue;
+      double gb = gval(A, T.mode, n0, nu, T.b, rho);
+      int row = (T.mode == RING) ? posmod(rho, A.N) : rho + T.pad;
+      acc += ga * gb * T.F[(size_t)row * np + pr];
+    }
+    T.outH[pr] = -acc;
+    T.outS[pr] = 0.0;
+  }
+}
+
+void launch_defects(const ProbDev* probs, const DefField* fields, int nf, const DefBlock* blocks, int nb,
+                    cudaStream_t st) {
+  if (nf) k_defect_field<<<dim3(64, nf), 256, 0, st>>>(probs, fields);
+  if (nb) k_defect_blocks<<<nb, 128, 0, st>>>(probs, blocks);
+}
+
 // ---------------------------------------------------------------- K4 ----
 
 
@@ -276,7 +330,7 @@ void launch_combine(const ProbDev* probs, const CombineTask* tasks, int n, cudaS
 void launch_axis_dft(const ProbDev* probs, const DftTask* tasks, int n, int maxL, cudaStream_t st) {
   if (!n) return;
   size_t sm = (size_t)maxL * sizeof(cplx);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_axis_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_axis_dft);
   k_axis_dft<<<dim3(32, n), 256, sm, st>>>(probs, tasks);
 }
 

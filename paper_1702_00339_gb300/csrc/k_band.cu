@@ -30,11 +30,19 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
   const BandTask T = tasks[blockIdx.x];
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L;
   __shared__ double inv[MAXM0 * MAXM0];
-  __shared__ int bad;
-  __shared__ double s_sigma;
-  if (threadIdx.x == 0) s_sigma = *T.sigma0;
+  __shared__ int bad, s_stop, s_nbis;
+  __shared__ double s_sigma, s_ok, s_bad;
+  if (threadIdx.x == 0) { s_sigma = *T.sigma0; s_ok = NAN; s_bad = NAN; s_nbis = 0; s_stop = 0; }
   __syncthreads();
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  // Shift search: A = H - sigma S must be positive definite.  The first
+  // sigma comes from the defect-free embedding; a bound state below that
+  // band (a substituted nucleus) makes A indefinite.  Descend geometrically
+  // until the factorisation succeeds, then bisect three times between the
+  // last failing and the succeeding shift, which brackets lambda_min in
+  // (ok, bad); the final shift is ok - (bad - ok), at least one bracket width
+  // below lambda_min (close enough for a strong shift-invert preconditioner,
+  // far enough for a well-conditioned factor), and the band holds its factor.
+  for (int attempt = 0; attempt < 24; ++attempt) {
     const double sg = s_sigma;
     // fill: Toeplitz part, then the boundary blocks (lower band, k >= m)
     const int tot = L * (D + 1) * m2;
@@ -116,13 +124,25 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
       __syncthreads();
     }
     __syncthreads();
-    if (!bad) break;
-    if (threadIdx.x == 0) s_sigma = sg - 0.05 * (1.0 + fabs(sg)) * (double)(1 << attempt);
+    if (threadIdx.x == 0) {
+      if (!bad) {
+        s_ok = sg;
+        if (isnan(s_bad) || s_nbis >= 3) s_stop = 1;
+      } else {
+        s_bad = sg;
+      }
+      if (!s_stop) {
+        if (isnan(s_ok)) s_sigma = sg - 0.05 * (1.0 + fabs(sg)) * (double)(1 << min(attempt, 30));
+        else if (s_nbis < 3) { s_sigma = 0.5 * (s_ok + s_bad); ++s_nbis; }
+        else { s_sigma = s_ok - (s_bad - s_ok); s_nbis = 99; }   // refactor one bracket below
+      }
+    }
     __syncthreads();
+    if (s_stop) break;
   }
   if (threadIdx.x == 0) {
     *T.sigma_used = s_sigma;
-    if (bad && T.fail) *T.fail = 1;
+    if (!s_stop && T.fail) *T.fail = 1;
   }
 }
 

@@ -533,7 +533,7 @@ void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, in
                     cudaStream_t st) {
   if (!ntask || !maxnj) return;
   size_t sm = fblocks_smem(maxm0);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_fblocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fblocks);
   k_fblocks<<<dim3(maxnj, ntask), 128, sm, st>>>(probs, tasks);
 }
 
@@ -542,7 +542,7 @@ void launch_precond(const ProbDev* probs, const PrecTask* tasks, int ntask, int 
   if (!ntask) return;
   k_sigma<<<ntask, 256, 0, st>>>(tasks);
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_precond, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_precond);
   k_precond<<<dim3(maxM, ntask), 128, sm, st>>>(probs, tasks);
 }
 
@@ -551,7 +551,7 @@ void launch_sort_small(const SortTask* tasks, int ntask, int maxn, cudaStream_t 
   int n2 = 1;
   while (n2 < maxn) n2 <<= 1;
   size_t sm = (size_t)n2 * (sizeof(double) + sizeof(int));
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_sort_small);
   k_sort_small<<<ntask, 512, sm, st>>>(tasks);
 }
 

@@ -11,6 +11,8 @@
 //             a chunk of columns of one problem in shared memory)
 //  k_blockmul per Fourier index: m0 x m0 complex block times m0 x nvec
 //  k_eapply   y += E x over the block rows that carry boundary/defect blocks
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fock {
@@ -189,10 +191,10 @@ void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc
   if (!ntask) return;
   size_t sm = fft_smem(maxM, cc);
   if (dir > 0) {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fft<1>);
     k_fft<1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
   } else {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fft<-1>);
     k_fft<-1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
   }
 }
@@ -200,12 +202,17 @@ void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc
 void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st) {
   if (!ntask) return;
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_blockmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul);
   k_blockmul<<<dim3(maxM, ntask), 256, sm, st>>>(tasks);
 }
 
-void launch_eapply(const EApplyTask* tasks, int ntask, cudaStream_t st) {
-  if (ntask) k_eapply<<<dim3(16, ntask), 256, 0, st>>>(tasks);
+// gx: CTAs per task, from the largest task's work (rows x m0 x columns / 256)
+int eapply_grid(long long items) {
+  long long g = (items + 255) / 256;
+  return (int)std::min<long long>(2048, std::max<long long>(16, g));
+}
+void launch_eapply(const EApplyTask* tasks, int ntask, int gx, cudaStream_t st) {
+  if (ntask) k_eapply<<<dim3(gx, ntask), 256, 0, st>>>(tasks);
 }
 
 }  // namespace fock

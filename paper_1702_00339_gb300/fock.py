@@ -173,9 +173,14 @@ class _Marshal:
         self.s = s
 
 
+def _structured(p):
+    """Box chains and problems with defects: lowest-k structured solve."""
+    return bool(p.is_box or p.defects)
+
+
 def n_evals(p):
     ncell = int(np.prod(p.L))
-    if p.is_box:
+    if _structured(p):
         return int(p.k_eig or 16)
     return ncell * len(p.exps)
 
@@ -240,7 +245,7 @@ class Context:
                 ev = np.zeros(n_evals(p))
                 blk = np.zeros(n_evals(p), np.int32)
                 outs[i].evals = ev.ctypes.data
-                outs[i].block_of = blk.ctypes.data if not p.is_box else None
+                outs[i].block_of = blk.ctypes.data if not _structured(p) else None
                 host.append((ev, blk))
             else:
                 outs[i].evals, outs[i].block_of = outputs[i]
@@ -253,7 +258,7 @@ class Context:
                  "status": outs[i].status}
             if outputs is None:
                 r["evals"] = host[i][0]
-                r["block_of"] = None if p.is_box else host[i][1]
+                r["block_of"] = None if _structured(p) else host[i][1]
             res.append(r)
         return res
 
@@ -393,7 +398,7 @@ class Plan:
                 ev = np.zeros(n_evals(p))
                 blk = np.zeros(n_evals(p), np.int32)
                 outs[i].evals = ev.ctypes.data
-                outs[i].block_of = blk.ctypes.data if not p.is_box else None
+                outs[i].block_of = blk.ctypes.data if not _structured(p) else None
                 host.append((ev, blk))
             else:
                 outs[i].evals, outs[i].block_of = device_ptrs[i]
@@ -406,7 +411,7 @@ class Plan:
                  "status": outs[i].status}
             if device_ptrs is None:
                 r["evals"] = host[i][0]
-                r["block_of"] = None if p.is_box else host[i][1]
+                r["block_of"] = None if _structured(p) else host[i][1]
             res.append(r)
         return res
 

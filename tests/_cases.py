@@ -82,7 +82,7 @@ def reference(p, H, S):
     its tolerance: periodic -> (sorted spectrum with +inf, tol, per-block
     spectra); box -> (lowest k_eig, tol, (eigenvectors, reduced overlap,
     block-diagonal cell basis))."""
-    if p.is_box:
+    if blocks.structured(p):
         ev, V, Sr = blocks.box_eigs(p, H, S, vectors=True)
         Xb, _ = blocks.box_basis(p)
         return ev, eig_tol(Sr, ev), (V, Sr, Xb)

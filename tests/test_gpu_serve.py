@@ -62,7 +62,7 @@ def test_results_equal_alone_and_in_the_mix(fock):
     for p, a, r in zip(ps, alone, res):
         assert r["status"] == 0 and a["status"] == 0
         assert np.array_equal(r["evals"], a["evals"])
-        if not p.is_box:
+        if not (p.is_box or p.defects):
             assert np.array_equal(r["block_of"], a["block_of"])
         assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_done_ns"]
 

@@ -416,3 +416,40 @@ def test_cell_reduction_is_variational():
     full = dense.eigvals(H, S, p.k_eig)
     red, _, _ = blocks.box_eigs(p, H, S)
     assert np.all(red >= full - _cases.eig_tol(S, full))
+
+
+def _chain_with_defects(p, defects):
+    import dataclasses
+    return dataclasses.replace(p, defects=list(defects))
+
+
+def test_defects_on_every_cell_equal_a_charge_change_periodic_odd_chain():
+    """On a periodic chain with an odd number of cells and the nucleus at the
+    cell centre, the minimum-image kernels of all L nuclei are exactly the
+    symmetric lattice window (Eq. 3.6), so substituting Z -> Z + dZ on every
+    cell gives H = A/2 - (1 + dZ/Z) V."""
+    p = _cases.periodic_chain_small(L=5, n0=6, n_perp=14, m0=4, R=12)
+    dz = 0.7
+    q = _chain_with_defects(p, [li.Defect(cell=(c, 0, 0), nucleus=0, newZ=1.0 + dz) for c in range(5)])
+    H, S, A, V = dense.build(p, with_parts=True)
+    Hq, Sq = dense.build(q)
+    ref = 0.5 * A - (1.0 + dz) * V
+    assert np.max(np.abs(Hq - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.array_equal(Sq, S)
+
+
+def test_defect_matrix_translation_covariance():
+    """A defect moved by one cell moves its matrix by one cell: cyclically on
+    a periodic chain (exact symmetry of the ring), and in the interior of a
+    box chain whose walls no function reaches."""
+    p = _cases.periodic_chain_small(L=6, n0=6, n_perp=14, m0=4, R=12)
+    m0 = p.m0
+    D0 = dense.defect_matrix(_chain_with_defects(p, [li.Defect((0, 0, 0), 0, 0.0)]))
+    D2 = dense.defect_matrix(_chain_with_defects(p, [li.Defect((2, 0, 0), 0, 0.0)]))
+    sh = np.roll(np.roll(D0, 2 * m0, axis=0), 2 * m0, axis=1)
+    assert np.max(np.abs(D2 - sh)) <= 1e-13 * np.max(np.abs(D0))
+    b = _cases.box_chain_small(L=7, n0=4, pad=90, n_perp=12, R=8, k=4, seed=3)
+    m0 = b.m0
+    E3 = dense.defect_matrix(_chain_with_defects(b, [li.Defect((3, 0, 0), 0, 2.0)]))
+    E4 = dense.defect_matrix(_chain_with_defects(b, [li.Defect((4, 0, 0), 0, 2.0)]))
+    assert np.max(np.abs(E4[m0:, m0:] - E3[:-m0, :-m0])) <= 1e-13 * np.max(np.abs(E3))
