@@ -58,6 +58,7 @@ __global__ void k_gemm_nn(const GemmTask*);
 __global__ void k_resid(const ResidTask*, double);
 __global__ void k_rr(const RRTask*, int);
 __global__ void k_copy_cols(const CopyTask*);
+__global__ void k_colnorm(const CopyTask*);
 }  // namespace fock
 
 using namespace fock;
@@ -149,6 +150,14 @@ struct HostProb {
 // eigenpair from lambda_{k+1} to lambda_{k+g+1} (clustered band edges).
 int lobpcg_guard(int k) { return std::max(2, k / 4); }
 
+// Block size of the structured iteration: k + guards, or the whole space
+// (N_b columns) when three blocks of it fit the Rayleigh-Ritz kernel -- then
+// the first Rayleigh-Ritz step is exact and the solve ends there.
+int lobpcg_block(int k, int Nb) {
+  if (3 * Nb <= 255) return Nb;
+  return k + lobpcg_guard(k);
+}
+
 int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (p.n0 <= 0 || !(p.b0 > 0.0)) { why = "n0 > 0 and b0 > 0 required"; return FOCK_EINVAL; }
   if (p.M0 < 1 || p.M0 > 8 || !p.Z || !p.frac) { why = "1 <= M0 <= 8 with Z and frac"; return FOCK_EINVAL; }
@@ -211,9 +220,9 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   H.k_eig = (p.k_eig > 0) ? p.k_eig : 16;
   if (H.kind == 1) {
     int Nb = H.L[0] * H.m0;
-    int kb = H.k_eig + lobpcg_guard(H.k_eig);
-    if (3 * kb > Nb || 3 * kb > 255) {
-      why = "k_eig too large: 3 (k + guard) must not exceed min(N_b, 255)"; return FOCK_EINVAL;
+    int kb = lobpcg_block(H.k_eig, Nb);
+    if (H.k_eig > Nb || 3 * kb > 255 || (kb < Nb && 3 * kb > Nb)) {
+      why = "k_eig too large: k <= N_b and 3 (k + guard) <= min(N_b, 255) on chains with 3 N_b > 255"; return FOCK_EINVAL;
     }
   }
   return FOCK_OK;
@@ -388,7 +397,7 @@ struct Batch {
   TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
   TL eHXP, eSXP, eHW, eSW;
   TL bandF, bandS;
-  TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid;
+  TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
   int eapply_gx = 16;
   int* d_ones = nullptr;
@@ -749,7 +758,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Q.nev = H.k_eig;
       Q.ev = S.take<double>(Q.nev);
       B.sidx.push_back(i);
-      B.kmax = std::max(B.kmax, H.k_eig + lobpcg_guard(H.k_eig));
+      B.kmax = std::max(B.kmax, lobpcg_block(H.k_eig, Q.Lc * H.m0));
     }
   }
   // ---- LOBPCG state ----
@@ -759,7 +768,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     const HostProb& H = B.hp[i];
     Batch::PerProb& Q = B.pp[i];
     Batch::Lob l;
-    l.n = Q.Lc * H.m0; l.kw = H.k_eig; l.k = H.k_eig + lobpcg_guard(H.k_eig);
+    l.n = Q.Lc * H.m0; l.kw = H.k_eig; l.k = lobpcg_block(H.k_eig, l.n);
     l.ld3 = 3 * l.k + 1;   // +1: Jacobi pads odd sizes
     size_t nk = (size_t)l.n * l.k;
     l.Y = S.take<double>(3 * nk); l.HY = S.take<double>(3 * nk); l.SY = S.take<double>(3 * nk);
@@ -809,7 +818,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     std::vector<InitTask> ini;
     std::vector<GemmTask> tcx, nw, tcp, npp, gg1, gg3, uu1, uu3;
     std::vector<RRTask> r1, r3;
-    std::vector<CopyTask> c2k;
+    std::vector<CopyTask> c2k, nP, nW;
     std::vector<ResidTask> rs;
     std::vector<BandTask> bnd;
     std::vector<int> ones(ns, 1);
@@ -821,7 +830,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Batch::Lob& l = B.lob[s2];
       const int n = l.n, k = l.k, m0 = H.m0, ld3 = l.ld3;
       const size_t nk = (size_t)n * k;
-      maxcols = std::max(maxcols, 2 * m0 * k);
+      maxcols = std::max(maxcols, m0 * k);   // packed: two real columns per transform
       B.eapply_gx = std::max(B.eapply_gx, eapply_grid((long long)Q.nErows * m0 * 2 * k));
       cplx* X = B.mvX + B.mv_off[s2];
       cplx* Y1 = B.mvY1 + B.mv_off[s2];
@@ -894,6 +903,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
       uu1.push_back(gt(k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
       uu3.push_back(gt(3 * k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
       c2k.push_back({l.active, n, 2 * k, l.T1, n, l.Y, n});
+      nP.push_back({l.active, n, k, nullptr, n, l.Y + nk, n});
+      nW.push_back({l.active, n, k, nullptr, n, l.Y + 2 * nk, n});
       rs.push_back({l.active, n, k, n, l.Y, l.HY, l.SY, l.lam, l.R, l.res});
     }
     B.fft_chunks = (maxcols + B.fft_cc - 1) / B.fft_cc;
@@ -915,6 +926,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
     TLp(uu1, B.u1); TLp(uu3, B.u3);
     TLp(c2k, B.cp2k);
+    TLp(nP, B.normP);
+    TLp(nW, B.normW);
     TLp(bnd, B.bandF);
     B.bandS = B.bandF;
     TLp(rs, B.resid, kk);
@@ -1076,6 +1089,14 @@ void rr(const Batch::TL& t, cudaStream_t st) {
   if (sm > 160 * 1024) sm = 0;
   k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm);
 }
+// unit 2-norm columns before a matvec: the FFT packs two real columns per
+// complex transform, and a column far smaller than its partner would get an
+// image accurate only relative to the partner (Rayleigh-Ritz is invariant
+// to column scaling)
+void normalize(const Batch::TL& t, int maxcols, cudaStream_t st) {
+  PROF("k_colnorm", 1);
+  if (t.n) k_colnorm<<<dim3(maxcols, t.n), 256, 0, st>>>(tl<CopyTask>(t));
+}
 void copies(const Batch::TL& t, cudaStream_t st) {
   PROF("k_copy_cols", 1);
   if (t.n) k_copy_cols<<<dim3(32, t.n), 256, 0, st>>>(tl<CopyTask>(t));
@@ -1203,6 +1224,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st); }
       mv_inv(B, B.invPW, st);
     }
+    normalize(B.normW, B.kmax, st);
     mv_HS(B, false, st);
     gemm_tn(B.tnCx, st);
     gemm_nn(B.nnW, st);
@@ -1213,6 +1235,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
     gemm_nn(B.u3, st);
     copies(B.cp2k, st);
+    normalize(B.normP, B.kmax, st);
     mv_HS(B, true, st);
     gemm_tn(B.tnCp, st);
     gemm_nn(B.nnP, st);
@@ -1673,7 +1696,7 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   std::memcpy(hbuf + 1024, &bm, sizeof(bm));
   std::memcpy(hbuf + 1536, &ea, sizeof(ea));
   CUDA_TRY(ctx, cudaMemcpyAsync(tasks, hbuf, 2048, cudaMemcpyHostToDevice, st));
-  int chunks = (H.m0 * nvec + cc - 1) / cc;
+  int chunks = (H.m0 * ((nvec + 1) / 2) + cc - 1) / cc;
   launch_fft((const FftTask*)tasks, 1, chunks, Q.M, cc, +1, st);
   launch_blockmul((const BmulTask*)(tasks + 1024), 1, Q.M, H.m0, st);
   launch_fft((const FftTask*)(tasks + 512), 1, chunks, Q.M, cc, -1, st);

@@ -396,6 +396,32 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   }
 }
 
+// One CTA per (column, task): scale dst's column to unit 2-norm (zero
+// columns stay zero).
+__global__ void k_colnorm(const CopyTask* __restrict__ tasks) {
+  const CopyTask T = tasks[blockIdx.y];
+  if (T.active && *T.active == 0) return;
+  const int c = blockIdx.x;
+  if (c >= T.ncols) return;
+  double* col = T.dst + (size_t)T.ldd * c;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < T.n; i += blockDim.x) s += col[i] * col[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) tot += red[w];
+    red[0] = tot;
+  }
+  __syncthreads();
+  const double nrm = sqrt(red[0]);
+  if (!(nrm > 0.0) || !isfinite(nrm)) return;
+  const double inv = 1.0 / nrm;
+  for (int i = threadIdx.x; i < T.n; i += blockDim.x) col[i] *= inv;
+}
+
 __global__ void k_copy_cols(const CopyTask* __restrict__ tasks) {
   const CopyTask T = tasks[blockIdx.y];
   if (T.active && *T.active == 0) return;

@@ -7,9 +7,11 @@
 //   w = exp(-2 pi i / M).
 //
 //  k_twiddle  table exp(-2 pi i t / M)
-//  k_fft      batched mixed-radix Stockham FFT of the columns (one CTA holds
-//             a chunk of columns of one problem in shared memory)
-//  k_blockmul per Fourier index: m0 x m0 complex block times m0 x nvec
+//  k_fft      batched mixed-radix Stockham FFT of the columns, two real
+//             columns packed per complex transform (z = x1 + i x2); one CTA
+//             holds a chunk of packed columns of one problem in shared memory
+//  k_blockmul per Fourier index pair (j, M-j): m0 x m0 complex block times the
+//             unpacked transforms of the real columns
 //  k_eapply   y += E x over the block rows that carry boundary/defect blocks
 #include <algorithm>
 
@@ -35,7 +37,8 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
   const FftTask T = tasks[blockIdx.y];
   const CircDev C = *T.circ;
   const int M = C.M, CC = T.cc;
-  const int ncols = T.m0 * T.ncol;
+  const int npair = (T.ncol + 1) >> 1;    // two real columns per complex transform
+  const int ncols = T.m0 * npair;
   const int c0 = blockIdx.x * CC;
   if (c0 >= ncols) return;
   const int ncc = min(CC, ncols - c0);
@@ -49,8 +52,9 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
       int c = c0 + cc;
       if (DIR > 0) {
         if (k < T.L) {
-          int mu = c % T.m0, v = c / T.m0;
-          val = cmk(T.x[(size_t)(k * T.m0 + mu) + (size_t)T.ldx * v], 0.0);
+          int mu = c % T.m0, p = c / T.m0;
+          const double* xc = T.x + (size_t)(k * T.m0 + mu) + (size_t)T.ldx * (2 * p);
+          val = cmk(xc[0], (2 * p + 1 < T.ncol) ? xc[T.ldx] : 0.0);
         }
       } else {
         val = T.X[(size_t)k * ncols + c];
@@ -121,10 +125,14 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
     for (int it = threadIdx.x; it < T.L * CC; it += blockDim.x) {
       int k = it / CC, cc = it % CC;
       if (cc < ncc) {
-        int c = c0 + cc, mu = c % T.m0, v = c / T.m0;
-        size_t o = (size_t)(k * T.m0 + mu) + (size_t)T.ldy * v;
-        double val = A[it].x * inv;
-        T.y[o] = (T.beta == 0.0) ? val : T.beta * T.y[o] + val;
+        int c = c0 + cc, mu = c % T.m0, p = c / T.m0;
+        size_t o = (size_t)(k * T.m0 + mu) + (size_t)T.ldy * (2 * p);
+        double re = A[it].x * inv, im = A[it].y * inv;
+        T.y[o] = (T.beta == 0.0) ? re : T.beta * T.y[o] + re;
+        if (2 * p + 1 < T.ncol) {
+          o += (size_t)T.ldy;
+          T.y[o] = (T.beta == 0.0) ? im : T.beta * T.y[o] + im;
+        }
       }
     }
   }
@@ -132,12 +140,18 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
 
 
 
+// Per Fourier index pair (j, M - j), j <= M/2.  X holds the transforms of
+// column pairs packed as z = x1 + i x2, so X1_j = (Z_j + conj Z_{M-j}) / 2 and
+// X2_j = -i (Z_j - conj Z_{M-j}) / 2.  With real generators
+// Chat_{M-j} = conj(Chat_j), hence Y_{M-j} = conj(Y_j) for each real column,
+// and the outputs are packed again as W = Y1 + i Y2 for the inverse transform.
 __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
   extern __shared__ cplx sb[];
   const BmulTask T = tasks[blockIdx.y];
   const int j = blockIdx.x;
-  if (j >= T.M) return;
-  const int m0 = T.m0, np = m0 * m0, nc = m0 * T.ncol;
+  if (2 * j > T.M) return;
+  const int jm = (T.M - j) % T.M;
+  const int m0 = T.m0, np = m0 * m0, nc = m0 * ((T.ncol + 1) >> 1);
   cplx* b1 = sb;
   cplx* b2 = sb + np;
   for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
@@ -145,21 +159,33 @@ __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
     if (T.B2) b2[pr] = T.B2[(size_t)j * np + pr];
   }
   __syncthreads();
-  const cplx* xj = T.X + (size_t)j * nc;
+  const cplx* zj = T.X + (size_t)j * nc;
+  const cplx* zm = T.X + (size_t)jm * nc;
   for (int it = threadIdx.x; it < nc; it += blockDim.x) {
-    int mu = it % m0, v = it / m0;
-    cplx a1 = cmk(0.0, 0.0), a2 = cmk(0.0, 0.0);
+    const int mu = it % m0, p = it / m0;
+    cplx y1a = cmk(0.0, 0.0), y2a = cmk(0.0, 0.0), y1b = cmk(0.0, 0.0), y2b = cmk(0.0, 0.0);
     for (int nu = 0; nu < m0; ++nu) {
-      cplx xv = xj[v * m0 + nu];
-      a1 = cadd(a1, cmul(b1[mu * m0 + nu], xv));
-      if (T.B2) a2 = cadd(a2, cmul(b2[mu * m0 + nu], xv));
+      const cplx a = zj[p * m0 + nu], b = zm[p * m0 + nu];
+      const cplx x1 = cmk(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));    // (a + conj b) / 2
+      const cplx x2 = cmk(0.5 * (a.y + b.y), -0.5 * (a.x - b.x));   // -i (a - conj b) / 2
+      const cplx c1 = b1[mu * m0 + nu];
+      y1a = cadd(y1a, cmul(c1, x1));
+      y2a = cadd(y2a, cmul(c1, x2));
+      if (T.B2) {
+        const cplx c2 = b2[mu * m0 + nu];
+        y1b = cadd(y1b, cmul(c2, x1));
+        y2b = cadd(y2b, cmul(c2, x2));
+      }
     }
-    T.Y1[(size_t)j * nc + it] = a1;
-    if (T.B2) T.Y2[(size_t)j * nc + it] = a2;
+    // W_j = Y1 + i Y2, W_{M-j} = conj(Y1) + i conj(Y2)
+    T.Y1[(size_t)j * nc + it] = cmk(y1a.x - y2a.y, y1a.y + y2a.x);
+    if (jm != j) T.Y1[(size_t)jm * nc + it] = cmk(y1a.x + y2a.y, -y1a.y + y2a.x);
+    if (T.B2) {
+      T.Y2[(size_t)j * nc + it] = cmk(y1b.x - y2b.y, y1b.y + y2b.x);
+      if (jm != j) T.Y2[(size_t)jm * nc + it] = cmk(y1b.x + y2b.y, -y1b.y + y2b.x);
+    }
   }
 }
-
-
 
 __global__ void k_eapply(const EApplyTask* __restrict__ tasks) {
   const EApplyTask T = tasks[blockIdx.y];
@@ -203,7 +229,7 @@ void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cuda
   if (!ntask) return;
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
   if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul);
-  k_blockmul<<<dim3(maxM, ntask), 256, sm, st>>>(tasks);
+  k_blockmul<<<dim3(maxM / 2 + 1, ntask), 256, sm, st>>>(tasks);
 }
 
 // gx: CTAs per task, from the largest task's work (rows x m0 x columns / 256)

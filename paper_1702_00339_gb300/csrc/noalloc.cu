@@ -102,7 +102,7 @@ extern "C" int fock_toeplitz_matvec_noalloc(fock_ctx* ctx, const fock_blocks* b,
     set_ctx_error(ctx, "matvec_noalloc: descriptor copy failed");
     return FOCK_ECUDA;
   }
-  const int chunks = (v.m0 * nvec + cc - 1) / cc;
+  const int chunks = (v.m0 * ((nvec + 1) / 2) + cc - 1) / cc;
   launch_fft((const FftTask*)s, 1, chunks, v.M, cc, +1, v.stream);
   launch_blockmul((const BmulTask*)(s + 512), 1, v.M, v.m0, v.stream);
   launch_fft((const FftTask*)(s + 256), 1, chunks, v.M, cc, -1, v.stream);

@@ -83,3 +83,19 @@ def test_defect_problems_batch_invariant(ctx):
     together = ctx.solve(ps)
     for p, t in zip(ps, together):
         assert np.array_equal(ctx.solve([p])[0]["evals"], t["evals"])
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_structured_matvec_with_defects(ctx, name):
+    """y = H x and S x through the embedded FFT plus the E blocks, against the
+    dense oracle matrices (odd and even column counts)."""
+    from paper_1702_00339_gb300 import fock
+    p = CASES[name]()
+    H, S = dense.build(p)
+    b = ctx.assemble(p)
+    for nvec in (1, 4, 7):
+        x = np.random.default_rng(nvec).standard_normal((p.Nb, nvec))
+        for which, M in ((fock.FOCK_OP_H, H), (fock.FOCK_OP_S, S)):
+            y = b.matvec(x, which)
+            assert np.max(np.abs(y - M @ x)) <= 1e-12 * np.max(np.abs(M)) * np.max(np.abs(x)) * p.m0 * 4
+    b.close()
