@@ -775,7 +775,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     l.T1 = S.take<double>(2 * nk);
     l.R = S.take<double>(nk);
     l.GH = S.take<double>((size_t)l.ld3 * l.ld3); l.GS = S.take<double>((size_t)l.ld3 * l.ld3);
-    l.work = S.take<double>((size_t)3 * l.ld3 * l.ld3);
+    l.work = S.take<double>((size_t)7 * l.ld3 * l.ld3);
     l.Cc = S.take<double>((size_t)l.ld3 * 2 * l.k);
     l.Cx = S.take<double>((size_t)l.k * l.k);
     B.lob.push_back(l);

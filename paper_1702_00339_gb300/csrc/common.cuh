@@ -1,6 +1,7 @@
 // Internal descriptors and device helpers of libfock (not part of the ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <float.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -233,7 +234,8 @@ struct RRTask {
   const int* active;
   int nb, k, ld;          // current basis size, wanted pairs, leading dim of G / C
   double* GH; double* GS; // [nb x nb] (ld), destroyed
-  double* work;           // [3 * ld * ld] scratch: C, V, Z
+  double* work;           // [7 * ld * ld] scratch: C, V, Z (global when they do not fit
+                          //   shared memory), then 4 ld^2 for the tridiagonal eigensolver
   double* lam;            // out [k]
   double* Cc;             // out [nb x 2k] (ld): [C | C with the first k rows zeroed]
   int* fail;              // out: 1 if Y^T S Y was not numerically positive definite
@@ -278,5 +280,41 @@ struct MatvecView {
   cudaStream_t stream;
   int device;
 };
+
+// ---- symmetric tridiagonal (d[0..m), e[0..m-1)) helpers ----
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
+__device__ inline int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += (q < 0.0);
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0);
+  }
+  return cnt;
+}
+
+// idx-th (0-based, ascending) eigenvalue by bisection.
+__device__ inline double tridiag_eig_bisect(const double* d, const double* e, int m, int idx) {
+  double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);   // Gershgorin
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < m - 1) emax = fmax(emax, fabs(e[i]));
+  }
+  double tnorm = fmax(fabs(lo), fabs(hi));
+  double pivmin = DBL_MIN * fmax(1.0, emax * emax);
+  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
+  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
 
 }  // namespace fock

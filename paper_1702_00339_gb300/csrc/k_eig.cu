@@ -272,41 +272,6 @@ __device__ void cta_tridiag(cplx* c, int m, double* d, double* e, cplx* v, cplx*
   __syncthreads();
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
-__device__ inline int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += (q < 0.0);
-  for (int i = 1; i < m; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
-  }
-  return cnt;
-}
-
-// idx-th (0-based, ascending) eigenvalue by bisection.
-__device__ double tridiag_eig_bisect(const double* d, const double* e, int m, int idx) {
-  double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
-  for (int i = 0; i < m; ++i) {
-    double r = (i > 0 ? e[i - 1] : 0.0) + (i < m - 1 ? e[i] : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
-    if (i < m - 1) emax = fmax(emax, e[i]);
-  }
-  double tnorm = fmax(fabs(lo), fabs(hi));
-  double pivmin = DBL_MIN * fmax(1.0, emax * emax);
-  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
-  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
 __device__ inline cplx twiddle(long long num, int M) {   // exp(-2 pi i num / M)
   double s, c;
   sincospi(-2.0 * (double)(num % M) / (double)M, &s, &c);

@@ -229,6 +229,260 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
   }
 }
 
+// idx-th (0-based, ascending) eigenvalue of the symmetric tridiagonal (d, e)
+// by Sturm bisection in FP32 (about 1e-7 of the spectral radius): used only
+// as the shift of FP64 inverse iteration, whose Rayleigh-Ritz step gives the
+// eigenvalues.  FP32 runs at 64x the FP64 rate on this part.
+__device__ inline float tridiag_bisect_f32(const double* d, const double* e, int m, int idx) {
+  float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.0f;
+  for (int i = 0; i < m; ++i) {
+    float r = (i > 0 ? fabsf((float)e[i - 1]) : 0.0f) + (i < m - 1 ? fabsf((float)e[i]) : 0.0f);
+    lo = fminf(lo, (float)d[i] - r);
+    hi = fmaxf(hi, (float)d[i] + r);
+    if (i < m - 1) emax = fmaxf(emax, fabsf((float)e[i]));
+  }
+  const float tnorm = fmaxf(fabsf(lo), fabsf(hi));
+  const float pivmin = FLT_MIN * fmaxf(1.0f, emax * emax);
+  lo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
+  hi += 4.0f * FLT_EPSILON * tnorm + pivmin;
+  for (int it = 0; it < 64; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    int cnt = 0;
+    float q = (float)d[0] - mid;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0f);
+    for (int i = 1; i < m; ++i) {
+      const float ei = (float)e[i - 1];
+      q = (float)d[i] - mid - ei * ei / q;
+      if (fabsf(q) < pivmin) q = -pivmin;
+      cnt += (q < 0.0f);
+    }
+    if (cnt > idx) hi = mid; else lo = mid;
+  }
+  return 0.5f * (lo + hi);
+}
+
+// ---- lowest eigenpairs of a dense symmetric matrix (whole CTA) ----
+//
+// Householder reduction to a tridiagonal T = Q^T A Q (reflectors kept below
+// the subdiagonal of a); shifts near the kk lowest eigenvalues of T by FP32
+// Sturm bisection; one FP64 inverse-iteration vector per shift (LU with partial pivoting of
+// T - lambda I, three sweeps, one thread per vector); Cholesky-QR applied
+// twice to those vectors and a Rayleigh-Ritz step in their span (Jacobi of
+// the kk x kk projection of T), which restores orthogonality inside clusters
+// of close eigenvalues; z = Q y by the reflectors (one warp per vector).
+// Eigenvector c lands in column c of z (rows 0..r-1, stride ld), eigenvalue
+// c in lam[c], ascending.  scr: 4 ld^2 doubles of scratch.  d, e, tau, pv:
+// shared arrays of >= r entries; ord: shared ints, >= kk + 1 entries.
+__device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, double* scr,
+                               double* d, double* e, double* tau, double* pv, double* lam, int* ord) {
+  __shared__ double red[32];
+  __shared__ double s_tau, s_K;
+  for (int k = 0; k + 2 < r; ++k) {
+    double part = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) part += a[i * ld + k] * a[i * ld + k];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+      const double x0 = a[(k + 1) * ld + k], xn = sqrt(s);
+      const double alpha = (x0 > 0.0) ? -xn : xn;
+      const double vtv = 2.0 * (s - x0 * alpha);
+      d[k] = a[k * ld + k];
+      e[k] = alpha;
+      s_tau = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      tau[k] = s_tau;
+      a[(k + 1) * ld + k] = x0 - alpha;   // v, first entry (the rest of x is v already)
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    if (tk == 0.0) continue;
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) {   // p = tau A22 v
+      double acc = 0.0;
+      for (int j = k + 1; j < r; ++j) acc += a[i * ld + j] * a[j * ld + k];
+      pv[i] = tk * acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double K = 0.0;
+      for (int i = k + 1; i < r; ++i) K += a[i * ld + k] * pv[i];
+      s_K = 0.5 * tk * K;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] -= s_K * a[i * ld + k];   // w
+    __syncthreads();
+    const int nt = r - k - 1;
+    for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
+      const int i = k + 1 + it / nt, j = k + 1 + it % nt;
+      a[i * ld + j] -= a[i * ld + k] * pv[j] + pv[i] * a[j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (r >= 2) {
+      d[r - 2] = a[(r - 2) * ld + (r - 2)];
+      d[r - 1] = a[(r - 1) * ld + (r - 1)];
+      e[r - 2] = a[(r - 1) * ld + (r - 2)];
+      if (r >= 3) tau[r - 2] = 0.0;
+    } else {
+      d[0] = a[0];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = (double)tridiag_bisect_f32(d, e, r, c);
+  __syncthreads();
+  double tn = 0.0;
+  for (int i = 0; i < r; ++i)
+    tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < r ? fabs(e[i]) : 0.0));
+  // inverse iteration, one thread per vector (workspace 5 r in scr[0, ld^2))
+  const int nw = max(1, min(kk, min((ld * ld) / (5 * r), (int)blockDim.x)));
+  if (threadIdx.x < nw) {
+    double* lv = scr + (size_t)threadIdx.x * 5 * r;
+    double* u0 = lv + r;
+    double* u1 = u0 + r;
+    double* u2 = u1 + r;
+    double* pvt = u2 + r;
+    const double eps = DBL_EPSILON * fmax(tn, DBL_MIN);
+    for (int c = threadIdx.x; c < kk; c += nw) {
+      const double lm = lam[c];
+      u0[0] = d[0] - lm;
+      u1[0] = (r > 1) ? e[0] : 0.0;
+      for (int i = 0; i + 1 < r; ++i) {
+        const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
+        if (fabs(u0[i]) >= fabs(sub)) {
+          if (u0[i] == 0.0) u0[i] = eps;
+          const double m = sub / u0[i];
+          lv[i] = m; pvt[i] = 0.0; u2[i] = 0.0;
+          u0[i + 1] = dn - m * u1[i];
+          u1[i + 1] = sn;
+        } else {
+          const double m = u0[i] / sub;
+          const double ou1 = u1[i];
+          lv[i] = m; pvt[i] = 1.0;
+          u0[i] = sub; u1[i] = dn; u2[i] = sn;
+          u0[i + 1] = ou1 - m * dn;
+          u1[i + 1] = -m * sn;
+        }
+      }
+      if (u0[r - 1] == 0.0) u0[r - 1] = eps;
+      u2[r - 1] = 0.0;
+      for (int i = 0; i < r; ++i) {   // reciprocal pivots (tiny ones raised to eps)
+        double u = u0[i];
+        if (fabs(u) < eps) u = (u < 0.0) ? -eps : eps;
+        u0[i] = 1.0 / u;
+      }
+      for (int i = 0; i < r; ++i) z[i * ld + c] = 1.0 + 0.25 * sin(0.7 * (double)(i + 1) * (double)(c + 1));
+      for (int sweep = 0; sweep < 3; ++sweep) {
+        for (int i = 0; i + 1 < r; ++i) {
+          double bi = z[i * ld + c], bn = z[(i + 1) * ld + c];
+          if (pvt[i] != 0.0) { double t2 = bi; bi = bn; bn = t2; }
+          z[i * ld + c] = bi;
+          z[(i + 1) * ld + c] = bn - lv[i] * bi;
+        }
+        for (int i = r - 1; i >= 0; --i) {
+          double s = z[i * ld + c];
+          if (i + 1 < r) s -= u1[i] * z[(i + 1) * ld + c];
+          if (i + 2 < r) s -= u2[i] * z[(i + 2) * ld + c];
+          z[i * ld + c] = s * u0[i];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < r; ++i) nn += z[i * ld + c] * z[i * ld + c];
+        const double inv = (nn > 0.0 && isfinite(nn)) ? 1.0 / sqrt(nn) : 0.0;
+        for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
+      }
+    }
+  }
+  __syncthreads();
+  // Cholesky-QR, twice: Z <- Z L^-T with Z^T Z = L L^T (G in scr[ld^2, 2 ld^2))
+  double* G = scr + (size_t)ld * ld;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) {
+      const int c1 = it / kk, c2 = it % kk;
+      if (c2 > c1) continue;
+      double s = 0.0;
+      for (int i = 0; i < r; ++i) s += z[i * ld + c1] * z[i * ld + c2];
+      G[c1 * kk + c2] = s;
+    }
+    __syncthreads();
+    for (int j = 0; j < kk; ++j) {
+      if (threadIdx.x == 0) G[j * kk + j] = sqrt(fmax(G[j * kk + j], DBL_MIN));
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < kk; i += blockDim.x) G[i * kk + j] /= G[j * kk + j];
+      __syncthreads();
+      const int nt = kk - j - 1;
+      for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
+        const int i = j + 1 + it / nt, l = j + 1 + it % nt;
+        if (l <= i) G[i * kk + l] -= G[i * kk + j] * G[l * kk + j];
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < r; i += blockDim.x)   // row i of Z times L^-T
+      for (int c = 0; c < kk; ++c) {
+        double s = z[i * ld + c];
+        for (int q = 0; q < c; ++q) s -= z[i * ld + q] * G[c * kk + q];
+        z[i * ld + c] = s / G[c * kk + c];
+      }
+    __syncthreads();
+  }
+  // Rayleigh-Ritz in span(Z): Tz = Z^T T Z, Jacobi (stride kj = kk + 1)
+  const int kj = kk + 1;
+  double* Tz = scr + (size_t)2 * ld * ld;
+  double* Qz = scr + (size_t)3 * ld * ld;
+  for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) {
+    const int c1 = it / kk, c2 = it % kk;
+    if (c2 > c1) continue;
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) {
+      double tzi = d[i] * z[i * ld + c2];
+      if (i > 0) tzi += e[i - 1] * z[(i - 1) * ld + c2];
+      if (i + 1 < r) tzi += e[i] * z[(i + 1) * ld + c2];
+      s += z[i * ld + c1] * tzi;
+    }
+    Tz[c1 * kj + c2] = s;
+    Tz[c2 * kj + c1] = s;
+  }
+  __syncthreads();
+  cta_jacobi(Tz, Qz, kk, kj);
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) {   // ascending order (ties by index)
+    const double di = Tz[i * kj + i];
+    int rank = 0;
+    for (int j = 0; j < kk; ++j) {
+      const double dj = Tz[j * kj + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    ord[rank] = i;
+  }
+  __syncthreads();
+  double* tmp = scr;   // r x kk
+  for (int it = threadIdx.x; it < r * kk; it += blockDim.x) {
+    const int i = it / kk, c = it % kk, oc = ord[c];
+    double s = 0.0;
+    for (int q = 0; q < kk; ++q) s += z[i * ld + q] * Qz[q * kj + oc];
+    tmp[it] = s;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < r * kk; it += blockDim.x) z[(it / kk) * ld + (it % kk)] = tmp[it];
+  for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = Tz[ord[c] * kj + ord[c]];
+  __syncthreads();
+  // back-transformation z = H_0 ... H_{r-3} y, one warp per vector
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  for (int c = warp; c < kk; c += nwarp)
+    for (int k = r - 3; k >= 0; --k) {
+      const double tk = tau[k];
+      if (tk == 0.0) continue;
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < r; i += 32) s += a[i * ld + k] * z[i * ld + c];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= tk;
+      for (int i = k + 1 + lane; i < r; i += 32) z[i * ld + c] -= s * a[i * ld + k];
+      __syncwarp();
+    }
+  __syncthreads();
+}
+
 // Rayleigh-Ritz on the basis Y (Gram matrices GH = Y^T H Y, GS = Y^T S Y):
 // scale by D = diag(GS)^-1/2; Cholesky of D GS D with diagonal pivoting,
 // stopping when the largest remaining pivot falls below kDropRel (the
@@ -250,6 +504,7 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram, then its pivoted factor
   __shared__ double dsc[256], dg[256], red[256];
   __shared__ int perm[256], order[256], rid[256];
+  __shared__ double tdd[256], tee[256], ttau[256], tpv[256], tlam[256];
   __shared__ int s_r, s_piv;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     double g = T.GS[(size_t)i * ld + i];
@@ -307,13 +562,13 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
       }
     __syncthreads();
     const int pj = perm[j];
-    const double ljj = sqrt(dg[pj]);
+    const double ljj = sqrt(dg[pj]), rlj = 1.0 / ljj;
     // column j of L (rows i > j in permuted order), L[j][j] = ljj
     for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
       const int pi = perm[i];
       double acc = G[pi * ld + pj];
       for (int q = 0; q < j; ++q) acc -= V[i * ld + q] * V[j * ld + q];
-      V[i * ld + j] = acc / ljj;
+      V[i * ld + j] = acc * rlj;
     }
     if (threadIdx.x == 0) V[j * ld + j] = ljj;
     __syncthreads();
@@ -335,20 +590,21 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
     int aa = it / r, bb = it % r;
     V[aa * ld + bb] = C[perm[aa] * ld + perm[bb]];
   }
+  for (int aa = threadIdx.x; aa < r; aa += blockDim.x) dg[aa] = 1.0 / G[aa * ld + aa];   // reciprocal diagonal of L
   __syncthreads();
   // V <- L^-1 V (thread per column), then C <- V L^-T (thread per row)
   for (int j = threadIdx.x; j < r; j += blockDim.x)
     for (int i = 0; i < r; ++i) {
       double acc = V[i * ld + j];
       for (int q = 0; q < i; ++q) acc -= G[i * ld + q] * V[q * ld + j];
-      V[i * ld + j] = acc / G[i * ld + i];
+      V[i * ld + j] = acc * dg[i];
     }
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x)
     for (int j = 0; j < r; ++j) {
       double acc = V[i * ld + j];
       for (int q = 0; q < j; ++q) acc -= C[i * ld + q] * G[j * ld + q];
-      C[i * ld + j] = acc / G[j * ld + j];
+      C[i * ld + j] = acc * dg[j];
     }
   __syncthreads();
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
@@ -360,24 +616,13 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
     }
   }
   __syncthreads();
-  cta_jacobi(C, V, r, ld);
-  // rank the eigenvalues (ties by index, NaN last), keep the k lowest
-  for (int i = threadIdx.x; i < r; i += blockDim.x) order[i] = i;
-  __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    double di = C[i * ld + i];
-    if (isnan(di)) di = DBL_MAX;
-    int rank = 0;
-    for (int j = 0; j < r; ++j) {
-      double dj = C[j * ld + j];
-      if (isnan(dj)) dj = DBL_MAX;
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    order[rank] = i;
-  }
-  __syncthreads();
+  // the kk lowest eigenpairs of C (ascending) into the columns of V
   const int kk = min(k, r);
-  for (int c = threadIdx.x; c < k; c += blockDim.x) T.lam[c] = (c < kk) ? C[order[c] * ld + order[c]] : NAN;
+  cta_sym_lowest(C, V, r, ld, kk, T.work + (size_t)3 * ld * ld, tdd, tee, ttau, tpv, tlam, order);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) T.lam[c] = (c < kk) ? tlam[c] : NAN;
+  __syncthreads();
+  for (int c = threadIdx.x; c < kk; c += blockDim.x) order[c] = c;
+  __syncthreads();
   // coefficients: w = L^-T v (back substitution in permuted order), z[perm a] = D w[a]
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     double* z = T.Cc + (size_t)ld * c;
@@ -388,7 +633,7 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
       for (int aa = r - 1; aa >= 0; --aa) {
         double acc = V[aa * ld + oc];
         for (int q = aa + 1; q < r; ++q) acc -= G[q * ld + aa] * z[perm[q]];
-        z[perm[aa]] = acc / G[aa * ld + aa];
+        z[perm[aa]] = acc * dg[aa];
       }
       for (int i = 0; i < nb; ++i) z[i] *= dsc[i];
     }
