@@ -149,6 +149,13 @@ int fock_blocks_copy_generators(const fock_blocks* b, double* H, double* S, doub
 /* Periodic eigenvalues by FFT block-diagonalisation (Lemma 3.1, Thm 3.3,
  * Eqs. 3.11-3.12): evals[|L|*m0] ascending (host), block_of optional. */
 int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of);
+/* The same for the Fourier indices jbar in [j0, j1) only: evals[(j1-j0)*m0]
+ * ascending (ties by Fourier index), block_of optional.  The blocks are
+ * independent (Thm. 3.3), so ranks that each take a contiguous range and
+ * merge the sorted parts obtain exactly fock_circulant_eig's output.
+ * Errors: FOCK_EINVAL (not periodic, range outside 0..|L|), FOCK_ECUDA. */
+int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1, double* evals,
+                             int* block_of);
 
 /* y = H x or y = S x (which = FOCK_OP_H / FOCK_OP_S) for an assembled box
  * chain or periodic problem, by the block-circulant embedding FFT matvec

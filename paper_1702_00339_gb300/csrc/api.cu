@@ -1659,6 +1659,45 @@ int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* 
   return FOCK_OK;
 }
 
+int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1, double* evals,
+                             int* block_of) {
+  if (!ctx || !b || !evals) return FOCK_EINVAL;
+  Batch& B = const_cast<Batch&>(b->B);
+  if (B.hp[0].kind != 0) return set_err(ctx, FOCK_EINVAL, "not a periodic problem");
+  const HostProb& H = B.hp[0];
+  const int ncell = H.L[0] * H.L[1] * H.L[2];
+  if (j0 < 0 || j1 < j0 || j1 > ncell) return set_err(ctx, FOCK_EINVAL, "need 0 <= j0 <= j1 <= |L|");
+  const int nj = j1 - j0, n = nj * H.m0;
+  if (n == 0) return FOCK_OK;
+  ProfBind pb(ctx);
+  cudaStream_t st = ctx->stream;
+  { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  char* mem = nullptr;
+  const size_t off_blk = ((size_t)n * 8 + 255) & ~(size_t)255;
+  const size_t off_pv = off_blk + (((size_t)n * 4 + 255) & ~(size_t)255);
+  const size_t off_pi = off_pv + (size_t)n2 * 8;
+  const size_t off_t = (off_pi + (size_t)n2 * 4 + 255) & ~(size_t)255;
+  CUDA_TRY(ctx, cudaMalloc(&mem, off_t + sizeof(FBlockTask)));
+  double* ev = (double*)mem;
+  int* blk = (int*)(mem + off_blk);
+  FBlockTask f = B.fbp[0];
+  f.j0 = j0; f.nj = nj; f.outH = nullptr; f.outS = nullptr; f.want = 1; f.ev = ev; f.blk = blk; f.fail = nullptr;
+  int rc = FOCK_OK;
+  cudaError_t e = cudaMemcpyAsync(mem + off_t, &f, sizeof(f), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, (const FBlockTask*)(mem + off_t), 1, nj, H.m0, st); }
+    { PROF("k_sort_global", 1); launch_sort_global(ev, blk, n, (double*)(mem + off_pv), (int*)(mem + off_pi), st); }
+    e = cudaMemcpyAsync(evals, ev, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && block_of) e = cudaMemcpyAsync(block_of, blk, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) rc = set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e));
+  cudaFree(mem);
+  return rc;
+}
+
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x, double* y,
                          int nvec, int on_device) {
   if (!ctx || !b || !x || !y || nvec <= 0) return FOCK_EINVAL;

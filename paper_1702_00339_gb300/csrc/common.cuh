@@ -158,7 +158,8 @@ struct DftTask {
 };
 
 struct FBlockTask {
-  int prob, source, nj;          // Fourier indices handled: j in [0, nj)
+  int prob, source, nj;          // Fourier indices handled: j in [j0, j0 + nj)
+  int j0;                        // first Fourier index (outputs are indexed from 0)
   int L[3];                      // lattice (FACTORS)
   const cplx* Xh[3];             // per-axis DFT'd factors [L_l][nF][m0*m0] (FACTORS)
   int M, D;                      // circulant size and generator reach (TOEPLITZ)

@@ -281,8 +281,9 @@ __device__ inline cplx twiddle(long long num, int M) {   // exp(-2 pi i num / M)
 __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* __restrict__ tasks) {
   extern __shared__ cplx sm[];
   const FBlockTask F = tasks[blockIdx.y];
-  const int j = blockIdx.x;
-  if (j >= F.nj) return;
+  const int jl = blockIdx.x;      // local output index
+  if (jl >= F.nj) return;
+  const int j = F.j0 + jl;        // Fourier index
   const ProbDev& P = probs[F.prob];
   const int m0 = P.m0, np = m0 * m0;
   const int ldj = m0 + (m0 & 1);
@@ -348,8 +349,8 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   __syncthreads();
   if (F.outH)
     for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
-      F.outH[(size_t)j * np + pr] = H[pr];
-      F.outS[(size_t)j * np + pr] = S[pr];
+      F.outH[(size_t)jl * np + pr] = H[pr];
+      F.outS[(size_t)jl * np + pr] = S[pr];
     }
   if (F.want == 0) return;
   __syncthreads();
@@ -360,11 +361,11 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
   if (F.want == 1) {
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-      F.ev[(size_t)j * m0 + i] = (i < r) ? tridiag_eig_bisect(dd, ee, r, i) : INFINITY;
-      if (F.blk) F.blk[(size_t)j * m0 + i] = j;
+      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_bisect(dd, ee, r, i) : INFINITY;
+      if (F.blk) F.blk[(size_t)jl * m0 + i] = j;
     }
   } else if (threadIdx.x == 0) {
-    F.ev[j] = (r > 0) ? tridiag_eig_bisect(dd, ee, r, 0) : INFINITY;
+    F.ev[jl] = (r > 0) ? tridiag_eig_bisect(dd, ee, r, 0) : INFINITY;
   }
 }
 

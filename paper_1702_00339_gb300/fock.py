@@ -93,6 +93,8 @@ def lib():
         L.fock_blocks_copy_generators.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double),
                                                   P(C.c_double), P(C.c_double), P(C.c_int)]
         L.fock_circulant_eig.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_int)]
+        L.fock_circulant_eig_range.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, P(C.c_double),
+                                               P(C.c_int)]
         L.fock_toeplitz_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_int, C.c_int]
         L.fock_toeplitz_matvec_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -328,6 +330,15 @@ class Blocks:
         blk = np.zeros(n, np.int32)
         self.ctx._check(lib().fock_circulant_eig(self.ctx.h, self.h, _dp(ev), _ip(blk)),
                         "fock_circulant_eig")
+        return ev, blk
+
+    def circulant_eig_range(self, j0, j1):
+        """Eigenvalues of the Fourier blocks j0 <= jbar < j1 only, ascending."""
+        n = (int(j1) - int(j0)) * len(self.p.exps)
+        ev = np.zeros(max(n, 0))
+        blk = np.zeros(max(n, 0), np.int32)
+        self.ctx._check(lib().fock_circulant_eig_range(self.ctx.h, self.h, int(j0), int(j1), _dp(ev), _ip(blk)),
+                        "fock_circulant_eig_range")
         return ev, blk
 
     def matvec(self, x, which=FOCK_OP_H):
