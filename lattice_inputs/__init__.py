@@ -51,6 +51,7 @@ class Problem:
     eps_support: float = 1e-14
     defects: list = field(default_factory=list)
     k_eig: int = 0              # eigenpairs wanted by a box solve (0 = all)
+    precision: int = 0          # 0 FP64, 1 mixed (FP32 preconditioner and early matvecs)
 
     # ---- plain derived sizes (no method arithmetic) ----
     @property

@@ -44,12 +44,12 @@ void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t
 void launch_sort_small(const SortTask*, int, int, cudaStream_t);
 void launch_sort_global(double*, int*, int, double*, int*, cudaStream_t);
 void launch_twiddles(CircDev*, int, cudaStream_t);
-void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t);
-void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
+void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t, bool);
+void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t, bool);
 void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
 int eapply_grid(long long items);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
-void launch_band_solve(const BandTask*, int, int, cudaStream_t);
+void launch_band_solve(const BandTask*, int, int, cudaStream_t, bool);
 void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
 void launch_cell_back(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 __global__ void k_init_x(const InitTask*);
@@ -142,6 +142,7 @@ struct HostProb {
   int k_eig;
   int kind;            // 0 periodic (circulant eigensolve), 1 structured iteration
   int pchain = 0;      // structured path of a periodic chain (defects on a periodic axis 0)
+  int mixed = 0;       // FOCK_MIXED: FP32 preconditioner, FP32 matvecs until the residual is small
   std::vector<fock_defect> defs;
 };
 
@@ -164,6 +165,8 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (p.m0 < 1 || p.m0 > MAXM0 || !p.exps || !p.ang || !p.centre) { why = "1 <= m0 <= 32 with exps/ang/centre"; return FOCK_EINVAL; }
   if (p.R < 3 || p.R > MAXR) { why = "3 <= R <= 64"; return FOCK_EINVAL; }
   if (p.ndef < 0 || (p.ndef > 0 && !p.defects)) { why = "ndef >= 0 with a defects array"; return FOCK_EINVAL; }
+  if (p.precision != FOCK_FP64 && p.precision != FOCK_MIXED) { why = "precision FOCK_FP64 or FOCK_MIXED"; return FOCK_EINVAL; }
+  H.mixed = (p.precision == FOCK_MIXED) ? 1 : 0;
   H.n0 = p.n0; H.b0 = p.b0; H.h = p.b0 / p.n0;
   H.eps = (p.eps_support > 0.0) ? p.eps_support : 1e-14;
   int nlong = 0;
@@ -237,6 +240,7 @@ uint64_t problem_seed(const HostProb& H) {
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
   };
   mix(H.L, sizeof(H.L)); mix(H.per, sizeof(H.per)); mix(H.N, sizeof(H.N)); mix(&H.n0, sizeof(H.n0));
+  mix(&H.mixed, sizeof(H.mixed));
   mix(&H.b0, sizeof(H.b0)); mix(&H.k_eig, sizeof(H.k_eig));
   mix(H.alpha.data(), H.alpha.size() * 8); mix(H.Z.data(), H.Z.size() * 8);
   mix(H.frac.data(), H.frac.size() * 8); mix(H.ang.data(), H.ang.size() * 4);
@@ -396,12 +400,16 @@ struct Batch {
   // basis layout Y = [X | P | W] (k columns each)
   TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
   TL eHXP, eSXP, eHW, eSW;
+  TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
   int eapply_gx = 16;
   int* d_ones = nullptr;
   int* d_active = nullptr;
+  int* d_mode = nullptr;             // per structured problem: 1 while its matvecs run in FP32
+  int* d_refresh = nullptr;          // per structured problem: 0 = refresh its [X | P] images now
+  bool any_mixed = false;
   int* d_fail = nullptr;
   double* d_res = nullptr;
   double* d_lam = nullptr;
@@ -421,6 +429,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
+  B.any_mixed = false;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
   for (int i = 0; i < np; ++i) {
@@ -785,6 +794,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
   if (!B.sidx.empty()) {
     const int ns = (int)B.sidx.size();
     B.d_active = S.take<int>(ns);
+    B.d_mode = S.take<int>(ns);
+    B.d_refresh = S.take<int>(ns);
     B.d_fail = S.take<int>(ns);
     B.d_res = S.take<double>((size_t)ns * B.kmax);
     B.d_lam = S.take<double>((size_t)ns * B.kmax);
@@ -814,7 +825,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
     int maxcols = 1;
     std::vector<FftTask> fXP, fW, fR, iHXP, iSXP, iHW, iSW, iPW;
     std::vector<BmulTask> bHS2, bHS1, bK;
-    std::vector<EApplyTask> ehxp, esxp, ehw, esw;
+    std::vector<EApplyTask> ehxp, esxp, ehw, esw, rehxp, resxp;
+    std::vector<FftTask> rfXP, riHXP, riSXP;
+    std::vector<BmulTask> rbHS2;
     std::vector<InitTask> ini;
     std::vector<GemmTask> tcx, nw, tcp, npp, gg1, gg3, uu1, uu3;
     std::vector<RRTask> r1, r3;
@@ -836,25 +849,30 @@ void plan(Batch& B, Slab& S, Slab& U) {
       cplx* Y1 = B.mvY1 + B.mv_off[s2];
       cplx* Y2 = B.mvY2 + B.mv_off[s2];
       const CircDev* cd = B.d_circs + Q.circ;
-      auto fwd = [&](const double* src, int ncol) {
+      // precision of the operator matvecs: the problem's current mode (mixed
+      // form) or FP64; the circulant preconditioner of a mixed problem is FP32
+      const int* opmode = H.mixed ? B.d_mode + s2 : nullptr;
+      const int* pcmode = H.mixed ? B.d_ones + s2 : nullptr;
+      if (H.mixed) B.any_mixed = true;
+      auto fwd = [&](const double* src, int ncol, const int* md) {
         FftTask t; std::memset(&t, 0, sizeof(t));
         t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.x = src; t.ldx = n; t.X = X;
-        t.cc = B.fft_cc;
+        t.cc = B.fft_cc; t.mode = md;
         return t;
       };
-      auto inv = [&](cplx* from, double* dst, int ncol) {
+      auto inv = [&](cplx* from, double* dst, int ncol, const int* md) {
         FftTask t; std::memset(&t, 0, sizeof(t));
         t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.X = from; t.y = dst; t.ldy = n;
-        t.beta = 0.0; t.cc = B.fft_cc;
+        t.beta = 0.0; t.cc = B.fft_cc; t.mode = md;
         return t;
       };
       double* Yx = l.Y;            // X: columns [0, k)
       double* Yw = l.Y + 2 * nk;   // W: columns [2k, 3k)
-      fXP.push_back(fwd(Yx, 2 * k)); fW.push_back(fwd(Yw, k));
-      iHXP.push_back(inv(Y1, l.HY, 2 * k)); iSXP.push_back(inv(Y2, l.SY, 2 * k));
-      iHW.push_back(inv(Y1, l.HY + 2 * nk, k)); iSW.push_back(inv(Y2, l.SY + 2 * nk, k));
-      bHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2});
-      bHS1.push_back({i, Q.M, m0, k, Q.CH, Q.CS, X, Y1, Y2});
+      fXP.push_back(fwd(Yx, 2 * k, opmode)); fW.push_back(fwd(Yw, k, opmode));
+      iHXP.push_back(inv(Y1, l.HY, 2 * k, opmode)); iSXP.push_back(inv(Y2, l.SY, 2 * k, opmode));
+      iHW.push_back(inv(Y1, l.HY + 2 * nk, k, opmode)); iSW.push_back(inv(Y2, l.SY + 2 * nk, k, opmode));
+      bHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, opmode});
+      bHS1.push_back({i, Q.M, m0, k, Q.CH, Q.CS, X, Y1, Y2, opmode});
       if (Q.use_band) {
         BandTask bt;
         std::memset(&bt, 0, sizeof(bt));
@@ -862,21 +880,32 @@ void plan(Batch& B, Slab& S, Slab& U) {
         bt.TH = Q.THc; bt.TS = Q.TSc; bt.nE = Q.nE; bt.Ek = U.put(Q.Ek); bt.Em = U.put(Q.Em);
         bt.EH = Q.EHc; bt.ES = Q.ESc; bt.sigma0 = Q.sigma; bt.band = Q.band; bt.sigma_used = Q.sigma_band;
         bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
+        bt.fp32 = H.mixed;
         bnd.push_back(bt);
       } else {
-        fR.push_back(fwd(l.R, k));
-        iPW.push_back(inv(Y1, Yw, k));
-        bK.push_back({i, Q.M, m0, k, Q.K, nullptr, X, Y1, nullptr});
+        fR.push_back(fwd(l.R, k, pcmode));
+        iPW.push_back(inv(Y1, Yw, k, pcmode));
+        bK.push_back({i, Q.M, m0, k, Q.K, nullptr, X, Y1, nullptr, pcmode});
       }
-      auto ea = [&](const double* vals, const double* x, double* y, int ncol) {
+      auto ea = [&](const double* vals, const double* x, double* y, int ncol, const int* md) {
         EApplyTask t;
+        std::memset(&t, 0, sizeof(t));
         t.prob = i; t.m0 = m0; t.ncol = ncol; t.nrows = Q.nErows; t.rows = Q.Erows; t.rowptr = Q.Erowptr;
-        t.cols = Q.Ecols; t.vals = vals; t.x = x; t.ldx = n; t.y = y; t.ldy = n;
+        t.cols = Q.Ecols; t.vals = vals; t.x = x; t.ldx = n; t.y = y; t.ldy = n; t.mode = md;
         return t;
       };
       if (Q.nE) {
-        ehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k)); esxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k));
-        ehw.push_back(ea(Q.EHc, Yw, l.HY + 2 * nk, k)); esw.push_back(ea(Q.ESc, Yw, l.SY + 2 * nk, k));
+        ehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k, nullptr)); esxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k, nullptr));
+        ehw.push_back(ea(Q.EHc, Yw, l.HY + 2 * nk, k, nullptr)); esw.push_back(ea(Q.ESc, Yw, l.SY + 2 * nk, k, nullptr));
+      }
+      // image refresh of [X | P] for the problems whose matvecs just switched to
+      // FP64 (flag 0 = refresh, 2 = leave: matches neither precision variant)
+      if (H.mixed) {
+        const int* rf = B.d_refresh + s2;
+        rfXP.push_back(fwd(Yx, 2 * k, rf));
+        riHXP.push_back(inv(Y1, l.HY, 2 * k, rf)); riSXP.push_back(inv(Y2, l.SY, 2 * k, rf));
+        rbHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, rf});
+        if (Q.nE) { rehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k, rf)); resxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k, rf)); }
       }
       ini.push_back({n, k, n, problem_seed(H), l.Y});   // start depends on the problem only
       auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
@@ -897,8 +926,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
       gg1.push_back(gt(k, k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
       gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0));
       gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
-      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail});
-      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail});
+      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
+      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
       // [X' | P'] = Y[:, :nb] Cc, then copied over [X | P]; images recomputed by a matvec
       uu1.push_back(gt(k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
       uu3.push_back(gt(3 * k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
@@ -918,6 +947,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(iHXP, B.invHXP); TLp(iSXP, B.invSXP); TLp(iHW, B.invHW); TLp(iSW, B.invSW); TLp(iPW, B.invPW);
     TLp(bHS2, B.bmulHS2); TLp(bHS1, B.bmulHS1); TLp(bK, B.bmulK);
     TLp(ehxp, B.eHXP); TLp(esxp, B.eSXP); TLp(ehw, B.eHW); TLp(esw, B.eSW);
+    TLp(rfXP, B.rfwdXP); TLp(riHXP, B.rinvHXP); TLp(riSXP, B.rinvSXP); TLp(rbHS2, B.rbmulHS2);
+    TLp(rehxp, B.reHXP); TLp(resxp, B.reSXP);
     TLp(ini, B.init);
     TLp(tcx, B.tnCx, (kk + 15) / 16, (kk + 15) / 16); TLp(tcp, B.tnCp, (kk + 15) / 16, (kk + 15) / 16);
     TLp(nw, B.nnW); TLp(npp, B.nnP);
@@ -1067,11 +1098,11 @@ template <class T> const T* tl(const Batch::TL& t) { return reinterpret_cast<con
 
 void mv_fwd(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_fft", 1);
-  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, +1, st);
+  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, +1, st, B.any_mixed);
 }
 void mv_inv(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_fft", 1);
-  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, -1, st);
+  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, -1, st, B.any_mixed);
 }
 void gemm_tn(const Batch::TL& t, cudaStream_t st) {
   PROF("k_gemm_tn", 1);
@@ -1106,7 +1137,7 @@ void copies(const Batch::TL& t, cudaStream_t st) {
 void mv_HS(Batch& B, bool xp, cudaStream_t st) {
   mv_fwd(B, xp ? B.fwdXP : B.fwdW, st);
   const Batch::TL& bm = xp ? B.bmulHS2 : B.bmulHS1;
-  { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(bm), bm.n, B.maxM, B.maxm0, st); }
+  { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(bm), bm.n, B.maxM, B.maxm0, st, B.any_mixed); }
   mv_inv(B, xp ? B.invHXP : B.invHW, st);
   mv_inv(B, xp ? B.invSXP : B.invSW, st);
   const Batch::TL& eh = xp ? B.eHXP : B.eHW;
@@ -1114,6 +1145,17 @@ void mv_HS(Batch& B, bool xp, cudaStream_t st) {
   if (eh.n) { PROF("k_eapply", 2);
     launch_eapply(tl<EApplyTask>(eh), eh.n, B.eapply_gx, st);
     launch_eapply(tl<EApplyTask>(es), es.n, B.eapply_gx, st); }
+}
+
+// [X | P] images in FP64 for the problems flagged in d_refresh only
+void refresh_XP(Batch& B, cudaStream_t st) {
+  mv_fwd(B, B.rfwdXP, st);
+  { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.rbmulHS2), B.rbmulHS2.n, B.maxM, B.maxm0, st, false); }
+  mv_inv(B, B.rinvHXP, st);
+  mv_inv(B, B.rinvSXP, st);
+  if (B.reHXP.n) { PROF("k_eapply", 2);
+    launch_eapply(tl<EApplyTask>(B.reHXP), B.reHXP.n, B.eapply_gx, st);
+    launch_eapply(tl<EApplyTask>(B.reSXP), B.reSXP.n, B.eapply_gx, st); }
 }
 
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
@@ -1126,6 +1168,18 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   if (!ns) return FOCK_OK;
   CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, B.d_ones, ns * sizeof(int), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(ctx, cudaMemsetAsync(B.d_fail, 0, ns * sizeof(int), st));
+  // mixed form: matvecs in FP32 until the wanted residual falls below
+  // kMixedSwitch, FP64 from then on (monotone), so that the converged pairs
+  // come from FP64 images; no convergence decision during the FP32 phase
+  // the FP32 phase also ends when its residual stops halving for two
+  // iterations or after kMixedMaxIt iterations (an ill-conditioned pencil
+  // cannot reach kMixedSwitch with FP32 images)
+  const double kMixedSwitch = 1e-5;
+  const int kMixedMaxIt = 10;
+  std::vector<int> mode(ns, 0), f32_it(ns, 0), f32_stall(ns, 0);
+  std::vector<double> f32_best(ns, INFINITY);
+  for (int s2 = 0; s2 < ns; ++s2) mode[s2] = B.hp[B.sidx[s2]].mixed;
+  CUDA_TRY(ctx, cudaMemcpyAsync(B.d_mode, mode.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
   const bool dbg = getenv("FOCK_DEBUG") != nullptr;
   auto dump = [&](const char* stage, int it) {
     if (!dbg) return;
@@ -1189,7 +1243,8 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     { PROF("k_resid", 1); k_resid<<<dim3(B.kmax, B.resid.n), 256, 0, st>>>(tl<ResidTask>(B.resid), tol); }
     CUDA_TRY(ctx, cudaMemcpyAsync(hres.data(), B.d_res, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    bool any = false, changed = false;
+    bool any = false, changed = false, switched = false;
+    std::vector<int> just(ns, 0);
     for (int s2 = 0; s2 < ns; ++s2) {
       if (!active[s2]) continue;
       double mx = 0.0;
@@ -1200,6 +1255,15 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       }
       resid[s2] = bad ? INFINITY : mx;
       iters[s2] = it;
+      if (mode[s2] && !bad) {   // FP32 phase of the mixed form
+        ++f32_it[s2];
+        if (mx < 0.5 * f32_best[s2]) { f32_best[s2] = mx; f32_stall[s2] = 0; } else ++f32_stall[s2];
+        if (mx <= kMixedSwitch || f32_stall[s2] >= 2 || f32_it[s2] >= kMixedMaxIt) {
+          mode[s2] = 0; changed = true; switched = true; just[s2] = 1;
+        }
+        any = true;
+        continue;
+      }
       if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
       if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
       else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
@@ -1216,12 +1280,22 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       fprintf(stderr, " lam %.14g %.14g %.14g\n", lm[0], lm[1], lm[B.lob[0].k - 1]);
     }
     if (!any || it >= maxit) break;
-    if (changed) CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, active.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (changed) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, active.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+      CUDA_TRY(ctx, cudaMemcpyAsync(B.d_mode, mode.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    if (switched) {   // FP64 images of [X | P] before mixing them with FP64 W images
+      std::vector<int> rf(ns, 2);
+      for (int s2 = 0; s2 < ns; ++s2) if (just[s2]) rf[s2] = 0;
+      CUDA_TRY(ctx, cudaMemcpyAsync(B.d_refresh, rf.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+      refresh_XP(B, st);
+      CUDA_TRY(ctx, cudaStreamSynchronize(st));   // rf is a host temporary
+    }
     // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
-    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, st); }
+    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, st, B.any_mixed); }
     if (B.fwdR.n) {
       mv_fwd(B, B.fwdR, st);
-      { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st); }
+      { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
       mv_inv(B, B.invPW, st);
     }
     normalize(B.normW, B.kmax, st);
@@ -1727,6 +1801,7 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   FftTask ti = tf; ti.x = nullptr; ti.X = Y; ti.y = dy; ti.ldy = n; ti.beta = 0.0;
   BmulTask bm = {0, Q.M, H.m0, nvec, which == FOCK_OP_H ? Q.CHo : Q.CSo, nullptr, X, Y, nullptr};
   EApplyTask ea;
+  std::memset(&ea, 0, sizeof(ea));
   ea.prob = 0; ea.m0 = H.m0; ea.ncol = nvec; ea.nrows = Q.nErows; ea.rows = Q.Erows; ea.rowptr = Q.Erowptr;
   ea.cols = Q.Ecols; ea.vals = which == FOCK_OP_H ? Q.EH : Q.ES; ea.x = dx; ea.ldx = n; ea.y = dy; ea.ldy = n;
   char hbuf[4096];
@@ -1736,9 +1811,9 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   std::memcpy(hbuf + 1536, &ea, sizeof(ea));
   CUDA_TRY(ctx, cudaMemcpyAsync(tasks, hbuf, 2048, cudaMemcpyHostToDevice, st));
   int chunks = (H.m0 * ((nvec + 1) / 2) + cc - 1) / cc;
-  launch_fft((const FftTask*)tasks, 1, chunks, Q.M, cc, +1, st);
-  launch_blockmul((const BmulTask*)(tasks + 1024), 1, Q.M, H.m0, st);
-  launch_fft((const FftTask*)(tasks + 512), 1, chunks, Q.M, cc, -1, st);
+  launch_fft((const FftTask*)tasks, 1, chunks, Q.M, cc, +1, st, false);
+  launch_blockmul((const BmulTask*)(tasks + 1024), 1, Q.M, H.m0, st, false);
+  launch_fft((const FftTask*)(tasks + 512), 1, chunks, Q.M, cc, -1, st, false);
   if (Q.nE) launch_eapply((const EApplyTask*)(tasks + 1536), 1, eapply_grid((long long)Q.nErows * H.m0 * nvec), st);
   if (!on_device) CUDA_TRY(ctx, cudaMemcpyAsync(y, dy, nbytes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(ctx, cudaStreamSynchronize(st));

@@ -192,6 +192,7 @@ struct FftTask {
   double* y; int ldy;             // inverse output
   double beta;                    // y = beta*y + Re(.)/M
   int cc;                         // columns per CTA
+  const int* mode;                // null: FP64 only; else the problem's mode (0 FP64, 1 FP32)
 };
 
 struct BmulTask {
@@ -199,6 +200,7 @@ struct BmulTask {
   const cplx* B1; const cplx* B2;  // [M][m0*m0] (B2 optional)
   const cplx* X;                   // [M][m0*ncol]
   cplx* Y1; cplx* Y2;
+  const int* mode;                 // as FftTask::mode
 };
 
 struct EApplyTask {
@@ -209,6 +211,7 @@ struct EApplyTask {
   const double* vals;   // [nnz][m0*m0]
   const double* x; int ldx;
   double* y; int ldy;
+  const int* mode;      // null: always; else only while *mode == 0 (image refresh lists)
 };
 
 struct InitTask { int n, k, ld; uint64_t seed; double* X; };
@@ -240,6 +243,7 @@ struct RRTask {
   double* lam;            // out [k]
   double* Cc;             // out [nb x 2k] (ld): [C | C with the first k rows zeroed]
   int* fail;              // out: 1 if Y^T S Y was not numerically positive definite
+  const int* mode;        // mixed form: 1 while the images are FP32 (coarser drop threshold)
 };
 
 struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };
@@ -256,6 +260,7 @@ struct BandTask {
   int* fail;                               // out: 1 if every attempt broke down
   const double* R; double* W; int ld;      // solve: W = A^-1 R (n x k, ld)
   const int* active;
+  int fp32;                                // 1: solve in FP32 arithmetic (mixed form)
 };
 
 // Canonical orthogonalisation of a box chain's cell basis: Xc (m0 x m0,

@@ -149,19 +149,23 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
 // W = (L L^T)^-1 R.  blockIdx.y picks a group of kBandCols columns; a work
 // item is (row mu of the block, column), and the nsplit threads of an item
 // share its sum over the D off-diagonal blocks (partial sums reduced in
-// shared memory).  The diagonal slots hold L_JJ^-1.
+// shared memory).  The diagonal slots hold L_JJ^-1.  R = float: the same
+// solve in FP32 arithmetic (mixed form: the preconditioner only shapes the
+// search directions); each variant skips the tasks of the other.
 constexpr int kBandCols = 4;
 
+template <typename R>
 __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
   const BandTask T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
+  if ((T.fp32 != 0) != (sizeof(R) == 4)) return;
   const int c0 = blockIdx.y * kBandCols;
   if (c0 >= T.k) return;
   const int nc = min(kBandCols, T.k - c0);
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L, ld = T.ld;
   const double* band = T.band;
-  __shared__ double part[256];
-  __shared__ double tv[MAXM0 * kBandCols];
+  __shared__ R part[256];
+  __shared__ R tv[MAXM0 * kBandCols];
   const int items = m0 * nc;
   const int nsplit = max(1, min((int)blockDim.x / items, 8));
   const int tid = threadIdx.x;
@@ -172,19 +176,19 @@ __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
   const double* Rc = T.R + (size_t)ld * c;
   // forward: y_J = L_JJ^-1 (r_J - sum_d L[J][J-d] y_{J-d})
   for (int J = 0; J < L; ++J) {
-    double s = 0.0;
+    R s = 0;
     if (on) {
       const int dmax = min(D, J);
       for (int d = 1 + sp; d <= dmax; d += nsplit) {
         const double* l = bblk(const_cast<double*>(band), D, m2, J - d, d) + mu * m0;   // block (J, J-d)
         const double* y = Wc + (size_t)((J - d) * m0);
-        for (int q = 0; q < m0; ++q) s -= l[q] * y[q];
+        for (int q = 0; q < m0; ++q) s -= (R)l[q] * (R)y[q];
       }
       part[tid] = s;
     }
     __syncthreads();
     if (on && sp == 0) {
-      double r = Rc[(size_t)(J * m0 + mu)];
+      R r = (R)Rc[(size_t)(J * m0 + mu)];
       for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
       tv[item] = r;
     }
@@ -192,27 +196,27 @@ __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
     if (on && sp == 0) {
       const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0) + mu * m0;
       const int cb = (item / m0) * m0;
-      double y = 0.0;
-      for (int q = 0; q <= mu; ++q) y += iv[q] * tv[cb + q];
-      Wc[(size_t)(J * m0 + mu)] = y;
+      R y = 0;
+      for (int q = 0; q <= mu; ++q) y += (R)iv[q] * tv[cb + q];
+      Wc[(size_t)(J * m0 + mu)] = (double)y;
     }
     __syncthreads();
   }
   // backward: x_J = L_JJ^-T (y_J - sum_d L[J+d][J]^T x_{J+d})
   for (int J = L - 1; J >= 0; --J) {
-    double s = 0.0;
+    R s = 0;
     if (on) {
       const int dmax = min(D, L - 1 - J);
       for (int d = 1 + sp; d <= dmax; d += nsplit) {
         const double* l = bblk(const_cast<double*>(band), D, m2, J, d);   // block (J+d, J): column mu
         const double* x = Wc + (size_t)((J + d) * m0);
-        for (int q = 0; q < m0; ++q) s -= l[q * m0 + mu] * x[q];
+        for (int q = 0; q < m0; ++q) s -= (R)l[q * m0 + mu] * (R)x[q];
       }
       part[tid] = s;
     }
     __syncthreads();
     if (on && sp == 0) {
-      double r = Wc[(size_t)(J * m0 + mu)];
+      R r = (R)Wc[(size_t)(J * m0 + mu)];
       for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
       tv[item] = r;
     }
@@ -220,9 +224,9 @@ __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
     if (on && sp == 0) {
       const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0);
       const int cb = (item / m0) * m0;
-      double x = 0.0;
-      for (int q = mu; q < m0; ++q) x += iv[q * m0 + mu] * tv[cb + q];
-      Wc[(size_t)(J * m0 + mu)] = x;
+      R x = 0;
+      for (int q = mu; q < m0; ++q) x += (R)iv[q * m0 + mu] * tv[cb + q];
+      Wc[(size_t)(J * m0 + mu)] = (double)x;
     }
     __syncthreads();
   }
@@ -231,8 +235,11 @@ __global__ void k_band_solve(const BandTask* __restrict__ tasks) {
 void launch_band_factor(const BandTask* t, int n, cudaStream_t st) {
   if (n) k_band_factor<<<n, 256, 0, st>>>(t);
 }
-void launch_band_solve(const BandTask* t, int n, int kmax, cudaStream_t st) {
-  if (n) k_band_solve<<<dim3(n, (kmax + kBandCols - 1) / kBandCols), 256, 0, st>>>(t);
+void launch_band_solve(const BandTask* t, int n, int kmax, cudaStream_t st, bool mixed) {
+  if (!n) return;
+  const dim3 g(n, (kmax + kBandCols - 1) / kBandCols);
+  k_band_solve<double><<<g, 256, 0, st>>>(t);
+  if (mixed) k_band_solve<float><<<g, 256, 0, st>>>(t);
 }
 
 }  // namespace fock

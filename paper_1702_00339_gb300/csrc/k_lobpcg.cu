@@ -446,11 +446,13 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
   }
   __syncthreads();
   cta_jacobi(Tz, Qz, kk, kj);
-  for (int i = threadIdx.x; i < kk; i += blockDim.x) {   // ascending order (ties by index)
-    const double di = Tz[i * kj + i];
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) {   // ascending order, ties by index, NaN last:
+    double di = Tz[i * kj + i];                          // the ranks are always a permutation
+    if (isnan(di)) di = DBL_MAX;
     int rank = 0;
     for (int j = 0; j < kk; ++j) {
-      const double dj = Tz[j * kj + j];
+      double dj = Tz[j * kj + j];
+      if (isnan(dj)) dj = DBL_MAX;
       rank += (dj < di) || (dj == di && j < i);
     }
     ord[rank] = i;
@@ -494,7 +496,9 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   const RRTask T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
   extern __shared__ double rr_smem[];
-  const double kDropRel = 1e-10;
+  // basis directions whose S-independent part is below kDropRel are dropped:
+  // 1e-10 with FP64 images, 1e-6 while the images are FP32 (their noise level)
+  const double kDropRel = (T.mode && *T.mode) ? 1e-6 : 1e-10;
   const int ld = T.ld, k = T.k, nb = T.nb;
   // working matrices in shared memory when 3 ld^2 doubles fit, else global
   const bool in_smem = (3 * ld * ld * (int)sizeof(double) <= smem_bytes);

@@ -30,42 +30,64 @@ __global__ void k_twiddle(CircDev* circs, int n) {
 
 
 
-// dir = +1 forward (w), -1 inverse (conj w).
-template <int DIR>
+// Complex type of the working precision.
+template <typename R> struct CT;
+template <> struct CT<double> { using T = cplx; };
+template <> struct CT<float> { using T = float2; };
+template <typename C, typename R> __device__ inline C mkc(R a, R b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ inline C addc(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ inline C subc(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ inline C mulc(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+
+// Does this launch variant handle the task?  mode null: FP64 only; else the
+// problem's current precision (0 FP64, 1 FP32).
+template <typename R> __device__ inline bool mode_match(const int* mode) {
+  const int m = mode ? *mode : 0;
+  return (sizeof(R) == 4) ? (m == 1) : (m == 0);
+}
+
+// dir = +1 forward (w), -1 inverse (conj w); R = double (FP64 form) or float
+// (early iterations of the mixed form).
+template <int DIR, typename R>
 __global__ void k_fft(const FftTask* __restrict__ tasks) {
-  extern __shared__ cplx sm[];
+  using C = typename CT<R>::T;
+  extern __shared__ __align__(16) unsigned char fft_sbuf[];
   const FftTask T = tasks[blockIdx.y];
-  const CircDev C = *T.circ;
-  const int M = C.M, CC = T.cc;
+  if (!mode_match<R>(T.mode)) return;
+  const CircDev Cd = *T.circ;
+  const int M = Cd.M, CC = T.cc;
   const int npair = (T.ncol + 1) >> 1;    // two real columns per complex transform
   const int ncols = T.m0 * npair;
   const int c0 = blockIdx.x * CC;
   if (c0 >= ncols) return;
   const int ncc = min(CC, ncols - c0);
-  cplx* A = sm;
-  cplx* B = sm + (size_t)M * CC;
+  C* A = reinterpret_cast<C*>(fft_sbuf);
+  C* B = A + (size_t)M * CC;
+  C* Xg = reinterpret_cast<C*>(T.X);
   // load
   for (int it = threadIdx.x; it < M * CC; it += blockDim.x) {
     int k = it / CC, cc = it % CC;
-    cplx val = cmk(0.0, 0.0);
+    C val = mkc<C, R>(0, 0);
     if (cc < ncc) {
       int c = c0 + cc;
       if (DIR > 0) {
         if (k < T.L) {
           int mu = c % T.m0, p = c / T.m0;
           const double* xc = T.x + (size_t)(k * T.m0 + mu) + (size_t)T.ldx * (2 * p);
-          val = cmk(xc[0], (2 * p + 1 < T.ncol) ? xc[T.ldx] : 0.0);
+          val = mkc<C, R>((R)xc[0], (2 * p + 1 < T.ncol) ? (R)xc[T.ldx] : (R)0);
         }
       } else {
-        val = T.X[(size_t)k * ncols + c];
+        val = Xg[(size_t)k * ncols + c];
       }
     }
     A[it] = val;
   }
   __syncthreads();
   int Ps = 1;
-  for (int s = 0; s < C.nfac; ++s) {
-    const int r = C.fac[s];
+  for (int s = 0; s < Cd.nfac; ++s) {
+    const int r = Cd.fac[s];
     const int Pn = Ps * r, m = M / Pn;
     const int nb = M / r;
     const int stepr = M / r;                 // w_r = tw[stepr]
@@ -73,37 +95,37 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
       const int b = it / CC, cc = it % CC;
       const int kp = b / Ps, j = b % Ps;
       // inputs times the stage twiddles w_{Pn}^{q j} = tw[q j m]
-      cplx a[5];
+      C a[5];
       const int jm = j * m;
       for (int q = 0; q < r; ++q) {
-        cplx x = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
+        C x = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
         if (q) {
-          cplx w = C.tw[(q * jm) % M];
-          if (DIR < 0) w.y = -w.y;
-          x = cmul(w, x);
+          cplx w64 = Cd.tw[(q * jm) % M];
+          C w = mkc<C, R>((R)w64.x, (R)(DIR < 0 ? -w64.y : w64.y));
+          x = mulc(w, x);
         }
         a[q] = x;
       }
-      cplx o[5];
+      C o[5];
       if (r == 2) {
-        o[0] = cadd(a[0], a[1]);
-        o[1] = csub(a[0], a[1]);
+        o[0] = addc(a[0], a[1]);
+        o[1] = subc(a[0], a[1]);
       } else if (r == 4) {
-        cplx t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-        cplx t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+        C t0 = addc(a[0], a[2]), t1 = subc(a[0], a[2]);
+        C t2 = addc(a[1], a[3]), t3 = subc(a[1], a[3]);
         // multiply t3 by -i (forward) or +i (inverse)
-        cplx t3r = (DIR > 0) ? cmk(t3.y, -t3.x) : cmk(-t3.y, t3.x);
-        o[0] = cadd(t0, t2);
-        o[2] = csub(t0, t2);
-        o[1] = cadd(t1, t3r);
-        o[3] = csub(t1, t3r);
+        C t3r = (DIR > 0) ? mkc<C, R>(t3.y, -t3.x) : mkc<C, R>(-t3.y, t3.x);
+        o[0] = addc(t0, t2);
+        o[2] = subc(t0, t2);
+        o[1] = addc(t1, t3r);
+        o[3] = subc(t1, t3r);
       } else {   // r = 3 or 5: direct small DFT with the table's r-th roots
         for (int p = 0; p < r; ++p) {
-          cplx acc = a[0];
+          C acc = a[0];
           for (int q = 1; q < r; ++q) {
-            cplx w = C.tw[((q * p) % r) * stepr];
-            if (DIR < 0) w.y = -w.y;
-            acc = cadd(acc, cmul(w, a[q]));
+            cplx w64 = Cd.tw[((q * p) % r) * stepr];
+            C w = mkc<C, R>((R)w64.x, (R)(DIR < 0 ? -w64.y : w64.y));
+            acc = addc(acc, mulc(w, a[q]));
           }
           o[p] = acc;
         }
@@ -111,14 +133,14 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
       for (int p = 0; p < r; ++p) B[(size_t)(kp * Pn + j + Ps * p) * CC + cc] = o[p];
     }
     __syncthreads();
-    cplx* t = A; A = B; B = t;
+    C* t = A; A = B; B = t;
     Ps = Pn;
   }
   // store
   if (DIR > 0) {
     for (int it = threadIdx.x; it < M * CC; it += blockDim.x) {
       int k = it / CC, cc = it % CC;
-      if (cc < ncc) T.X[(size_t)k * ncols + c0 + cc] = A[it];
+      if (cc < ncc) Xg[(size_t)k * ncols + c0 + cc] = A[it];
     }
   } else {
     const double inv = 1.0 / (double)M;
@@ -127,7 +149,7 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
       if (cc < ncc) {
         int c = c0 + cc, mu = c % T.m0, p = c / T.m0;
         size_t o = (size_t)(k * T.m0 + mu) + (size_t)T.ldy * (2 * p);
-        double re = A[it].x * inv, im = A[it].y * inv;
+        double re = (double)A[it].x * inv, im = (double)A[it].y * inv;
         T.y[o] = (T.beta == 0.0) ? re : T.beta * T.y[o] + re;
         if (2 * p + 1 < T.ncol) {
           o += (size_t)T.ldy;
@@ -138,57 +160,63 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
   }
 }
 
-
-
 // Per Fourier index pair (j, M - j), j <= M/2.  X holds the transforms of
 // column pairs packed as z = x1 + i x2, so X1_j = (Z_j + conj Z_{M-j}) / 2 and
 // X2_j = -i (Z_j - conj Z_{M-j}) / 2.  With real generators
 // Chat_{M-j} = conj(Chat_j), hence Y_{M-j} = conj(Y_j) for each real column,
 // and the outputs are packed again as W = Y1 + i Y2 for the inverse transform.
+template <typename R>
 __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
-  extern __shared__ cplx sb[];
+  using C = typename CT<R>::T;
+  extern __shared__ __align__(16) unsigned char bm_smem[];
   const BmulTask T = tasks[blockIdx.y];
+  if (!mode_match<R>(T.mode)) return;
   const int j = blockIdx.x;
   if (2 * j > T.M) return;
   const int jm = (T.M - j) % T.M;
   const int m0 = T.m0, np = m0 * m0, nc = m0 * ((T.ncol + 1) >> 1);
-  cplx* b1 = sb;
-  cplx* b2 = sb + np;
+  C* b1 = reinterpret_cast<C*>(bm_smem);
+  C* b2 = b1 + np;
   for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
-    b1[pr] = T.B1[(size_t)j * np + pr];
-    if (T.B2) b2[pr] = T.B2[(size_t)j * np + pr];
+    cplx v = T.B1[(size_t)j * np + pr];
+    b1[pr] = mkc<C, R>((R)v.x, (R)v.y);
+    if (T.B2) { v = T.B2[(size_t)j * np + pr]; b2[pr] = mkc<C, R>((R)v.x, (R)v.y); }
   }
   __syncthreads();
-  const cplx* zj = T.X + (size_t)j * nc;
-  const cplx* zm = T.X + (size_t)jm * nc;
+  const C* zj = reinterpret_cast<const C*>(T.X) + (size_t)j * nc;
+  const C* zm = reinterpret_cast<const C*>(T.X) + (size_t)jm * nc;
+  C* Y1 = reinterpret_cast<C*>(T.Y1);
+  C* Y2 = reinterpret_cast<C*>(T.Y2);
+  const R half = (R)0.5;
   for (int it = threadIdx.x; it < nc; it += blockDim.x) {
     const int mu = it % m0, p = it / m0;
-    cplx y1a = cmk(0.0, 0.0), y2a = cmk(0.0, 0.0), y1b = cmk(0.0, 0.0), y2b = cmk(0.0, 0.0);
+    C y1a = mkc<C, R>(0, 0), y2a = mkc<C, R>(0, 0), y1b = mkc<C, R>(0, 0), y2b = mkc<C, R>(0, 0);
     for (int nu = 0; nu < m0; ++nu) {
-      const cplx a = zj[p * m0 + nu], b = zm[p * m0 + nu];
-      const cplx x1 = cmk(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));    // (a + conj b) / 2
-      const cplx x2 = cmk(0.5 * (a.y + b.y), -0.5 * (a.x - b.x));   // -i (a - conj b) / 2
-      const cplx c1 = b1[mu * m0 + nu];
-      y1a = cadd(y1a, cmul(c1, x1));
-      y2a = cadd(y2a, cmul(c1, x2));
+      const C a = zj[p * m0 + nu], b = zm[p * m0 + nu];
+      const C x1 = mkc<C, R>(half * (a.x + b.x), half * (a.y - b.y));    // (a + conj b) / 2
+      const C x2 = mkc<C, R>(half * (a.y + b.y), -half * (a.x - b.x));   // -i (a - conj b) / 2
+      const C c1 = b1[mu * m0 + nu];
+      y1a = addc(y1a, mulc(c1, x1));
+      y2a = addc(y2a, mulc(c1, x2));
       if (T.B2) {
-        const cplx c2 = b2[mu * m0 + nu];
-        y1b = cadd(y1b, cmul(c2, x1));
-        y2b = cadd(y2b, cmul(c2, x2));
+        const C c2 = b2[mu * m0 + nu];
+        y1b = addc(y1b, mulc(c2, x1));
+        y2b = addc(y2b, mulc(c2, x2));
       }
     }
     // W_j = Y1 + i Y2, W_{M-j} = conj(Y1) + i conj(Y2)
-    T.Y1[(size_t)j * nc + it] = cmk(y1a.x - y2a.y, y1a.y + y2a.x);
-    if (jm != j) T.Y1[(size_t)jm * nc + it] = cmk(y1a.x + y2a.y, -y1a.y + y2a.x);
+    Y1[(size_t)j * nc + it] = mkc<C, R>(y1a.x - y2a.y, y1a.y + y2a.x);
+    if (jm != j) Y1[(size_t)jm * nc + it] = mkc<C, R>(y1a.x + y2a.y, -y1a.y + y2a.x);
     if (T.B2) {
-      T.Y2[(size_t)j * nc + it] = cmk(y1b.x - y2b.y, y1b.y + y2b.x);
-      if (jm != j) T.Y2[(size_t)jm * nc + it] = cmk(y1b.x + y2b.y, -y1b.y + y2b.x);
+      Y2[(size_t)j * nc + it] = mkc<C, R>(y1b.x - y2b.y, y1b.y + y2b.x);
+      if (jm != j) Y2[(size_t)jm * nc + it] = mkc<C, R>(y1b.x + y2b.y, -y1b.y + y2b.x);
     }
   }
 }
 
 __global__ void k_eapply(const EApplyTask* __restrict__ tasks) {
   const EApplyTask T = tasks[blockIdx.y];
+  if (T.mode && *T.mode != 0) return;
   const int m0 = T.m0, np = m0 * m0;
   const int tot = T.nrows * m0 * T.ncol;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
@@ -212,24 +240,35 @@ void launch_twiddles(CircDev* circs, int n, cudaStream_t st) {
 
 size_t fft_smem(int M, int cc) { return (size_t)2 * M * cc * sizeof(cplx); }
 
+// mixed: the batch has problems in the mixed form; their FP32 variant is
+// launched too (each variant skips the tasks of the other precision).
 void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
-                cudaStream_t st) {
+                cudaStream_t st, bool mixed) {
   if (!ntask) return;
   size_t sm = fft_smem(maxM, cc);
   if (dir > 0) {
-    if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fft<1>);
-    k_fft<1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    if (sm > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<1, double>));
+    k_fft<1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    if (mixed) {
+      if (sm / 2 > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<1, float>));
+      k_fft<1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
+    }
   } else {
-    if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fft<-1>);
-    k_fft<-1><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    if (sm > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<-1, double>));
+    k_fft<-1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    if (mixed) {
+      if (sm / 2 > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<-1, float>));
+      k_fft<-1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
+    }
   }
 }
 
-void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st) {
+void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st, bool mixed) {
   if (!ntask) return;
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul);
-  k_blockmul<<<dim3(maxM / 2 + 1, ntask), 256, sm, st>>>(tasks);
+  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul<double>);
+  k_blockmul<double><<<dim3(maxM / 2 + 1, ntask), 256, sm, st>>>(tasks);
+  if (mixed) k_blockmul<float><<<dim3(maxM / 2 + 1, ntask), 256, sm / 2, st>>>(tasks);
 }
 
 // gx: CTAs per task, from the largest task's work (rows x m0 x columns / 256)

@@ -18,8 +18,8 @@
 namespace fock {
 int blocks_matvec_view(const fock_blocks* b, MatvecView* v);
 void set_ctx_error(fock_ctx* c, const char* msg);
-void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t);
-void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t);
+void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t, bool);
+void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t, bool);
 void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
 int eapply_grid(long long items);
 }  // namespace fock
@@ -103,9 +103,9 @@ extern "C" int fock_toeplitz_matvec_noalloc(fock_ctx* ctx, const fock_blocks* b,
     return FOCK_ECUDA;
   }
   const int chunks = (v.m0 * ((nvec + 1) / 2) + cc - 1) / cc;
-  launch_fft((const FftTask*)s, 1, chunks, v.M, cc, +1, v.stream);
-  launch_blockmul((const BmulTask*)(s + 512), 1, v.M, v.m0, v.stream);
-  launch_fft((const FftTask*)(s + 256), 1, chunks, v.M, cc, -1, v.stream);
+  launch_fft((const FftTask*)s, 1, chunks, v.M, cc, +1, v.stream, false);
+  launch_blockmul((const BmulTask*)(s + 512), 1, v.M, v.m0, v.stream, false);
+  launch_fft((const FftTask*)(s + 256), 1, chunks, v.M, cc, -1, v.stream, false);
   if (v.nE) launch_eapply((const EApplyTask*)(s + 768), 1, eapply_grid((long long)v.nErows * v.m0 * nvec), v.stream);
   cudaError_t e = cudaStreamSynchronize(v.stream);
   if (e == cudaSuccess) e = cudaGetLastError();

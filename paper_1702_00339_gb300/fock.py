@@ -18,6 +18,7 @@ _LIBPATH = os.path.join(_PKG, "libfock.so")
 FOCK_OK, FOCK_EINVAL, FOCK_ENOMEM, FOCK_ENOCONV = 0, -1, -2, -3
 FOCK_ETIMEOUT, FOCK_EAGAIN, FOCK_ECUDA = -4, -5, -6
 FOCK_OP_H, FOCK_OP_S = 0, 1
+FOCK_FP64, FOCK_MIXED = 0, 1
 _NAMES = {0: "FOCK_OK", -1: "FOCK_EINVAL", -2: "FOCK_ENOMEM", -3: "FOCK_ENOCONV",
           -4: "FOCK_ETIMEOUT", -5: "FOCK_EAGAIN", -6: "FOCK_ECUDA"}
 
@@ -171,7 +172,7 @@ class _Marshal:
             self.keep.append(d)
             s.defects = C.cast(d, C.POINTER(c_defect))
         s.k_eig = int(p.k_eig)
-        s.precision = 0
+        s.precision = int(getattr(p, "precision", 0))
         self.s = s
 
 
