@@ -1232,9 +1232,10 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   std::vector<double> hres((size_t)ns * B.kmax);
   std::vector<int> active(ns, 1);
   // a residual that stops improving below kFloorTol is at the rounding floor
-  // of the pencil (it scales with kappa(S)); Rayleigh quotients are then
-  // accurate to about the square of the residual, so the problem is done
-  const double kFloorTol = 1e-8;
+  // of the pencil (it scales with kappa(S), up to ~1e8 after the cell
+  // reduction); Rayleigh quotients are then accurate to about the square of
+  // the residual over the gap, so the problem is done
+  const double kFloorTol = 1e-6;
   const int kStagnation = 8;
   std::vector<double> best(ns, INFINITY);
   std::vector<int> best_it(ns, 0);
