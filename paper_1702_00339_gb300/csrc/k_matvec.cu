@@ -10,8 +10,8 @@
 //  k_fft      batched mixed-radix Stockham FFT of the columns, two real
 //             columns packed per complex transform (z = x1 + i x2); one CTA
 //             holds a chunk of packed columns of one problem in shared memory
-//  k_blockmul per Fourier index pair (j, M-j): m0 x m0 complex block times the
-//             unpacked transforms of the real columns
+//  k_blockmul per Fourier index: m0 x m0 complex block times the packed
+//             columns (linear in them, so no unpacking is needed)
 //  k_eapply   y += E x over the block rows that carry boundary/defect blocks
 #include <algorithm>
 
@@ -90,7 +90,6 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
     const int r = Cd.fac[s];
     const int Pn = Ps * r, m = M / Pn;
     const int nb = M / r;
-    const int stepr = M / r;                 // w_r = tw[stepr]
     for (int it = threadIdx.x; it < nb * CC; it += blockDim.x) {
       const int b = it / CC, cc = it % CC;
       const int kp = b / Ps, j = b % Ps;
@@ -119,16 +118,32 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
         o[2] = subc(t0, t2);
         o[1] = addc(t1, t3r);
         o[3] = subc(t1, t3r);
-      } else {   // r = 3 or 5: direct small DFT with the table's r-th roots
-        for (int p = 0; p < r; ++p) {
-          C acc = a[0];
-          for (int q = 1; q < r; ++q) {
-            cplx w64 = Cd.tw[((q * p) % r) * stepr];
-            C w = mkc<C, R>((R)w64.x, (R)(DIR < 0 ? -w64.y : w64.y));
-            acc = addc(acc, mulc(w, a[q]));
-          }
-          o[p] = acc;
-        }
+      } else if (r == 3) {
+        // o1,2 = a0 - (a1 + a2)/2 -/+ i sin(2pi/3) (a1 - a2) (forward; + / - inverse)
+        const R h3 = (R)0.86602540378443864676;   // sin(2 pi / 3)
+        C t1 = addc(a[1], a[2]);
+        C t2 = mkc<C, R>(a[0].x - (R)0.5 * t1.x, a[0].y - (R)0.5 * t1.y);
+        C d = subc(a[1], a[2]);
+        C id = (DIR > 0) ? mkc<C, R>(h3 * d.y, -h3 * d.x) : mkc<C, R>(-h3 * d.y, h3 * d.x);
+        o[0] = addc(a[0], t1);
+        o[1] = addc(t2, id);
+        o[2] = subc(t2, id);
+      } else {   // r == 5
+        const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;   // cos 2pi/5, cos 4pi/5
+        const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;    // sin 2pi/5, sin 4pi/5
+        C b1 = addc(a[1], a[4]), b2 = addc(a[2], a[3]);
+        C d1 = subc(a[1], a[4]), d2 = subc(a[2], a[3]);
+        C e1 = mkc<C, R>(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
+        C e2 = mkc<C, R>(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
+        C f1 = mkc<C, R>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);   // times -i (forward)
+        C f2 = mkc<C, R>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+        C g1 = (DIR > 0) ? mkc<C, R>(f1.y, -f1.x) : mkc<C, R>(-f1.y, f1.x);
+        C g2 = (DIR > 0) ? mkc<C, R>(f2.y, -f2.x) : mkc<C, R>(-f2.y, f2.x);
+        o[0] = addc(a[0], addc(b1, b2));
+        o[1] = addc(e1, g1);
+        o[4] = subc(e1, g1);
+        o[2] = addc(e2, g2);
+        o[3] = subc(e2, g2);
       }
       for (int p = 0; p < r; ++p) B[(size_t)(kp * Pn + j + Ps * p) * CC + cc] = o[p];
     }
@@ -160,11 +175,10 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
   }
 }
 
-// Per Fourier index pair (j, M - j), j <= M/2.  X holds the transforms of
-// column pairs packed as z = x1 + i x2, so X1_j = (Z_j + conj Z_{M-j}) / 2 and
-// X2_j = -i (Z_j - conj Z_{M-j}) / 2.  With real generators
-// Chat_{M-j} = conj(Chat_j), hence Y_{M-j} = conj(Y_j) for each real column,
-// and the outputs are packed again as W = Y1 + i Y2 for the inverse transform.
+// Per Fourier index j: W_j = Chat_j Z_j on the packed columns.  A packed
+// column is z = x1 + i x2 of two real columns; the operator is linear and the
+// same for both, so Chat_j Z_j = Chat_j X1_j + i Chat_j X2_j, and the inverse
+// transform returns y1 + i y2 with y1, y2 real (Chat_{M-j} = conj Chat_j).
 template <typename R>
 __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
   using C = typename CT<R>::T;
@@ -172,8 +186,7 @@ __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
   const BmulTask T = tasks[blockIdx.y];
   if (!mode_match<R>(T.mode)) return;
   const int j = blockIdx.x;
-  if (2 * j > T.M) return;
-  const int jm = (T.M - j) % T.M;
+  if (j >= T.M) return;
   const int m0 = T.m0, np = m0 * m0, nc = m0 * ((T.ncol + 1) >> 1);
   C* b1 = reinterpret_cast<C*>(bm_smem);
   C* b2 = b1 + np;
@@ -184,33 +197,18 @@ __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
   }
   __syncthreads();
   const C* zj = reinterpret_cast<const C*>(T.X) + (size_t)j * nc;
-  const C* zm = reinterpret_cast<const C*>(T.X) + (size_t)jm * nc;
-  C* Y1 = reinterpret_cast<C*>(T.Y1);
-  C* Y2 = reinterpret_cast<C*>(T.Y2);
-  const R half = (R)0.5;
+  C* Y1 = reinterpret_cast<C*>(T.Y1) + (size_t)j * nc;
+  C* Y2 = reinterpret_cast<C*>(T.Y2) + (size_t)j * nc;
   for (int it = threadIdx.x; it < nc; it += blockDim.x) {
     const int mu = it % m0, p = it / m0;
-    C y1a = mkc<C, R>(0, 0), y2a = mkc<C, R>(0, 0), y1b = mkc<C, R>(0, 0), y2b = mkc<C, R>(0, 0);
+    C a1 = mkc<C, R>(0, 0), a2 = mkc<C, R>(0, 0);
     for (int nu = 0; nu < m0; ++nu) {
-      const C a = zj[p * m0 + nu], b = zm[p * m0 + nu];
-      const C x1 = mkc<C, R>(half * (a.x + b.x), half * (a.y - b.y));    // (a + conj b) / 2
-      const C x2 = mkc<C, R>(half * (a.y + b.y), -half * (a.x - b.x));   // -i (a - conj b) / 2
-      const C c1 = b1[mu * m0 + nu];
-      y1a = addc(y1a, mulc(c1, x1));
-      y2a = addc(y2a, mulc(c1, x2));
-      if (T.B2) {
-        const C c2 = b2[mu * m0 + nu];
-        y1b = addc(y1b, mulc(c2, x1));
-        y2b = addc(y2b, mulc(c2, x2));
-      }
+      const C x = zj[p * m0 + nu];
+      a1 = addc(a1, mulc(b1[mu * m0 + nu], x));
+      if (T.B2) a2 = addc(a2, mulc(b2[mu * m0 + nu], x));
     }
-    // W_j = Y1 + i Y2, W_{M-j} = conj(Y1) + i conj(Y2)
-    Y1[(size_t)j * nc + it] = mkc<C, R>(y1a.x - y2a.y, y1a.y + y2a.x);
-    if (jm != j) Y1[(size_t)jm * nc + it] = mkc<C, R>(y1a.x + y2a.y, -y1a.y + y2a.x);
-    if (T.B2) {
-      Y2[(size_t)j * nc + it] = mkc<C, R>(y1b.x - y2b.y, y1b.y + y2b.x);
-      if (jm != j) Y2[(size_t)jm * nc + it] = mkc<C, R>(y1b.x + y2b.y, -y1b.y + y2b.x);
-    }
+    Y1[it] = a1;
+    if (T.B2) Y2[it] = a2;
   }
 }
 
@@ -267,8 +265,8 @@ void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cuda
   if (!ntask) return;
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
   if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul<double>);
-  k_blockmul<double><<<dim3(maxM / 2 + 1, ntask), 256, sm, st>>>(tasks);
-  if (mixed) k_blockmul<float><<<dim3(maxM / 2 + 1, ntask), 256, sm / 2, st>>>(tasks);
+  k_blockmul<double><<<dim3(maxM, ntask), 256, sm, st>>>(tasks);
+  if (mixed) k_blockmul<float><<<dim3(maxM, ntask), 256, sm / 2, st>>>(tasks);
 }
 
 // gx: CTAs per task, from the largest task's work (rows x m0 x columns / 256)
