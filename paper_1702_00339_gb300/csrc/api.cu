@@ -224,6 +224,10 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (H.kind == 1) {
     int Nb = H.L[0] * H.m0;
     int kb = lobpcg_block(H.k_eig, Nb);
+    // whole-space block: the first Rayleigh-Ritz step is exact, so the mixed
+    // form has nothing to gain, and an FP32 Rayleigh-Ritz over [X | P | W]
+    // (P, W inside span X) would only see noise: solved in FP64
+    if (kb == Nb) H.mixed = 0;
     if (H.k_eig > Nb || 3 * kb > 255 || (kb < Nb && 3 * kb > Nb)) {
       why = "k_eig too large: k <= N_b and 3 (k + guard) <= min(N_b, 255) on chains with 3 N_b > 255"; return FOCK_EINVAL;
     }
@@ -911,7 +915,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
                     double alpha, double beta) {
         GemmTask g; g.active = l.active; g.n = n; g.a = a; g.b = b; g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb;
-        g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+        g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta; g.sym = 0;
         return g;
       };
       // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C  (same for HW, SW)
@@ -922,10 +926,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
         nw.push_back(gt(k, k, base, n, l.Cx, k, base + 2 * nk, n, -1.0, 1.0));
         npp.push_back(gt(k, k, base, n, l.Cx, k, base + nk, n, -1.0, 1.0));
       }
-      gg1.push_back(gt(k, k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0));
-      gg1.push_back(gt(k, k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
-      gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0));
-      gg3.push_back(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0));
+      // Gram matrices Y^T H Y, Y^T S Y: symmetric, upper tiles only
+      auto sym = [](GemmTask g) { g.sym = 1; return g; };
+      gg1.push_back(sym(gt(k, k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0)));
+      gg1.push_back(sym(gt(k, k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
+      gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0)));
+      gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
       r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
       r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
       // [X' | P'] = Y[:, :nb] Cc, then copied over [X | P]; images recomputed by a matvec

@@ -223,6 +223,7 @@ struct GemmTask {
   const double* B; int ldb;
   double* C; int ldc;
   double alpha, beta;
+  int sym;                     // TN with a symmetric result: upper tiles computed, mirrored
 };
 
 struct ResidTask {
@@ -323,4 +324,66 @@ __device__ inline double tridiag_eig_bisect(const double* d, const double* e, in
   return 0.5 * (lo + hi);
 }
 
+// idx-th (0-based, ascending) eigenvalue of the symmetric tridiagonal (d, e)
+// by Sturm bisection in FP32 (about 1e-7 of the spectral radius): used only
+// as the shift of FP64 inverse iteration, whose Rayleigh-Ritz step gives the
+// eigenvalues.  FP32 runs at 64x the FP64 rate on this part.
+__device__ inline float tridiag_bisect_f32(const double* d, const double* e, int m, int idx) {
+  float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.0f;
+  for (int i = 0; i < m; ++i) {
+    float r = (i > 0 ? fabsf((float)e[i - 1]) : 0.0f) + (i < m - 1 ? fabsf((float)e[i]) : 0.0f);
+    lo = fminf(lo, (float)d[i] - r);
+    hi = fmaxf(hi, (float)d[i] + r);
+    if (i < m - 1) emax = fmaxf(emax, fabsf((float)e[i]));
+  }
+  const float tnorm = fmaxf(fabsf(lo), fabsf(hi));
+  const float pivmin = FLT_MIN * fmaxf(1.0f, emax * emax);
+  lo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
+  hi += 4.0f * FLT_EPSILON * tnorm + pivmin;
+  for (int it = 0; it < 64; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    int cnt = 0;
+    float q = (float)d[0] - mid;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0f);
+    for (int i = 1; i < m; ++i) {
+      const float ei = (float)e[i - 1];
+      q = (float)d[i] - mid - ei * ei / q;
+      if (fabsf(q) < pivmin) q = -pivmin;
+      cnt += (q < 0.0f);
+    }
+    if (cnt > idx) hi = mid; else lo = mid;
+  }
+  return 0.5f * (lo + hi);
+}
+
+
+// idx-th eigenvalue to FP64 accuracy: the FP32 bisection's estimate is
+// bracketed by FP64 Sturm counts (the bracket widened when it misses) and
+// FP64 bisection runs only inside it -- about half the FP64 divisions of a
+// bisection over the whole Gershgorin interval.
+__device__ inline double tridiag_eig_hybrid(const double* d, const double* e, int m, int idx) {
+  double emax = 0.0, tn = 0.0;
+  for (int i = 0; i < m; ++i) {
+    tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0));
+    if (i < m - 1) emax = fmax(emax, fabs(e[i]));
+  }
+  const double pivmin = DBL_MIN * fmax(1.0, emax * emax);
+  const double g = (double)tridiag_bisect_f32(d, e, m, idx);
+  double w = 8.0 * (double)FLT_EPSILON * tn + pivmin;
+  double lo = g - w, hi = g + w;
+  bool ok = false;
+  for (int t = 0; t < 3 && !ok; ++t) {
+    ok = sturm_count(d, e, m, lo, pivmin) <= idx && sturm_count(d, e, m, hi, pivmin) > idx;
+    if (!ok) { w *= 16.0; lo = g - w; hi = g + w; }
+  }
+  if (!ok) return tridiag_eig_bisect(d, e, m, idx);
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
 }  // namespace fock

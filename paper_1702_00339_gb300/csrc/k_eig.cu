@@ -361,11 +361,11 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
   if (F.want == 1) {
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_bisect(dd, ee, r, i) : INFINITY;
+      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_hybrid(dd, ee, r, i) : INFINITY;
       if (F.blk) F.blk[(size_t)jl * m0 + i] = j;
     }
   } else if (threadIdx.x == 0) {
-    F.ev[jl] = (r > 0) ? tridiag_eig_bisect(dd, ee, r, 0) : INFINITY;
+    F.ev[jl] = (r > 0) ? tridiag_eig_hybrid(dd, ee, r, 0) : INFINITY;
   }
 }
 

@@ -46,12 +46,17 @@ __global__ void k_init_x(const InitTask* __restrict__ tasks) {
 
 
 
+// G = alpha A^T B (+ beta G), one output per thread of a 16 x 16 tile.  With
+// T.sym the result is symmetric: tiles below the diagonal are skipped and the
+// tiles above also write their transposes (diagonal tiles are computed in
+// full and not mirrored, so no entry has two writers).
 #define TT 16
 __global__ void k_gemm_tn(const GemmTask* __restrict__ tasks) {
   const GemmTask T = tasks[blockIdx.z];
   if (T.active && *T.active == 0) return;
   const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
   if (i0 >= T.a || j0 >= T.b) return;
+  if (T.sym && j0 < i0) return;
   __shared__ double As[TT][TT + 1], Bs[TT][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
   double acc = 0.0;
@@ -67,7 +72,9 @@ __global__ void k_gemm_tn(const GemmTask* __restrict__ tasks) {
   // thread (tx, ty) holds G[i0+tx][j0+ty]
   if (i0 + tx < T.a && j0 + ty < T.b) {
     double* g = T.C + (size_t)(i0 + tx) + (size_t)T.ldc * (j0 + ty);
-    *g = (T.beta == 0.0) ? T.alpha * acc : T.beta * *g + T.alpha * acc;
+    const double v = (T.beta == 0.0) ? T.alpha * acc : T.beta * *g + T.alpha * acc;
+    *g = v;
+    if (T.sym && j0 > i0) T.C[(size_t)(j0 + ty) + (size_t)T.ldc * (i0 + tx)] = v;
   }
 }
 
@@ -84,8 +91,6 @@ __global__ void k_gemm_nn(const GemmTask* __restrict__ tasks) {
     *c = (T.beta == 0.0) ? T.alpha * acc : T.beta * *c + T.alpha * acc;
   }
 }
-
-
 
 // Columns at or below lock_tol get R = 0 (soft locking).
 __global__ void k_resid(const ResidTask* __restrict__ tasks, double lock_tol) {
@@ -134,7 +139,8 @@ __global__ void k_resid(const ResidTask* __restrict__ tasks, double lock_tol) {
   __shared__ int lock;
   if (threadIdx.x == 0) {
     double den = fmax(fabs(l), 1e-300) * sqrt(r2[0]);
-    double rv = (den > 0.0) ? sqrt(r1[0]) / den : 0.0;
+    // a column with no S-image (zero or non-finite) is broken, never converged
+    double rv = (den > 0.0) ? sqrt(r1[0]) / den : NAN;
     T.res[c] = rv;
     lock = (rv <= lock_tol);
   }
@@ -227,40 +233,6 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
     __syncthreads();
     if (done) break;
   }
-}
-
-// idx-th (0-based, ascending) eigenvalue of the symmetric tridiagonal (d, e)
-// by Sturm bisection in FP32 (about 1e-7 of the spectral radius): used only
-// as the shift of FP64 inverse iteration, whose Rayleigh-Ritz step gives the
-// eigenvalues.  FP32 runs at 64x the FP64 rate on this part.
-__device__ inline float tridiag_bisect_f32(const double* d, const double* e, int m, int idx) {
-  float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.0f;
-  for (int i = 0; i < m; ++i) {
-    float r = (i > 0 ? fabsf((float)e[i - 1]) : 0.0f) + (i < m - 1 ? fabsf((float)e[i]) : 0.0f);
-    lo = fminf(lo, (float)d[i] - r);
-    hi = fmaxf(hi, (float)d[i] + r);
-    if (i < m - 1) emax = fmaxf(emax, fabsf((float)e[i]));
-  }
-  const float tnorm = fmaxf(fabsf(lo), fabsf(hi));
-  const float pivmin = FLT_MIN * fmaxf(1.0f, emax * emax);
-  lo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
-  hi += 4.0f * FLT_EPSILON * tnorm + pivmin;
-  for (int it = 0; it < 64; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    int cnt = 0;
-    float q = (float)d[0] - mid;
-    if (fabsf(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0f);
-    for (int i = 1; i < m; ++i) {
-      const float ei = (float)e[i - 1];
-      q = (float)d[i] - mid - ei * ei / q;
-      if (fabsf(q) < pivmin) q = -pivmin;
-      cnt += (q < 0.0f);
-    }
-    if (cnt > idx) hi = mid; else lo = mid;
-  }
-  return 0.5f * (lo + hi);
 }
 
 // ---- lowest eigenpairs of a dense symmetric matrix (whole CTA) ----
