@@ -694,6 +694,24 @@ void plan(Batch& B, Slab& S, Slab& U) {
         CanonTask ct;
         ct.m0 = H.m0; ct.D = Q.D; ct.nE = Q.nE; ct.TH = Q.TH; ct.TS = Q.TS; ct.EH = Q.EH; ct.ES = Q.ES;
         ct.Xc = Q.Xc; ct.kept = Q.kept; ct.THc = Q.THc; ct.TSc = Q.TSc; ct.EHc = Q.EHc; ct.ESc = Q.ESc;
+        // transposed partner of each boundary block: itself on the diagonal;
+        // else the entry at the mirrored position of the same kind and the
+        // same rank among that position's entries (a position can hold a
+        // wall block and a defect block)
+        std::vector<int> part(std::max(Q.nE, 1), -1);
+        for (int e = 0; e < Q.nE; ++e) {
+          if (Q.Ek[e] == Q.Em[e]) { part[e] = e; continue; }
+          int rank = 0;
+          for (int f = 0; f < e; ++f) rank += (Q.Ek[f] == Q.Ek[e] && Q.Em[f] == Q.Em[e]);
+          for (int f = 0, seen = 0; f < Q.nE; ++f)
+            if (Q.Ek[f] == Q.Em[e] && Q.Em[f] == Q.Ek[e] && seen++ == rank) {
+              if (Q.Ekind[f] == Q.Ekind[e]) part[e] = f;
+              break;
+            }
+        }
+        for (int e = 0; e < Q.nE; ++e)   // pairs must be mutual
+          if (part[e] >= 0 && part[part[e]] != e) part[e] = -1;
+        ct.Epart = U.put(part);
         B.canon.push_back(ct);
         B.maxcblk = std::max(B.maxcblk, 2 * (Q.D + 1) + 2 * Q.nE);
       }
@@ -1240,7 +1258,9 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   // a residual that stops improving below kFloorTol is at the rounding floor
   // of the pencil (it scales with kappa(S), up to ~1e8 after the cell
   // reduction); Rayleigh quotients are then accurate to about the square of
-  // the residual over the gap, so the problem is done
+  // the residual over the gap, so the problem is done, provided the current
+  // residual is still within a factor 10 of that floor (a state that broke
+  // down after reaching it keeps iterating, or ends unconverged)
   const double kFloorTol = 1e-6;
   const int kStagnation = 8;
   std::vector<double> best(ns, INFINITY);
@@ -1274,7 +1294,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
       if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
       else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
-      else if (best[s2] <= kFloorTol && it - best_it[s2] >= kStagnation) {
+      else if (best[s2] <= kFloorTol && mx <= 10.0 * best[s2] && it - best_it[s2] >= kStagnation) {
         active[s2] = 0; conv[s2] = 1; changed = true;
       }
       else any = true;
@@ -1285,6 +1305,10 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       std::vector<double> lm(B.kmax);
       cudaMemcpy(lm.data(), B.lob[0].lam, B.lob[0].k * 8, cudaMemcpyDeviceToHost);
       fprintf(stderr, " lam %.14g %.14g %.14g\n", lm[0], lm[1], lm[B.lob[0].k - 1]);
+      if (getenv("FOCK_DEBUG")[0] == '2') {   // per-column residuals and Ritz values of the first problem
+        for (int c = 0; c < B.lob[0].k; ++c)
+          fprintf(stderr, "   c%-3d %.3e %.12g\n", c, hres[c], lm[c]);
+      }
     }
     if (!any || it >= maxit) break;
     if (changed) {
@@ -1312,7 +1336,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     // Rayleigh-Ritz on [X | P | W]
     gemm_tn(B.g3, st);
     rr(B.rr3, st);
-    if (it < 3) dump("rr", it);
+    if (dbg && (it < 3 || (getenv("FOCK_DEBUG_IT") && it == atoi(getenv("FOCK_DEBUG_IT"))))) dump("rr", it);
     // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
     gemm_nn(B.u3, st);
     copies(B.cp2k, st);

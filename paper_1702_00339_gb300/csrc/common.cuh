@@ -275,6 +275,8 @@ struct CanonTask {
   int* kept;                              // out: kept directions
   double* THc; double* TSc;               // out transformed generators
   double* EHc; double* ESc;               // out transformed boundary blocks
+  const int* Epart;                       // [nE] index of the transposed partner block
+                                          // (self on the diagonal, -1 if none)
 };
 
 // Device pointers and sizes the matvec of an assembled box chain needs.

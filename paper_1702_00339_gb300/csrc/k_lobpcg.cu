@@ -278,12 +278,19 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
       pv[i] = tk * acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double K = 0.0;
-      for (int i = k + 1; i < r; ++i) K += a[i * ld + k] * pv[i];
-      s_K = 0.5 * tk * K;
+    {   // K = (tau / 2) v^T p, block reduction (red is free again here)
+      double kp = 0.0;
+      for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) kp += a[i * ld + k] * pv[i];
+      for (int o = 16; o > 0; o >>= 1) kp += __shfl_down_sync(0xffffffffu, kp, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = kp;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double K = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) K += red[w];
+        s_K = 0.5 * tk * K;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] -= s_K * a[i * ld + k];   // w
     __syncthreads();
     const int nt = r - k - 1;
@@ -503,27 +510,25 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   if (threadIdx.x == 0) s_r = nb;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    // argmax of the remaining diagonal over positions j..nb-1
+    // argmax of the remaining diagonal over positions j..nb-1 (larger value,
+    // ties to the lower position): per thread, per warp by shuffles, then
+    // across the warps by thread 0
     double best = -1.0;
     int bi = j;
     for (int i = j + threadIdx.x; i < nb; i += blockDim.x) {
       double d = dg[perm[i]];
       if (d > best) { best = d; bi = i; }
     }
-    red[threadIdx.x] = best;
-    rid[threadIdx.x] = bi;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) {
-        double o = red[threadIdx.x + st];
-        int oi = rid[threadIdx.x + st];
-        if (o > red[threadIdx.x] || (o == red[threadIdx.x] && oi < rid[threadIdx.x])) {
-          red[threadIdx.x] = o; rid[threadIdx.x] = oi;
-        }
-      }
-      __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = best; rid[threadIdx.x >> 5] = bi; }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w)
+        if (red[w] > red[0] || (red[w] == red[0] && rid[w] < rid[0])) { red[0] = red[w]; rid[0] = rid[w]; }
       s_piv = rid[0];
       if (!(red[0] > kDropRel)) s_r = j;       // the diagonal scale is 1: drop below kDropRel
       else { int t = perm[j]; perm[j] = perm[s_piv]; perm[s_piv] = t; }
@@ -696,6 +701,16 @@ __global__ void k_cell_canon(const CanonTask* __restrict__ tasks) {
 // then the boundary blocks (H then S).  The dropped directions of the cell
 // (zero columns of Xc) get a decoupled diagonal in T_H[0], T_S[0]: H = big,
 // S = 1, so their eigenvalue `big` stays above every wanted one.
+// Transformed blocks Xc^T B Xc of the generators and boundary blocks, made
+// exactly symmetric where the operator is: the zero-offset generators and the
+// diagonal boundary blocks are replaced by the mean of the product and its
+// transpose, and a boundary pair (k, m) / (m, k) is written by the block with
+// k < m as the mean of its product and the transpose of its partner's, the
+// partner receiving the bitwise transpose.  (Xc carries factors up to
+// tau^{-1/2}; products computed independently differ by rounding amplified by
+// that factor squared, which would make the structured operator slightly
+// non-symmetric and the one-sided Gram products of the block iteration
+// inconsistent.)
 __global__ void k_cell_transform(const CanonTask* __restrict__ tasks) {
   extern __shared__ double ts[];
   const CanonTask T = tasks[blockIdx.y];
@@ -703,30 +718,56 @@ __global__ void k_cell_transform(const CanonTask* __restrict__ tasks) {
   const int nblk = 2 * (T.D + 1) + 2 * T.nE;
   const int b = blockIdx.x;
   if (b >= nblk) return;
-  const double* src; double* dst;
+  const double* src; const double* srcp = nullptr; double* dst; double* dstp = nullptr;
   const int g = T.D + 1;
-  if (b < g) { src = T.TH + (size_t)b * m2; dst = T.THc + (size_t)b * m2; }
-  else if (b < 2 * g) { src = T.TS + (size_t)(b - g) * m2; dst = T.TSc + (size_t)(b - g) * m2; }
-  else if (b < 2 * g + T.nE) { src = T.EH + (size_t)(b - 2 * g) * m2; dst = T.EHc + (size_t)(b - 2 * g) * m2; }
-  else { src = T.ES + (size_t)(b - 2 * g - T.nE) * m2; dst = T.ESc + (size_t)(b - 2 * g - T.nE) * m2; }
+  bool sym = false;
+  if (b < 2 * g) {
+    const int d = b < g ? b : b - g;
+    src = (b < g ? T.TH : T.TS) + (size_t)d * m2;
+    dst = (b < g ? T.THc : T.TSc) + (size_t)d * m2;
+    sym = (d == 0);
+  } else {
+    const bool hs = b < 2 * g + T.nE;
+    const int e = hs ? b - 2 * g : b - 2 * g - T.nE;
+    const int pe = T.Epart ? T.Epart[e] : -1;
+    const double* E = hs ? T.EH : T.ES;
+    double* Ec = hs ? T.EHc : T.ESc;
+    if (pe >= 0 && pe < e) return;        // written by its partner
+    src = E + (size_t)e * m2;
+    dst = Ec + (size_t)e * m2;
+    if (pe == e) sym = true;
+    else if (pe > e) { srcp = E + (size_t)pe * m2; dstp = Ec + (size_t)pe * m2; }
+  }
   double* X = ts;
   double* Y = ts + m2;
+  double* Yp = ts + 2 * m2;
   for (int it = threadIdx.x; it < m2; it += blockDim.x) X[it] = T.Xc[it];
   __syncthreads();
-  for (int it = threadIdx.x; it < m2; it += blockDim.x) {   // Y = B Xc
+  for (int it = threadIdx.x; it < m2; it += blockDim.x) {   // Y = B Xc (and the partner's)
     int mu = it / m0, j = it % m0;
-    double acc = 0.0;
+    double acc = 0.0, accp = 0.0;
     for (int nu = 0; nu < m0; ++nu) acc += src[mu * m0 + nu] * X[nu * m0 + j];
     Y[it] = acc;
+    if (srcp) {
+      for (int nu = 0; nu < m0; ++nu) accp += srcp[mu * m0 + nu] * X[nu * m0 + j];
+      Yp[it] = accp;
+    }
   }
   __syncthreads();
   const int r = *T.kept;
+  const double* Yt = srcp ? Yp : Y;         // the product whose transpose is averaged in
   for (int it = threadIdx.x; it < m2; it += blockDim.x) {   // dst = Xc^T Y
     int i = it / m0, j = it % m0;
     double acc = 0.0;
     for (int mu = 0; mu < m0; ++mu) acc += X[mu * m0 + i] * Y[mu * m0 + j];
+    if (sym || srcp) {
+      double acct = 0.0;                    // (Xc^T Yt)[j][i]
+      for (int mu = 0; mu < m0; ++mu) acct += X[mu * m0 + j] * Yt[mu * m0 + i];
+      acc = 0.5 * (acc + acct);
+    }
     if ((b == 0 || b == g) && i == j && i >= r) acc = (b == 0) ? kDecoupledEig : 1.0;
     dst[it] = acc;
+    if (dstp) dstp[j * m0 + i] = acc;
   }
 }
 
@@ -746,7 +787,7 @@ void launch_cell_canon(const CanonTask* t, int n, int maxm0, int maxblk, cudaStr
   if (!n) return;
   size_t sm = (size_t)2 * (maxm0 + 1) * (maxm0 + 1) * sizeof(double);
   k_cell_canon<<<n, 256, sm, st>>>(t);
-  k_cell_transform<<<dim3(maxblk, n), 256, (size_t)2 * maxm0 * maxm0 * sizeof(double), st>>>(t);
+  k_cell_transform<<<dim3(maxblk, n), 256, (size_t)3 * maxm0 * maxm0 * sizeof(double), st>>>(t);
 }
 
 void launch_cell_back(const double* Xc, int m0, int L, int ncol, const double* Vr, double* V, int ld,
