@@ -5,6 +5,7 @@
 // the device slab, once with the real base address to fill the descriptors.
 // Every array of the path lives in that slab; all arithmetic of the method
 // runs in the kernels (k_assemble.cu, k_eig.cu, k_matvec.cu, k_lobpcg.cu).
+#include <chrono>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -1263,6 +1264,10 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   // down after reaching it keeps iterating, or ends unconverged)
   const double kFloorTol = 1e-6;
   const int kStagnation = 8;
+  // a floor within 100 tol of the target is recognised after 3 iterations
+  // (Rayleigh quotients are then exact to ~(100 tol)^2 / gap)
+  const double kNearFactor = 100.0;
+  const int kStagnationNear = 3;
   std::vector<double> best(ns, INFINITY);
   std::vector<int> best_it(ns, 0);
   int it = 0;
@@ -1294,13 +1299,21 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
       if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
       else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
-      else if (best[s2] <= kFloorTol && mx <= 10.0 * best[s2] && it - best_it[s2] >= kStagnation) {
+      else if (mx <= 10.0 * best[s2] &&
+               ((best[s2] <= kNearFactor * tol && it - best_it[s2] >= kStagnationNear) ||
+                (best[s2] <= kFloorTol && it - best_it[s2] >= kStagnation))) {
         active[s2] = 0; conv[s2] = 1; changed = true;
       }
       else any = true;
     }
     if (dbg) {
-      fprintf(stderr, "[fock dbg] it %d res", it);
+      static auto t_prev = std::chrono::steady_clock::now();
+      const auto t_now = std::chrono::steady_clock::now();
+      int nact = 0;
+      for (int s2 = 0; s2 < ns; ++s2) nact += active[s2];
+      fprintf(stderr, "[fock dbg] it %d active %d dt %.3f ms res", it, nact,
+              std::chrono::duration<double, std::milli>(t_now - t_prev).count());
+      t_prev = t_now;
       for (int s2 = 0; s2 < std::min(ns, 2); ++s2) fprintf(stderr, " %.3e", resid[s2]);
       std::vector<double> lm(B.kmax);
       cudaMemcpy(lm.data(), B.lob[0].lam, B.lob[0].k * 8, cudaMemcpyDeviceToHost);

@@ -290,6 +290,47 @@ struct MatvecView {
   int device;
 };
 
+// ---- FP64 with few FP64-pipe instructions ----
+// On this part a warp-wide FP64 instruction holds a sub-partition's FP64
+// unit for ~64 cycles whether 1 or 32 lanes are active; an IEEE FP64
+// division takes ~440 cycles and a square root ~690 (measured).  Reciprocal
+// and inverse square root below: an FP32 seed refined by two Newton-Raphson
+// steps in FP64 (quadratic convergence, relative error 2^-22 -> 2^-44 ->
+// rounding level), 4 and 8 FP64 instructions.  Arguments outside
+// [2^-100, 2^100] in magnitude (where the FP32 seed could over- or
+// underflow) take the IEEE operation; the test is on the exponent bits.
+__device__ inline bool nr_range(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return ex > 1023 - 100 && ex < 1023 + 100;
+}
+__device__ inline double rcp_nr(double x) {
+  if (!nr_range(x)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+// x > 0
+__device__ inline double rsqrt_nr(double x) {
+  if (!nr_range(x)) return 1.0 / sqrt(x);
+  double r = (double)__frsqrt_rn((float)x);
+  // Newton for r^-2 = x: r <- r + (r / 2)(1 - x r^2)
+  double e = fma(-x * r, r, 1.0);
+  r = fma(0.5 * r, e, r);
+  e = fma(-x * r, r, 1.0);
+  return fma(0.5 * r, e, r);
+}
+// |x| as a bit pattern: orders like |x| (integer compare, no FP64 pipe)
+__device__ inline long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
+// ordering key for "largest non-negative value" searches: non-negative
+// finite values order by their bit pattern; negative, infinite and NaN
+// values map below all of them
+__device__ inline long long pivot_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return (b < 0 || (b & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) ? -1ll : b;
+}
+
 // ---- symmetric tridiagonal (d[0..m), e[0..m-1)) helpers ----
 // Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
 __device__ inline int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {

@@ -237,66 +237,92 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
 
 // ---- lowest eigenpairs of a dense symmetric matrix (whole CTA) ----
 //
-// Householder reduction to a tridiagonal T = Q^T A Q (reflectors kept below
-// the subdiagonal of a); shifts near the kk lowest eigenvalues of T by FP32
-// Sturm bisection; one FP64 inverse-iteration vector per shift (LU with partial pivoting of
+// FP64 cost model of this part (measured): a warp-wide FP64 instruction
+// holds a sub-partition's FP64 unit for ~64 cycles with 1 or 32 active lanes
+// alike, a division ~440 cycles, a square root ~690.  The phases below keep
+// FP64 work in right-looking (trailing-update) form spread over all warps,
+// compare doubles by their bit patterns, take reciprocals and inverse square
+// roots by Newton-Raphson from FP32 seeds, and locate eigenvalues by FP32
+// multisection.
+//
+// Householder reduction to a tridiagonal T = Q^T A Q (A symmetric, only its
+// lower triangle is read or kept; reflectors stay below the subdiagonal of
+// a); the kk lowest eigenvalues of T by FP32 Sturm multisection; one FP64
+// inverse-iteration vector per eigenvalue (LU with partial pivoting of
 // T - lambda I, three sweeps, one thread per vector); Cholesky-QR applied
 // twice to those vectors and a Rayleigh-Ritz step in their span (Jacobi of
-// the kk x kk projection of T), which restores orthogonality inside clusters
-// of close eigenvalues; z = Q y by the reflectors (one warp per vector).
+// the kk x kk projection of T), which restores orthogonality inside
+// clusters of close eigenvalues; z = Q y (groups of 8 lanes per vector).
 // Eigenvector c lands in column c of z (rows 0..r-1, stride ld), eigenvalue
 // c in lam[c], ascending.  scr: 4 ld^2 doubles of scratch.  d, e, tau, pv:
-// shared arrays of >= r entries; ord: shared ints, >= kk + 1 entries.
+// shared arrays of >= 256 entries; ord: shared ints, >= kk + 1 entries.
 __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, double* scr,
                                double* d, double* e, double* tau, double* pv, double* lam, int* ord) {
-  __shared__ double red[32];
   __shared__ double s_tau, s_K;
+  double (*s_pw)[64] = reinterpret_cast<double (*)[64]>(lam);   // lam is written only at the end
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto A = [&](int i, int j) -> double& { return i >= j ? a[i * ld + j] : a[j * ld + i]; };
   for (int k = 0; k + 2 < r; ++k) {
-    double part = 0.0;
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) part += a[i * ld + k] * a[i * ld + k];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
-      const double x0 = a[(k + 1) * ld + k], xn = sqrt(s);
-      const double alpha = (x0 > 0.0) ? -xn : xn;
-      const double vtv = 2.0 * (s - x0 * alpha);
-      d[k] = a[k * ld + k];
-      e[k] = alpha;
-      s_tau = (vtv > 0.0) ? 2.0 / vtv : 0.0;
-      tau[k] = s_tau;
-      a[(k + 1) * ld + k] = x0 - alpha;   // v, first entry (the rest of x is v already)
+    const int n = r - k - 1;                     // order of the trailing block
+    if (warp == 0) {                             // x = a[k+1.., k]: norm, reflector, tau
+      double part = 0.0;
+      for (int i = k + 1 + lane; i < r; i += 32) part = fma(a[i * ld + k], a[i * ld + k], part);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) {
+        const double s = part;
+        const double x0 = a[(k + 1) * ld + k];
+        const double xn = (s > 0.0) ? s * rsqrt_nr(s) : 0.0;
+        const double alpha = (x0 > 0.0) ? -xn : xn;
+        const double vtv = 2.0 * (s - x0 * alpha);
+        d[k] = a[k * ld + k];
+        e[k] = alpha;
+        s_tau = (vtv > 0.0) ? 2.0 * rcp_nr(vtv) : 0.0;
+        tau[k] = s_tau;
+        a[(k + 1) * ld + k] = x0 - alpha;       // v, first entry (the rest of x is v already)
+      }
     }
     __syncthreads();
     const double tk = s_tau;
-    if (tk == 0.0) continue;
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) {   // p = tau A22 v
-      double acc = 0.0;
-      for (int j = k + 1; j < r; ++j) acc += a[i * ld + j] * a[j * ld + k];
-      pv[i] = tk * acc;
-    }
-    __syncthreads();
-    {   // K = (tau / 2) v^T p, block reduction (red is free again here)
-      double kp = 0.0;
-      for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) kp += a[i * ld + k] * pv[i];
-      for (int o = 16; o > 0; o >>= 1) kp += __shfl_down_sync(0xffffffffu, kp, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = kp;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double K = 0.0;
-        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) K += red[w];
-        s_K = 0.5 * tk * K;
+    if (__double_as_longlong(tk) == 0) continue;
+    // p = tau A22 v: thread (part q, row k+1+ri) sums over every 4th column
+    if (n <= 64) {
+      const int q = threadIdx.x >> 6, ri = threadIdx.x & 63;
+      if (ri < n && q < 4) {
+        const int i = k + 1 + ri;
+        double acc = 0.0;
+        for (int j = k + 1 + q; j < r; j += 4) acc = fma(A(i, j), a[j * ld + k], acc);
+        s_pw[q][ri] = acc;
       }
       __syncthreads();
+      for (int ri2 = threadIdx.x; ri2 < n; ri2 += blockDim.x)
+        pv[k + 1 + ri2] = tk * ((s_pw[0][ri2] + s_pw[1][ri2]) + (s_pw[2][ri2] + s_pw[3][ri2]));
+    } else {
+      for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = k + 1; j < r; ++j) acc = fma(A(i, j), a[j * ld + k], acc);
+        pv[i] = tk * acc;
+      }
     }
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] -= s_K * a[i * ld + k];   // w
     __syncthreads();
-    const int nt = r - k - 1;
-    for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
-      const int i = k + 1 + it / nt, j = k + 1 + it % nt;
-      a[i * ld + j] -= a[i * ld + k] * pv[j] + pv[i] * a[j * ld + k];
+    if (warp == 0) {                             // K = (tau / 2) v^T p
+      double kp = 0.0;
+      for (int i = k + 1 + lane; i < r; i += 32) kp = fma(a[i * ld + k], pv[i], kp);
+      for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+      if (lane == 0) s_K = 0.5 * tk * kp;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] = fma(-s_K, a[i * ld + k], pv[i]);   // w
+    __syncthreads();
+    // A22 -= v w^T + w v^T on the lower triangle: linear index over rows of
+    // 1, 2, ..., n entries
+    const int nt = n * (n + 1) / 2;
+    for (int it = threadIdx.x; it < nt; it += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
+      while (ii * (ii + 1) / 2 > it) --ii;
+      const int jj = it - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      a[i * ld + j] -= fma(a[i * ld + k], pv[j], pv[i] * a[j * ld + k]);
     }
     __syncthreads();
   }
@@ -311,115 +337,187 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
     }
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = (double)tridiag_bisect_f32(d, e, r, c);
-  __syncthreads();
-  double tn = 0.0;
-  for (int i = 0; i < r; ++i)
-    tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < r ? fabs(e[i]) : 0.0));
-  // inverse iteration, one thread per vector (workspace 5 r in scr[0, ld^2))
-  const int nw = max(1, min(kk, min((ld * ld) / (5 * r), (int)blockDim.x)));
+  float tnorm;                                   // Gershgorin bound of |T|, FP32
+  // ---- kk lowest eigenvalues of T: FP32 Sturm multisection ----
+  // Eigenvalue c is assigned a group of g = blockDim / kk threads; each round
+  // the group counts the eigenvalues below g interior points of its bracket
+  // and keeps the sub-interval holding eigenvalue c (g + 1 times narrower).
+  {
+    __shared__ float s_lo[128], s_hi[128];       // kk <= 128
+    __shared__ int s_cnt[256];
+    float* df = reinterpret_cast<float*>(pv);    // pv is free here: d and e^2 in FP32
+    float* e2f = df + 256;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      df[i] = (float)d[i];
+      e2f[i] = (i + 1 < r) ? (float)(e[i] * e[i]) : 0.0f;
+    }
+    __syncthreads();
+    float glo = FLT_MAX, ghi = -FLT_MAX, emax2 = 0.0f;   // Gershgorin bounds (every thread)
+    for (int i = 0; i < r; ++i) {
+      const float rad = (i > 0 ? sqrtf(e2f[i - 1]) : 0.0f) + (i + 1 < r ? sqrtf(e2f[i]) : 0.0f);
+      glo = fminf(glo, df[i] - rad);
+      ghi = fmaxf(ghi, df[i] + rad);
+      if (i + 1 < r) emax2 = fmaxf(emax2, e2f[i]);
+    }
+    tnorm = fmaxf(fabsf(glo), fabsf(ghi));
+    const float pivmin = FLT_MIN * fmaxf(1.0f, emax2);
+    glo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
+    ghi += 4.0f * FLT_EPSILON * tnorm + pivmin;
+    const int g = max(1, (int)blockDim.x / max(kk, 1));
+    const int grp = threadIdx.x / g, mem = threadIdx.x % g;
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) { s_lo[c] = glo; s_hi[c] = ghi; }
+    __syncthreads();
+    for (int round = 0; round < 40; ++round) {
+      float x = 0.0f;
+      if (grp < kk) {
+        const float lo = s_lo[grp], hi = s_hi[grp];
+        x = lo + (hi - lo) * ((float)(mem + 1) / (float)(g + 1));
+        int cnt = 0;
+        float q = df[0] - x;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += (q < 0.0f);
+        for (int i = 1; i < r; ++i) {
+          q = (df[i] - x) - __fdividef(e2f[i - 1], q);
+          if (fabsf(q) < pivmin) q = -pivmin;
+          cnt += (q < 0.0f);
+        }
+        s_cnt[threadIdx.x] = cnt;
+      }
+      __syncthreads();
+      int open = 0;
+      if (grp < kk && mem == 0) {                // the group's new bracket
+        const float lo = s_lo[grp], hi = s_hi[grp];
+        float nlo = lo, nhi = hi;
+        for (int m = 0; m < g; ++m) {
+          const float xm = lo + (hi - lo) * ((float)(m + 1) / (float)(g + 1));
+          if (s_cnt[grp * g + m] > grp) { nhi = fminf(nhi, xm); break; }
+          nlo = fmaxf(nlo, xm);
+        }
+        if (!(nlo < nhi)) nhi = nlo;             // bracket collapsed to rounding
+        s_lo[grp] = nlo;
+        s_hi[grp] = nhi;
+        open = (nhi - nlo > 2.0f * FLT_EPSILON * fmaxf(fabsf(nlo), fabsf(nhi)) + pivmin);
+      }
+      if (!__syncthreads_or(open)) break;
+    }
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = 0.5 * ((double)s_lo[c] + (double)s_hi[c]);
+    __syncthreads();
+  }
+  // ---- inverse iteration, one thread per vector (workspace 5 r per thread in scr) ----
+  const int nw = max(1, min(kk, min((4 * ld * ld) / (5 * r), (int)blockDim.x)));
   if (threadIdx.x < nw) {
-    double* lv = scr + (size_t)threadIdx.x * 5 * r;
-    double* u0 = lv + r;
-    double* u1 = u0 + r;
+    double* lv = scr + (size_t)threadIdx.x * 5 * r;   // multipliers
+    double* rp = lv + r;                               // reciprocal pivots
+    double* u1 = rp + r;
     double* u2 = u1 + r;
-    double* pvt = u2 + r;
-    const double eps = DBL_EPSILON * fmax(tn, DBL_MIN);
+    double* pvt = u2 + r;                              // row swap flags (bit pattern tested)
+    const double eps = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
+    const long long eps_bits = abs_bits(eps);
     for (int c = threadIdx.x; c < kk; c += nw) {
       const double lm = lam[c];
-      u0[0] = d[0] - lm;
-      u1[0] = (r > 1) ? e[0] : 0.0;
+      // LU of T - lm I with partial pivoting between rows i and i+1, branch-free
+      double a0 = d[0] - lm, a1 = (r > 1) ? e[0] : 0.0;
       for (int i = 0; i + 1 < r; ++i) {
         const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
-        if (fabs(u0[i]) >= fabs(sub)) {
-          if (u0[i] == 0.0) u0[i] = eps;
-          const double m = sub / u0[i];
-          lv[i] = m; pvt[i] = 0.0; u2[i] = 0.0;
-          u0[i + 1] = dn - m * u1[i];
-          u1[i + 1] = sn;
-        } else {
-          const double m = u0[i] / sub;
-          const double ou1 = u1[i];
-          lv[i] = m; pvt[i] = 1.0;
-          u0[i] = sub; u1[i] = dn; u2[i] = sn;
-          u0[i + 1] = ou1 - m * dn;
-          u1[i + 1] = -m * sn;
-        }
+        const bool sw = abs_bits(sub) > abs_bits(a0);
+        double p0 = sw ? sub : a0;
+        const double p1 = sw ? dn : a1, p2 = sw ? sn : 0.0;
+        const double o0 = sw ? a0 : sub, o1 = sw ? a1 : dn, o2 = sw ? 0.0 : sn;
+        if (abs_bits(p0) < eps_bits) p0 = (__double_as_longlong(p0) < 0) ? -eps : eps;   // tiny pivot raised to eps
+        const double rq = rcp_nr(p0);
+        const double m = o0 * rq;
+        lv[i] = m; rp[i] = rq; u1[i] = p1; u2[i] = p2; pvt[i] = sw ? 1.0 : 0.0;
+        a0 = fma(-m, p1, o1);
+        a1 = fma(-m, p2, o2);
       }
-      if (u0[r - 1] == 0.0) u0[r - 1] = eps;
-      u2[r - 1] = 0.0;
-      for (int i = 0; i < r; ++i) {   // reciprocal pivots (tiny ones raised to eps)
-        double u = u0[i];
-        if (fabs(u) < eps) u = (u < 0.0) ? -eps : eps;
-        u0[i] = 1.0 / u;
+      if (abs_bits(a0) < eps_bits) a0 = (__double_as_longlong(a0) < 0) ? -eps : eps;
+      rp[r - 1] = rcp_nr(a0);
+      u1[r - 1] = 0.0; u2[r - 1] = 0.0;
+      if (r >= 2) u2[r - 2] = 0.0;
+      // start vector: counter hash of (row, vector), uniform in [0.5, 1.5)
+      for (int i = 0; i < r; ++i) {
+        const uint32_t h = (uint32_t)(splitmix64(((uint64_t)(c + 1) << 32) | (uint64_t)(i + 1)) >> 40);
+        z[i * ld + c] = 0.5 + (double)h * (1.0 / 16777216.0);
       }
-      for (int i = 0; i < r; ++i) z[i * ld + c] = 1.0 + 0.25 * sin(0.7 * (double)(i + 1) * (double)(c + 1));
       for (int sweep = 0; sweep < 3; ++sweep) {
-        for (int i = 0; i + 1 < r; ++i) {
-          double bi = z[i * ld + c], bn = z[(i + 1) * ld + c];
-          if (pvt[i] != 0.0) { double t2 = bi; bi = bn; bn = t2; }
+        for (int i = 0; i + 1 < r; ++i) {              // P and L^-1
+          const double zi = z[i * ld + c], zn = z[(i + 1) * ld + c];
+          const bool sw = __double_as_longlong(pvt[i]) != 0;
+          const double bi = sw ? zn : zi, bn = sw ? zi : zn;
           z[i * ld + c] = bi;
-          z[(i + 1) * ld + c] = bn - lv[i] * bi;
+          z[(i + 1) * ld + c] = fma(-lv[i], bi, bn);
         }
+        double nxt = 0.0, nxt2 = 0.0, nn = 0.0;        // U^-1, and the squared norm
         for (int i = r - 1; i >= 0; --i) {
-          double s = z[i * ld + c];
-          if (i + 1 < r) s -= u1[i] * z[(i + 1) * ld + c];
-          if (i + 2 < r) s -= u2[i] * z[(i + 2) * ld + c];
-          z[i * ld + c] = s * u0[i];
+          double s = fma(-u1[i], nxt, z[i * ld + c]);
+          s = fma(-u2[i], nxt2, s);
+          s *= rp[i];
+          z[i * ld + c] = s;
+          nn = fma(s, s, nn);
+          nxt2 = nxt; nxt = s;
         }
-        double nn = 0.0;
-        for (int i = 0; i < r; ++i) nn += z[i * ld + c] * z[i * ld + c];
-        const double inv = (nn > 0.0 && isfinite(nn)) ? 1.0 / sqrt(nn) : 0.0;
+        const double inv = (nn > 0.0 && isfinite(nn)) ? rsqrt_nr(nn) : 0.0;
         for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
       }
     }
   }
   __syncthreads();
-  // Cholesky-QR, twice: Z <- Z L^-T with Z^T Z = L L^T (G in scr[ld^2, 2 ld^2))
+  // ---- Cholesky-QR, twice: Z <- Z L^-T with Z^T Z = L L^T (G in scr[ld^2, 2 ld^2)) ----
+  double* s_rl = pv;                             // reciprocal diagonal of the Gram factor
   double* G = scr + (size_t)ld * ld;
   for (int pass = 0; pass < 2; ++pass) {
     for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) {
       const int c1 = it / kk, c2 = it % kk;
       if (c2 > c1) continue;
       double s = 0.0;
-      for (int i = 0; i < r; ++i) s += z[i * ld + c1] * z[i * ld + c2];
+      for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], z[i * ld + c2], s);
       G[c1 * kk + c2] = s;
     }
     __syncthreads();
-    for (int j = 0; j < kk; ++j) {
-      if (threadIdx.x == 0) G[j * kk + j] = sqrt(fmax(G[j * kk + j], DBL_MIN));
+    for (int j = 0; j < kk; ++j) {               // right-looking Cholesky, reciprocal diagonal in s_rl
+      if (threadIdx.x == 0) {
+        const double gjj = fmax(G[j * kk + j], DBL_MIN);
+        const double rl = rsqrt_nr(gjj);
+        s_rl[j] = rl;
+        G[j * kk + j] = gjj * rl;
+      }
       __syncthreads();
-      for (int i = j + 1 + threadIdx.x; i < kk; i += blockDim.x) G[i * kk + j] /= G[j * kk + j];
+      const double rl = s_rl[j];
+      for (int i = j + 1 + threadIdx.x; i < kk; i += blockDim.x) G[i * kk + j] *= rl;
       __syncthreads();
       const int nt = kk - j - 1;
       for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
         const int i = j + 1 + it / nt, l = j + 1 + it % nt;
-        if (l <= i) G[i * kk + l] -= G[i * kk + j] * G[l * kk + j];
+        if (l <= i) G[i * kk + l] = fma(-G[i * kk + j], G[l * kk + j], G[i * kk + l]);
       }
       __syncthreads();
     }
     for (int i = threadIdx.x; i < r; i += blockDim.x)   // row i of Z times L^-T
       for (int c = 0; c < kk; ++c) {
         double s = z[i * ld + c];
-        for (int q = 0; q < c; ++q) s -= z[i * ld + q] * G[c * kk + q];
-        z[i * ld + c] = s / G[c * kk + c];
+        for (int q = 0; q < c; ++q) s = fma(-z[i * ld + q], G[c * kk + q], s);
+        z[i * ld + c] = s * s_rl[c];
       }
     __syncthreads();
   }
-  // Rayleigh-Ritz in span(Z): Tz = Z^T T Z, Jacobi (stride kj = kk + 1)
+  // ---- Rayleigh-Ritz in span(Z): Tz = Z^T (T Z), Jacobi (stride kj = kk + 1) ----
   const int kj = kk + 1;
   double* Tz = scr + (size_t)2 * ld * ld;
   double* Qz = scr + (size_t)3 * ld * ld;
+  double* tmp = scr;   // r x kk: T Z, then Z Qz
+  for (int it = threadIdx.x; it < r * kk; it += blockDim.x) {
+    const int i = it / kk, c = it % kk;
+    double s = d[i] * z[i * ld + c];
+    if (i > 0) s = fma(e[i - 1], z[(i - 1) * ld + c], s);
+    if (i + 1 < r) s = fma(e[i], z[(i + 1) * ld + c], s);
+    tmp[it] = s;
+  }
+  __syncthreads();
   for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) {
     const int c1 = it / kk, c2 = it % kk;
     if (c2 > c1) continue;
     double s = 0.0;
-    for (int i = 0; i < r; ++i) {
-      double tzi = d[i] * z[i * ld + c2];
-      if (i > 0) tzi += e[i - 1] * z[(i - 1) * ld + c2];
-      if (i + 1 < r) tzi += e[i] * z[(i + 1) * ld + c2];
-      s += z[i * ld + c1] * tzi;
-    }
+    for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], tmp[i * kk + c2], s);
     Tz[c1 * kj + c2] = s;
     Tz[c2 * kj + c1] = s;
   }
@@ -437,41 +535,54 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
     ord[rank] = i;
   }
   __syncthreads();
-  double* tmp = scr;   // r x kk
   for (int it = threadIdx.x; it < r * kk; it += blockDim.x) {
     const int i = it / kk, c = it % kk, oc = ord[c];
     double s = 0.0;
-    for (int q = 0; q < kk; ++q) s += z[i * ld + q] * Qz[q * kj + oc];
+    for (int q = 0; q < kk; ++q) s = fma(z[i * ld + q], Qz[q * kj + oc], s);
     tmp[it] = s;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < r * kk; it += blockDim.x) z[(it / kk) * ld + (it % kk)] = tmp[it];
   for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = Tz[ord[c] * kj + ord[c]];
   __syncthreads();
-  // back-transformation z = H_0 ... H_{r-3} y, one warp per vector
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-  for (int c = warp; c < kk; c += nwarp)
-    for (int k = r - 3; k >= 0; --k) {
-      const double tk = tau[k];
-      if (tk == 0.0) continue;
-      double s = 0.0;
-      for (int i = k + 1 + lane; i < r; i += 32) s += a[i * ld + k] * z[i * ld + c];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      s *= tk;
-      for (int i = k + 1 + lane; i < r; i += 32) z[i * ld + c] -= s * a[i * ld + k];
-      __syncwarp();
+  // ---- back-transformation z = H_0 ... H_{r-3} y ----
+  // a group of 8 lanes per vector, lane q of the group owning rows = q mod 8:
+  // the dot product needs 3 shuffles and no block barrier
+  {
+    const int grp = threadIdx.x >> 3, q = threadIdx.x & 7;
+    for (int c0 = 0; c0 < kk; c0 += (int)(blockDim.x >> 3)) {
+      const int c = c0 + grp;
+      const bool act = c < kk;
+      if (__all_sync(0xffffffffu, !act)) continue;      // whole warp idle
+      for (int k = r - 3; k >= 0; --k) {
+        const double tk = tau[k];
+        if (__double_as_longlong(tk) == 0) continue;
+        const int i0 = k + 1 + ((q - (k + 1)) & 7);      // first owned row > k
+        double s = 0.0;
+        if (act)
+          for (int i = i0; i < r; i += 8) s = fma(a[i * ld + k], z[i * ld + c], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s *= tk;
+        if (act)
+          for (int i = i0; i < r; i += 8) z[i * ld + c] = fma(-s, a[i * ld + k], z[i * ld + c]);
+      }
     }
+  }
   __syncthreads();
 }
 
 // Rayleigh-Ritz on the basis Y (Gram matrices GH = Y^T H Y, GS = Y^T S Y):
-// scale by D = diag(GS)^-1/2; Cholesky of D GS D with diagonal pivoting,
-// stopping when the largest remaining pivot falls below kDropRel (the
-// remaining columns are numerically in the span of the kept ones and are
-// dropped, as are zero columns); with the kept set K and G_KK = L L^T,
-// eigendecompose C = L^-1 (D GH D)_KK L^-T by Jacobi and keep the k lowest.
-// Coefficients in the Y basis: D P [L^-T w; 0].
-__global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
+// scale by D = diag(GS)^-1/2; LDL^T factorisation of D GS D with diagonal
+// pivoting (right-looking, through a permutation, unit lower factor L and
+// pivots delta), stopping when the largest remaining pivot falls below
+// kDropRel (the remaining columns are numerically in the span of the kept
+// ones and are dropped, as are zero columns); with the kept set K the
+// reduced matrix is C = Delta^-1/2 L^-1 (D GH D)_KK L^-T Delta^-1/2, whose k
+// lowest eigenpairs give the Ritz pairs.  Coefficients in the Y basis:
+// D P [L^-T Delta^-1/2 w; 0].
+__global__ void __launch_bounds__(256) k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   const RRTask T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
   extern __shared__ double rr_smem[];
@@ -482,143 +593,160 @@ __global__ void k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
   // working matrices in shared memory when 3 ld^2 doubles fit, else global
   const bool in_smem = (3 * ld * ld * (int)sizeof(double) <= smem_bytes);
   double* base = in_smem ? rr_smem : T.work;
-  double* C = base;                          // scaled H-Gram, then the reduced matrix
-  double* V = base + (size_t)ld * ld;        // Jacobi eigenvectors
-  double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram, then its pivoted factor
-  __shared__ double dsc[256], dg[256], red[256];
-  __shared__ int perm[256], order[256], rid[256];
+  double* C = base;                          // scaled H-Gram, then the reduced matrix (lower)
+  double* V = base + (size_t)ld * ld;        // work matrix, then the eigenvectors
+  double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram (lower, original indices), then L
+  __shared__ double dsc[256], rl[256];
+  __shared__ long long wkey[8];
+  __shared__ int perm[256], order[256], wpos[8];
   __shared__ double tdd[256], tee[256], ttau[256], tpv[256], tlam[256];
   __shared__ int s_r, s_piv;
+  __shared__ double s_rd;
+  double* colS = tlam;                       // column of the Schur complement (until the eigensolver)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    double g = T.GS[(size_t)i * ld + i];
-    dsc[i] = (g > 0.0) ? 1.0 / sqrt(g) : 0.0;
+    const double g = T.GS[(size_t)i * ld + i];
+    dsc[i] = (g > 0.0) ? rsqrt_nr(g) : 0.0;
     perm[i] = i;
   }
   __syncthreads();
+  // lower triangles (i >= j, original indices) of D GS D and D GH D
   for (int it = threadIdx.x; it < nb * nb; it += blockDim.x) {
-    int i = it / nb, j = it % nb;
-    double gs = 0.5 * (T.GS[(size_t)i + (size_t)ld * j] + T.GS[(size_t)j + (size_t)ld * i]);
-    double gh = 0.5 * (T.GH[(size_t)i + (size_t)ld * j] + T.GH[(size_t)j + (size_t)ld * i]);
-    G[i * ld + j] = gs * dsc[i] * dsc[j];
-    C[i * ld + j] = gh * dsc[i] * dsc[j];
+    const int i = it / nb, j = it % nb;
+    if (j > i) continue;
+    const double gs = 0.5 * (T.GS[(size_t)i + (size_t)ld * j] + T.GS[(size_t)j + (size_t)ld * i]);
+    const double gh = 0.5 * (T.GH[(size_t)i + (size_t)ld * j] + T.GH[(size_t)j + (size_t)ld * i]);
+    const double sc = dsc[i] * dsc[j];
+    G[i * ld + j] = gs * sc;
+    C[i * ld + j] = gh * sc;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) dg[i] = G[i * ld + i];
-  __syncthreads();
-  // pivoted Cholesky: L is kept in V (row j = j-th pivot position, column q),
-  // G is read through perm
   if (threadIdx.x == 0) s_r = nb;
   __syncthreads();
+  // S(a, b) at positions a, b: the lower-triangle entry of the original indices
+  auto GP = [&](int pa, int pb) -> double& { return pa >= pb ? G[pa * ld + pb] : G[pb * ld + pa]; };
   for (int j = 0; j < nb; ++j) {
-    // argmax of the remaining diagonal over positions j..nb-1 (larger value,
-    // ties to the lower position): per thread, per warp by shuffles, then
-    // across the warps by thread 0
-    double best = -1.0;
+    // pivot: the largest remaining diagonal over positions j..nb-1 (bit-pattern
+    // keys, ties to the lower position)
+    long long bk = -2;
     int bi = j;
     for (int i = j + threadIdx.x; i < nb; i += blockDim.x) {
-      double d = dg[perm[i]];
-      if (d > best) { best = d; bi = i; }
+      const long long kq = pivot_key(G[perm[i] * ld + perm[i]]);
+      if (kq > bk) { bk = kq; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
     }
-    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = best; rid[threadIdx.x >> 5] = bi; }
+    if (lane == 0) { wkey[warp] = bk; wpos[warp] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w)
-        if (red[w] > red[0] || (red[w] == red[0] && rid[w] < rid[0])) { red[0] = red[w]; rid[0] = rid[w]; }
-      s_piv = rid[0];
-      if (!(red[0] > kDropRel)) s_r = j;       // the diagonal scale is 1: drop below kDropRel
-      else { int t = perm[j]; perm[j] = perm[s_piv]; perm[s_piv] = t; }
+      for (int w = 1; w < nwarp; ++w)
+        if (wkey[w] > wkey[0] || (wkey[w] == wkey[0] && wpos[w] < wpos[0])) { wkey[0] = wkey[w]; wpos[0] = wpos[w]; }
+      const int piv = wpos[0];
+      const double dj = G[perm[piv] * ld + perm[piv]];
+      if (!(wkey[0] >= 0 && dj > kDropRel)) {  // the diagonal scale is 1: drop below kDropRel
+        s_r = j;
+      } else {
+        const int t = perm[j]; perm[j] = perm[piv]; perm[piv] = t;
+        s_rd = rcp_nr(dj);
+        rl[j] = rsqrt_nr(dj);
+      }
     }
     __syncthreads();
     if (s_r == j) break;
-    if (s_piv != j)   // the computed part of the two rows of L moves with the pivot
-      for (int q = threadIdx.x; q < j; q += blockDim.x) {
-        double t = V[j * ld + q];
-        V[j * ld + q] = V[s_piv * ld + q];
-        V[s_piv * ld + q] = t;
-      }
-    __syncthreads();
     const int pj = perm[j];
-    const double ljj = sqrt(dg[pj]), rlj = 1.0 / ljj;
-    // column j of L (rows i > j in permuted order), L[j][j] = ljj
+    const double rd = s_rd;
+    // column j: L(a, j) = S(a, j) / delta_j (stored in place), S(a, j) kept in colS
     for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
-      const int pi = perm[i];
-      double acc = G[pi * ld + pj];
-      for (int q = 0; q < j; ++q) acc -= V[i * ld + q] * V[j * ld + q];
-      V[i * ld + j] = acc * rlj;
+      double& sij = GP(perm[i], pj);
+      colS[i] = sij;
+      sij *= rd;
     }
-    if (threadIdx.x == 0) V[j * ld + j] = ljj;
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
-      double l = V[i * ld + j];
-      dg[perm[i]] -= l * l;
+    // trailing update S(a, b) -= L(a, j) S(b, j), a >= b > j
+    const int n = nb - j - 1, nt = n * (n + 1) / 2;
+    for (int it = threadIdx.x; it < nt; it += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
+      while (ii * (ii + 1) / 2 > it) --ii;
+      const int aa = j + 1 + ii, bb = j + 1 + (it - ii * (ii + 1) / 2);
+      double& s = GP(perm[aa], perm[bb]);
+      s = fma(-GP(perm[aa], pj), colS[bb], s);
     }
     __syncthreads();
   }
   const int r = s_r;
   if (r < k && threadIdx.x == 0 && T.fail) *T.fail = 1;
-  // L (r x r) into G, then C <- L^-1 Hpp L^-T with Hpp[a][b] = C[perm a][perm b]
+  // V = (D GH D) at the kept positions: A(a, b) = C(perm a, perm b), a >= b
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
-    int aa = it / r, bb = it % r;
-    G[aa * ld + bb] = (bb <= aa) ? V[aa * ld + bb] : 0.0;
+    const int aa = it / r, bb = it % r;
+    if (bb > aa) continue;
+    const int pa = perm[aa], pb = perm[bb];
+    V[aa * ld + bb] = pa >= pb ? C[pa * ld + pb] : C[pb * ld + pa];
+    V[bb * ld + aa] = V[aa * ld + bb];
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
-    int aa = it / r, bb = it % r;
-    V[aa * ld + bb] = C[perm[aa] * ld + perm[bb]];
+  auto Lp = [&](int aa, int bb) -> double { return GP(perm[aa], perm[bb]); };   // unit lower factor, aa > bb
+  // V <- L^-1 V (right-looking over rows), then the lower triangle of V L^-T
+  for (int i = 0; i + 1 < r; ++i) {
+    const int n = r - i - 1;
+    for (int it = threadIdx.x; it < n * r; it += blockDim.x) {
+      const int aa = i + 1 + it / r, col = it % r;
+      V[aa * ld + col] = fma(-Lp(aa, i), V[i * ld + col], V[aa * ld + col]);
+    }
+    __syncthreads();
   }
-  for (int aa = threadIdx.x; aa < r; aa += blockDim.x) dg[aa] = 1.0 / G[aa * ld + aa];   // reciprocal diagonal of L
-  __syncthreads();
-  // V <- L^-1 V (thread per column), then C <- V L^-T (thread per row)
-  for (int j = threadIdx.x; j < r; j += blockDim.x)
-    for (int i = 0; i < r; ++i) {
-      double acc = V[i * ld + j];
-      for (int q = 0; q < i; ++q) acc -= G[i * ld + q] * V[q * ld + j];
-      V[i * ld + j] = acc * dg[i];
+  for (int i = 0; i + 1 < r; ++i) {            // columns a > i, rows x >= a
+    const int n = r - i - 1, nt = n * (n + 1) / 2;
+    for (int it = threadIdx.x; it < nt; it += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
+      while (ii * (ii + 1) / 2 > it) --ii;
+      const int x = i + 1 + ii, aa = i + 1 + (it - ii * (ii + 1) / 2);
+      V[x * ld + aa] = fma(-Lp(aa, i), V[x * ld + i], V[x * ld + aa]);
     }
-  __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x)
-    for (int j = 0; j < r; ++j) {
-      double acc = V[i * ld + j];
-      for (int q = 0; q < j; ++q) acc -= C[i * ld + q] * G[j * ld + q];
-      C[i * ld + j] = acc * dg[j];
-    }
-  __syncthreads();
+    __syncthreads();
+  }
+  // C = Delta^-1/2 V Delta^-1/2, lower triangle
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {
-    int aa = it / r, bb = it % r;
-    if (aa < bb) {
-      double mm = 0.5 * (C[aa * ld + bb] + C[bb * ld + aa]);
-      C[aa * ld + bb] = mm;
-      C[bb * ld + aa] = mm;
-    }
+    const int aa = it / r, bb = it % r;
+    if (bb > aa) continue;
+    C[aa * ld + bb] = V[aa * ld + bb] * (rl[aa] * rl[bb]);
   }
   __syncthreads();
   // the kk lowest eigenpairs of C (ascending) into the columns of V
   const int kk = min(k, r);
   cta_sym_lowest(C, V, r, ld, kk, T.work + (size_t)3 * ld * ld, tdd, tee, ttau, tpv, tlam, order);
   for (int c = threadIdx.x; c < k; c += blockDim.x) T.lam[c] = (c < kk) ? tlam[c] : NAN;
+  // coefficients: w = L^-T Delta^-1/2 v (right-looking over positions, in V)
+  for (int it = threadIdx.x; it < r * kk; it += blockDim.x) {
+    const int aa = it / kk, c = it % kk;
+    V[aa * ld + c] *= rl[aa];
+  }
   __syncthreads();
-  for (int c = threadIdx.x; c < kk; c += blockDim.x) order[c] = c;
-  __syncthreads();
-  // coefficients: w = L^-T v (back substitution in permuted order), z[perm a] = D w[a]
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double* z = T.Cc + (size_t)ld * c;
-    double* zp = T.Cc + (size_t)ld * (k + c);
-    for (int i = 0; i < nb; ++i) z[i] = 0.0;
-    if (c < kk) {
-      const int oc = order[c];
-      for (int aa = r - 1; aa >= 0; --aa) {
-        double acc = V[aa * ld + oc];
-        for (int q = aa + 1; q < r; ++q) acc -= G[q * ld + aa] * z[perm[q]];
-        z[perm[aa]] = acc * dg[aa];
-      }
-      for (int i = 0; i < nb; ++i) z[i] *= dsc[i];
+  for (int aa = r - 1; aa > 0; --aa) {
+    for (int it = threadIdx.x; it < aa * kk; it += blockDim.x) {
+      const int qq = it / kk, c = it % kk;
+      V[qq * ld + c] = fma(-Lp(aa, qq), V[aa * ld + c], V[qq * ld + c]);
     }
-    for (int i = 0; i < nb; ++i) zp[i] = (i < k) ? 0.0 : z[i];
+    __syncthreads();
+  }
+  // z[perm a] = D w[a]; the second block is z with the first k rows zeroed
+  for (int it = threadIdx.x; it < k * nb; it += blockDim.x) {
+    const int c = it / nb, i = it % nb;
+    T.Cc[(size_t)ld * c + i] = 0.0;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < kk * r; it += blockDim.x) {
+    const int c = it / r, aa = it % r;
+    const int p = perm[aa];
+    T.Cc[(size_t)ld * c + p] = V[aa * ld + c] * dsc[p];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < k * nb; it += blockDim.x) {
+    const int c = it / nb, i = it % nb;
+    T.Cc[(size_t)ld * (k + c) + i] = (i < k) ? 0.0 : T.Cc[(size_t)ld * c + i];
   }
 }
 
