@@ -231,19 +231,32 @@ def fp64_flops_per_step(problems, outs):
             k = p.k_eig
             n = p.L[0] * m0
             it = max(o["iters"], 1)
-            # Rayleigh-Ritz of the 3k-column basis: two symmetric eigensolves
-            # (eigenvalues + vectors, ~9 n^3 each by tridiagonal QR) and the
-            # n^2 x r reduction products
-            nb = 3 * k
-            w["k_rr"] = w.get("k_rr", 0) + it * (2 * 9 * nb ** 3 + 4 * nb ** 3)
-            w["k_gemm_tn"] = w.get("k_gemm_tn", 0) + it * (2 * 2 * n * nb * nb + 2 * 2 * n * k * k)
-            w["k_gemm_nn"] = w.get("k_gemm_nn", 0) + it * (2 * n * nb * 2 * k + 6 * 2 * n * k * k)
-            # circulant-embedding FFTs: per iteration 9 k m0 column transforms (forward of W
-            # and [X|P], inverse of their H and S images), 12 k m0 at start; conventional
+            # block size kb (k wanted + guards, or the whole space) and basis 3 kb
+            kb = n if 3 * n <= 255 else k + max(2, k // 4)
+            nb = 3 * kb
+            # Rayleigh-Ritz per launch: pivoted LDL^T nb^3/3, the two triangular
+            # solves 4 nb^3/3, Householder tridiagonal 4 nb^3/3, back-transformation
+            # and coefficients 3 nb^2 kb, Cholesky-QR and Ritz projection 6 nb kb^2;
+            # `it` launches on 3 kb columns plus the start on kb
+            rr = lambda b: 3 * b ** 3 + 3 * b * b * kb + 6 * b * kb * kb
+            w["k_rr"] = w.get("k_rr", 0) + it * rr(nb) + rr(kb)
+            # Gram products: the two symmetric nb x nb products of the basis
+            # (n nb (nb + 1) flops each) and the two kb x kb projections onto X;
+            # the start: the two symmetric kb x kb products
+            w["k_gemm_tn"] = (w.get("k_gemm_tn", 0) + it * (2 * n * nb * (nb + 1) + 2 * 2 * n * kb * kb)
+                              + 2 * n * kb * (kb + 1))
+            w["k_gemm_nn"] = w.get("k_gemm_nn", 0) + it * (2 * n * nb * 2 * kb + 6 * 2 * n * kb * kb)
+            # banded preconditioner: forward and backward block substitution over
+            # L cells with D + 1 blocks of m0 x m0 per block row, kb columns
+            D = o.get("D")
+            if D is not None:
+                w["k_band_solve"] = w.get("k_band_solve", 0) + it * 4 * p.L[0] * (D + 1) * m0 * m0 * kb
+            # circulant-embedding FFTs: per iteration 9 kb m0 column transforms (forward of W
+            # and [X|P], inverse of their H and S images), 12 kb m0 at start; conventional
             # 5 M log2 M flops per complex transform of length M
             M = o.get("M")
             if M:
-                w["k_fft"] = w.get("k_fft", 0) + (it * 9 + 12) * k * m0 * 5 * M * math.log2(M)
+                w["k_fft"] = w.get("k_fft", 0) + (it * 9 + 12) * kb * m0 * 5 * M * math.log2(M)
         else:
             ncell = int(np.prod(p.L))
             T = len(p.Z) * p.R
@@ -297,7 +310,7 @@ def main():
         plan.execute()
     outs = plan.outputs(check=False)
     for i, o in enumerate(outs):
-        o["M"] = plan.sizes(i)[1]
+        _, o["M"], o["D"], _ = plan.sizes(i)
     bad = [o["status"] for o in outs if o["status"] != 0]
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
     ctx.profile(True)

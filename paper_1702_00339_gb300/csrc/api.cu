@@ -50,8 +50,10 @@ void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t, bool);
 void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
 int eapply_grid(long long items);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
-void launch_band_solve(const BandTask*, int, int, cudaStream_t, bool);
+void launch_band_solve(const BandTask*, int, int, int, cudaStream_t, bool);
+int band_stage_doubles(int);
 void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
+void launch_gather(const GatherSeg*, int, uint32_t*, cudaStream_t);
 void launch_cell_back(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 __global__ void k_init_x(const InitTask*);
 __global__ void k_gemm_tn(const GemmTask*);
@@ -71,6 +73,8 @@ struct fock_ctx {
   size_t budget = 0;
   char* arena = nullptr;
   size_t arena_cap = 0;
+  uint32_t* hstage = nullptr;        // pinned host staging of gathered results
+  size_t hstage_cap = 0;             // (words)
   cudaMemPool_t mempool = nullptr;   // serving workers: batches allocated stream-ordered from this pool
   std::string err;
   // kernel timers: events recorded around launches while enabled
@@ -342,6 +346,13 @@ struct Batch {
   // device descriptors
   ProbDev* d_probs = nullptr;
   std::vector<ProbDev> probs;
+  // results gathered into one staging buffer: per problem the word offsets of
+  // its eigenvalues, block indices and fail flag (-1: none)
+  std::vector<GatherSeg> gseg;
+  const GatherSeg* d_gseg = nullptr;
+  uint32_t* d_ostage = nullptr;
+  size_t ostage_words = 0;
+  std::vector<long long> o_ev, o_blk, o_fail;
   std::vector<SegDesc> gsegs, psegs;
   SegDesc *d_gsegs = nullptr, *d_psegs = nullptr;
   std::vector<GramTask> gram; GramTask* d_gram = nullptr;
@@ -407,6 +418,7 @@ struct Batch {
   TL eHXP, eSXP, eHW, eSW;
   TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
+  int band_stage = 0;                // doubles of a band-solve shared-memory stage
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
   int eapply_gx = 16;
@@ -435,6 +447,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   B.any_mixed = false;
+  B.band_stage = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
   for (int i = 0; i < np; ++i) {
@@ -905,6 +918,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
         bt.fp32 = H.mixed;
         bnd.push_back(bt);
+        if (m0 % 2 == 0) B.band_stage = std::max(B.band_stage, (Q.D + 1) * m0 * m0);
       } else {
         fR.push_back(fwd(l.R, k, pcmode));
         iPW.push_back(inv(Y1, Yw, k, pcmode));
@@ -986,6 +1000,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(nW, B.normW);
     TLp(bnd, B.bandF);
     B.bandS = B.bandF;
+    B.band_stage = band_stage_doubles(B.band_stage);
     TLp(rs, B.resid, kk);
   }
   // ---- descriptor arrays (uploaded in one copy with the parameters) ----
@@ -1005,6 +1020,33 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.d_canon = U.put(B.canon);
   B.d_fbo = U.put(B.fbo);
   B.d_sorts = U.put(B.sorts);
+  // ---- result gather: eigenvalues, block indices and fail flags of every problem ----
+  B.gseg.clear();
+  B.o_ev.assign(np, -1); B.o_blk.assign(np, -1); B.o_fail.assign(np, -1);
+  {
+    size_t w = 0;
+    auto seg = [&](const void* src, size_t words) {
+      B.gseg.push_back({reinterpret_cast<const uint32_t*>(src), (unsigned int)words, (unsigned int)w});
+      const long long off = (long long)w;
+      w += (words + 1) & ~(size_t)1;   // 8-byte aligned starts
+      return off;
+    };
+    for (int i = 0; i < np; ++i) {
+      const Batch::PerProb& Q = B.pp[i];
+      if (B.hp[i].kind == 0) {
+        B.o_ev[i] = seg(Q.ev, 2 * (size_t)Q.nev);
+        B.o_blk[i] = seg(Q.blk, (size_t)Q.nev);
+        B.o_fail[i] = seg(Q.fail, 1);
+      }
+    }
+    for (size_t s2 = 0; s2 < B.sidx.size(); ++s2) {
+      const int i = B.sidx[s2];
+      B.o_ev[i] = seg(B.lob[s2].lam, 2 * (size_t)B.pp[i].nev);
+    }
+    B.ostage_words = w;
+    B.d_ostage = S.take<uint32_t>(std::max<size_t>(w, 2));
+    B.d_gseg = U.put(B.gseg);
+  }
   B.bytes = S.off;
   B.ubytes = U.off;
 }
@@ -1015,6 +1057,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
 namespace {
 
 int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
+  const bool dbg = getenv("FOCK_DEBUG") != nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
   Slab S0, U0;
   plan(B, S0, U0);
   size_t need = S0.off + 256, uneed = U0.off + 256;
@@ -1049,6 +1093,12 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
   U.stage = &B.stage;
   plan(B, S, U);
   CUDA_TRY(ctx, cudaMemcpyAsync(ub, B.stage.data(), U.off, cudaMemcpyHostToDevice, ctx->stream));
+  if (dbg) {
+    cudaStreamSynchronize(ctx->stream);
+    fprintf(stderr, "[fock dbg] plan: %d problems, slab %.1f MB, upload %.1f MB, %.2f ms host+upload\n", B.nprob,
+            S.off / 1e6, U.off / 1e6,
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
   return FOCK_OK;
 }
 
@@ -1336,7 +1386,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       CUDA_TRY(ctx, cudaStreamSynchronize(st));   // rf is a host temporary
     }
     // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
-    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, st, B.any_mixed); }
+    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, st, B.any_mixed); }
     if (B.fwdR.n) {
       mv_fwd(B, B.fwdR, st);
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
@@ -1390,31 +1440,59 @@ int plan_outputs(fock_plan& P, fock_output* outs, int on_device) {
   fock_ctx* ctx = P.ctx;
   Batch& B = P.B;
   const int nprob = B.nprob;
-  const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   std::vector<int> pfail(nprob, 0);
   for (int i = 0; i < nprob; ++i) {
-    Batch::PerProb& Q = B.pp[i];
-    outs[i].n_evals = Q.nev;
+    outs[i].n_evals = B.pp[i].nev;
     outs[i].iters = 0;
     outs[i].resid = 0.0;
     outs[i].status = FOCK_OK;
-    if (B.hp[i].kind == 0) {
-      if (outs[i].evals) CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, Q.ev, Q.nev * sizeof(double), kd, ctx->stream));
-      if (outs[i].block_of) CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].block_of, Q.blk, Q.nev * sizeof(int), kd, ctx->stream));
-      CUDA_TRY(ctx, cudaMemcpyAsync(&pfail[i], Q.fail, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  for (size_t s2 = 0; s2 < B.sidx.size() && s2 < P.iters.size(); ++s2) {
+    const int i = B.sidx[s2];
+    outs[i].iters = P.iters[s2];
+    outs[i].resid = P.resid[s2];
+    if (!P.conv[s2]) outs[i].status = FOCK_ENOCONV;
+  }
+  if (on_device) {   // device destinations: one device-to-device copy per array
+    for (int i = 0; i < nprob; ++i) {
+      const Batch::PerProb& Q = B.pp[i];
+      const double* ev = (B.hp[i].kind == 0) ? Q.ev : nullptr;
+      if (B.hp[i].kind == 0) {
+        if (outs[i].block_of)
+          CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].block_of, Q.blk, Q.nev * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(&pfail[i], Q.fail, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      }
+      if (ev && outs[i].evals)
+        CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, ev, Q.nev * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    for (size_t s2 = 0; s2 < B.sidx.size(); ++s2) {
+      const int i = B.sidx[s2];
+      if (outs[i].evals)
+        CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, B.lob[s2].lam, B.pp[i].nev * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {           // host destinations: gather on the device, one copy to pinned memory
+    const size_t nw = B.ostage_words;
+    if (ctx->hstage_cap < nw) {
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (ctx->hstage) cudaFreeHost(ctx->hstage);
+      ctx->hstage = nullptr; ctx->hstage_cap = 0;
+      CUDA_TRY(ctx, cudaMallocHost(&ctx->hstage, (nw + nw / 4 + 2) * sizeof(uint32_t)));
+      ctx->hstage_cap = nw + nw / 4 + 2;
+    }
+    launch_gather(B.d_gseg, (int)B.gseg.size(), B.d_ostage, ctx->stream);
+    CUDA_TRY(ctx, cudaGetLastError());
+    if (nw) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, B.d_ostage, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const uint32_t* hs = ctx->hstage;
+    for (int i = 0; i < nprob; ++i) {
+      const size_t nev = (size_t)B.pp[i].nev;
+      if (outs[i].evals && B.o_ev[i] >= 0) std::memcpy(outs[i].evals, hs + B.o_ev[i], nev * sizeof(double));
+      if (outs[i].block_of && B.o_blk[i] >= 0) std::memcpy(outs[i].block_of, hs + B.o_blk[i], nev * sizeof(int));
+      if (B.o_fail[i] >= 0) std::memcpy(&pfail[i], hs + B.o_fail[i], sizeof(int));
     }
   }
-  for (size_t s2 = 0; s2 < B.sidx.size(); ++s2) {
-    int i = B.sidx[s2];
-    if (outs[i].evals)
-      CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, B.lob[s2].lam, B.pp[i].nev * sizeof(double), kd, ctx->stream));
-    if (s2 < P.iters.size()) {
-      outs[i].iters = P.iters[s2];
-      outs[i].resid = P.resid[s2];
-      if (!P.conv[s2]) outs[i].status = FOCK_ENOCONV;
-    }
-  }
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   int first = FOCK_OK;
   for (int i = 0; i < nprob; ++i) {
     if (pfail[i]) outs[i].status = FOCK_EINVAL;
@@ -1530,6 +1608,7 @@ void fock_destroy(fock_ctx* c) {
   for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->arena) cudaFree(c->arena);
+  if (c->hstage) cudaFreeHost(c->hstage);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -249,6 +249,10 @@ struct RRTask {
 
 struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };
 
+// One piece of a batch's results gathered into a contiguous staging buffer
+// (4-byte words) for a single device-to-host copy.
+struct GatherSeg { const uint32_t* src; unsigned int words; unsigned int dst; };
+
 struct BandTask {
   int m0, L, D, k, n;
   const double* TH; const double* TS;      // [D+1][m0*m0]
@@ -332,101 +336,97 @@ __device__ inline long long pivot_key(double x) {
 }
 
 // ---- symmetric tridiagonal (d[0..m), e[0..m-1)) helpers ----
-// Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
-__device__ inline int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x, from
+// FP32 copies df = d and e2f = e^2 (Kahan's recurrence of the pivots of
+// T - x I; a pivot below pivmin in magnitude counts as negative).
+__device__ inline int sturm_count_f32(const float* df, const float* e2f, int m, float x, float pivmin) {
   int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += (q < 0.0);
+  float q = df[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  cnt += (q < 0.0f);
   for (int i = 1; i < m; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    q = (df[i] - x) - __fdividef(e2f[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0f);
   }
   return cnt;
 }
 
-// idx-th (0-based, ascending) eigenvalue by bisection.
-__device__ inline double tridiag_eig_bisect(const double* d, const double* e, int m, int idx) {
-  double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
-  for (int i = 0; i < m; ++i) {
-    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);   // Gershgorin
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
-    if (i < m - 1) emax = fmax(emax, fabs(e[i]));
+// Number of eigenvalues below x in FP64 without divisions: the sign changes
+// of the leading principal minors p_0 = 1, p_1 = d_0 - x,
+// p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2} (Sturm sequence).  A minor
+// leaving [2^-500, 2^500] in magnitude rescales the last two minors by a
+// power of two (exact); an exactly zero minor takes the sign opposite to its
+// predecessor.  Three FP64 instructions per row; signs and exponents are
+// tested on the bit patterns.
+__device__ inline int sturm_count_minors(const double* d, const double* e2, int m, double x) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = 0;
+  long long sp = 0;   // sign bit of the previous minor
+  for (int i = 0;; ++i) {
+    long long b = __double_as_longlong(p);
+    if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) {        // zero minor
+      p = pm * -0x1p-200;
+      b = __double_as_longlong(p);
+    }
+    const long long sb = (long long)((unsigned long long)b >> 63);
+    cnt += (int)(sb ^ sp);
+    sp = sb;
+    if (i + 1 >= m) break;
+    const int ex = max((int)((b >> 52) & 0x7FF), (int)((__double_as_longlong(pm) >> 52) & 0x7FF));
+    if (ex > 1023 + 500 || ex < 1023 - 500) {      // rescale both by 2^(1023 - the larger exponent)
+      const double sc = __longlong_as_double((long long)(2046 - min(ex, 2046)) << 52);
+      p *= sc;
+      pm *= sc;
+    }
+    const double pn = fma(d[i + 1] - x, p, -e2[i] * pm);
+    pm = p;
+    p = pn;
   }
-  double tnorm = fmax(fabs(lo), fabs(hi));
-  double pivmin = DBL_MIN * fmax(1.0, emax * emax);
-  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
-  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
-  }
-  return 0.5 * (lo + hi);
+  return cnt;
 }
 
-// idx-th (0-based, ascending) eigenvalue of the symmetric tridiagonal (d, e)
-// by Sturm bisection in FP32 (about 1e-7 of the spectral radius): used only
-// as the shift of FP64 inverse iteration, whose Rayleigh-Ritz step gives the
-// eigenvalues.  FP32 runs at 64x the FP64 rate on this part.
-__device__ inline float tridiag_bisect_f32(const double* d, const double* e, int m, int idx) {
-  float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.0f;
+// idx-th (0-based, ascending) eigenvalue of the symmetric tridiagonal of
+// order m given by FP32 copies (df, e2f) and FP64 (d, e2 = e^2), with tnf a
+// Gershgorin bound of its spectral radius: FP32 bisection to ~1e-7 of the
+// spectral radius, then (fp64) a bracket around that value verified by FP64
+// Sturm counts (widened up to three times, else the Gershgorin interval)
+// and FP64 bisection inside it to 2 u |lambda|, or to rtol (1 + |lambda|)
+// when that is wider (shifts and bounds that need no more).
+__device__ inline double tridiag_eig_fast(const float* df, const float* e2f, const double* d, const double* e2,
+                                          int m, int idx, double rtol) {
+  float lo = FLT_MAX, hi = -FLT_MAX, emax2 = 0.0f;
   for (int i = 0; i < m; ++i) {
-    float r = (i > 0 ? fabsf((float)e[i - 1]) : 0.0f) + (i < m - 1 ? fabsf((float)e[i]) : 0.0f);
-    lo = fminf(lo, (float)d[i] - r);
-    hi = fmaxf(hi, (float)d[i] + r);
-    if (i < m - 1) emax = fmaxf(emax, fabsf((float)e[i]));
+    const float r = (i > 0 ? sqrtf(e2f[i - 1]) : 0.0f) + (i + 1 < m ? sqrtf(e2f[i]) : 0.0f);
+    lo = fminf(lo, df[i] - r);
+    hi = fmaxf(hi, df[i] + r);
+    if (i + 1 < m) emax2 = fmaxf(emax2, e2f[i]);
   }
-  const float tnorm = fmaxf(fabsf(lo), fabsf(hi));
-  const float pivmin = FLT_MIN * fmaxf(1.0f, emax * emax);
-  lo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
-  hi += 4.0f * FLT_EPSILON * tnorm + pivmin;
+  const float tnf = fmaxf(fabsf(lo), fabsf(hi));
+  const float pivmin = FLT_MIN * fmaxf(1.0f, emax2);
+  const float glo = lo - (4.0f * FLT_EPSILON * tnf + pivmin), ghi = hi + (4.0f * FLT_EPSILON * tnf + pivmin);
+  lo = glo; hi = ghi;
   for (int it = 0; it < 64; ++it) {
     const float mid = 0.5f * (lo + hi);
     if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    int cnt = 0;
-    float q = (float)d[0] - mid;
-    if (fabsf(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0f);
-    for (int i = 1; i < m; ++i) {
-      const float ei = (float)e[i - 1];
-      q = (float)d[i] - mid - ei * ei / q;
-      if (fabsf(q) < pivmin) q = -pivmin;
-      cnt += (q < 0.0f);
-    }
-    if (cnt > idx) hi = mid; else lo = mid;
+    if (sturm_count_f32(df, e2f, m, mid, pivmin) > idx) hi = mid; else lo = mid;
   }
-  return 0.5f * (lo + hi);
-}
-
-
-// idx-th eigenvalue to FP64 accuracy: the FP32 bisection's estimate is
-// bracketed by FP64 Sturm counts (the bracket widened when it misses) and
-// FP64 bisection runs only inside it -- about half the FP64 divisions of a
-// bisection over the whole Gershgorin interval.
-__device__ inline double tridiag_eig_hybrid(const double* d, const double* e, int m, int idx) {
-  double emax = 0.0, tn = 0.0;
-  for (int i = 0; i < m; ++i) {
-    tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0));
-    if (i < m - 1) emax = fmax(emax, fabs(e[i]));
-  }
-  const double pivmin = DBL_MIN * fmax(1.0, emax * emax);
-  const double g = (double)tridiag_bisect_f32(d, e, m, idx);
-  double w = 8.0 * (double)FLT_EPSILON * tn + pivmin;
-  double lo = g - w, hi = g + w;
+  const double g = 0.5 * ((double)lo + (double)hi);
+  const double pivmin64 = DBL_MIN * fmax(1.0, (double)emax2);
+  double w = 8.0 * (double)FLT_EPSILON * (double)tnf + (double)pivmin;
+  double dlo = g - w, dhi = g + w;
   bool ok = false;
   for (int t = 0; t < 3 && !ok; ++t) {
-    ok = sturm_count(d, e, m, lo, pivmin) <= idx && sturm_count(d, e, m, hi, pivmin) > idx;
-    if (!ok) { w *= 16.0; lo = g - w; hi = g + w; }
+    ok = sturm_count_minors(d, e2, m, dlo) <= idx && sturm_count_minors(d, e2, m, dhi) > idx;
+    if (!ok) { w *= 16.0; dlo = g - w; dhi = g + w; }
   }
-  if (!ok) return tridiag_eig_bisect(d, e, m, idx);
+  if (!ok) { dlo = (double)glo - w; dhi = (double)ghi + w; }
   for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, m, mid, pivmin) > idx) hi = mid; else lo = mid;
+    const double mid = 0.5 * (dlo + dhi);
+    const double am = fmax(fabs(dlo), fabs(dhi));
+    if (dhi - dlo <= fmax(2.0 * DBL_EPSILON * am + pivmin64, rtol * (1.0 + am)) || mid <= dlo || mid >= dhi) break;
+    if (sturm_count_minors(d, e2, m, mid) > idx) dhi = mid; else dlo = mid;
   }
-  return 0.5 * (lo + hi);
+  return 0.5 * (dlo + dhi);
 }
 }  // namespace fock

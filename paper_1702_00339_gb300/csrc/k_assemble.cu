@@ -330,7 +330,7 @@ void launch_combine(const ProbDev* probs, const CombineTask* tasks, int n, cudaS
 void launch_axis_dft(const ProbDev* probs, const DftTask* tasks, int n, int maxL, cudaStream_t st) {
   if (!n) return;
   size_t sm = (size_t)maxL * sizeof(cplx);
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_axis_dft);
+  FOCK_SMEM_OPTIN(k_axis_dft);
   k_axis_dft<<<dim3(32, n), 256, sm, st>>>(probs, tasks);
 }
 

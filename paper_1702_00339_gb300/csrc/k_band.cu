@@ -30,6 +30,7 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
   const BandTask T = tasks[blockIdx.x];
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L;
   __shared__ double inv[MAXM0 * MAXM0];
+  __shared__ double rlv[MAXM0];              // reciprocal pivots of the diagonal block's factor
   __shared__ int bad, s_stop, s_nbis;
   __shared__ double s_sigma, s_ok, s_bad;
   if (threadIdx.x == 0) { s_sigma = *T.sigma0; s_ok = NAN; s_bad = NAN; s_nbis = 0; s_stop = 0; }
@@ -64,15 +65,18 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
     for (int J = 0; J < L; ++J) {
       double* Ajj = bblk(T.band, D, m2, J, 0);
       // Cholesky of the diagonal block (lower, in place)
+      // (square roots and reciprocals by Newton-Raphson from FP32 seeds)
       for (int c = 0; c < m0; ++c) {
         if (threadIdx.x == 0) {
           double dv = Ajj[c * m0 + c];
           if (!(dv > 0.0)) { bad = 1; dv = 1.0; }
-          Ajj[c * m0 + c] = sqrt(dv);
+          const double rl = rsqrt_nr(dv);
+          rlv[c] = rl;
+          Ajj[c * m0 + c] = dv * rl;
         }
         __syncthreads();
-        double dc = Ajj[c * m0 + c];
-        for (int i = c + 1 + threadIdx.x; i < m0; i += blockDim.x) Ajj[i * m0 + c] /= dc;
+        const double rl = rlv[c];
+        for (int i = c + 1 + threadIdx.x; i < m0; i += blockDim.x) Ajj[i * m0 + c] *= rl;
         __syncthreads();
         const int nt = m0 - c - 1;
         for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
@@ -90,7 +94,7 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
         for (int c = 0; c < m0; ++c) {
           double s = b[c];
           for (int q = 0; q < c; ++q) s -= b[q] * Ajj[c * m0 + q];
-          b[c] = s / Ajj[c * m0 + c];
+          b[c] = s * rlv[c];
         }
       }
       __syncthreads();
@@ -100,7 +104,7 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
           double s = (i == c) ? 1.0 : 0.0;
           if (i >= c)
             for (int q = c; q < i; ++q) s -= Ajj[i * m0 + q] * inv[q * m0 + c];
-          inv[i * m0 + c] = (i >= c) ? s / Ajj[i * m0 + i] : 0.0;
+          inv[i * m0 + c] = (i >= c) ? s * rlv[i] : 0.0;
         }
       }
       __syncthreads();
@@ -109,7 +113,7 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
       const int npair = dmax * (dmax + 1) / 2;
       for (int it = threadIdx.x; it < npair * m2; it += blockDim.x) {
         int pr = it / m2, e = it % m2, mu = e / m0, nu = e % m0;
-        int d1 = (int)((sqrt(8.0 * pr + 1.0) - 1.0) * 0.5);
+        int d1 = (int)((sqrtf(8.0f * (float)pr + 1.0f) - 1.0f) * 0.5f);   // FP32: the loops below correct it
         while ((d1 + 1) * (d1 + 2) / 2 <= pr) ++d1;
         while (d1 * (d1 + 1) / 2 > pr) --d1;
         int d2 = pr - d1 * (d1 + 1) / 2;   // 0 <= d2 <= d1
@@ -154,92 +158,151 @@ __global__ void k_band_factor(const BandTask* __restrict__ tasks) {
 // search directions); each variant skips the tasks of the other.
 constexpr int kBandCols = 4;
 
+// 16-byte asynchronous global -> shared copies (L2 only), grouped per row
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kBandWarps = 4;   // warps per CTA of the solve
+
 template <typename R>
-__global__ void k_band_solve(const BandTask* __restrict__ tasks) {
-  const BandTask T = tasks[blockIdx.x];
+__global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* __restrict__ tasks, int ntask,
+                                                               int ngroup, int stage) {
+  // One warp per (problem, group of kBandCols columns); lane l owns the
+  // items l, l + 32, ... of a block row (item = (row mu, column)).  A row's
+  // D-term sum and its diagonal-block product run inside the warp, with no
+  // block barrier, and the warps of a CTA solve independent groups.  When a
+  // block row of the band fits `stage` doubles (and m0 is even, so blocks
+  // start on 16-byte boundaries), the warp copies the next row's blocks into
+  // its shared-memory stage while it computes the current one
+  // (double-buffered cp.async), hiding the latency of the band's loads.
+  extern __shared__ __align__(16) double bst[];
+  __shared__ R tvs[kBandWarps][MAXM0 * kBandCols];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kBandWarps + warp;
+  if (w >= ntask * ngroup) return;
+  const BandTask& T = tasks[w / ngroup];
   if (T.active && *T.active == 0) return;
   if ((T.fp32 != 0) != (sizeof(R) == 4)) return;
-  const int c0 = blockIdx.y * kBandCols;
+  const int c0 = (w % ngroup) * kBandCols;
   if (c0 >= T.k) return;
   const int nc = min(kBandCols, T.k - c0);
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L, ld = T.ld;
-  const double* band = T.band;
-  __shared__ R part[256];
-  __shared__ R tv[MAXM0 * kBandCols];
   const int items = m0 * nc;
-  const int nsplit = max(1, min((int)blockDim.x / items, 8));
-  const int tid = threadIdx.x;
-  const int item = tid % items, sp = tid / items;
-  const bool on = sp < nsplit;
-  const int mu = item % m0, c = c0 + item / m0;
-  double* Wc = T.W + (size_t)ld * c;
-  const double* Rc = T.R + (size_t)ld * c;
+  const double* band = T.band;
+  double* W = T.W;
+  const double* Rm = T.R;
+  R* tv = tvs[warp];
+  const bool staged = stage > 0 && (m0 % 2 == 0) && (D + 1) * m2 <= stage;
+  double* buf0 = bst + (size_t)warp * 2 * stage;
+  double* buf1 = buf0 + stage;
+  const int ch = m2 / 2;   // 16-byte chunks per block
+  // forward row J: slot d holds block (J, J - d) (d = 0: L_JJ^-1)
+  auto fetch_fwd = [&](int J, double* dst) {
+    const int nd = min(D, J) + 1;
+    for (int it = lane; it < nd * ch; it += 32) {
+      const int d = it / ch, cq = it % ch;
+      cp_async16(dst + d * m2 + 2 * cq, bblk(const_cast<double*>(band), D, m2, J - d, d) + 2 * cq);
+    }
+  };
+  // backward row J: slot d holds block (J + d, J), stored contiguously from (J, 0)
+  auto fetch_bwd = [&](int J, double* dst) {
+    const int nd = min(D, L - 1 - J) + 1;
+    const double* src = bblk(const_cast<double*>(band), D, m2, J, 0);
+    for (int it = lane; it < nd * ch; it += 32) cp_async16(dst + 2 * it, src + 2 * it);
+  };
   // forward: y_J = L_JJ^-1 (r_J - sum_d L[J][J-d] y_{J-d})
+  if (staged) { fetch_fwd(0, buf0); cp_async_commit(); }
   for (int J = 0; J < L; ++J) {
-    R s = 0;
-    if (on) {
-      const int dmax = min(D, J);
-      for (int d = 1 + sp; d <= dmax; d += nsplit) {
-        const double* l = bblk(const_cast<double*>(band), D, m2, J - d, d) + mu * m0;   // block (J, J-d)
+    const double* cur = nullptr;
+    if (staged) {
+      if (J + 1 < L) fetch_fwd(J + 1, (J & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncwarp();
+      cur = (J & 1) ? buf1 : buf0;
+    }
+    const int dmax = min(D, J);
+    for (int i = lane; i < items; i += 32) {
+      const int mu = i % m0, c = c0 + i / m0;
+      const double* Wc = W + (size_t)ld * c;
+      R s = (R)Rm[(size_t)ld * c + J * m0 + mu];
+      for (int d = 1; d <= dmax; ++d) {
+        const double* l = (staged ? cur + d * m2 : bblk(const_cast<double*>(band), D, m2, J - d, d)) + mu * m0;
         const double* y = Wc + (size_t)((J - d) * m0);
         for (int q = 0; q < m0; ++q) s -= (R)l[q] * (R)y[q];
       }
-      part[tid] = s;
+      tv[i] = s;
     }
-    __syncthreads();
-    if (on && sp == 0) {
-      R r = (R)Rc[(size_t)(J * m0 + mu)];
-      for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
-      tv[item] = r;
-    }
-    __syncthreads();
-    if (on && sp == 0) {
-      const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0) + mu * m0;
-      const int cb = (item / m0) * m0;
+    __syncwarp();
+    for (int i = lane; i < items; i += 32) {
+      const int mu = i % m0, c = c0 + i / m0, cb = (i / m0) * m0;
+      const double* iv = (staged ? cur : bblk(const_cast<double*>(band), D, m2, J, 0)) + mu * m0;
       R y = 0;
       for (int q = 0; q <= mu; ++q) y += (R)iv[q] * tv[cb + q];
-      Wc[(size_t)(J * m0 + mu)] = (double)y;
+      W[(size_t)ld * c + J * m0 + mu] = (double)y;
     }
-    __syncthreads();
+    __syncwarp();
   }
+  if (staged) { cp_async_wait0(); __syncwarp(); }
   // backward: x_J = L_JJ^-T (y_J - sum_d L[J+d][J]^T x_{J+d})
-  for (int J = L - 1; J >= 0; --J) {
-    R s = 0;
-    if (on) {
-      const int dmax = min(D, L - 1 - J);
-      for (int d = 1 + sp; d <= dmax; d += nsplit) {
-        const double* l = bblk(const_cast<double*>(band), D, m2, J, d);   // block (J+d, J): column mu
+  if (staged) { fetch_bwd(L - 1, buf0); cp_async_commit(); }
+  for (int J = L - 1, step = 0; J >= 0; --J, ++step) {
+    const double* cur = nullptr;
+    if (staged) {
+      if (J > 0) fetch_bwd(J - 1, (step & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncwarp();
+      cur = (step & 1) ? buf1 : buf0;
+    }
+    const int dmax = min(D, L - 1 - J);
+    for (int i = lane; i < items; i += 32) {
+      const int mu = i % m0, c = c0 + i / m0;
+      const double* Wc = W + (size_t)ld * c;
+      R s = (R)Wc[(size_t)(J * m0 + mu)];
+      for (int d = 1; d <= dmax; ++d) {
+        const double* l = staged ? cur + d * m2 : bblk(const_cast<double*>(band), D, m2, J, d);   // block (J+d, J)
         const double* x = Wc + (size_t)((J + d) * m0);
         for (int q = 0; q < m0; ++q) s -= (R)l[q * m0 + mu] * (R)x[q];
       }
-      part[tid] = s;
+      tv[i] = s;
     }
-    __syncthreads();
-    if (on && sp == 0) {
-      R r = (R)Wc[(size_t)(J * m0 + mu)];
-      for (int p2 = 0; p2 < nsplit; ++p2) r += part[p2 * items + item];
-      tv[item] = r;
-    }
-    __syncthreads();
-    if (on && sp == 0) {
-      const double* iv = bblk(const_cast<double*>(band), D, m2, J, 0);
-      const int cb = (item / m0) * m0;
+    __syncwarp();
+    for (int i = lane; i < items; i += 32) {
+      const int mu = i % m0, c = c0 + i / m0, cb = (i / m0) * m0;
+      const double* iv = staged ? cur : bblk(const_cast<double*>(band), D, m2, J, 0);
       R x = 0;
       for (int q = mu; q < m0; ++q) x += (R)iv[q * m0 + mu] * tv[cb + q];
-      Wc[(size_t)(J * m0 + mu)] = (double)x;
+      W[(size_t)ld * c + J * m0 + mu] = (double)x;
     }
-    __syncthreads();
+    __syncwarp();
   }
+  if (staged) cp_async_wait0();
 }
 
 void launch_band_factor(const BandTask* t, int n, cudaStream_t st) {
   if (n) k_band_factor<<<n, 256, 0, st>>>(t);
 }
-void launch_band_solve(const BandTask* t, int n, int kmax, cudaStream_t st, bool mixed) {
+// stage: doubles of one shared-memory stage per warp (0: loads from global)
+void launch_band_solve(const BandTask* t, int n, int kmax, int stage, cudaStream_t st, bool mixed) {
   if (!n) return;
-  const dim3 g(n, (kmax + kBandCols - 1) / kBandCols);
-  k_band_solve<double><<<g, 256, 0, st>>>(t);
-  if (mixed) k_band_solve<float><<<g, 256, 0, st>>>(t);
+  const int ng = (kmax + kBandCols - 1) / kBandCols;
+  const int nb = (n * ng + kBandWarps - 1) / kBandWarps;
+  const size_t sm = (size_t)kBandWarps * 2 * stage * sizeof(double);
+  // (the 48 KB default covers static plus dynamic shared memory: always opt in)
+  FOCK_SMEM_OPTIN(k_band_solve<double>);
+  FOCK_SMEM_OPTIN(k_band_solve<float>);
+  k_band_solve<double><<<nb, kBandWarps * 32, sm, st>>>(t, n, ng, stage);
+  if (mixed) k_band_solve<float><<<nb, kBandWarps * 32, sm, st>>>(t, n, ng, stage);
 }
+
+// doubles of one band-solve stage for the largest block row among the tasks
+// that can be staged (even m0), capped at 12 KB per stage
+int band_stage_doubles(int maxrow) { return std::min(maxrow, 1536); }
 
 }  // namespace fock

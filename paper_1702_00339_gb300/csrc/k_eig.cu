@@ -67,7 +67,7 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
   __shared__ cplx rph[MAXM0 / 2 + 1];
   __shared__ int rp[MAXM0 / 2 + 1], rq[MAXM0 / 2 + 1];
   __shared__ int nrot;
-  __shared__ double red[32], s_thr;
+  __shared__ double red[32], s_thr2;
   const int ne = n + (n & 1);
   double part = 0.0;
   for (int it = threadIdx.x; it < n * n; it += blockDim.x) part += cabs2(a[(it / n) * ld + (it % n)]);
@@ -77,7 +77,7 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
-    s_thr = 1e-15 * sqrt(t);
+    s_thr2 = 1e-30 * t;   // (1e-15 ||a||_F)^2
   }
   for (int it = threadIdx.x; it < ne * ne; it += blockDim.x) {
     int i = it / ne, j = it % ne;
@@ -85,7 +85,7 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
     if (i == n || j == n) a[i * ld + j] = cmk(0.0, 0.0);
   }
   __syncthreads();
-  const double thr = s_thr;
+  const double thr2 = s_thr2;
   const int np2 = ne / 2;
   for (int sweep = 0; sweep < 30; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
@@ -96,14 +96,18 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
         int y = ((ne - 2 - pi + rnd) % (ne - 1)) + 1;
         int p = min(x, y), q = max(x, y);
         cplx apq = a[p * ld + q];
-        double r = sqrt(cabs2(apq)), app = a[p * ld + p].x, aqq = a[q * ld + q].x;
+        const double r2 = cabs2(apq), app = a[p * ld + p].x, aqq = a[q * ld + q].x;
         double c = 1.0, s = 0.0;
         cplx ph = cmk(1.0, 0.0);
-        if (r > thr && r > 1e-17 * sqrt(fabs(app * aqq))) {
-          ph = cscale(apq, 1.0 / r);
-          double th = (aqq - app) / (2.0 * r);
-          double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
+        if (r2 > thr2 && r2 > 1e-34 * fabs(app * aqq)) {   // |a_pq| > thr and > 1e-17 sqrt|a_pp a_qq|
+          // reciprocals and square roots by Newton-Raphson from FP32 seeds
+          const double rr = rsqrt_nr(r2);                    // 1 / |a_pq|
+          ph = cscale(apq, rr);
+          const double th = (aqq - app) * (0.5 * rr);
+          const double y = fma(th, th, 1.0);
+          double t = rcp_nr(fabs(th) + y * rsqrt_nr(y));     // 1 / (|th| + sqrt(th^2 + 1))
+          if (th < 0.0) t = -t;
+          c = rsqrt_nr(fma(t, t, 1.0));
           s = t * c;
           atomicAdd(&nrot, 1);
         }
@@ -218,15 +222,18 @@ __device__ void cta_tridiag(cplx* c, int m, double* d, double* e, cplx* v, cplx*
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
-      double xn = sqrt(s);
-      cplx x0 = c[(k + 1) * m + k];
-      double ax0 = sqrt(cabs2(x0));
-      cplx ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
+      // square roots and reciprocals by Newton-Raphson from FP32 seeds
+      const double xn = (s > 0.0) ? s * rsqrt_nr(s) : 0.0;
+      const cplx x0 = c[(k + 1) * m + k];
+      const double a2 = cabs2(x0);
+      const double ra = (a2 > 0.0) ? rsqrt_nr(a2) : 0.0;
+      const double ax0 = a2 * ra;
+      cplx ph = (a2 > 0.0) ? cscale(x0, ra) : cmk(1.0, 0.0);
       cplx alpha = cscale(ph, -xn);
       d[k] = c[k * m + k].x;
       e[k] = xn;
       double vn2 = 2.0 * (s + xn * ax0);
-      s_tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+      s_tau = (vn2 > 0.0) ? 2.0 * rcp_nr(vn2) : 0.0;
       s_norm = xn;
       v[k + 1] = csub(x0, alpha);
     }
@@ -295,6 +302,9 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   cplx* pv = v + MAXM0;
   double* dd = (double*)(pv + MAXM0);
   double* ee = dd + MAXM0;
+  double* e2 = ee + MAXM0;                 // e^2, and FP32 copies of d and e^2
+  float* df = (float*)(e2 + MAXM0);
+  float* e2f = df + MAXM0;
 
   if (F.source == FROM_FACTORS) {
     const int j3 = j % F.L[2], j2 = (j / F.L[2]) % F.L[1], j1 = j / (F.L[1] * F.L[2]);
@@ -318,11 +328,19 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
       S[pr] = cmul(s0, s12);
     }
   } else {
+    // twiddles exp(-2 pi i j d / M), d = 1..D, once per block (in the Jacobi
+    // scratch, free until the canonical reduction) when they fit
+    cplx* tw = Aj;
+    const bool tab = (F.D <= 2 * ldj * ldj);
+    if (tab) {
+      for (int dd2 = 1 + threadIdx.x; dd2 <= F.D; dd2 += blockDim.x) tw[dd2 - 1] = twiddle((long long)j * dd2, F.M);
+      __syncthreads();
+    }
     for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
       int mu = pr / m0, nu = pr % m0, tr = nu * m0 + mu;
       cplx h = cmk(F.TH[pr], 0.0), s = cmk(F.TS[pr], 0.0);
       for (int dd2 = 1; dd2 <= F.D; ++dd2) {
-        cplx w = twiddle((long long)j * dd2, F.M);
+        cplx w = tab ? tw[dd2 - 1] : twiddle((long long)j * dd2, F.M);
         const double* th = F.TH + (size_t)dd2 * np;
         const double* ts = F.TS + (size_t)dd2 * np;
         // w T_d[mu][nu] + conj(w) T_d[nu][mu]
@@ -359,13 +377,22 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   __shared__ double sv[MAXM0];
   const int r = cta_lowdin_reduce(H, S, Aj, Qj, m0, kCanonTau, sv, keep);
   if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double e2i = (i + 1 < r) ? ee[i] * ee[i] : 0.0;
+    e2[i] = e2i;
+    df[i] = (float)dd[i];
+    e2f[i] = (float)e2i;
+  }
+  __syncthreads();
   if (F.want == 1) {
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_hybrid(dd, ee, r, i) : INFINITY;
+      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_fast(df, e2f, dd, e2, r, i, 0.0) : INFINITY;
       if (F.blk) F.blk[(size_t)jl * m0 + i] = j;
     }
   } else if (threadIdx.x == 0) {
-    F.ev[jl] = (r > 0) ? tridiag_eig_hybrid(dd, ee, r, 0) : INFINITY;
+    // the lowest eigenvalue of an embedding block only sets the preconditioner
+    // shift (lowered by 2e-3 relative afterwards): 1e-9 relative suffices
+    F.ev[jl] = (r > 0) ? tridiag_eig_fast(df, e2f, dd, e2, r, 0, 1e-9) : INFINITY;
   }
 }
 
@@ -492,14 +519,15 @@ __global__ void k_unpad_copy(const double* pv, const int* pidx, int n, double* v
 // ---- launchers ----
 size_t fblocks_smem(int m0) {
   const int ldj = m0 + (m0 & 1);
-  return (size_t)(2 * m0 * m0 + 2 * ldj * ldj + 2 * MAXM0) * sizeof(cplx) + 2 * MAXM0 * sizeof(double);
+  return (size_t)(2 * m0 * m0 + 2 * ldj * ldj + 2 * MAXM0) * sizeof(cplx) + 3 * MAXM0 * sizeof(double) +
+         2 * MAXM0 * sizeof(float);
 }
 
 void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,
                     cudaStream_t st) {
   if (!ntask || !maxnj) return;
   size_t sm = fblocks_smem(maxm0);
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_fblocks);
+  FOCK_SMEM_OPTIN(k_fblocks);
   k_fblocks<<<dim3(maxnj, ntask), 128, sm, st>>>(probs, tasks);
 }
 
@@ -508,7 +536,7 @@ void launch_precond(const ProbDev* probs, const PrecTask* tasks, int ntask, int 
   if (!ntask) return;
   k_sigma<<<ntask, 256, 0, st>>>(tasks);
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_precond);
+  FOCK_SMEM_OPTIN(k_precond);
   k_precond<<<dim3(maxM, ntask), 128, sm, st>>>(probs, tasks);
 }
 
@@ -517,7 +545,7 @@ void launch_sort_small(const SortTask* tasks, int ntask, int maxn, cudaStream_t 
   int n2 = 1;
   while (n2 < maxn) n2 <<= 1;
   size_t sm = (size_t)n2 * (sizeof(double) + sizeof(int));
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_sort_small);
+  FOCK_SMEM_OPTIN(k_sort_small);
   k_sort_small<<<ntask, 512, sm, st>>>(tasks);
 }
 

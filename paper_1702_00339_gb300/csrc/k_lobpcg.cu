@@ -192,10 +192,13 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
         int p = min(x, y), q = max(x, y);
         double apq = a[p * ld + q], app = a[p * ld + p], aqq = a[q * ld + q];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > thr && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
-          double th = (aqq - app) / (2.0 * apq);
-          double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
+        if (fabs(apq) > thr && apq * apq > 1e-34 * fabs(app * aqq)) {   // |a_pq| > 1e-17 sqrt|a_pp a_qq|
+          // reciprocals and square roots by Newton-Raphson from FP32 seeds
+          const double th = (aqq - app) * (0.5 * rcp_nr(apq));
+          const double y = fma(th, th, 1.0);
+          double t = rcp_nr(fabs(th) + y * rsqrt_nr(y));
+          if (th < 0.0) t = -t;
+          c = rsqrt_nr(fma(t, t, 1.0));
           s = t * c;
           atomicAdd(&nrot, 1);
         }
@@ -776,6 +779,12 @@ __global__ void k_colnorm(const CopyTask* __restrict__ tasks) {
   for (int i = threadIdx.x; i < T.n; i += blockDim.x) col[i] *= inv;
 }
 
+// One CTA per segment: dst[seg.dst + w] = seg.src[w].
+__global__ void k_gather(const GatherSeg* __restrict__ segs, uint32_t* __restrict__ dst) {
+  const GatherSeg g = segs[blockIdx.x];
+  for (unsigned int w = threadIdx.x; w < g.words; w += blockDim.x) dst[g.dst + w] = g.src[w];
+}
+
 __global__ void k_copy_cols(const CopyTask* __restrict__ tasks) {
   const CopyTask T = tasks[blockIdx.y];
   if (T.active && *T.active == 0) return;
@@ -909,6 +918,10 @@ __global__ void k_cell_back(const double* __restrict__ Xc, int m0, int L, int nc
     for (int j = 0; j < m0; ++j) acc += Xc[mu * m0 + j] * Vr[(size_t)(cell * m0 + j) + (size_t)ld * c];
     V[(size_t)(cell * m0 + mu) + (size_t)ld * c] = acc;
   }
+}
+
+void launch_gather(const GatherSeg* segs, int n, uint32_t* dst, cudaStream_t st) {
+  if (n) k_gather<<<n, 128, 0, st>>>(segs, dst);
 }
 
 void launch_cell_canon(const CanonTask* t, int n, int maxm0, int maxblk, cudaStream_t st) {

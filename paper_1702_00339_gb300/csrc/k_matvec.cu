@@ -245,17 +245,17 @@ void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc
   if (!ntask) return;
   size_t sm = fft_smem(maxM, cc);
   if (dir > 0) {
-    if (sm > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<1, double>));
+    FOCK_SMEM_OPTIN((k_fft<1, double>));
     k_fft<1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
     if (mixed) {
-      if (sm / 2 > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<1, float>));
+      FOCK_SMEM_OPTIN((k_fft<1, float>));
       k_fft<1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
     }
   } else {
-    if (sm > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<-1, double>));
+    FOCK_SMEM_OPTIN((k_fft<-1, double>));
     k_fft<-1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
     if (mixed) {
-      if (sm / 2 > 48 * 1024) FOCK_SMEM_OPTIN((k_fft<-1, float>));
+      FOCK_SMEM_OPTIN((k_fft<-1, float>));
       k_fft<-1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
     }
   }
@@ -264,7 +264,8 @@ void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc
 void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st, bool mixed) {
   if (!ntask) return;
   size_t sm = (size_t)2 * maxm0 * maxm0 * sizeof(cplx);
-  if (sm > 48 * 1024) FOCK_SMEM_OPTIN(k_blockmul<double>);
+  FOCK_SMEM_OPTIN(k_blockmul<double>);
+  FOCK_SMEM_OPTIN(k_blockmul<float>);
   k_blockmul<double><<<dim3(maxM, ntask), 256, sm, st>>>(tasks);
   if (mixed) k_blockmul<float><<<dim3(maxM, ntask), 256, sm / 2, st>>>(tasks);
 }
