@@ -35,7 +35,7 @@ namespace fock {
 
 
 // launchers (defined in the .cu files)
-void launch_vec1d(const ProbDev*, const SegDesc*, int, const SegDesc*, int, const DefTab*, int, cudaStream_t);
+void launch_vec1d(const ProbDev*, const SegDesc*, int, const SegDesc*, int, const DefTab*, int, int, int, cudaStream_t);
 void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream_t);
 void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
@@ -419,6 +419,7 @@ struct Batch {
   TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
   int band_stage = 0;                // doubles of a band-solve shared-memory stage
+  int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
   int eapply_gx = 16;
@@ -448,6 +449,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   B.any_mixed = false;
   B.band_stage = 0;
+  B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
   for (int i = 0; i < np; ++i) {
@@ -475,10 +477,13 @@ void plan(Batch& B, Slab& S, Slab& U) {
       AxisDev& D = P.ax[a];
       D.N = H.N[a]; D.L = H.L[a]; D.per = H.per[a]; D.pad = A.pad;
       D.jlo = A.jlo; D.W = A.W; D.rlo = A.rlo; D.nr = A.nr;
+      D.smin = A.jmin; D.slen = A.jmax - A.jmin + 1;
       D.g = S.take<double>((size_t)H.m0 * A.W);
       D.p = S.take<double>((size_t)H.T * A.nr);
       B.gsegs.push_back({i, a, H.m0 * A.W});
       B.psegs.push_back({i, a, H.T * A.nr});
+      B.ptab_maxT = std::max(B.ptab_maxT, H.T);
+      B.ptab_maxni = std::max(B.ptab_maxni, A.nr + 2 * (H.L[a] == 1 ? 0 : H.L[a] / 2) * H.n0 + 1);
     }
     // gram tasks
     for (int a = 0; a < 3; ++a) {
@@ -1130,7 +1135,7 @@ int build_batch(fock_ctx* ctx, int nprob, const fock_problem* probs, Batch& B, b
 void run_assemble(fock_ctx* ctx, Batch& B) {
   cudaStream_t st = ctx->stream;
   { PROF("k_vec1d", 2); launch_vec1d(B.d_probs, B.d_gsegs, (int)B.gsegs.size(), B.d_psegs, (int)B.psegs.size(),
-                                     B.d_dtabs, (int)B.dtabs.size(), st); }
+                                     B.d_dtabs, (int)B.dtabs.size(), B.ptab_maxT, B.ptab_maxni, st); }
   { PROF("k_gram", 2); launch_gram(B.d_probs, B.d_gram, (int)B.gram.size(), B.d_dtabs, st); }
   if (!B.combT.empty()) { PROF("k_combine", 2);
     launch_combine(B.d_probs, B.d_combT, (int)B.combT.size(), st);

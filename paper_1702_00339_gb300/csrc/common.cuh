@@ -48,6 +48,7 @@ struct AxisDev {
   int N, L, per, pad;
   int jlo, W;           // reference-cell function window: j in [jlo, jlo + W)
   int rlo, nr;          // potential table: reduced node r in [rlo, rlo + nr)
+  int smin, slen;       // support of the reference-cell functions: virtual nodes [smin, smin + slen)
   double* g;            // [m0][W]   nodal GTO factors of the reference cell
   double* p;            // [T][nr]   window-summed P0 Gaussian integrals
 };

@@ -86,6 +86,56 @@ __global__ void k_ptab(const ProbDev* __restrict__ probs, const SegDesc* __restr
   }
 }
 
+// One CTA per (segment, potential term t): the erfc values at every cell
+// endpoint of the window once (shared memory), then each reduced node's
+// window sum from them.  Adjacent cells share endpoints, so each endpoint is
+// evaluated once instead of twice per cell (and once for all the nodes whose
+// windows meet there); the cell across the nucleus (endpoints of both
+// signs) takes erf directly, as gauss_cell does.  Same cells and weights as
+// k_ptab.
+__global__ void k_ptab_nodes(const ProbDev* __restrict__ probs, const SegDesc* __restrict__ segs) {
+  extern __shared__ double Eq[];
+  const SegDesc sg = segs[blockIdx.y];
+  const ProbDev& P = probs[sg.prob];
+  const AxisDev& A = P.ax[sg.axis];
+  const int t = blockIdx.x;
+  if (t >= P.T) return;
+  const int L = A.L, n0 = P.n0;
+  const int hw = (L == 1) ? 0 : L / 2;
+  const int nu = t / P.R, q = t % P.R;
+  const double f = P.frac[nu * 3 + sg.axis];
+  const double tq = P.tq[q];
+  const double reach = 7.0 / tq;
+  const double cn = (double)n0 * P.h;
+  const int i0 = A.rlo - hw * n0;                 // endpoint index i of s_i = (i - f n0) h
+  const int ni = A.nr + 2 * hw * n0 + 1;
+  for (int j = threadIdx.x; j < ni; j += blockDim.x) {
+    const double s = ((double)(i0 + j) - f * (double)n0) * P.h;
+    // the cells kept below meet (-reach, reach): their endpoints lie within reach + h
+    Eq[j] = (fabs(s) <= reach + 2.0 * P.h) ? erfc(tq * fabs(s)) : 0.0;
+  }
+  __syncthreads();
+  const double sc = 0.88622692545275801365 / tq;   // sqrt(pi)/2 / t
+  for (int rr = threadIdx.x; rr < A.nr; rr += blockDim.x) {
+    const double r = (double)(A.rlo + rr);
+    const int klo = (int)fmax((double)-hw, floor((r * P.h - reach) / cn - f) - 1.0);
+    const int khi = (int)fmin((double)hw, ceil((r * P.h + reach + P.h) / cn - f) + 1.0);
+    double acc = 0.0;
+    for (int k = klo; k <= khi; ++k) {
+      const double w = (L > 1 && (L % 2 == 0) && (k == -hw || k == hw)) ? 0.5 : 1.0;
+      const int j = rr + (hw - k) * n0;           // cell [s_i, s_{i+1}], i = rlo + rr - k n0
+      const double u = (r - ((double)k + f) * (double)n0) * P.h;
+      const double a = tq * u, b = tq * (u + P.h);
+      double v;
+      if (a >= 0.0) v = Eq[j] - Eq[j + 1];
+      else if (b <= 0.0) v = Eq[j + 1] - Eq[j];
+      else v = erf(b) - erf(a);
+      acc += w * (v * sc);
+    }
+    A.p[(size_t)t * A.nr + rr] = acc;
+  }
+}
+
 __global__ void k_deftab(const ProbDev* __restrict__ probs, const DefTab* __restrict__ tabs) {
   const DefTab D = tabs[blockIdx.y];
   const ProbDev& P = probs[D.prob];
@@ -131,9 +181,20 @@ __global__ void k_gram_fold(const ProbDev* __restrict__ probs, const GramTask* _
       if (r >= T.rho0 && r < T.rho1)
         acc = gval(A, T.mode, n0, mu, T.a, r) * gval(A, T.mode, n0, nu, T.b, r);
     } else if (T.mode == RING) {
-      for (int c = 0; c < A.L; ++c) {
-        int rho = r + c * n0;
-        acc += gval(A, RING, n0, mu, T.a, rho) * gval(A, RING, n0, nu, T.b, rho);
+      // only the cells c whose node r + c n0 meets the support of g_mu(cell a):
+      // c n0 in [a n0 + smin - r, a n0 + smin - r + slen) modulo the ring
+      const int lo = T.a * n0 + A.smin - r;
+      const int c0 = floordiv(lo + n0 - 1, n0), c1 = floordiv(lo + A.slen - 1, n0);
+      if (A.slen >= A.N || c1 - c0 + 1 >= A.L) {
+        for (int c = 0; c < A.L; ++c) {
+          int rho = r + c * n0;
+          acc += gval(A, RING, n0, mu, T.a, rho) * gval(A, RING, n0, nu, T.b, rho);
+        }
+      } else {
+        for (int c = c0; c <= c1; ++c) {
+          int rho = r + posmod(c, A.L) * n0;
+          acc += gval(A, RING, n0, mu, T.a, rho) * gval(A, RING, n0, nu, T.b, rho);
+        }
       }
     } else if (T.mode == VIRT || (r >= 0 && r < n0)) {
       // all nodes rho = r (mod n0) in the window (WALL: interior cells 0..L-1)
@@ -152,10 +213,14 @@ __global__ void k_gram_fold(const ProbDev* __restrict__ probs, const GramTask* _
     T.Zs[it] = acc;
   }
   if (direct) return;   // defect forms carry no mass / stiffness part
+  // RING: only the nodes of the support of g_mu(cell a) (the others add zeros)
+  const bool ring_sup = (T.mode == RING && A.slen < A.N);
+  const int nrho = ring_sup ? A.slen : T.rho1 - T.rho0;
   for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
     int mu = pr / m0, nu = pr % m0;
     double s = 0.0, a = 0.0;
-    for (int rho = T.rho0; rho < T.rho1; ++rho) {
+    for (int t = 0; t < nrho; ++t) {
+      const int rho = ring_sup ? posmod(T.a * n0 + A.smin + t, A.N) : T.rho0 + t;
       double ga = gval(A, T.mode, n0, mu, T.a, rho);
       if (ga == 0.0) continue;
       double b0 = gval(A, T.mode, n0, nu, T.b, rho);
@@ -309,10 +374,19 @@ __global__ void k_axis_dft(const ProbDev* __restrict__ probs, const DftTask* __r
 }
 
 // ------------------------------------------------------------ launchers ----
+// maxT, maxni: the largest term count and endpoint count of the segments
 void launch_vec1d(const ProbDev* probs, const SegDesc* gsegs, int ngseg, const SegDesc* psegs,
-                  int npseg, const DefTab* dtabs, int ndtab, cudaStream_t st) {
+                  int npseg, const DefTab* dtabs, int ndtab, int maxT, int maxni, cudaStream_t st) {
   if (ngseg) k_gref<<<dim3(8, ngseg), 256, 0, st>>>(probs, gsegs);
-  if (npseg) k_ptab<<<dim3(16, npseg), 256, 0, st>>>(probs, psegs);
+  if (npseg) {
+    const size_t sm = (size_t)maxni * sizeof(double);
+    if (sm <= 160 * 1024) {
+      FOCK_SMEM_OPTIN(k_ptab_nodes);
+      k_ptab_nodes<<<dim3(maxT, npseg), 256, sm, st>>>(probs, psegs);
+    } else {
+      k_ptab<<<dim3(16, npseg), 256, 0, st>>>(probs, psegs);
+    }
+  }
   if (ndtab) k_deftab<<<dim3(8, ndtab), 256, 0, st>>>(probs, dtabs);
 }
 
