@@ -898,13 +898,13 @@ void plan(Batch& B, Slab& S, Slab& U) {
       auto fwd = [&](const double* src, int ncol, const int* md) {
         FftTask t; std::memset(&t, 0, sizeof(t));
         t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.x = src; t.ldx = n; t.X = X;
-        t.cc = B.fft_cc; t.mode = md;
+        t.cc = B.fft_cc; t.mode = md; t.active = l.active;   // converged problems: no more matvecs
         return t;
       };
       auto inv = [&](cplx* from, double* dst, int ncol, const int* md) {
         FftTask t; std::memset(&t, 0, sizeof(t));
         t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.X = from; t.y = dst; t.ldy = n;
-        t.beta = 0.0; t.cc = B.fft_cc; t.mode = md;
+        t.beta = 0.0; t.cc = B.fft_cc; t.mode = md; t.active = l.active;
         return t;
       };
       double* Yx = l.Y;            // X: columns [0, k)
@@ -912,8 +912,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
       fXP.push_back(fwd(Yx, 2 * k, opmode)); fW.push_back(fwd(Yw, k, opmode));
       iHXP.push_back(inv(Y1, l.HY, 2 * k, opmode)); iSXP.push_back(inv(Y2, l.SY, 2 * k, opmode));
       iHW.push_back(inv(Y1, l.HY + 2 * nk, k, opmode)); iSW.push_back(inv(Y2, l.SY + 2 * nk, k, opmode));
-      bHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, opmode});
-      bHS1.push_back({i, Q.M, m0, k, Q.CH, Q.CS, X, Y1, Y2, opmode});
+      bHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, opmode, l.active});
+      bHS1.push_back({i, Q.M, m0, k, Q.CH, Q.CS, X, Y1, Y2, opmode, l.active});
       if (Q.use_band) {
         BandTask bt;
         std::memset(&bt, 0, sizeof(bt));
@@ -927,13 +927,13 @@ void plan(Batch& B, Slab& S, Slab& U) {
       } else {
         fR.push_back(fwd(l.R, k, pcmode));
         iPW.push_back(inv(Y1, Yw, k, pcmode));
-        bK.push_back({i, Q.M, m0, k, Q.K, nullptr, X, Y1, nullptr, pcmode});
+        bK.push_back({i, Q.M, m0, k, Q.K, nullptr, X, Y1, nullptr, pcmode, l.active});
       }
       auto ea = [&](const double* vals, const double* x, double* y, int ncol, const int* md) {
         EApplyTask t;
         std::memset(&t, 0, sizeof(t));
         t.prob = i; t.m0 = m0; t.ncol = ncol; t.nrows = Q.nErows; t.rows = Q.Erows; t.rowptr = Q.Erowptr;
-        t.cols = Q.Ecols; t.vals = vals; t.x = x; t.ldx = n; t.y = y; t.ldy = n; t.mode = md;
+        t.cols = Q.Ecols; t.vals = vals; t.x = x; t.ldx = n; t.y = y; t.ldy = n; t.mode = md; t.active = l.active;
         return t;
       };
       if (Q.nE) {
@@ -946,7 +946,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         const int* rf = B.d_refresh + s2;
         rfXP.push_back(fwd(Yx, 2 * k, rf));
         riHXP.push_back(inv(Y1, l.HY, 2 * k, rf)); riSXP.push_back(inv(Y2, l.SY, 2 * k, rf));
-        rbHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, rf});
+        rbHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, rf, l.active});
         if (Q.nE) { rehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k, rf)); resxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k, rf)); }
       }
       ini.push_back({n, k, n, problem_seed(H), l.Y});   // start depends on the problem only

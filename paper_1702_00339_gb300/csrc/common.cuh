@@ -194,6 +194,7 @@ struct FftTask {
   double beta;                    // y = beta*y + Re(.)/M
   int cc;                         // columns per CTA
   const int* mode;                // null: FP64 only; else the problem's mode (0 FP64, 1 FP32)
+  const int* active;              // null: always; else skipped once the problem has converged
 };
 
 struct BmulTask {
@@ -202,6 +203,7 @@ struct BmulTask {
   const cplx* X;                   // [M][m0*ncol]
   cplx* Y1; cplx* Y2;
   const int* mode;                 // as FftTask::mode
+  const int* active;               // as FftTask::active
 };
 
 struct EApplyTask {
@@ -213,6 +215,7 @@ struct EApplyTask {
   const double* x; int ldx;
   double* y; int ldy;
   const int* mode;      // null: always; else only while *mode == 0 (image refresh lists)
+  const int* active;    // as FftTask::active
 };
 
 struct InitTask { int n, k, ld; uint64_t seed; double* X; };

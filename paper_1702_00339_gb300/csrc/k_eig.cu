@@ -528,7 +528,11 @@ void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, in
   if (!ntask || !maxnj) return;
   size_t sm = fblocks_smem(maxm0);
   FOCK_SMEM_OPTIN(k_fblocks);
-  k_fblocks<<<dim3(maxnj, ntask), 128, sm, st>>>(probs, tasks);
+  // the rotation and update phases of an m0 x m0 block have about m0^2 / 2
+  // parallel items: one warp for m0 <= 8 (more independent blocks resident
+  // per SM keep the FP64 pipe busy), up to four warps for m0 = 32
+  const int threads = (maxm0 <= 8) ? 32 : (maxm0 <= 16) ? 64 : 128;
+  k_fblocks<<<dim3(maxnj, ntask), threads, sm, st>>>(probs, tasks);
 }
 
 void launch_precond(const ProbDev* probs, const PrecTask* tasks, int ntask, int maxM, int maxm0,

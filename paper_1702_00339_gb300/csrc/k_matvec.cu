@@ -56,6 +56,7 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char fft_sbuf[];
   const FftTask T = tasks[blockIdx.y];
   if (!mode_match<R>(T.mode)) return;
+  if (T.active && *T.active == 0) return;
   const CircDev Cd = *T.circ;
   const int M = Cd.M, CC = T.cc;
   const int npair = (T.ncol + 1) >> 1;    // two real columns per complex transform
@@ -185,6 +186,7 @@ __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char bm_smem[];
   const BmulTask T = tasks[blockIdx.y];
   if (!mode_match<R>(T.mode)) return;
+  if (T.active && *T.active == 0) return;
   const int j = blockIdx.x;
   if (j >= T.M) return;
   const int m0 = T.m0, np = m0 * m0, nc = m0 * ((T.ncol + 1) >> 1);
@@ -215,6 +217,7 @@ __global__ void k_blockmul(const BmulTask* __restrict__ tasks) {
 __global__ void k_eapply(const EApplyTask* __restrict__ tasks) {
   const EApplyTask T = tasks[blockIdx.y];
   if (T.mode && *T.mode != 0) return;
+  if (T.active && *T.active == 0) return;
   const int m0 = T.m0, np = m0 * m0;
   const int tot = T.nrows * m0 * T.ncol;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
