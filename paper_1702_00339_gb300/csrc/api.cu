@@ -56,7 +56,7 @@ void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
 void launch_gather(const GatherSeg*, int, uint32_t*, cudaStream_t);
 void launch_cell_back(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 __global__ void k_init_x(const InitTask*);
-__global__ void k_gemm_tn(const GemmTask*);
+void launch_gemm_tn(const GemmTask*, int, int, int, int, cudaStream_t);
 __global__ void k_gemm_nn(const GemmTask*);
 __global__ void k_resid(const ResidTask*, double);
 __global__ void k_rr(const RRTask*, int);
@@ -412,13 +412,14 @@ struct Batch {
   int kmax = 0;
   cplx *mvX = nullptr, *mvY1 = nullptr, *mvY2 = nullptr;   // FFT work (shared by all structured)
   std::vector<size_t> mv_off;        // per structured problem: offset (cplx) into mv buffers
-  struct TL { void* d = nullptr; int n = 0; int ga = 1, gb = 1; };
+  struct TL { void* d = nullptr; int n = 0; int ga = 1, gb = 1, tile = 16; };
   // basis layout Y = [X | P | W] (k columns each)
   TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
   TL eHXP, eSXP, eHW, eSW;
   TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
   int band_stage = 0;                // doubles of a band-solve shared-memory stage
+  int gemm_tiles = 0;                // TN tile sizes in use: bit 0 = 16, bit 1 = 20
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
@@ -449,6 +450,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   B.any_mixed = false;
   B.band_stage = 0;
+  B.gemm_tiles = 0;
   B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
@@ -954,6 +956,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
                     double alpha, double beta) {
         GemmTask g; g.active = l.active; g.n = n; g.a = a; g.b = b; g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb;
         g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta; g.sym = 0;
+        g.tile = (k % 20 == 0) ? 20 : 16;   // a property of the problem alone
+        B.gemm_tiles |= (g.tile == 20) ? 2 : 1;
         return g;
       };
       // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C  (same for HW, SW)
@@ -994,10 +998,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(rfXP, B.rfwdXP); TLp(riHXP, B.rinvHXP); TLp(riSXP, B.rinvSXP); TLp(rbHS2, B.rbmulHS2);
     TLp(rehxp, B.reHXP); TLp(resxp, B.reSXP);
     TLp(ini, B.init);
-    TLp(tcx, B.tnCx, (kk + 15) / 16, (kk + 15) / 16); TLp(tcp, B.tnCp, (kk + 15) / 16, (kk + 15) / 16);
+    // TN products: ga, gb carry the largest output dimensions (tiles per launch)
+    TLp(tcx, B.tnCx, kk, kk); TLp(tcp, B.tnCp, kk, kk);
     TLp(nw, B.nnW); TLp(npp, B.nnP);
-    TLp(gg1, B.g1, (kk + 15) / 16, (kk + 15) / 16);
-    TLp(gg3, B.g3, (3 * kk + 15) / 16, (3 * kk + 15) / 16);
+    TLp(gg1, B.g1, kk, kk);
+    TLp(gg3, B.g3, 3 * kk, 3 * kk);
+    B.tnCx.tile = B.tnCp.tile = B.g1.tile = B.g3.tile = B.gemm_tiles;
     TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
     TLp(uu1, B.u1); TLp(uu3, B.u3);
     TLp(c2k, B.cp2k);
@@ -1186,7 +1192,7 @@ void mv_inv(Batch& B, const Batch::TL& t, cudaStream_t st) {
 }
 void gemm_tn(const Batch::TL& t, cudaStream_t st) {
   PROF("k_gemm_tn", 1);
-  if (t.n) k_gemm_tn<<<dim3(t.ga, t.gb, t.n), 256, 0, st>>>(tl<GemmTask>(t));
+  launch_gemm_tn(tl<GemmTask>(t), t.n, t.ga, t.gb, t.tile, st);   // ga, gb: output dims; tile: tile-size bits
 }
 void gemm_nn(const Batch::TL& t, cudaStream_t st) {
   PROF("k_gemm_nn", 1);

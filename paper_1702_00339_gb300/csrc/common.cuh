@@ -228,6 +228,7 @@ struct GemmTask {
   double* C; int ldc;
   double alpha, beta;
   int sym;                     // TN with a symmetric result: upper tiles computed, mirrored
+  int tile;                    // TN output tile: 20 when the problem's block size is a multiple of 20, else 16
 };
 
 struct ResidTask {

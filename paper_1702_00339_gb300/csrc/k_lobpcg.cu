@@ -51,22 +51,27 @@ __global__ void k_init_x(const InitTask* __restrict__ tasks) {
 // tiles above also write their transposes (diagonal tiles are computed in
 // full and not mirrored, so no entry has two writers).
 #define TT 16
-__global__ void k_gemm_tn(const GemmTask* __restrict__ tasks) {
+// C = alpha A^T B + beta C on TILE x TILE output tiles, one thread per
+// output; TILE = 20 when the block sizes are multiples of 20 (less padding
+// than 16 for the 3k x 3k Gram and the k x k projections at k = 20).
+template <int TILE>
+__global__ void __launch_bounds__(TILE * TILE) k_gemm_tn(const GemmTask* __restrict__ tasks) {
   const GemmTask T = tasks[blockIdx.z];
+  if (T.tile != TILE) return;                // the other tile size's launch
   if (T.active && *T.active == 0) return;
-  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+  const int i0 = blockIdx.x * TILE, j0 = blockIdx.y * TILE;
   if (i0 >= T.a || j0 >= T.b) return;
   if (T.sym && j0 < i0) return;
-  __shared__ double As[TT][TT + 1], Bs[TT][TT + 1];
-  const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
+  __shared__ double As[TILE][TILE + 1], Bs[TILE][TILE + 1];
+  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
   double acc = 0.0;
-  for (int n0 = 0; n0 < T.n; n0 += TT) {
+  for (int n0 = 0; n0 < T.n; n0 += TILE) {
     int r = n0 + tx;
     As[ty][tx] = (r < T.n && i0 + ty < T.a) ? T.A[(size_t)r + (size_t)T.lda * (i0 + ty)] : 0.0;
     Bs[ty][tx] = (r < T.n && j0 + ty < T.b) ? T.B[(size_t)r + (size_t)T.ldb * (j0 + ty)] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < TT; ++q) acc += As[tx][q] * Bs[ty][q];
+    for (int q = 0; q < TILE; ++q) acc += As[tx][q] * Bs[ty][q];
     __syncthreads();
   }
   // thread (tx, ty) holds G[i0+tx][j0+ty]
@@ -76,6 +81,15 @@ __global__ void k_gemm_tn(const GemmTask* __restrict__ tasks) {
     *g = v;
     if (T.sym && j0 > i0) T.C[(size_t)(j0 + ty) + (size_t)T.ldc * (i0 + tx)] = v;
   }
+}
+
+// amax, bmax: largest output dimensions; tiles: bit 0 = some task uses 16,
+// bit 1 = some task uses 20 (one launch per tile size, each skipping the
+// other's tasks, so a problem's products never depend on its batch)
+void launch_gemm_tn(const GemmTask* t, int n, int amax, int bmax, int tiles, cudaStream_t st) {
+  if (!n) return;
+  if (tiles & 1) k_gemm_tn<16><<<dim3((amax + 15) / 16, (bmax + 15) / 16, n), 256, 0, st>>>(t);
+  if (tiles & 2) k_gemm_tn<20><<<dim3((amax + 19) / 20, (bmax + 19) / 20, n), 400, 0, st>>>(t);
 }
 
 __global__ void k_gemm_nn(const GemmTask* __restrict__ tasks) {

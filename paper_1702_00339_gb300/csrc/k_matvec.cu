@@ -99,7 +99,7 @@ __global__ void k_fft(const FftTask* __restrict__ tasks) {
       const int jm = j * m;
       for (int q = 0; q < r; ++q) {
         C x = A[(size_t)((kp + m * q) * Ps + j) * CC + cc];
-        if (q) {
+        if (q && j) {   // w^0 = 1 (the whole first stage)
           cplx w64 = Cd.tw[(q * jm) % M];
           C w = mkc<C, R>((R)w64.x, (R)(DIR < 0 ? -w64.y : w64.y));
           x = mulc(w, x);
