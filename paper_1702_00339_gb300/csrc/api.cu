@@ -50,7 +50,7 @@ void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t, bool);
 void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
 int eapply_grid(long long items);
 void launch_band_factor(const BandTask*, int, cudaStream_t);
-void launch_band_solve(const BandTask*, int, int, int, cudaStream_t, bool);
+void launch_band_solve(const BandTask*, int, int, int, int, cudaStream_t, bool);
 int band_stage_doubles(int);
 void launch_cell_canon(const CanonTask*, int, int, int, cudaStream_t);
 void launch_gather(const GatherSeg*, int, uint32_t*, cudaStream_t);
@@ -419,6 +419,7 @@ struct Batch {
   TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
   int band_stage = 0;                // doubles of a band-solve shared-memory stage
+  int band_ringrow = 0;              // largest (D + 1) m0 of the staged band solves
   int gemm_tiles = 0;                // TN tile sizes in use: bit 0 = 16, bit 1 = 20
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
@@ -450,6 +451,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   B.any_mixed = false;
   B.band_stage = 0;
+  B.band_ringrow = 0;
   B.gemm_tiles = 0;
   B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
@@ -925,7 +927,10 @@ void plan(Batch& B, Slab& S, Slab& U) {
         bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
         bt.fp32 = H.mixed;
         bnd.push_back(bt);
-        if (m0 % 2 == 0) B.band_stage = std::max(B.band_stage, (Q.D + 1) * m0 * m0);
+        if (m0 % 2 == 0 && (Q.D + 1) * m0 * m0 <= band_stage_doubles(1 << 30)) {   // stageable
+          B.band_stage = std::max(B.band_stage, (Q.D + 1) * m0 * m0);
+          B.band_ringrow = std::max(B.band_ringrow, (Q.D + 1) * m0);
+        }
       } else {
         fR.push_back(fwd(l.R, k, pcmode));
         iPW.push_back(inv(Y1, Yw, k, pcmode));
@@ -1397,7 +1402,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       CUDA_TRY(ctx, cudaStreamSynchronize(st));   // rf is a host temporary
     }
     // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
-    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, st, B.any_mixed); }
+    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, B.band_ringrow, st, B.any_mixed); }
     if (B.fwdR.n) {
       mv_fwd(B, B.fwdR, st);
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }

@@ -167,44 +167,39 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\
 __device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-constexpr int kBandWarps = 4;   // warps per CTA of the solve
-
 template <typename R>
-__global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* __restrict__ tasks, int ntask,
-                                                               int ngroup, int stage) {
-  // One warp per (problem, group of kBandCols columns); lane l owns the
-  // items l, l + 32, ... of a block row (item = (row mu, column)).  A row's
-  // D-term sum and its diagonal-block product run inside the warp, with no
-  // block barrier, and the warps of a CTA solve independent groups.  When a
-  // block row of the band fits `stage` doubles (and m0 is even, so blocks
-  // start on 16-byte boundaries), the warp copies the next row's blocks into
-  // its shared-memory stage while it computes the current one
-  // (double-buffered cp.async), hiding the latency of the band's loads.
+__global__ void __launch_bounds__(1024) k_band_solve(const BandTask* __restrict__ tasks, int stage, int ringd) {
+  // One CTA per problem, one warp per group of kBandCols columns; lane l of
+  // a warp owns the items l, l + 32, ... of a block row (item = (row mu,
+  // column)).  A row's D-term sum and its diagonal-block product run inside
+  // the warp.  When a block row of the band fits `stage` doubles (and m0 is
+  // even, so blocks start on 16-byte boundaries), the CTA copies the next
+  // row's blocks once into a shared-memory stage, for all its warps, while
+  // they compute the current row (double-buffered cp.async), and each warp
+  // keeps its last D + 1 solution rows in a shared-memory ring.
   extern __shared__ __align__(16) double bst[];
-  __shared__ R tvs[kBandWarps][MAXM0 * kBandCols];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * kBandWarps + warp;
-  if (w >= ntask * ngroup) return;
-  const BandTask& T = tasks[w / ngroup];
+  const BandTask& T = tasks[blockIdx.x];
   if (T.active && *T.active == 0) return;
   if ((T.fp32 != 0) != (sizeof(R) == 4)) return;
-  const int c0 = (w % ngroup) * kBandCols;
-  if (c0 >= T.k) return;
-  const int nc = min(kBandCols, T.k - c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = T.m0, m2 = m0 * m0, D = T.D, L = T.L, ld = T.ld;
+  const int c0 = warp * kBandCols;
+  const int nc = max(0, min(kBandCols, T.k - c0));
   const int items = m0 * nc;
   const double* band = T.band;
   double* W = T.W;
   const double* Rm = T.R;
-  R* tv = tvs[warp];
-  const bool staged = stage > 0 && (m0 % 2 == 0) && (D + 1) * m2 <= stage;
-  double* buf0 = bst + (size_t)warp * 2 * stage;
-  double* buf1 = buf0 + stage;
+  const int rw = m0 * kBandCols;              // one solution row of a warp's group
+  const bool staged = stage > 0 && (m0 % 2 == 0) && (D + 1) * m2 <= stage && (D + 1) * rw <= ringd;
+  double* buf0 = bst;
+  double* buf1 = bst + stage;
+  R* ring = reinterpret_cast<R*>(bst + 2 * (size_t)stage + (size_t)warp * ringd);
+  R* tv = reinterpret_cast<R*>(bst + 2 * (size_t)stage + (size_t)(blockDim.x >> 5) * ringd) + warp * rw;
   const int ch = m2 / 2;   // 16-byte chunks per block
   // forward row J: slot d holds block (J, J - d) (d = 0: L_JJ^-1)
   auto fetch_fwd = [&](int J, double* dst) {
     const int nd = min(D, J) + 1;
-    for (int it = lane; it < nd * ch; it += 32) {
+    for (int it = threadIdx.x; it < nd * ch; it += blockDim.x) {
       const int d = it / ch, cq = it % ch;
       cp_async16(dst + d * m2 + 2 * cq, bblk(const_cast<double*>(band), D, m2, J - d, d) + 2 * cq);
     }
@@ -213,28 +208,34 @@ __global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* 
   auto fetch_bwd = [&](int J, double* dst) {
     const int nd = min(D, L - 1 - J) + 1;
     const double* src = bblk(const_cast<double*>(band), D, m2, J, 0);
-    for (int it = lane; it < nd * ch; it += 32) cp_async16(dst + 2 * it, src + 2 * it);
+    for (int it = threadIdx.x; it < nd * ch; it += blockDim.x) cp_async16(dst + 2 * it, src + 2 * it);
   };
   // forward: y_J = L_JJ^-1 (r_J - sum_d L[J][J-d] y_{J-d})
   if (staged) { fetch_fwd(0, buf0); cp_async_commit(); }
   for (int J = 0; J < L; ++J) {
     const double* cur = nullptr;
     if (staged) {
+      __syncthreads();                         // every warp is done with row J - 1's stage
       if (J + 1 < L) fetch_fwd(J + 1, (J & 1) ? buf0 : buf1);
       cp_async_commit();
       cp_async_wait1();
-      __syncwarp();
+      __syncthreads();                         // row J's stage complete and visible
       cur = (J & 1) ? buf1 : buf0;
     }
     const int dmax = min(D, J);
     for (int i = lane; i < items; i += 32) {
-      const int mu = i % m0, c = c0 + i / m0;
+      const int mu = i % m0, c = c0 + i / m0, cb = (i / m0) * m0;
       const double* Wc = W + (size_t)ld * c;
       R s = (R)Rm[(size_t)ld * c + J * m0 + mu];
       for (int d = 1; d <= dmax; ++d) {
         const double* l = (staged ? cur + d * m2 : bblk(const_cast<double*>(band), D, m2, J - d, d)) + mu * m0;
-        const double* y = Wc + (size_t)((J - d) * m0);
-        for (int q = 0; q < m0; ++q) s -= (R)l[q] * (R)y[q];
+        if (staged) {
+          const R* y = ring + ((J - d) % (D + 1)) * rw + cb;
+          for (int q = 0; q < m0; ++q) s -= (R)l[q] * y[q];
+        } else {
+          const double* y = Wc + (size_t)((J - d) * m0);
+          for (int q = 0; q < m0; ++q) s -= (R)l[q] * (R)y[q];
+        }
       }
       tv[i] = s;
     }
@@ -245,30 +246,37 @@ __global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* 
       R y = 0;
       for (int q = 0; q <= mu; ++q) y += (R)iv[q] * tv[cb + q];
       W[(size_t)ld * c + J * m0 + mu] = (double)y;
+      if (staged) ring[(J % (D + 1)) * rw + cb + mu] = y;
     }
     __syncwarp();
   }
-  if (staged) { cp_async_wait0(); __syncwarp(); }
+  if (staged) { cp_async_wait0(); __syncthreads(); }
   // backward: x_J = L_JJ^-T (y_J - sum_d L[J+d][J]^T x_{J+d})
   if (staged) { fetch_bwd(L - 1, buf0); cp_async_commit(); }
   for (int J = L - 1, step = 0; J >= 0; --J, ++step) {
     const double* cur = nullptr;
     if (staged) {
+      __syncthreads();
       if (J > 0) fetch_bwd(J - 1, (step & 1) ? buf0 : buf1);
       cp_async_commit();
       cp_async_wait1();
-      __syncwarp();
+      __syncthreads();
       cur = (step & 1) ? buf1 : buf0;
     }
     const int dmax = min(D, L - 1 - J);
     for (int i = lane; i < items; i += 32) {
-      const int mu = i % m0, c = c0 + i / m0;
+      const int mu = i % m0, c = c0 + i / m0, cb = (i / m0) * m0;
       const double* Wc = W + (size_t)ld * c;
       R s = (R)Wc[(size_t)(J * m0 + mu)];
       for (int d = 1; d <= dmax; ++d) {
         const double* l = staged ? cur + d * m2 : bblk(const_cast<double*>(band), D, m2, J, d);   // block (J+d, J)
-        const double* x = Wc + (size_t)((J + d) * m0);
-        for (int q = 0; q < m0; ++q) s -= (R)l[q * m0 + mu] * (R)x[q];
+        if (staged) {
+          const R* x = ring + ((J + d) % (D + 1)) * rw + cb;
+          for (int q = 0; q < m0; ++q) s -= (R)l[q * m0 + mu] * x[q];
+        } else {
+          const double* x = Wc + (size_t)((J + d) * m0);
+          for (int q = 0; q < m0; ++q) s -= (R)l[q * m0 + mu] * (R)x[q];
+        }
       }
       tv[i] = s;
     }
@@ -279,6 +287,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* 
       R x = 0;
       for (int q = mu; q < m0; ++q) x += (R)iv[q * m0 + mu] * tv[cb + q];
       W[(size_t)ld * c + J * m0 + mu] = (double)x;
+      if (staged) ring[(J % (D + 1)) * rw + cb + mu] = x;
     }
     __syncwarp();
   }
@@ -288,17 +297,21 @@ __global__ void __launch_bounds__(kBandWarps * 32) k_band_solve(const BandTask* 
 void launch_band_factor(const BandTask* t, int n, cudaStream_t st) {
   if (n) k_band_factor<<<n, 256, 0, st>>>(t);
 }
-// stage: doubles of one shared-memory stage per warp (0: loads from global)
-void launch_band_solve(const BandTask* t, int n, int kmax, int stage, cudaStream_t st, bool mixed) {
+// stage: doubles of the CTA's shared-memory stage (0: loads from global);
+// ringrow: the largest (D + 1) m0 among the staged tasks (solution rings).
+// One CTA per problem, one warp per kBandCols columns.
+void launch_band_solve(const BandTask* t, int n, int kmax, int stage, int ringrow, cudaStream_t st, bool mixed) {
   if (!n) return;
-  const int ng = (kmax + kBandCols - 1) / kBandCols;
-  const int nb = (n * ng + kBandWarps - 1) / kBandWarps;
-  const size_t sm = (size_t)kBandWarps * 2 * stage * sizeof(double);
+  const int nwarp = (kmax + kBandCols - 1) / kBandCols;
+  const int ringd = stage > 0 ? ((ringrow * kBandCols + 1) & ~1) : 0;   // doubles, even (16-byte stages)
+  // stages, rings, and the per-warp row buffers (one row of a warp's group)
+  const size_t sm = ((size_t)2 * stage + (size_t)nwarp * ringd) * sizeof(double) +
+                    (size_t)nwarp * MAXM0 * kBandCols * sizeof(double);
   // (the 48 KB default covers static plus dynamic shared memory: always opt in)
   FOCK_SMEM_OPTIN(k_band_solve<double>);
   FOCK_SMEM_OPTIN(k_band_solve<float>);
-  k_band_solve<double><<<nb, kBandWarps * 32, sm, st>>>(t, n, ng, stage);
-  if (mixed) k_band_solve<float><<<nb, kBandWarps * 32, sm, st>>>(t, n, ng, stage);
+  k_band_solve<double><<<n, nwarp * 32, sm, st>>>(t, stage, ringd);
+  if (mixed) k_band_solve<float><<<n, nwarp * 32, sm, st>>>(t, stage, ringd);
 }
 
 // doubles of one band-solve stage for the largest block row among the tasks
