@@ -722,15 +722,21 @@ void plan(Batch& B, Slab& S, Slab& U) {
         // same rank among that position's entries (a position can hold a
         // wall block and a defect block)
         std::vector<int> part(std::max(Q.nE, 1), -1);
-        for (int e = 0; e < Q.nE; ++e) {
-          if (Q.Ek[e] == Q.Em[e]) { part[e] = e; continue; }
-          int rank = 0;
-          for (int f = 0; f < e; ++f) rank += (Q.Ek[f] == Q.Ek[e] && Q.Em[f] == Q.Em[e]);
-          for (int f = 0, seen = 0; f < Q.nE; ++f)
-            if (Q.Ek[f] == Q.Em[e] && Q.Em[f] == Q.Ek[e] && seen++ == rank) {
-              if (Q.Ekind[f] == Q.Ekind[e]) part[e] = f;
-              break;
-            }
+        {
+          // entries are grouped by (row cell, column cell): index the groups
+          std::vector<std::pair<long long, int>> key(Q.nE);
+          for (int e = 0; e < Q.nE; ++e) key[e] = {(long long)Q.Ek[e] * (Q.Lc + 1) + Q.Em[e], e};
+          std::sort(key.begin(), key.end());
+          std::vector<int> rank(std::max(Q.nE, 1), 0);
+          for (int a = 1; a < Q.nE; ++a)
+            if (key[a].first == key[a - 1].first) rank[key[a].second] = rank[key[a - 1].second] + 1;
+          for (int e = 0; e < Q.nE; ++e) {
+            if (Q.Ek[e] == Q.Em[e]) { part[e] = e; continue; }
+            const long long want = (long long)Q.Em[e] * (Q.Lc + 1) + Q.Ek[e];
+            auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(want, -1));
+            it += rank[e];
+            if (it < key.end() && it->first == want && Q.Ekind[it->second] == Q.Ekind[e]) part[e] = it->second;
+          }
         }
         for (int e = 0; e < Q.nE; ++e)   // pairs must be mutual
           if (part[e] >= 0 && part[part[e]] != e) part[e] = -1;
