@@ -555,6 +555,10 @@ void plan(Batch& B, Slab& S, Slab& U) {
         for (int k = 0; k < L; ++k)
           for (int m = std::max(0, k - D); m <= std::min(L - 1, k + D); ++m)
             if (aff[k] && aff[m]) {
+              if (k > m) {   // E(k, m) = E(m, k)^T: written by the combine task of (m, k)
+                Q.Ek.push_back(k); Q.Em.push_back(m); Q.Ekind.push_back(3); Q.Esrc.push_back(-1);
+                continue;
+              }
               int lo = std::max(A.jlo + k * n0, A.jlo + m * n0) - 1;
               int hi = std::min(A.jlo + A.W + k * n0, A.jlo + A.W + m * n0) + 1;
               lo = std::max(lo, -A.pad); hi = std::min(hi, N - A.pad);
@@ -735,7 +739,10 @@ void plan(Batch& B, Slab& S, Slab& U) {
             const long long want = (long long)Q.Em[e] * (Q.Lc + 1) + Q.Ek[e];
             auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(want, -1));
             it += rank[e];
-            if (it < key.end() && it->first == want && Q.Ekind[it->second] == Q.Ekind[e]) part[e] = it->second;
+            // kinds must match (a wall block and its mirror entry, kind 3, count as one kind)
+            auto base = [](int kd) { return kd == 3 ? 0 : kd; };
+            if (it < key.end() && it->first == want && base(Q.Ekind[it->second]) == base(Q.Ekind[e]))
+              part[e] = it->second;
           }
         }
         for (int e = 0; e < Q.nE; ++e)   // pairs must be mutual
@@ -744,8 +751,14 @@ void plan(Batch& B, Slab& S, Slab& U) {
         B.canon.push_back(ct);
         B.maxcblk = std::max(B.maxcblk, 2 * (Q.D + 1) + 2 * Q.nE);
       }
+      // mirror entries (kind 3) of the wall blocks, by position
+      std::vector<std::pair<long long, int>> mirror;
+      for (int e = 0; e < Q.nE; ++e)
+        if (Q.Ekind[e] == 3) mirror.push_back({(long long)Q.Ek[e] * (Q.Lc + 1) + Q.Em[e], e});
+      std::sort(mirror.begin(), mirror.end());
       for (int e = 0; e < Q.nE; ++e) {
         int k = Q.Ek[e], m = Q.Em[e], d = std::abs(k - m);
+        if (Q.Ekind[e] == 3) continue;   // written transposed by the (m, k) wall block's combine task
         if (Q.Ekind[e] == 2) {   // defect block: written by k_defect_blocks
           B.dblocks[Q.Esrc[e]].outH = Q.EH + (size_t)e * m2;
           B.dblocks[Q.Esrc[e]].outS = Q.ES + (size_t)e * m2;
@@ -757,6 +770,14 @@ void plan(Batch& B, Slab& S, Slab& U) {
         if (Q.Ekind[e] == 0) {   // wall block: the block minus its Toeplitz generator
           c.X0 = B.gram[Q.Esrc[e]].X;
           c.subH = Q.TH + (size_t)d * m2; c.subS = Q.TS + (size_t)d * m2; c.subT = (k < m);
+          if (k < m) {
+            auto it = std::lower_bound(mirror.begin(), mirror.end(),
+                                       std::make_pair((long long)m * (Q.Lc + 1) + k, -1));
+            if (it != mirror.end() && it->first == (long long)m * (Q.Lc + 1) + k) {
+              c.outHT = Q.EH + (size_t)it->second * m2;
+              c.outST = Q.ES + (size_t)it->second * m2;
+            }
+          }
         } else {                 // wrap-around block of a periodic chain: A_{(k-m) mod L}
           c.X0 = Q.ringX[Q.Esrc[e]];
         }

@@ -149,6 +149,7 @@ struct CombineTask {
   const double* D0; const double* D1; const double* D2;    // defect forms [R][m0*m0] or null
   double dZ;
   double* outH; double* outS;
+  double* outHT; double* outST;        // optional: the transposed block as well (mirror entry)
 };
 
 struct DftTask {

@@ -294,6 +294,11 @@ __global__ void k_combine(const ProbDev* __restrict__ probs, const CombineTask* 
     }
     if (C.outH) C.outH[pr] = h;
     if (C.outS) C.outS[pr] = s;
+    if (C.outHT) {
+      const int tr = (pr % m0) * m0 + pr / m0;
+      C.outHT[tr] = h;
+      C.outST[tr] = s;
+    }
   }
 }
 
