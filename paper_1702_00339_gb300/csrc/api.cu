@@ -1353,7 +1353,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   // of the pencil (it scales with kappa(S), up to ~1e8 after the cell
   // reduction); Rayleigh quotients are then accurate to about the square of
   // the residual over the gap, so the problem is done, provided the current
-  // residual is still within a factor 10 of that floor (a state that broke
+  // residual is still within a factor 100 of that floor (a state that broke
   // down after reaching it keeps iterating, or ends unconverged)
   const double kFloorTol = 1e-6;
   const int kStagnation = 8;
@@ -1392,7 +1392,12 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
       if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
       else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
-      else if (mx <= 10.0 * best[s2] &&
+      else if (it == 0 && B.lob[s2].k == B.lob[s2].n) {
+        // whole-space block: the start's Rayleigh-Ritz step over all n directions
+        // is exact up to rounding, and [X | P | W] would add only noise directions
+        active[s2] = 0; conv[s2] = 1; changed = true;
+      }
+      else if (mx <= 100.0 * best[s2] &&
                ((best[s2] <= kNearFactor * tol && it - best_it[s2] >= kStagnationNear) ||
                 (best[s2] <= kFloorTol && it - best_it[s2] >= kStagnation))) {
         active[s2] = 0; conv[s2] = 1; changed = true;

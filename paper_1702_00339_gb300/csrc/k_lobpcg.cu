@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(256) k_rr(const RRTask* __restrict__ tasks, in
 }
 
 // One CTA per (column, task): scale dst's column to unit 2-norm (zero
-// columns stay zero).
+// columns stay zero, non-finite ones become zero).
 __global__ void k_colnorm(const CopyTask* __restrict__ tasks) {
   const CopyTask T = tasks[blockIdx.y];
   if (T.active && *T.active == 0) return;
@@ -788,7 +788,11 @@ __global__ void k_colnorm(const CopyTask* __restrict__ tasks) {
   }
   __syncthreads();
   const double nrm = sqrt(red[0]);
-  if (!(nrm > 0.0) || !isfinite(nrm)) return;
+  if (!isfinite(nrm)) {   // a non-finite search direction: zeroed, so the Rayleigh-Ritz step drops it
+    for (int i = threadIdx.x; i < T.n; i += blockDim.x) col[i] = 0.0;
+    return;
+  }
+  if (!(nrm > 0.0)) return;
   const double inv = 1.0 / nrm;
   for (int i = threadIdx.x; i < T.n; i += blockDim.x) col[i] *= inv;
 }
