@@ -99,3 +99,20 @@ def test_structured_matvec_with_defects(ctx, name):
             y = b.matvec(x, which)
             assert np.max(np.abs(y - M @ x)) <= 1e-12 * np.max(np.abs(M)) * np.max(np.abs(x)) * p.m0 * 4
     b.close()
+
+
+def test_whole_space_defect_chains_of_the_serving_mix(ctx):
+    """Periodic defect chains small enough for the whole-space block (3 N_b
+    <= 255): the start's Rayleigh-Ritz step over all directions is exact, and
+    the solve ends there (iterating on such a block once broke these two
+    requests of the serving mix down).  Against the oracle's dense solve."""
+    ps = [li.serving_stream(128, seed=3100)[102], li.serving_stream(512, seed=3000)[262]]
+    for p in ps:
+        assert 3 * p.Nb <= 255 and p.defects
+        q = _cases.with_table(p)
+        q.k_eig = p.k_eig
+        H, S = dense.build(q)
+        ref, tol, _ = _cases.reference(q, H, S)
+        out = ctx.solve([p])[0]
+        assert out["status"] == 0 and out["iters"] == 0
+        assert np.max(np.abs(out["evals"] - ref)) <= tol
