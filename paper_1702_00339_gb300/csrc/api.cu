@@ -992,12 +992,14 @@ void plan(Batch& B, Slab& S, Slab& U) {
         B.gemm_tiles |= (g.tile == 20) ? 2 : 1;
         return g;
       };
-      // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C  (same for HW, SW)
+      // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C.  W is projected
+      // before its images are formed (fresh images of the projected vectors); P
+      // after its fresh images, which are then updated by linearity (HP, SP)
       tcx.push_back(gt(k, k, l.SY, n, Yw, n, l.Cx, k, 1.0, 0.0));
       tcp.push_back(gt(k, k, l.SY, n, l.Y + nk, n, l.Cx, k, 1.0, 0.0));
+      nw.push_back(gt(k, k, l.Y, n, l.Cx, k, l.Y + 2 * nk, n, -1.0, 1.0));
       for (int w = 0; w < 3; ++w) {
         double* base = w == 0 ? l.Y : (w == 1 ? l.HY : l.SY);
-        nw.push_back(gt(k, k, base, n, l.Cx, k, base + 2 * nk, n, -1.0, 1.0));
         npp.push_back(gt(k, k, base, n, l.Cx, k, base + nk, n, -1.0, 1.0));
       }
       // Gram matrices Y^T H Y, Y^T S Y: symmetric, upper tiles only
@@ -1358,7 +1360,8 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   const double kFloorTol = 1e-6;
   const int kStagnation = 8;
   // a floor within 100 tol of the target is recognised after 3 iterations
-  // (Rayleigh quotients are then exact to ~(100 tol)^2 / gap)
+  // without a halving of the residual (Rayleigh quotients are then exact to
+  // ~(100 tol)^2 / gap)
   const double kNearFactor = 100.0;
   const int kStagnationNear = 3;
   std::vector<double> best(ns, INFINITY);
@@ -1389,7 +1392,9 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
         any = true;
         continue;
       }
-      if (!bad && mx < best[s2]) { best[s2] = mx; best_it[s2] = it; }
+      // the floor clock restarts only on a halving of the residual (fluctuations
+      // at the floor within a factor 2 do not count as progress)
+      if (!bad && mx < 0.5 * best[s2]) { best[s2] = mx; best_it[s2] = it; }
       if (bad) { active[s2] = 0; changed = true; }            // broken: stop, report no convergence
       else if (mx <= tol) { active[s2] = 0; conv[s2] = 1; changed = true; }
       else if (it == 0 && B.lob[s2].k == B.lob[s2].n) {
@@ -1440,10 +1445,10 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
       mv_inv(B, B.invPW, st);
     }
-    normalize(B.normW, B.kmax, st);
-    mv_HS(B, false, st);
     gemm_tn(B.tnCx, st);
     gemm_nn(B.nnW, st);
+    normalize(B.normW, B.kmax, st);
+    mv_HS(B, false, st);
     // Rayleigh-Ritz on [X | P | W]
     gemm_tn(B.g3, st);
     rr(B.rr3, st);
