@@ -92,17 +92,30 @@ void launch_gemm_tn(const GemmTask* t, int n, int amax, int bmax, int tiles, cud
   if (tiles & 2) k_gemm_tn<20><<<dim3((amax + 19) / 20, (bmax + 19) / 20, n), 400, 0, st>>>(t);
 }
 
+// C = alpha A B + beta C; a thread owns row i of four consecutive columns,
+// so each load of A serves four FP64 FMAs.
 __global__ void k_gemm_nn(const GemmTask* __restrict__ tasks) {
   const GemmTask T = tasks[blockIdx.y];
   if (T.active && *T.active == 0) return;
-  const int tot = T.n * T.b;
+  const int nb4 = (T.b + 3) >> 2;
+  const int tot = T.n * nb4;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
-    int i = it % T.n, j = it / T.n;
-    double acc = 0.0;
-    const double* bj = T.B + (size_t)T.ldb * j;
-    for (int q = 0; q < T.a; ++q) acc += T.A[(size_t)i + (size_t)T.lda * q] * bj[q];
-    double* c = T.C + (size_t)i + (size_t)T.ldc * j;
-    *c = (T.beta == 0.0) ? T.alpha * acc : T.beta * *c + T.alpha * acc;
+    const int i = it % T.n, j0 = (it / T.n) * 4;
+    const int nj = min(4, T.b - j0);
+    const double* b0 = T.B + (size_t)T.ldb * j0;
+    const double* b1 = b0 + (nj > 1 ? T.ldb : 0);
+    const double* b2 = b0 + (nj > 2 ? 2 * (size_t)T.ldb : 0);
+    const double* b3 = b0 + (nj > 3 ? 3 * (size_t)T.ldb : 0);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int q = 0; q < T.a; ++q) {
+      const double x = T.A[(size_t)i + (size_t)T.lda * q];
+      a0 = fma(x, b0[q], a0); a1 = fma(x, b1[q], a1); a2 = fma(x, b2[q], a2); a3 = fma(x, b3[q], a3);
+    }
+    const double acc[4] = {a0, a1, a2, a3};
+    for (int c = 0; c < nj; ++c) {
+      double* cp = T.C + (size_t)i + (size_t)T.ldc * (j0 + c);
+      *cp = (T.beta == 0.0) ? T.alpha * acc[c] : T.beta * *cp + T.alpha * acc[c];
+    }
   }
 }
 
