@@ -415,8 +415,8 @@ struct Batch {
   struct TL { void* d = nullptr; int n = 0; int ga = 1, gb = 1, tile = 16; };
   // basis layout Y = [X | P | W] (k columns each)
   TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
-  TL eHXP, eSXP, eHW, eSW;
-  TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP, reSXP;   // image refresh at the FP32 -> FP64 switch
+  TL eHXP, eHW;                      // boundary blocks (H and S in one task)
+  TL rfwdXP, rinvHXP, rinvSXP, rbmulHS2, reHXP;   // image refresh at the FP32 -> FP64 switch
   TL bandF, bandS;
   int band_stage = 0;                // doubles of a band-solve shared-memory stage
   int band_ringrow = 0;              // largest (D + 1) m0 of the staged band solves
@@ -897,7 +897,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     int maxcols = 1;
     std::vector<FftTask> fXP, fW, fR, iHXP, iSXP, iHW, iSW, iPW;
     std::vector<BmulTask> bHS2, bHS1, bK;
-    std::vector<EApplyTask> ehxp, esxp, ehw, esw, rehxp, resxp;
+    std::vector<EApplyTask> ehxp, ehw, rehxp;
     std::vector<FftTask> rfXP, riHXP, riSXP;
     std::vector<BmulTask> rbHS2;
     std::vector<InitTask> ini;
@@ -971,8 +971,10 @@ void plan(Batch& B, Slab& S, Slab& U) {
         return t;
       };
       if (Q.nE) {
-        ehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k, nullptr)); esxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k, nullptr));
-        ehw.push_back(ea(Q.EHc, Yw, l.HY + 2 * nk, k, nullptr)); esw.push_back(ea(Q.ESc, Yw, l.SY + 2 * nk, k, nullptr));
+        // H and S boundary blocks applied to the same columns in one task
+        auto hs = [](EApplyTask t, const double* v2, double* y2) { t.vals2 = v2; t.y2 = y2; return t; };
+        ehxp.push_back(hs(ea(Q.EHc, Yx, l.HY, 2 * k, nullptr), Q.ESc, l.SY));
+        ehw.push_back(hs(ea(Q.EHc, Yw, l.HY + 2 * nk, k, nullptr), Q.ESc, l.SY + 2 * nk));
       }
       // image refresh of [X | P] for the problems whose matvecs just switched to
       // FP64 (flag 0 = refresh, 2 = leave: matches neither precision variant)
@@ -981,7 +983,11 @@ void plan(Batch& B, Slab& S, Slab& U) {
         rfXP.push_back(fwd(Yx, 2 * k, rf));
         riHXP.push_back(inv(Y1, l.HY, 2 * k, rf)); riSXP.push_back(inv(Y2, l.SY, 2 * k, rf));
         rbHS2.push_back({i, Q.M, m0, 2 * k, Q.CH, Q.CS, X, Y1, Y2, rf, l.active});
-        if (Q.nE) { rehxp.push_back(ea(Q.EHc, Yx, l.HY, 2 * k, rf)); resxp.push_back(ea(Q.ESc, Yx, l.SY, 2 * k, rf)); }
+        if (Q.nE) {
+          EApplyTask t2 = ea(Q.EHc, Yx, l.HY, 2 * k, rf);
+          t2.vals2 = Q.ESc; t2.y2 = l.SY;
+          rehxp.push_back(t2);
+        }
       }
       ini.push_back({n, k, n, problem_seed(H), l.Y});   // start depends on the problem only
       auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
@@ -1028,9 +1034,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(fXP, B.fwdXP); TLp(fW, B.fwdW); TLp(fR, B.fwdR);
     TLp(iHXP, B.invHXP); TLp(iSXP, B.invSXP); TLp(iHW, B.invHW); TLp(iSW, B.invSW); TLp(iPW, B.invPW);
     TLp(bHS2, B.bmulHS2); TLp(bHS1, B.bmulHS1); TLp(bK, B.bmulK);
-    TLp(ehxp, B.eHXP); TLp(esxp, B.eSXP); TLp(ehw, B.eHW); TLp(esw, B.eSW);
+    TLp(ehxp, B.eHXP); TLp(ehw, B.eHW);
     TLp(rfXP, B.rfwdXP); TLp(riHXP, B.rinvHXP); TLp(riSXP, B.rinvSXP); TLp(rbHS2, B.rbmulHS2);
-    TLp(rehxp, B.reHXP); TLp(resxp, B.reSXP);
+    TLp(rehxp, B.reHXP);
     TLp(ini, B.init);
     // TN products: ga, gb carry the largest output dimensions (tiles per launch)
     TLp(tcx, B.tnCx, kk, kk); TLp(tcp, B.tnCp, kk, kk);
@@ -1260,11 +1266,8 @@ void mv_HS(Batch& B, bool xp, cudaStream_t st) {
   { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(bm), bm.n, B.maxM, B.maxm0, st, B.any_mixed); }
   mv_inv(B, xp ? B.invHXP : B.invHW, st);
   mv_inv(B, xp ? B.invSXP : B.invSW, st);
-  const Batch::TL& eh = xp ? B.eHXP : B.eHW;
-  const Batch::TL& es = xp ? B.eSXP : B.eSW;
-  if (eh.n) { PROF("k_eapply", 2);
-    launch_eapply(tl<EApplyTask>(eh), eh.n, B.eapply_gx, st);
-    launch_eapply(tl<EApplyTask>(es), es.n, B.eapply_gx, st); }
+  const Batch::TL& eh = xp ? B.eHXP : B.eHW;   // each task applies the H and the S blocks
+  if (eh.n) { PROF("k_eapply", 1); launch_eapply(tl<EApplyTask>(eh), eh.n, B.eapply_gx, st); }
 }
 
 // [X | P] images in FP64 for the problems flagged in d_refresh only
@@ -1273,9 +1276,7 @@ void refresh_XP(Batch& B, cudaStream_t st) {
   { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.rbmulHS2), B.rbmulHS2.n, B.maxM, B.maxm0, st, false); }
   mv_inv(B, B.rinvHXP, st);
   mv_inv(B, B.rinvSXP, st);
-  if (B.reHXP.n) { PROF("k_eapply", 2);
-    launch_eapply(tl<EApplyTask>(B.reHXP), B.reHXP.n, B.eapply_gx, st);
-    launch_eapply(tl<EApplyTask>(B.reSXP), B.reSXP.n, B.eapply_gx, st); }
+  if (B.reHXP.n) { PROF("k_eapply", 1); launch_eapply(tl<EApplyTask>(B.reHXP), B.reHXP.n, B.eapply_gx, st); }
 }
 
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,

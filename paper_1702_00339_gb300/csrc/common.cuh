@@ -217,6 +217,8 @@ struct EApplyTask {
   double* y; int ldy;
   const int* mode;      // null: always; else only while *mode == 0 (image refresh lists)
   const int* active;    // as FftTask::active
+  const double* vals2;  // optional second operator on the same x (S beside H), into y2 (ldy)
+  double* y2;
 };
 
 struct InitTask { int n, k, ld; uint64_t seed; double* X; };

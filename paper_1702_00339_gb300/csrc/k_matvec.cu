@@ -224,13 +224,19 @@ __global__ void k_eapply(const EApplyTask* __restrict__ tasks) {
     int mu = it % m0, rest = it / m0;
     int ri = rest % T.nrows, v = rest / T.nrows;
     int row = T.rows[ri];
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     for (int e = T.rowptr[ri]; e < T.rowptr[ri + 1]; ++e) {
       const double* Eb = T.vals + (size_t)e * np + mu * m0;
       const double* xv = T.x + (size_t)T.cols[e] * m0 + (size_t)T.ldx * v;
-      for (int nu = 0; nu < m0; ++nu) acc += Eb[nu] * xv[nu];
+      if (T.vals2) {   // H and S blocks on the same x: one pass over x
+        const double* Eb2 = T.vals2 + (size_t)e * np + mu * m0;
+        for (int nu = 0; nu < m0; ++nu) { acc += Eb[nu] * xv[nu]; acc2 += Eb2[nu] * xv[nu]; }
+      } else {
+        for (int nu = 0; nu < m0; ++nu) acc += Eb[nu] * xv[nu];
+      }
     }
     T.y[(size_t)row * m0 + mu + (size_t)T.ldy * v] += acc;
+    if (T.vals2) T.y2[(size_t)row * m0 + mu + (size_t)T.ldy * v] += acc2;
   }
 }
 
