@@ -35,12 +35,12 @@ class c_defect(C.Structure):
 
 class c_problem(C.Structure):
     _fields_ = [("L", C.c_int * 3), ("periodic", C.c_int * 3), ("N", C.c_int * 3), ("n0", C.c_int),
-                ("b0", C.c_double), ("M0", C.c_int), ("Z", C.POINTER(C.c_double)),
-                ("frac", C.POINTER(C.c_double)), ("m0", C.c_int), ("exps", C.POINTER(C.c_double)),
-                ("ang", C.POINTER(C.c_int)), ("centre", C.POINTER(C.c_int)), ("R", C.c_int),
-                ("sinc_t", C.POINTER(C.c_double)), ("sinc_c", C.POINTER(C.c_double)),
+                ("b0", C.c_double), ("M0", C.c_int), ("Z", C.c_void_p),          # const double*
+                ("frac", C.c_void_p), ("m0", C.c_int), ("exps", C.c_void_p),        # const double*
+                ("ang", C.c_void_p), ("centre", C.c_void_p), ("R", C.c_int),        # const int*
+                ("sinc_t", C.c_void_p), ("sinc_c", C.c_void_p),                     # const double*
                 ("eps_support", C.c_double), ("ndef", C.c_int),
-                ("defects", C.POINTER(c_defect)), ("k_eig", C.c_int), ("precision", C.c_int)]
+                ("defects", C.c_void_p), ("k_eig", C.c_int), ("precision", C.c_int)]   # const fock_defect*
 
 
 class c_serve_config(C.Structure):
@@ -134,33 +134,39 @@ def _ip(a):
 
 
 class _Marshal:
-    """Keeps the numpy arrays behind one c_problem alive."""
+    """Keeps the arrays behind one c_problem alive.  The double parameters
+    (Z, frac, exps, sinc nodes and weights) share one contiguous array and the
+    int ones (ang, centre) another; the struct holds their addresses."""
 
     def __init__(self, p):
-        self.keep = []
-
-        def arr(x, dt):
-            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
-            self.keep.append(a)
-            return a
-
+        M0, m0 = len(p.Z), len(p.exps)
+        table = p.sinc_t is not None
+        parts = [np.asarray(p.Z, np.float64).ravel(), np.asarray(p.frac, np.float64).ravel(),
+                 np.asarray(p.exps, np.float64).ravel()]
+        if table:
+            parts += [np.asarray(p.sinc_t, np.float64).ravel(), np.asarray(p.sinc_c, np.float64).ravel()]
+        dv = np.concatenate(parts)
+        iv = np.concatenate([np.asarray(p.ang, np.int32).ravel(), np.asarray(p.centre, np.int32).ravel()])
+        self.keep = [dv, iv]
+        bd, bi = dv.ctypes.data, iv.ctypes.data
+        off = np.cumsum([0] + [a.size for a in parts]) * 8   # byte offsets of the parts in dv
         s = c_problem()
         s.L[:] = [int(v) for v in p.L]
         s.periodic[:] = [int(v) for v in p.periodic]
         s.N[:] = [int(v) for v in p.N]
         s.n0 = int(p.n0)
         s.b0 = float(p.b0)
-        s.M0 = int(len(p.Z))
-        s.Z = _dp(arr(p.Z, np.float64))
-        s.frac = _dp(arr(np.asarray(p.frac, float).reshape(-1), np.float64))
-        s.m0 = int(len(p.exps))
-        s.exps = _dp(arr(p.exps, np.float64))
-        s.ang = _ip(arr(p.ang, np.int32))
-        s.centre = _ip(arr(p.centre, np.int32))
+        s.M0 = M0
+        s.Z = bd + int(off[0])
+        s.frac = bd + int(off[1])
+        s.m0 = m0
+        s.exps = bd + int(off[2])
+        s.ang = bi
+        s.centre = bi + 4 * len(p.ang)
         s.R = int(p.R)
-        if p.sinc_t is not None:
-            s.sinc_t = _dp(arr(p.sinc_t, np.float64))
-            s.sinc_c = _dp(arr(p.sinc_c, np.float64))
+        if table:
+            s.sinc_t = bd + int(off[3])
+            s.sinc_c = bd + int(off[4])
         s.eps_support = float(p.eps_support)
         s.ndef = len(p.defects)
         if p.defects:
@@ -170,7 +176,7 @@ class _Marshal:
                 d[i].nucleus = int(x.nucleus)
                 d[i].newZ = float(x.newZ)
             self.keep.append(d)
-            s.defects = C.cast(d, C.POINTER(c_defect))
+            s.defects = C.addressof(d)
         s.k_eig = int(p.k_eig)
         s.precision = int(getattr(p, "precision", 0))
         self.s = s
