@@ -5,12 +5,18 @@
 // embedding (a Fourier-block solve).  All dense work is FP64.
 //
 //  k_init_x     deterministic pseudo-random start X (splitmix64 counter hash), P = W = 0
-//  k_gemm_tn    G = A^T B            (Gram blocks of the Rayleigh-Ritz step)
+//  k_gemm_tn    G = A^T B            (Gram blocks of the Rayleigh-Ritz step; 16- or 20-wide tiles)
 //  k_gemm_nn    C = beta C + alpha A B
-//  k_resid      R = HX - SX diag(lambda), relative residual norms
-//  k_rr         Rayleigh-Ritz: diagonal scaling, Cholesky of Y^T S Y,
-//               C = L^-1 (Y^T H Y) L^-T, parallel cyclic Jacobi, lowest k
+//  k_resid      R = HX - SX diag(lambda), relative residual norms, soft locking
+//  k_rr         Rayleigh-Ritz: diagonal scaling, pivoted LDL^T of Y^T S Y (rank-revealing),
+//               C = Delta^-1/2 L^-1 (Y^T H Y) L^-T Delta^-1/2, Householder tridiagonal,
+//               FP32 multisection shifts, FP64 inverse iteration, Cholesky-QR twice and a
+//               Rayleigh-Ritz step in their span, back-transformation; lowest k
+//  k_colnorm    unit 2-norm columns (non-finite ones zeroed)
 //  k_copy_cols  column-block copies
+//  k_gather     results of a batch into one staging buffer
+//  k_cell_canon / k_cell_transform / k_cell_back
+//               canonical cell basis and the exactly symmetric transformed operator
 #include <float.h>
 #include "common.cuh"
 
