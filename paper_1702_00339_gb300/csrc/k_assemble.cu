@@ -1,7 +1,10 @@
 // Stage (a): separable rank-R assembly (Lemma 2.1, Prop. 2.2, Lemma 3.4).
 //
 //  k_gref     nodal 1D GTO factors of the reference cell      (Sec. 2.4)
-//  k_ptab     window-summed P0 Gaussian integrals per axis    (Eq. 2.13, Eq. 3.6)
+//  k_ptab_nodes / k_ptab
+//             window-summed P0 Gaussian integrals per axis    (Eq. 2.13, Eq. 3.6);
+//             k_ptab_nodes evaluates erfc once per cell endpoint (shared
+//             memory), k_ptab (windows too wide for shared memory) per cell
 //  k_deftab   one nucleus' P0 Gaussian integrals per axis     (defects)
 //  k_gram_fold / k_gram_pot
 //             1D Galerkin forms  X_f[mu][nu] = <g_{a,mu}, W_f g_{b,nu}>  with
@@ -11,7 +14,8 @@
 //             per-residue pair products Z[r][mu nu] and then contracts with
 //             the n0-long potential rows: X_t = P_t . Z.
 //  k_combine  Hadamard combine over the axes into m0 x m0 blocks
-//             H = A/2 - V, S (Lemma 3.4, Eqs. 2.16-2.17).
+//             H = A/2 - V, S (Lemma 3.4, Eqs. 2.16-2.17); a wall block also
+//             writes its transpose into the mirror entry (E(m,k) = E(k,m)^T).
 //  k_axis_dft sparse DFT of the per-axis factors over the lattice offset
 //             (Thm. 3.3: only 1D transforms of the factors are needed).
 #include "common.cuh"

@@ -13,9 +13,10 @@
 //                 sigma and start again (at most 4 attempts)
 //                 (the diagonal slots then hold L_JJ^-1, which the solve
 //                 applies as a mat-vec)
-//  k_band_solve   forward and back substitution for the k columns of R;
-//                 the columns of a problem are spread over several CTAs
-//                 (they are independent), the D-term sums over threads
+//  k_band_solve   forward and back substitution for the k columns of R:
+//                 one CTA per problem, one warp per group of 4 columns; the
+//                 next block row staged once per CTA in shared memory
+//                 (double-buffered cp.async), solution rows in per-warp rings
 #include "common.cuh"
 
 namespace fock {

@@ -15,8 +15,11 @@
 //       eigendecomposition Sbar = Q diag(s) Q^H, X = Q_K diag(s_K)^-1/2 over
 //       the kept directions K = {s > kCanonTau max s}, C = X^H Hbar X --
 //       then Householder reduction of C to a real tridiagonal and
-//       Sturm-sequence bisection per eigenvalue (ascending, so the block
-//       spectrum comes out sorted); the removed directions report +inf.
+//       Sturm-sequence bisection per eigenvalue, FP32 first then FP64 with
+//       division-free counts (ascending, so the block spectrum comes out
+//       sorted); the removed directions report +inf.  The lowest eigenvalue
+//       of an embedding block (preconditioner shift only) stops at 1e-9
+//       relative.  One warp per block for m0 <= 8.
 //  k_sigma      shift of the preconditioner: min_j lambda_min(Chat_j) - delta.
 //  k_precond    K_j = (Chat_H,j - sigma Chat_S,j)^-1 per Fourier index.
 //  k_sort_*     ascending sort of (eigenvalue, Fourier index) pairs.
