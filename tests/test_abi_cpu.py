@@ -78,3 +78,41 @@ def test_serve_start_without_a_device_fails_cleanly(libpath):
     h = C.c_void_p()
     rc = fock.lib().fock_serve_start(0, None, C.byref(h))
     assert rc == fock.FOCK_ECUDA and not h.value
+
+
+def _read(addr, n, ctype):
+    import ctypes as C
+    if not addr:
+        return None
+    return np.ctypeslib.as_array(C.cast(C.c_void_p(addr), C.POINTER(ctype)), shape=(n,)).copy()
+
+
+def test_problem_marshalling_round_trip():
+    """The struct handed to the C ABI carries every parameter of the problem
+    (the double and int parameters live in two packed arrays): read back
+    through the struct's addresses, they equal the problem's own arrays."""
+    import ctypes as C
+    from paper_1702_00339_gb300 import fock
+    ps = [li.config2(s) for s in range(3)] + li.serving_stream(16, seed=3000)
+    t, c, _ = sinc.table_for(ps[0])
+    ps.append(ps[0].with_table(t, c))
+    for p in ps:
+        m = fock._Marshal(p)
+        s = m.s
+        assert list(s.L) == list(p.L) and list(s.periodic) == list(p.periodic) and list(s.N) == list(p.N)
+        assert s.M0 == len(p.Z) and s.m0 == len(p.exps) and s.R == p.R and s.k_eig == p.k_eig
+        assert np.array_equal(_read(s.Z, s.M0, C.c_double), np.asarray(p.Z, float))
+        assert np.array_equal(_read(s.frac, 3 * s.M0, C.c_double), np.asarray(p.frac, float).ravel())
+        assert np.array_equal(_read(s.exps, s.m0, C.c_double), np.asarray(p.exps, float))
+        assert np.array_equal(_read(s.ang, s.m0, C.c_int), np.asarray(p.ang, np.int32))
+        assert np.array_equal(_read(s.centre, s.m0, C.c_int), np.asarray(p.centre, np.int32))
+        if p.sinc_t is None:
+            assert not s.sinc_t and not s.sinc_c
+        else:
+            assert np.array_equal(_read(s.sinc_t, p.R, C.c_double), np.asarray(p.sinc_t, float))
+            assert np.array_equal(_read(s.sinc_c, p.R, C.c_double), np.asarray(p.sinc_c, float))
+        assert s.ndef == len(p.defects)
+        if p.defects:
+            d = C.cast(C.c_void_p(s.defects), C.POINTER(fock.c_defect))
+            for i, x in enumerate(p.defects):
+                assert list(d[i].cell) == list(x.cell) and d[i].nucleus == x.nucleus and d[i].newZ == x.newZ
