@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import struct
 
 import numpy as np
 
@@ -64,6 +65,12 @@ class c_serve_stats(C.Structure):
 class c_output(C.Structure):
     _fields_ = [("evals", C.c_void_p), ("block_of", C.c_void_p), ("n_evals", C.c_int),
                 ("iters", C.c_int), ("resid", C.c_double), ("status", C.c_int)]
+
+
+# numpy view of c_output (same offsets), for filling many entries at once
+_OUT_DTYPE = np.dtype({"names": ["evals", "block_of"], "formats": [np.uint64, np.uint64],
+                       "offsets": [c_output.evals.offset, c_output.block_of.offset],
+                       "itemsize": C.sizeof(c_output)})
 
 
 _lib = None
@@ -133,42 +140,31 @@ def _ip(a):
     return a.ctypes.data_as(C.POINTER(C.c_int))
 
 
+# native layout of fock_problem (the same field order and alignment as c_problem)
+_PROBLEM_FMT = "@3i3i3iidiPPiPPPiPPdiPii"
+
+
 class _Marshal:
     """Keeps the arrays behind one c_problem alive.  The double parameters
     (Z, frac, exps, sinc nodes and weights) share one contiguous array and the
-    int ones (ang, centre) another; the struct holds their addresses."""
+    int ones (ang, centre) another; the struct, packed in one call, holds
+    their addresses."""
 
     def __init__(self, p):
-        M0, m0 = len(p.Z), len(p.exps)
         table = p.sinc_t is not None
         parts = [np.asarray(p.Z, np.float64).ravel(), np.asarray(p.frac, np.float64).ravel(),
                  np.asarray(p.exps, np.float64).ravel()]
         if table:
             parts += [np.asarray(p.sinc_t, np.float64).ravel(), np.asarray(p.sinc_c, np.float64).ravel()]
         dv = np.concatenate(parts)
-        iv = np.concatenate([np.asarray(p.ang, np.int32).ravel(), np.asarray(p.centre, np.int32).ravel()])
+        ang = np.asarray(p.ang, np.int32).ravel()
+        iv = np.concatenate([ang, np.asarray(p.centre, np.int32).ravel()])
         self.keep = [dv, iv]
         bd, bi = dv.ctypes.data, iv.ctypes.data
-        off = np.cumsum([0] + [a.size for a in parts]) * 8   # byte offsets of the parts in dv
-        s = c_problem()
-        s.L[:] = [int(v) for v in p.L]
-        s.periodic[:] = [int(v) for v in p.periodic]
-        s.N[:] = [int(v) for v in p.N]
-        s.n0 = int(p.n0)
-        s.b0 = float(p.b0)
-        s.M0 = M0
-        s.Z = bd + int(off[0])
-        s.frac = bd + int(off[1])
-        s.m0 = m0
-        s.exps = bd + int(off[2])
-        s.ang = bi
-        s.centre = bi + 4 * len(p.ang)
-        s.R = int(p.R)
-        if table:
-            s.sinc_t = bd + int(off[3])
-            s.sinc_c = bd + int(off[4])
-        s.eps_support = float(p.eps_support)
-        s.ndef = len(p.defects)
+        off = [0]
+        for a in parts:
+            off.append(off[-1] + 8 * a.size)   # byte offsets of the parts in dv
+        dptr = 0
         if p.defects:
             d = (c_defect * len(p.defects))()
             for i, x in enumerate(p.defects):
@@ -176,10 +172,35 @@ class _Marshal:
                 d[i].nucleus = int(x.nucleus)
                 d[i].newZ = float(x.newZ)
             self.keep.append(d)
-            s.defects = C.addressof(d)
-        s.k_eig = int(p.k_eig)
-        s.precision = int(getattr(p, "precision", 0))
-        self.s = s
+            dptr = C.addressof(d)
+        L, per, N = p.L, p.periodic, p.N
+        self.s = c_problem.from_buffer_copy(struct.pack(
+            _PROBLEM_FMT, int(L[0]), int(L[1]), int(L[2]), int(per[0]), int(per[1]), int(per[2]),
+            int(N[0]), int(N[1]), int(N[2]), int(p.n0), float(p.b0), len(p.Z), bd + off[0], bd + off[1],
+            len(p.exps), bd + off[2], bi, bi + 4 * ang.size, int(p.R),
+            bd + off[3] if table else 0, bd + off[4] if table else 0, float(p.eps_support),
+            len(p.defects), dptr, int(p.k_eig), int(getattr(p, "precision", 0))))
+
+
+def _host_outputs(problems):
+    """c_output array for host results: every problem's eigenvalues (and block
+    indices) are views into two batch-wide arrays (two allocations per call)."""
+    n = len(problems)
+    ne = [n_evals(p) for p in problems]
+    st = [_structured(p) for p in problems]
+    off = np.concatenate([[0], np.cumsum(ne, dtype=np.int64)]).astype(np.int64)
+    ev_all = np.zeros(int(off[-1]))
+    blk_all = np.zeros(int(off[-1]), np.int32)
+    outs = (c_output * n)()
+    be, bb = ev_all.ctypes.data, blk_all.ctypes.data
+    # the two pointer fields of every entry at once, through a numpy view of the array
+    rec = np.frombuffer(outs, dtype=_OUT_DTYPE, count=n) if n else None
+    if n:
+        rec["evals"] = be + 8 * off[:-1]
+        rec["block_of"] = np.where(np.asarray(st, bool), 0, bb + 4 * off[:-1])
+    views = [(ev_all[int(off[i]):int(off[i + 1])], None if st[i] else blk_all[int(off[i]):int(off[i + 1])])
+             for i in range(n)]
+    return outs, views
 
 
 def _structured(p):
@@ -188,7 +209,7 @@ def _structured(p):
 
 
 def n_evals(p):
-    ncell = int(np.prod(p.L))
+    ncell = int(p.L[0]) * int(p.L[1]) * int(p.L[2])
     if _structured(p):
         return int(p.k_eig or 16)
     return ncell * len(p.exps)
@@ -247,16 +268,11 @@ class Context:
         n = len(problems)
         ms = [_Marshal(p) for p in problems]
         arr = (c_problem * n)(*[m.s for m in ms])
-        outs = (c_output * n)()
-        host = []
-        for i, p in enumerate(problems):
-            if outputs is None:
-                ev = np.zeros(n_evals(p))
-                blk = np.zeros(n_evals(p), np.int32)
-                outs[i].evals = ev.ctypes.data
-                outs[i].block_of = blk.ctypes.data if not _structured(p) else None
-                host.append((ev, blk))
-            else:
+        if outputs is None:
+            outs, host = _host_outputs(problems)
+        else:
+            outs = (c_output * n)()
+            for i in range(n):
                 outs[i].evals, outs[i].block_of = outputs[i]
         rc = lib().fock_solve(self.h, n, arr, outs, 0 if outputs is None else 1)
         if rc and check:
@@ -266,8 +282,7 @@ class Context:
             r = {"n_evals": outs[i].n_evals, "iters": outs[i].iters, "resid": outs[i].resid,
                  "status": outs[i].status}
             if outputs is None:
-                r["evals"] = host[i][0]
-                r["block_of"] = None if _structured(p) else host[i][1]
+                r["evals"], r["block_of"] = host[i]
             res.append(r)
         return res
 
@@ -409,16 +424,11 @@ class Plan:
         """Host copies (list of dicts) or, with device_ptrs = [(evals_ptr,
         block_of_ptr_or_0), ...], device-to-device copies."""
         n = len(self.problems)
-        outs = (c_output * n)()
-        host = []
-        for i, p in enumerate(self.problems):
-            if device_ptrs is None:
-                ev = np.zeros(n_evals(p))
-                blk = np.zeros(n_evals(p), np.int32)
-                outs[i].evals = ev.ctypes.data
-                outs[i].block_of = blk.ctypes.data if not _structured(p) else None
-                host.append((ev, blk))
-            else:
+        if device_ptrs is None:
+            outs, host = _host_outputs(self.problems)
+        else:
+            outs = (c_output * n)()
+            for i in range(n):
                 outs[i].evals, outs[i].block_of = device_ptrs[i]
         rc = lib().fock_plan_outputs(self.h, outs, 0 if device_ptrs is None else 1)
         if rc and check:
@@ -428,8 +438,7 @@ class Plan:
             r = {"n_evals": outs[i].n_evals, "iters": outs[i].iters, "resid": outs[i].resid,
                  "status": outs[i].status}
             if device_ptrs is None:
-                r["evals"] = host[i][0]
-                r["block_of"] = None if _structured(p) else host[i][1]
+                r["evals"], r["block_of"] = host[i]
             res.append(r)
         return res
 
