@@ -367,8 +367,9 @@ __global__ void k_axis_dft(const ProbDev* __restrict__ probs, const DftTask* __r
     tw[t] = cmk(c, s);
   }
   __syncthreads();
+  // the factors are real: Xh[L - j] = conj(Xh[j]), so only j <= L / 2 is summed
   const int per = P.nF * P.m0 * P.m0;
-  const int tot = D.L * per;
+  const int tot = (D.L / 2 + 1) * per;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < tot; it += gridDim.x * blockDim.x) {
     int j = it / per, e = it % per;
     double re = 0.0, im = 0.0;
@@ -379,6 +380,7 @@ __global__ void k_axis_dft(const ProbDev* __restrict__ probs, const DftTask* __r
       im += w.y * x;
     }
     D.Xh[it] = cmk(re, im);
+    if (j > 0 && 2 * j != D.L) D.Xh[(size_t)(D.L - j) * per + e] = cmk(re, -im);
   }
 }
 
