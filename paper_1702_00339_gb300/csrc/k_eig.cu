@@ -294,6 +294,18 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   const int jl = blockIdx.x;      // local output index
   if (jl >= F.nj) return;
   const int j = F.j0 + jl;        // Fourier index
+  // Real generators: the block at -j (componentwise mod L) is the complex
+  // conjugate of the block at j, with the same spectrum.  When both indices
+  // are in this task's range and no blocks are stored, the lower index
+  // solves the pair and writes both; the higher one does nothing.
+  int jm = -1;
+  if (F.source == FROM_FACTORS && F.want == 1 && !F.outH) {
+    const int j3 = j % F.L[2], j2 = (j / F.L[2]) % F.L[1], j1 = j / (F.L[1] * F.L[2]);
+    const int m1 = (F.L[0] - j1) % F.L[0], m2 = (F.L[1] - j2) % F.L[1], m3 = (F.L[2] - j3) % F.L[2];
+    jm = (m1 * F.L[1] + m2) * F.L[2] + m3;
+    if (jm == j || jm < F.j0 || jm >= F.j0 + F.nj) jm = -1;
+    else if (jm < j) return;
+  }
   const ProbDev& P = probs[F.prob];
   const int m0 = P.m0, np = m0 * m0;
   const int ldj = m0 + (m0 & 1);
@@ -389,8 +401,13 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   __syncthreads();
   if (F.want == 1) {
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-      F.ev[(size_t)jl * m0 + i] = (i < r) ? tridiag_eig_fast(df, e2f, dd, e2, r, i, 0.0) : INFINITY;
+      const double lam = (i < r) ? tridiag_eig_fast(df, e2f, dd, e2, r, i, 0.0) : INFINITY;
+      F.ev[(size_t)jl * m0 + i] = lam;
       if (F.blk) F.blk[(size_t)jl * m0 + i] = j;
+      if (jm >= 0) {   // the conjugate block's spectrum
+        F.ev[(size_t)(jm - F.j0) * m0 + i] = lam;
+        if (F.blk) F.blk[(size_t)(jm - F.j0) * m0 + i] = jm;
+      }
     }
   } else if (threadIdx.x == 0) {
     // the lowest eigenvalue of an embedding block only sets the preconditioner
