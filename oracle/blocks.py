@@ -239,11 +239,12 @@ def structured(p):
     return bool(p.is_box or p.defects)
 
 
-def solve(p):
+def solve(p, box_potential="replicated"):
     """The problem's answer under the canonical-orthogonalisation reading:
     a periodic problem's whole spectrum (+inf for removed directions), a box
-    chain's or a defect problem's lowest k_eig eigenvalues."""
-    H, S = dense.build(p)
+    chain's or a defect problem's lowest k_eig eigenvalues.  box_potential
+    selects reading R1 or R2 of a box's potential (grid.potential_slabs)."""
+    H, S = dense.build(p, box_potential=box_potential)
     if structured(p):
         return box_eigs(p, H, S)[0]
     return periodic_eigs(p, H, S)[0]

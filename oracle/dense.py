@@ -108,9 +108,11 @@ def _contract(p, Gs, slab_of, slabs, col_cells=None):
     return V
 
 
-def potential_matrix(p, forms=None, slab=None):
+def potential_matrix(p, forms=None, slab=None, box_potential="replicated"):
+    """Dense V; box_potential selects reading R1 ("replicated") or R2
+    ("lattice_sum") of the box potential (grid.potential_slabs)."""
     forms = forms or axis_forms(p)
-    slab_of, slabs = slab if slab is not None else grid.potential_slabs(p)
+    slab_of, slabs = slab if slab is not None else grid.potential_slabs(p, box_potential)
     V = _contract(p, [f[0] for f in forms], slab_of, slabs)
     return V.reshape(p.Nb, p.Nb)
 
@@ -120,7 +122,9 @@ def defect_matrix(p, forms=None):
     the rank-R kernel of the one substituted nucleus (no window, no
     replication, minimum image on periodic axes).  Reading R-DEF of the
     design notes: the paper only motivates defects (Sec. 1, Sec. 2.3 (B)).
-    Parity unpinned beyond the reduction to the single-molecule potential."""
+    Pins: the single-molecule charge change, every cell of an odd periodic
+    chain substituted (= a charge change of the window sum), every nucleus
+    of a box vacated (= minus the box's lattice-sum potential)."""
     forms = forms or axis_forms(p)
     D = np.zeros((p.Nb, p.Nb))
     if not p.defects:
@@ -144,11 +148,11 @@ def defect_matrix(p, forms=None):
     return D
 
 
-def build(p, with_parts=False):
+def build(p, with_parts=False, box_potential="replicated"):
     """Dense (H, S) of problem p (and optionally A, V)."""
     forms = axis_forms(p)
     S, A = mass_kinetic(p, forms)
-    V = potential_matrix(p, forms)
+    V = potential_matrix(p, forms, box_potential=box_potential)
     if p.defects:
         V = V + defect_matrix(p, forms)
     H = 0.5 * A - V
@@ -164,6 +168,6 @@ def eigvals(H, S, k=None):
     return scipy.linalg.eigh(H, S, eigvals_only=True, subset_by_index=[0, k - 1])
 
 
-def solve(p):
-    H, S = build(p)
+def solve(p, box_potential="replicated"):
+    H, S = build(p, box_potential=box_potential)
     return eigvals(H, S, p.k_eig if (p.k_eig and p.is_box) else None)

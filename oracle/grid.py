@@ -20,7 +20,9 @@ design notes of the repository):
   (Sec. 3.3).  On a Dirichlet axis the replication keeps the end cells'
   values over the padding (cell index clamped to 0..L-1), so an axis with a
   single cell is evaluated directly.  The same potential serves periodic
-  and box problems.
+  and box problems (reading R1).  Reading R2, the plain lattice sum over
+  the box's cells of Sec. 2.3 case (B), is available for box problems
+  through potential_slabs(p, "lattice_sum"); the library computes R1.
 * The Newton kernel is projected on piecewise-constant cells centred at the
   nodes (Eq. 2.6) and approximated by the R-term Gaussian sum (Eq. 2.7), so
   one axis factor is the cell integral of exp(-t_q^2 (x - a)^2), which has
@@ -134,15 +136,51 @@ def potential_axis(p, ax):
     return out
 
 
-def potential_slabs(p):
+def potential_axis_lattice_sum(p, ax):
+    """Box potential read as the plain lattice sum of Sec. 2.3 case (B)
+    (reading R2): on a Dirichlet axis pB[nu, q, i] is the sum over the
+    axis' cells k = 0..L-1 of int_{cell(x_i)} exp(-t_q^2 (s - a_nu - k b0)^2)
+    ds at the node's own position: no window, no replication, so each
+    nucleus of the box is counted once with its full charge.  A periodic
+    axis keeps the window-summed, replicated factor of potential_axis
+    (case (A)).  The 3D kernel of the box, a sum over all cells of products
+    of these axis terms, is the product of the per-axis sums because the
+    cell set is a product of per-axis ranges (Eq. 2.13 summed over k)."""
+    if p.periodic[ax]:
+        return potential_axis(p, ax)
+    x, X0, _ = axis_nodes(p, ax)
+    h = p.h
+    t = np.asarray(p.sinc_t, float)
+    out = np.zeros((p.M0, len(t), len(x)))
+    for nu in range(p.M0):
+        for k in range(p.L[ax]):
+            a = X0 + (p.frac[nu, ax] + k) * p.b0
+            out[nu] += gauss_cell_integral(t[:, None], (x - h / 2 - a)[None, :],
+                                           (x + h / 2 - a)[None, :])
+    return out
+
+
+BOX_POTENTIALS = ("replicated", "lattice_sum")
+
+
+def potential_slabs(p, box_potential="replicated"):
     """The 3D potential tensor P(i1,i2,i3) = sum_nu Z_nu sum_q c_q
-    prod_l pt_l[nu,q,i_l] (Eq. 2.13 restricted to the reference cell and
-    replicated, Eq. 3.6), returned as the distinct axis-0 slabs: (slab
-    index per i1, array (nslab, N2, N3)).  Two nodes of axis 0 share a slab
-    exactly when they replicate to the same reference-cell node."""
+    prod_l pt_l[nu,q,i_l], returned as the distinct axis-0 slabs: (slab
+    index per i1, array (nslab, N2, N3)).  box_potential "replicated"
+    (reading R1): Eq. 2.13 restricted to the reference cell and replicated
+    (Eq. 3.6); two nodes of axis 0 share a slab exactly when they replicate
+    to the same reference-cell node.  "lattice_sum" (reading R2): the plain
+    sum over the box's cells on Dirichlet axes (potential_axis_lattice_sum);
+    every node of a Dirichlet axis 0 has its own slab."""
+    if box_potential not in BOX_POTENTIALS:
+        raise ValueError(f"box_potential must be one of {BOX_POTENTIALS}")
     c = np.asarray(p.sinc_c, float)
-    pt = [potential_axis(p, a) for a in range(3)]
-    y0 = reduced_nodes(p, 0)
+    if box_potential == "replicated":
+        pt = [potential_axis(p, a) for a in range(3)]
+        y0 = reduced_nodes(p, 0)
+    else:
+        pt = [potential_axis_lattice_sum(p, a) for a in range(3)]
+        y0 = reduced_nodes(p, 0) if p.periodic[0] else axis_nodes(p, 0)[0]
     uniq, slab_of = np.unique(np.round(y0 / p.h * 2).astype(np.int64), return_inverse=True)
     first = np.array([np.nonzero(slab_of == s)[0][0] for s in range(len(uniq))])
     N2, N3 = p.N[1], p.N[2]
@@ -174,6 +212,32 @@ def potential_full_window(p):
                         e.append(gauss_cell_integral(t[:, None], (ys[a] - h / 2 - aa)[None, :],
                                                      (ys[a] + h / 2 - aa)[None, :]))
                     P += p.Z[nu] * w1 * w2 * w3 * np.einsum("q,qi,qj,qk->ijk", c, *e)
+    return P
+
+
+def potential_lattice_sum_brute(p):
+    """Brute-force 3D tensor of the box potential under reading R2: an
+    explicit loop over every cell (k1, k2, k3) of a box whose axes are all
+    Dirichlet and every nucleus, each term the full 3D product of cell
+    integrals at the nodes' own positions (tiny grids only)."""
+    if any(p.periodic):
+        raise ValueError("the lattice-sum brute force takes Dirichlet axes only")
+    c = np.asarray(p.sinc_c, float)
+    t = np.asarray(p.sinc_t, float)
+    h = p.h
+    xs = [axis_nodes(p, a)[0] for a in range(3)]
+    X0s = [axis_nodes(p, a)[1] for a in range(3)]
+    P = np.zeros(tuple(p.N))
+    for nu in range(p.M0):
+        for k1 in range(p.L[0]):
+            for k2 in range(p.L[1]):
+                for k3 in range(p.L[2]):
+                    e = []
+                    for a, k in enumerate((k1, k2, k3)):
+                        aa = X0s[a] + (p.frac[nu, a] + k) * p.b0
+                        e.append(gauss_cell_integral(t[:, None], (xs[a] - h / 2 - aa)[None, :],
+                                                     (xs[a] + h / 2 - aa)[None, :]))
+                    P += p.Z[nu] * np.einsum("q,qi,qj,qk->ijk", c, *e)
     return P
 
 
