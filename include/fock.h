@@ -80,7 +80,9 @@ typedef struct {
   int ndef;              /* number of defects */
   const fock_defect* defects;
   int k_eig;             /* box / defect solves: eigenpairs wanted (0: 16) */
-  int precision;         /* FOCK_FP64 (FOCK_MIXED reserved) */
+  int precision;         /* FOCK_FP64, or FOCK_MIXED: box and defect solves run the
+                            band preconditioner, and their matvecs until the residual
+                            falls below 1e-5, in FP32 (periodic solves: FP64 always) */
 } fock_problem;
 
 /* Output slot of one problem in a batched solve. */
@@ -117,6 +119,14 @@ int fock_sinc_table(int R, double zmin, double zmax, double* t, double* c, doubl
 /* The default z-range of a problem (zmin = h/100, zmax = twice a bound on
  * the nucleus-node distance over the lattice window). */
 int fock_default_range(const fock_problem* p, double* zmin, double* zmax);
+/* Checks a problem as every solve entry point does, on the host only (no
+ * device, no context).  On success writes *kind (0: periodic, solved
+ * through its Fourier blocks, Thm. 3.3; 1: box chain or problem with
+ * defects, solved for the lowest k_eig by the structured iteration,
+ * Remark 3.2) and *n_evals (|L|*m0, or k_eig) when the pointers are not
+ * NULL.  On FOCK_EINVAL writes the reason, NUL-terminated and truncated to
+ * why_cap bytes, into `why` (may be NULL). */
+int fock_problem_check(const fock_problem* p, int* kind, int* n_evals, char* why, int why_cap);
 
 /* Batched solve (stages (a)+(b) for periodic problems, (a)+(c) for box
  * chains and problems with defects).  nprob problems, outs[nprob].

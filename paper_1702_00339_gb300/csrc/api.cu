@@ -1669,6 +1669,25 @@ void fock_destroy(fock_ctx* c) {
 
 const char* fock_last_error(const fock_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int fock_problem_check(const fock_problem* p, int* kind, int* n_evals, char* why, int why_cap) {
+  if (why && why_cap > 0) why[0] = '\0';
+  if (!p) return FOCK_EINVAL;
+  HostProb H;
+  std::string msg;
+  const int rc = validate(*p, H, msg);
+  if (rc != FOCK_OK) {
+    if (why && why_cap > 0) {
+      const size_t n = std::min(msg.size(), (size_t)(why_cap - 1));
+      std::memcpy(why, msg.data(), n);
+      why[n] = '\0';
+    }
+    return rc;
+  }
+  if (kind) *kind = H.kind;
+  if (n_evals) *n_evals = (H.kind == 1) ? H.k_eig : H.L[0] * H.L[1] * H.L[2] * H.m0;
+  return FOCK_OK;
+}
+
 int fock_synchronize(fock_ctx* c) {
   if (!c) return FOCK_EINVAL;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

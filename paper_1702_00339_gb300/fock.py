@@ -93,6 +93,7 @@ def lib():
         L.fock_sinc_table.argtypes = [C.c_int, C.c_double, C.c_double, P(C.c_double), P(C.c_double),
                                       P(C.c_double)]
         L.fock_default_range.argtypes = [P(c_problem), P(C.c_double), P(C.c_double)]
+        L.fock_problem_check.argtypes = [P(c_problem), P(C.c_int), P(C.c_int), C.c_char_p, C.c_int]
         L.fock_solve.argtypes = [C.c_void_p, C.c_int, P(c_problem), P(c_output), C.c_int]
         L.fock_assemble.argtypes = [C.c_void_p, P(c_problem), P(C.c_void_p)]
         L.fock_blocks_free.argtypes = [C.c_void_p]
@@ -232,6 +233,19 @@ def default_range(p):
     if rc:
         raise FockError(rc, "fock_default_range")
     return a.value, b.value
+
+
+def check_problem(p):
+    """The library's own host-side check of a problem (fock_problem_check):
+    returns {"kind": 0 periodic | 1 structured, "n_evals": ...}; raises
+    FockError(FOCK_EINVAL, reason) for a malformed problem."""
+    m = _Marshal(p)
+    kind, ne = C.c_int(-1), C.c_int(-1)
+    why = C.create_string_buffer(256)
+    rc = lib().fock_problem_check(C.byref(m.s), C.byref(kind), C.byref(ne), why, len(why))
+    if rc:
+        raise FockError(rc, why.value.decode())
+    return {"kind": kind.value, "n_evals": ne.value}
 
 
 class Context:

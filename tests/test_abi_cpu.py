@@ -116,3 +116,84 @@ def test_problem_marshalling_round_trip():
             d = C.cast(C.c_void_p(s.defects), C.POINTER(fock.c_defect))
             for i, x in enumerate(p.defects):
                 assert list(d[i].cell) == list(x.cell) and d[i].nucleus == x.nucleus and d[i].newZ == x.newZ
+
+
+def test_problem_check_accepts_the_workloads(libpath):
+    """The library's own host check (the one every solve runs first) accepts
+    every workload recipe and agrees with the binding on the solve kind and
+    the number of eigenvalues returned."""
+    from paper_1702_00339_gb300 import fock
+    ps = [li.config1(), li.config2(0), li.config3(0), li.config5_box(0), li.config5_periodic(0)]
+    ps += li.serving_stream(128, seed=3000)
+    for p in ps:
+        r = fock.check_problem(p)
+        assert r["kind"] == int(fock._structured(p))
+        assert r["n_evals"] == fock.n_evals(p)
+
+
+def _bad_problems():
+    """(mutation, expected reason fragment) pairs on a small box chain."""
+    import dataclasses
+    base = li.config2(0, L=8, n0=5, pad=4, n_perp=16, R=16)
+    base.k_eig = 4
+    r = dataclasses.replace
+    per = r(base, periodic=(1, 0, 0), N=(8 * 5, 16, 16), k_eig=0)
+    yield r(base, n0=0), "n0 > 0"
+    yield r(base, b0=0.0), "b0 > 0"
+    yield r(base, Z=np.zeros(0), frac=np.zeros((0, 3))), "M0"
+    yield r(base, exps=np.ones(33), ang=np.zeros(33, int), centre=np.zeros(33, int)), "m0"
+    yield r(base, R=2), "R <= 64"
+    yield r(base, R=65), "R <= 64"
+    yield r(base, precision=2), "precision"
+    yield r(base, L=(0, 1, 1)), "L >= 1"
+    yield r(per, N=(41, 16, 16)), "N = L*n0"
+    yield r(base, N=(39, 16, 16)), "N >= L*n0"
+    yield r(base, L=(2, 2, 1), N=(14, 14, 16)), "chains"
+    yield r(base, L=(1, 1, 1), N=(9, 16, 16), defects=[li.Defect((0, 0, 0), 0, 0.0)]), "chains"
+    yield r(per, periodic=(1, 1, 0), N=(40, 5, 16), defects=[li.Defect((1, 0, 0), 0, 0.0)]), "transverse"
+    yield r(base, defects=[li.Defect((8, 0, 0), 0, 0.0)]), "defect cell"
+    yield r(base, defects=[li.Defect((1, 0, 0), 1, 0.0)]), "defect cell"
+    yield r(base, defects=[li.Defect((1, 0, 0), 0, float("nan"))]), "newZ"
+    e = base.exps.copy()
+    e[3] = -1.0
+    yield r(base, exps=e), "exponents"
+    a = base.ang.copy()
+    a[0] = 4
+    yield r(base, ang=a), "ang"
+    c = base.centre.copy()
+    c[0] = 1
+    yield r(base, centre=c), "centre"
+    t, cq, _ = sinc.table_for(base)
+    t = t.copy()
+    t[0] = 0.0
+    yield base.with_table(t, cq), "sinc_t"
+    yield r(base, k_eig=65), "k_eig"
+    long = li.config2(0, L=64, n0=5, pad=4, n_perp=16, R=16)
+    yield r(long, k_eig=80), "k_eig"
+
+
+@pytest.mark.parametrize("case", list(range(22)))
+def test_problem_check_rejects_malformed_problems(libpath, case):
+    """Every malformed field is refused with FOCK_EINVAL and a reason, by the
+    host check alone (no device)."""
+    from paper_1702_00339_gb300 import fock
+    bad = list(_bad_problems())
+    assert len(bad) == 22
+    p, frag = bad[case]
+    with pytest.raises(fock.FockError) as ei:
+        fock.check_problem(p)
+    assert ei.value.code == fock.FOCK_EINVAL
+    assert frag in str(ei.value)
+
+
+def test_problem_check_truncates_the_reason(libpath):
+    import ctypes as C
+    import dataclasses
+    from paper_1702_00339_gb300 import fock
+    p = dataclasses.replace(li.config2(0), n0=0)
+    m = fock._Marshal(p)
+    why = C.create_string_buffer(b"x" * 8, 8)
+    rc = fock.lib().fock_problem_check(C.byref(m.s), None, None, why, 5)
+    assert rc == fock.FOCK_EINVAL
+    assert why.raw[:5] == b"n0 > "[:4] + b"\0"
+    assert fock.lib().fock_problem_check(None, None, None, None, 0) == fock.FOCK_EINVAL
