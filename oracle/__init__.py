@@ -21,7 +21,9 @@ problem of Sec. 2 of the paper:
               and their dense generalized eigensolve;
 * `blocks`  - generator blocks read off the dense matrices, the direct
               (non-FFT) DFT over the lattice index and per-block eigensolves
-              (Lemma 3.1, Prop. A.1), the dense Toeplitz/box matvec;
+              (Lemma 3.1, Prop. A.1), the back-transform of block
+              eigenvectors to the lattice and the real-space orbitals on the
+              grid, the dense Toeplitz/box matvec;
 * `closed_forms` - textbook Gaussian integrals and the exact cell integral
               of 1/|x|, used only to pin the grid quantities.
 

@@ -191,6 +191,66 @@ def periodic_eigs(p, H=None, S=None, tau=CANON_TAU):
     return np.sort(per.ravel()), per, np.array(kap)
 
 
+def bloch_phases(p, jbar):
+    """Lattice factor of the back-transform at linear Fourier index jbar:
+    f[kbar] = prod_l exp(+2 pi i j_l k_l / L_l) / sqrt(|L|).  With
+    H = sum_k pi^k (x) A_k and Abar_j = sum_k omega^{jk} A_k,
+    omega = exp(-2 pi i / L) (Eq. A.3), the vector u[k] = f[k] y gives
+    (H u)[k] = f[k] Abar_j y block by block, so an eigenpair of the block
+    pencil is one of the lattice pencil (Prop. A.1; the columns of the
+    inverse DFT, U = (F^* (x) I) Ubar)."""
+    L1, L2, L3 = p.L
+    j3 = jbar % L3
+    j2 = (jbar // L3) % L2
+    j1 = jbar // (L2 * L3)
+    k = np.arange(p.ncell)
+    k3 = k % L3
+    k2 = (k // L3) % L2
+    k1 = k // (L2 * L3)
+    ph = np.exp(2j * np.pi * (j1 * k1 / L1 + j2 * k2 / L2 + j3 * k3 / L3))
+    return ph / np.sqrt(p.ncell)
+
+
+def periodic_eigvecs(p, H=None, S=None, tau=CANON_TAU):
+    """Eigenpairs of a periodic problem through its Fourier blocks: each
+    block's canonical eigenpairs (kept directions only), back-transformed to
+    the lattice by bloch_phases.  Returns (eigenvalues ascending, complex
+    eigenvectors (N_b, n) in the basis order a = kbar*m0 + mu, Fourier index
+    of each); the vectors are S-orthonormal."""
+    if H is None:
+        H, S = dense.build(p)
+    Hb = fourier_blocks(p, generators_from_dense(p, H))
+    Sb = fourier_blocks(p, generators_from_dense(p, S))
+    evs, vecs, js = [], [], []
+    for j in range(p.ncell):
+        ev, Y, _ = canonical(Hb[j], Sb[j], tau)
+        r = Y.shape[1]
+        f = bloch_phases(p, j)
+        evs.append(ev[:r])
+        vecs.append(np.kron(f[:, None], Y))          # u[(k, mu), c] = f[k] Y[mu, c]
+        js.append(np.full(r, j))
+    ev = np.concatenate(evs)
+    U = np.concatenate(vecs, axis=1)
+    jj = np.concatenate(js)
+    order = np.lexsort((jj, ev))
+    return ev[order], U[:, order], jj[order]
+
+
+def orbital_on_grid(p, u):
+    """Real-space orbital psi(i1, i2, i3) = sum_{k, mu} u[(k, mu)]
+    prod_l g_l(k_l, mu)(x_{i_l}) at the grid nodes (the separable GTO factors
+    of Sec. 2.4; the P1 interpolant of psi is the Galerkin function)."""
+    from . import grid
+    m0 = p.m0
+    L1, L2, L3 = p.L
+    Gs = [grid.basis_axis(p, a) for a in range(3)]
+    C = np.asarray(u).reshape(L1, L2, L3, m0)
+    # contract one axis at a time: the cell index of each axis and mu
+    T = np.einsum("iam,abcm->ibcm", Gs[0], C)                # (N1, L2, L3, m0)
+    T = np.einsum("jbm,ibcm->ijcm", Gs[1], T)                # (N1, N2, L3, m0)
+    return np.einsum("kcm,ijcm->ijk", Gs[2], T)              # (N1, N2, N3)
+
+
 def cell_overlap(p):
     """Overlap of one cell's basis with itself as the structured (chain)
     solve sees it: for a box chain the interior cell of the Toeplitz
