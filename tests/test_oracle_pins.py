@@ -453,3 +453,30 @@ def test_defect_matrix_translation_covariance():
     E3 = dense.defect_matrix(_chain_with_defects(b, [li.Defect((3, 0, 0), 0, 2.0)]))
     E4 = dense.defect_matrix(_chain_with_defects(b, [li.Defect((4, 0, 0), 0, 2.0)]))
     assert np.max(np.abs(E4[m0:, m0:] - E3[:-m0, :-m0])) <= 1e-13 * np.max(np.abs(E3))
+
+
+# ---------------- box vs periodic chains as L grows (Sec. 4, the average energy per cell) ----------------
+
+def test_box_and_periodic_chains_relax_to_each_other():
+    """A box chain and its periodic supercell (same basis, grid and rank):
+    the lowest eigenvalues differ by a confinement term that falls like
+    1/L^2, and the average of the lowest L eigenvalues (the energy per cell
+    of the lowest band) differs by an end term that falls like 1/L -- the
+    relaxation of the average energy per cell for both boundary conditions
+    that the paper's chain experiments show.  (Higher in the spectrum the
+    two keep a systematic difference, which the paper also reports.)"""
+    base = li.config1()
+    d_low, d_avg = [], []
+    for L in (4, 8, 16):
+        n0, nperp, pad = 8, 16, 40
+        box = _cases.with_table(li.Problem(
+            L=(L, 1, 1), periodic=(0, 0, 0), N=(L * n0 + 2 * pad, nperp, nperp), n0=n0, b0=2.0,
+            Z=base.Z, frac=base.frac, exps=base.exps, ang=base.ang, centre=base.centre, R=16))
+        per = box.as_periodic_chain().with_table(box.sinc_t, box.sinc_c)
+        eb = dense.eigvals(*dense.build(box))
+        ep = dense.eigvals(*dense.build(per))
+        d_low.append(eb[0] - ep[0])
+        d_avg.append(abs(eb[:L].mean() - ep[:L].mean()))
+    assert all(d > 0 for d in d_low)                     # confinement raises the band bottom
+    assert d_low[1] < d_low[0] / 2.5 and d_low[2] < d_low[1] / 2.5
+    assert d_avg[1] < d_avg[0] / 1.6 and d_avg[2] < d_avg[1] / 1.6
