@@ -138,11 +138,30 @@ def oracle_sample(npairs, seed0=0):
     return len(ps), dt
 
 
-def cpu_baseline(npairs):
+def oracle_sample_one_thread(npairs):
+    """The oracle sample in a fresh interpreter whose BLAS / OpenMP pools are
+    limited to one thread (the limit must be set before numpy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(npairs)],
+                       env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["n"], d["dt"]
+
+
+def cpu_baseline(npairs, one_thread_pairs=2):
     n, dt = oracle_sample(npairs)
-    return {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{npairs} box + {npairs} periodic requests of the workload (dense FP64 Galerkin "
-                      f"matrices by 3D grid contraction + LAPACK eigh), {dt:.1f} s"}
+    out = {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{npairs} box + {npairs} periodic requests of the workload (dense FP64 Galerkin "
+                     f"matrices by 3D grid contraction + LAPACK eigh), {dt:.1f} s"}
+    if one_thread_pairs > 0:
+        one = oracle_sample_one_thread(one_thread_pairs)
+        if one is not None:
+            out["value_1thread"] = one[0] / one[1]
+            out["sample_1thread"] = (f"{one_thread_pairs} box + {one_thread_pairs} periodic requests, "
+                                     f"one BLAS thread, {one[1]:.1f} s")
+    return out
 
 
 def run_reference(args, rank, world):
@@ -283,7 +302,12 @@ def main():
     ap.add_argument("--profile-json", default="")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:   # child of cpu_baseline: time the oracle only, print one JSON line
+        n, dt = oracle_sample(args.oracle_sample)
+        print(json.dumps({"n": n, "dt": dt}), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
