@@ -257,6 +257,52 @@ def test_fourier_blocks_hermitian_and_conjugate_pairs():
         assert np.max(np.abs(Hb[jm] - np.conj(Hb[j]))) < 1e-12
 
 
+def test_periodic_matrix_is_multilevel_block_circulant():
+    """Lemma 3.4: on a periodic lattice H and S are symmetric three-level
+    block circulant -- the block of cells (k + d, m + d) (componentwise mod
+    L) equals that of (k, m) for every shift d -- so A_{L-k} = A_k^T."""
+    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    H, S = dense.build(p)
+    m0 = p.m0
+    cells = list(np.ndindex(*p.L))
+    kb = lambda c: (c[0] * p.L[1] + c[1]) * p.L[2] + c[2]
+    for M in (H, S):
+        scale = np.max(np.abs(M))
+        assert np.max(np.abs(M - M.T)) <= 1e-14 * scale
+        blk = lambda a, b: M[kb(a) * m0:(kb(a) + 1) * m0, kb(b) * m0:(kb(b) + 1) * m0]
+        for k in cells:
+            for d in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 1, 3)]:
+                k2 = tuple((np.array(k) + d) % p.L)
+                m2 = tuple(np.array(d) % p.L)
+                assert np.max(np.abs(blk(k2, m2) - blk(k, (0, 0, 0)))) <= 1e-13 * scale
+        gen = blocks.generators_from_dense(p, M)
+        for k in cells:
+            km = tuple((-np.array(k)) % p.L)
+            assert np.max(np.abs(gen[kb(km)] - gen[kb(k)].T)) <= 1e-13 * scale
+
+
+def test_block_band_follows_the_support_overlap():
+    """Sec. 2.3 (the overlap constant L0): a block is nonzero exactly when the
+    two cells' basis supports (plus the one-node reach of the P1 stencils)
+    meet; with support half-width r_cut the band has 2 L0 + 1 blocks per
+    interior row, L0 = floor((2 r_cut + h) / b0)."""
+    n0, L = 5, 16
+    exps = np.array([2.0, 3.0])
+    p = _cases.with_table(li.Problem(L=(L, 1, 1), periodic=(0, 0, 0), N=(L * n0 + 20, 12, 12), n0=n0,
+                                     b0=2.0, Z=np.array([1.0]), frac=np.array([[0.5, 0.5, 0.5]]),
+                                     exps=exps, ang=np.zeros(2, int), centre=np.zeros(2, int), R=8))
+    rcut = math.sqrt(math.log(1.0 / p.eps_support) / exps.min())
+    L0 = int((2 * rcut + p.h) // p.b0)
+    assert 0.1 < (2 * rcut + p.h) / p.b0 - L0 < 0.9        # not at a rounding edge
+    H, S = dense.build(p)
+    m0 = p.m0
+    for M in (H, S):
+        for k in range(L):
+            for m in range(L):
+                nz = np.any(M[k * m0:(k + 1) * m0, m * m0:(m + 1) * m0] != 0.0)
+                assert nz == (abs(k - m) <= L0), (k, m)
+
+
 # ---------------- box chains: Toeplitz interior, boundary defect ----------------
 
 def test_box_chain_toeplitz_interior_and_wall_defect():
