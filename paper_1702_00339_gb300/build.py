@@ -30,8 +30,8 @@ def _run(cmd):
 def _stale(obj, src):
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"),
-            os.path.join(os.path.dirname(PKG), "include", "fock.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    deps = [src, *headers, os.path.join(os.path.dirname(PKG), "include", "fock.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -3,10 +3,15 @@
 // Requests are deep-copied at submission, checked and sized (the same
 // planner that lays out a batch's device slab), and queued FIFO.  `slots`
 // worker threads each own a private context (its own CUDA stream); a free
-// worker admits the queue's head requests while they fit the server's HBM
-// budget (bytes reserved by the batches already on the device are
-// subtracted) and the batch cap, solves them as one batch, publishes the
-// per-request results and releases its reservation.  Requests arriving
+// worker admits the queue's head request and, in queue order, the following
+// requests of the same kind -- periodic (one pass: Fourier blocks) or
+// structured (an iteration: box chains and defects) -- while they fit the
+// server's HBM budget (bytes reserved by the batches already on the device
+// are subtracted) and the batch cap, solves them as one batch, publishes
+// the per-request results and releases its reservation.  A batch ends with
+// its slowest problem, so one-pass problems are not batched with iterated
+// ones; the head of the queue is always admitted first, so neither kind
+// waits more than the batches ahead of it.  Requests arriving
 // while batches run are admitted by the next free worker, so their work
 // overlaps on the device with the batches in flight.  Batch slabs come from
 // one stream-ordered memory pool owned by the server (no device-wide
@@ -28,6 +33,7 @@
 #include <vector>
 
 #include "../../include/fock.h"
+#include "admission.h"
 
 namespace fock {
 int detail_estimate(const fock_problem& p, size_t* bytes, int* n_evals, std::string& why);
@@ -131,14 +137,12 @@ void fock_server::worker(int slot) {
       std::unique_lock<std::mutex> lk(m);
       for (;;) {
         if (!pending.empty()) {
-          // FIFO admission: the head requests that fit the free budget
-          while (!pending.empty() && (int)batch.size() < cfg.max_batch) {
-            Req* r = pending.front();
-            if (reserved + bytes + r->bytes > cfg.hbm_budget_bytes) break;
-            batch.push_back(r);
-            bytes += r->bytes;
-            pending.pop_front();
-          }
+          // the head request, then the later ones of its kind in queue order,
+          // up to the first of that kind that does not fit the free budget
+          const size_t free_bytes = cfg.hbm_budget_bytes > reserved ? cfg.hbm_budget_bytes - reserved : 0;
+          batch = fock::admit_batch(
+              pending, [](const Req* r) { return structured(r->op.p); },
+              [](const Req* r) { return r->bytes; }, free_bytes, cfg.max_batch, &bytes);
           if (!batch.empty()) break;
         } else if (stopping) {
           return;
