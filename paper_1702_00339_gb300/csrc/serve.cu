@@ -160,6 +160,8 @@ void fock_server::worker(int slot) {
         r->batch_id = bid;
         r->batch_size = (int)batch.size();
       }
+      // requests left behind (the other kind, or beyond the cap): wake an idle slot
+      if (!pending.empty()) cv_work.notify_one();
     }
     const int n = (int)batch.size();
     std::vector<fock_problem> probs(n);
