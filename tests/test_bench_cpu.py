@@ -42,3 +42,14 @@ def test_work_models_scale_with_iterations_and_batch():
     kb = box.k_eig + max(2, box.k_eig // 4)
     one = bench.fp64_flops_per_step([box], [{"iters": 1, "M": 128, "D": 20}])
     assert one["k_band_solve"] == 4 * box.L[0] * 21 * 64 * kb
+
+
+def test_latency_summary_per_kind():
+    import bench
+    lat = [1.0, 2.0, 3.0, 100.0, 200.0]
+    kind = [False, False, False, True, True]
+    s = bench.latency_summary(lat, kind)
+    assert s["p50_ms"] == 3.0 and s["p50_ms_periodic"] == 2.0 and s["p50_ms_structured"] == 150.0
+    assert s["n_periodic"] == 3 and s["n_structured"] == 2
+    only = bench.latency_summary([5.0, 7.0], [False, False])
+    assert "p50_ms_structured" not in only and only["p99_ms_periodic"] == np.percentile([5.0, 7.0], 99)
