@@ -80,7 +80,22 @@ def latency_summary(lat_ms, structured):
     return out
 
 
-def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plain_s=4.0):
+def _poll_all(srv, tickets, deadline):
+    """Every ticket's result, or TimeoutError once `deadline` (perf_counter
+    seconds) has passed with results outstanding."""
+    out = []
+    for t in tickets:
+        left_ms = int(1000 * (deadline - time.perf_counter()))
+        r = srv.poll(t, timeout_ms=max(left_ms, 1))
+        if r is None:
+            raise TimeoutError(f"{len(tickets) - len(out)} of {len(tickets)} serving results "
+                               "outstanding at the deadline")
+        out.append(r)
+    return out
+
+
+def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plain_s=4.0,
+                limit_s=300.0):
     """Continuous-batching leg: capacity from a burst of n_warm requests, then
     n_stream requests with Poisson arrivals at 80 % of that capacity; latency
     = done - submit per request (server clock).  Also the plain per-lattice
@@ -89,7 +104,7 @@ def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plai
     warm = serving_requests(n_warm, seed=3100)
     t0 = time.perf_counter()
     tk = [srv.submit(p) for p in warm]
-    rw = [srv.poll(t, timeout_ms=600000) for t in tk]
+    rw = _poll_all(srv, tk, t0 + limit_s)
     cap = n_warm / (time.perf_counter() - t0)
     stream = serving_requests(n_stream, seed=3000)
     rate = 0.8 * cap
@@ -103,7 +118,7 @@ def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plai
         if d > 0:
             time.sleep(d)
         tickets.append(srv.submit(p))
-    res = [srv.poll(t, timeout_ms=600000) for t in tickets]
+    res = _poll_all(srv, tickets, time.perf_counter() + limit_s)
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.stop()

@@ -53,3 +53,21 @@ def test_latency_summary_per_kind():
     assert s["n_periodic"] == 3 and s["n_structured"] == 2
     only = bench.latency_summary([5.0, 7.0], [False, False])
     assert "p50_ms_structured" not in only and only["p99_ms_periodic"] == np.percentile([5.0, 7.0], 99)
+
+
+def test_poll_all_deadline():
+    import time
+
+    import bench
+
+    class Srv:
+        def __init__(self, ready):
+            self.ready = ready
+
+        def poll(self, t, timeout_ms):
+            return {"t": t} if t in self.ready else None
+
+    assert bench._poll_all(Srv({1, 2}), [1, 2], time.perf_counter() + 5) == [{"t": 1}, {"t": 2}]
+    import pytest
+    with pytest.raises(TimeoutError):
+        bench._poll_all(Srv({1}), [1, 2], time.perf_counter() + 0.01)
