@@ -127,6 +127,19 @@ int fock_default_range(const fock_problem* p, double* zmin, double* zmax);
  * NULL.  On FOCK_EINVAL writes the reason, NUL-terminated and truncated to
  * why_cap bytes, into `why` (may be NULL). */
 int fock_problem_check(const fock_problem* p, int* kind, int* n_evals, char* why, int why_cap);
+/* The block structure the planner lays out for one problem, on the host
+ * only (no device, no context), as fock_plan_problem_sizes reports it for a
+ * planned batch: *Nb = |L|*m0; box chains and problems with defects
+ * (Remark 3.2, Sec. 2.3): *D = reach of the Toeplitz generators T_d
+ * (|d| <= D), *mcirc = size of the circulant embedding, and the cell pairs
+ * (Ek[e], Em[e]) of the blocks E added to the banded Toeplitz part, sorted
+ * by (row, column), with Ekind[e] = 0 wall block, 1 wrap-around block of a
+ * periodic chain, 2 defect block, 3 wall block stored as the transpose of
+ * its mirror (E(k,m) = E(m,k)^T); at most `cap` entries are written (the
+ * pointers may be NULL), *nbound = their full number.  Periodic problems:
+ * *mcirc = |L|, *D = *nbound = 0.  FOCK_EINVAL for a malformed problem. */
+int fock_problem_layout(const fock_problem* p, int* Nb, int* mcirc, int* D, int* nbound, int* Ek,
+                        int* Em, int* Ekind, int cap);
 
 /* Batched solve (stages (a)+(b) for periodic problems, (a)+(c) for box
  * chains and problems with defects).  nprob problems, outs[nprob].

@@ -1605,6 +1605,19 @@ int detail_estimate(const fock_problem& p, size_t* bytes, int* n_evals, std::str
   return FOCK_OK;
 }
 
+// Host-only planning of one problem (no device): the sizing pass of plan().
+int detail_layout(const fock_problem& p, Batch& B, std::string& why) {
+  B.nprob = 1;
+  B.hp.assign(1, HostProb());
+  B.ap.assign(3, AxisPlan());
+  int rc = validate(p, B.hp[0], why);
+  if (rc) return rc;
+  for (int a = 0; a < 3; ++a) axis_plan(B.hp[0], a, B.ap[a]);
+  Slab S0, U0;
+  plan(B, S0, U0);
+  return FOCK_OK;
+}
+
 fock_ctx* detail_worker_ctx(int device, cudaMemPool_t pool, size_t budget) {
   if (cudaSetDevice(device) != cudaSuccess) return nullptr;
   fock_ctx* c = new fock_ctx();
@@ -1668,6 +1681,29 @@ void fock_destroy(fock_ctx* c) {
 }
 
 const char* fock_last_error(const fock_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int fock_problem_layout(const fock_problem* p, int* Nb, int* mcirc, int* D, int* nbound, int* Ek,
+                        int* Em, int* Ekind, int cap) {
+  if (!p) return FOCK_EINVAL;
+  Batch B;
+  std::string why;
+  const int rc = fock::detail_layout(*p, B, why);
+  if (rc != FOCK_OK) return rc;
+  const HostProb& H = B.hp[0];
+  const Batch::PerProb& Q = B.pp[0];
+  const int ncell = H.L[0] * H.L[1] * H.L[2];
+  if (Nb) *Nb = ncell * H.m0;
+  if (mcirc) *mcirc = H.kind == 1 ? Q.M : ncell;
+  if (D) *D = H.kind == 1 ? Q.D : 0;
+  const int nE = H.kind == 1 ? Q.nE : 0;
+  if (nbound) *nbound = nE;
+  for (int e = 0; e < std::min(nE, cap); ++e) {
+    if (Ek) Ek[e] = Q.Ek[e];
+    if (Em) Em[e] = Q.Em[e];
+    if (Ekind) Ekind[e] = Q.Ekind[e];
+  }
+  return FOCK_OK;
+}
 
 int fock_problem_check(const fock_problem* p, int* kind, int* n_evals, char* why, int why_cap) {
   if (why && why_cap > 0) why[0] = '\0';

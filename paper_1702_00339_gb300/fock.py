@@ -94,6 +94,8 @@ def lib():
                                       P(C.c_double)]
         L.fock_default_range.argtypes = [P(c_problem), P(C.c_double), P(C.c_double)]
         L.fock_problem_check.argtypes = [P(c_problem), P(C.c_int), P(C.c_int), C.c_char_p, C.c_int]
+        L.fock_problem_layout.argtypes = [P(c_problem), P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int),
+                                          P(C.c_int), P(C.c_int), P(C.c_int), C.c_int]
         L.fock_solve.argtypes = [C.c_void_p, C.c_int, P(c_problem), P(c_output), C.c_int]
         L.fock_assemble.argtypes = [C.c_void_p, P(c_problem), P(C.c_void_p)]
         L.fock_blocks_free.argtypes = [C.c_void_p]
@@ -246,6 +248,25 @@ def check_problem(p):
     if rc:
         raise FockError(rc, why.value.decode())
     return {"kind": kind.value, "n_evals": ne.value}
+
+
+def problem_layout(p):
+    """The planner's block structure of one problem, host only
+    (fock_problem_layout): {"Nb", "mcirc", "D", "E": int array (n, 3) of
+    (row cell, column cell, kind)}."""
+    m = _Marshal(p)
+    nb, mc, d, ne = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    rc = lib().fock_problem_layout(C.byref(m.s), C.byref(nb), C.byref(mc), C.byref(d), C.byref(ne),
+                                   None, None, None, 0)
+    if rc:
+        raise FockError(rc, "fock_problem_layout")
+    n = ne.value
+    ek, em, kd = (np.zeros(max(n, 1), np.int32) for _ in range(3))
+    rc = lib().fock_problem_layout(C.byref(m.s), None, None, None, None, _ip(ek), _ip(em), _ip(kd), n)
+    if rc:
+        raise FockError(rc, "fock_problem_layout")
+    return {"Nb": nb.value, "mcirc": mc.value, "D": d.value,
+            "E": np.stack([ek[:n], em[:n], kd[:n]], axis=1)}
 
 
 class Context:
