@@ -119,6 +119,51 @@ def test_periodic_chain_with_defect_maps(fock):
                 assert np.max(np.abs(_blk(X, m0, k, m) - ref)) <= 1e-12 * scale, (k, m)
 
 
+def _check_ring(fock, p):
+    """Periodic chain with defects: unlisted blocks are the ring generators
+    inside the band or zero; defect-changed blocks carry defect entries."""
+    base = dataclasses.replace(p, defects=[])
+    lay = fock.problem_layout(p)
+    m0, L, D = p.m0, p.L[0], lay["D"]
+    listed = {(int(k), int(m)) for k, m, _ in lay["E"]}
+    Hp, Sp = dense.build(base)
+    Dm = dense.defect_matrix(p)
+    for X, Xp in ((Hp - Dm, Hp), (Sp, Sp)):
+        scale = np.max(np.abs(X))
+        for k in range(L):
+            for m in range(L):
+                if (k, m) in listed:
+                    continue
+                ref = _blk(Xp, m0, (k - m) % L, 0) if abs(k - m) <= D else np.zeros((m0, m0))
+                assert np.max(np.abs(_blk(X, m0, k, m) - ref)) <= 1e-12 * scale, (k, m)
+    dblocks = {(int(k), int(m)) for k, m, c in lay["E"] if c == 2}
+    changed = {(k, m) for k in range(L) for m in range(L) if np.any(_blk(Dm, m0, k, m) != 0.0)}
+    assert changed <= dblocks
+
+
+# chains of the serving mix (16 nodes per cell, box or periodic, 0-4 defects), with the
+# cross-section reduced to 16 x 16 nodes (the block maps depend on the chain axis only);
+# box chains long enough to have a cell that no wall reaches, which gives the generators
+SERVING_CHAINS = [27, 34, 49, 151, 167, 174, 185, 192, 200, 222]
+
+
+@pytest.mark.parametrize("rid", SERVING_CHAINS)
+def test_serving_mix_chain_maps(fock, rid):
+    p = li.serving_stream(rid + 1, seed=3000)[rid]
+    q = _cases.with_table(dataclasses.replace(p, N=(p.N[0], 16, 16)))
+    q.k_eig = p.k_eig
+    if q.periodic[0]:
+        _check_ring(fock, q)
+    else:
+        lay = _check_box(fock, q, dataclasses.replace(q, defects=[]) if q.defects else None)
+        if q.defects:
+            Dm = dense.defect_matrix(q)
+            m0, L = q.m0, q.L[0]
+            dblocks = {(int(k), int(m)) for k, m, c in lay["E"] if c == 2}
+            changed = {(k, m) for k in range(L) for m in range(L) if np.any(_blk(Dm, m0, k, m) != 0.0)}
+            assert changed <= dblocks
+
+
 def test_periodic_lattice_layout(fock):
     p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
     lay = fock.problem_layout(p)
