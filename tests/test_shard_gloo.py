@@ -1,5 +1,5 @@
 """Multi-rank path of the periodic Fourier-block solve on CPU (gloo,
-world size 2): each rank solves its contiguous Fourier-index range, the
+world sizes 2 and 3, ranges of unequal and zero length): each rank solves its contiguous Fourier-index range, the
 sorted parts are gathered and merged, and the result equals the unsharded
 spectrum (values and block map).  Per-rank compute is the oracle's block
 route here (no GPU); on GPUs it is fock_circulant_eig_range."""
@@ -26,14 +26,22 @@ def test_merge_orders_by_value_then_block():
     assert ev.tolist() == [1.0, 1.0, 1.5, 2.0, np.inf] and blk.tolist() == [0, 3, 3, 0, 0]
 
 
-def _worker(rank, world, port, out):
+def _problem(which):
+    from tests import _cases
+    if which == "3d":
+        return _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    if which == "chain5":
+        return _cases.periodic_chain_small(L=5, n0=6, n_perp=12, m0=4, R=8)
+    return _cases.periodic_chain_small(L=2, n0=6, n_perp=12, m0=4, R=8)      # "chain2"
+
+
+def _worker(rank, world, port, out, which="3d"):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from oracle import blocks, dense
-    from tests import _cases
-    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    p = _problem(which)
     H, S = dense.build(p)
     _, per, _ = blocks.periodic_eigs(p, H, S)
 
@@ -50,14 +58,16 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_rank_gloo_merge_equals_unsharded(tmp_path):
+@pytest.mark.parametrize("world,which", [(2, "3d"), (3, "chain5"), (3, "chain2")])
+def test_gloo_merge_equals_unsharded(tmp_path, world, which):
+    """Two ranks on a 3D lattice; three ranks on 5 blocks (ranges of 2, 2, 1)
+    and on 2 blocks (one rank with an empty range)."""
     out = str(tmp_path / "merged.npy")
-    port = 29500 + os.getpid() % 1000
-    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    port = 29500 + (os.getpid() * 7 + 31 * world + len(which)) % 2000
+    mp.spawn(_worker, args=(world, port, out, which), nprocs=world, join=True)
     merged = np.load(out)
     from oracle import blocks, dense
-    from tests import _cases
-    p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
+    p = _problem(which)
     H, S = dense.build(p)
     ev, per, _ = blocks.periodic_eigs(p, H, S)
     bl = np.concatenate([[j] * p.m0 for j in range(p.ncell)])
