@@ -526,3 +526,27 @@ def test_box_and_periodic_chains_relax_to_each_other():
     assert all(d > 0 for d in d_low)                     # confinement raises the band bottom
     assert d_low[1] < d_low[0] / 2.5 and d_low[2] < d_low[1] / 2.5
     assert d_avg[1] < d_avg[0] / 1.6 and d_avg[2] < d_avg[1] / 1.6
+
+
+def test_chain_lattice_sum_diverges_like_the_harmonic_series():
+    """The lattice sum of a charged chain converges only conditionally (Sec.
+    2.3, Eq. 2.13): on a periodic chain of protons the window of the central
+    cell grows with L, and doubling L adds the charges between L/2 and L
+    cells away on both sides, which lowers the band bottom by
+    (2 Z / b0) ln 2 (the harmonic series) up to the discretisation error of
+    the P0 potential against the P1 mass, O(h^2)."""
+    base = li.config1()
+    target = 2.0 * math.log(2.0) / 2.0
+    excess = []
+    for n0 in (8, 16, 32):
+        low = []
+        for L in (32, 64):
+            p = _cases.with_table(li.Problem(
+                L=(L, 1, 1), periodic=(1, 0, 0), N=(L * n0, 2 * n0, 2 * n0), n0=n0, b0=2.0, Z=base.Z,
+                frac=base.frac, exps=base.exps, ang=base.ang, centre=base.centre, R=24))
+            H, S = dense.build(p)
+            low.append(blocks.periodic_eigs(p, H, S)[0][0])
+        excess.append((low[0] - low[1]) - target)
+    assert all(e > 0 for e in excess)
+    assert excess[1] < excess[0] / 3.5 and excess[2] < excess[1] / 3.5      # O(h^2)
+    assert excess[2] < 1e-3 * target * 2
