@@ -486,13 +486,14 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof, "clocks": clk, "mixed": mixed,
                 "box_iters": [int(o["iters"]) for o in outs[:args.batch]][:8],
                 "statuses_nonzero": len(bad)}
-        # the side legs never cost the step's line: a failure is reported in place
-        if not args.no_serve:
+        # the side legs (one GPU, N = 1 only) never cost the step's line: a failure
+        # is reported in place
+        if not args.no_serve and world == 1:
             try:
                 line["serving"] = serving_run(fock, dev, n_stream=args.serve_requests)
             except Exception as e:   # noqa: BLE001
                 line["serving"] = {"error": f"{type(e).__name__}: {e}"}
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
             try:
                 line["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
             except Exception as e:   # noqa: BLE001
