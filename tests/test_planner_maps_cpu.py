@@ -164,6 +164,18 @@ def test_serving_mix_chain_maps(fock, rid):
             assert changed <= dblocks
 
 
+def test_short_periodic_chain_is_its_whole_circulant(fock):
+    """A ring too short for the band and the corners to separate is planned
+    as its whole circulant written as a Toeplitz matrix (D = L - 1): no
+    wrap-around entries, only the defect blocks."""
+    base = _cases.periodic_chain_small(L=6, n0=6, n_perp=14, m0=4, R=12)
+    p = dataclasses.replace(base, defects=[li.Defect((1, 0, 0), 0, 0.0)])
+    p.k_eig = 4
+    lay = fock.problem_layout(p)
+    assert lay["D"] == p.L[0] - 1 and set(lay["E"][:, 2]) == {2}
+    _check_ring(fock, p)
+
+
 def test_periodic_lattice_layout(fock):
     p = _cases.periodic_3d_small(L=(3, 2, 4), n0=4, R=8)
     lay = fock.problem_layout(p)
