@@ -216,9 +216,11 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": dict(config_dict(npairs, 1), workload="CPU oracle on " + config_dict(npairs, 1)["workload"]),
+            "config": config_dict(args.batch, world),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{npairs} box + {npairs} periodic requests per step"},
+                             "sample": f"{npairs} box + {npairs} periodic requests of the workload per step "
+                                       f"(dense FP64 Galerkin matrices by 3D grid contraction + LAPACK eigh), "
+                                       f"{args.steps} steps after {args.warmup} warm-up"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
