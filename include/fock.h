@@ -144,14 +144,20 @@ int fock_problem_layout(const fock_problem* p, int* Nb, int* mcirc, int* D, int*
 /* Batched solve (stages (a)+(b) for periodic problems, (a)+(c) for box
  * chains and problems with defects).  nprob problems, outs[nprob].
  * Evals pointers are device pointers when outputs_on_device != 0.
- * Returns the first non-zero per-problem status, or FOCK_OK. */
+ * Returns the first non-zero per-problem status, or FOCK_OK.  Errors:
+ * FOCK_EINVAL (no problems, a malformed problem: see fock_problem_check),
+ * FOCK_ENOMEM (the batch exceeds the context's budget), FOCK_ECUDA; per
+ * problem, out->status FOCK_ENOCONV when the block iteration hit its cap
+ * (best estimates written). */
 int fock_solve(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_output* outs,
                int outputs_on_device);
 
 /* Stage (a) for one problem: separable rank-R assembly of the generator
  * blocks (Lemma 2.1, Prop. 2.2, Lemma 3.4).  The handle keeps the per-axis
  * factor tensors and (box) the Toeplitz generators, the embedding Fourier
- * blocks and the boundary perturbation resident on the device. */
+ * blocks and the boundary perturbation resident on the device; it is owned
+ * by the caller and freed by fock_blocks_free before fock_destroy.
+ * Errors: FOCK_EINVAL, FOCK_ENOMEM, FOCK_ECUDA. */
 int fock_assemble(fock_ctx* ctx, const fock_problem* p, fock_blocks** out);
 void fock_blocks_free(fock_blocks* b);
 
@@ -181,9 +187,12 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
                              int* block_of);
 
 /* y = H x or y = S x (which = FOCK_OP_H / FOCK_OP_S) for an assembled box
- * chain or periodic problem, by the block-circulant embedding FFT matvec
- * plus the boundary/defect blocks (Remark 3.2, Sec. 2.3).  x, y: N_b x nvec,
- * column-major; device pointers when on_device != 0, else host. */
+ * chain or problem with defects, by the block-circulant embedding FFT
+ * matvec plus the boundary/defect blocks (Remark 3.2, Sec. 2.3).  x, y:
+ * N_b x nvec, column-major; device pointers when on_device != 0, else
+ * host.  Errors: FOCK_EINVAL (a periodic handle -- its operator is applied
+ * through its Fourier blocks -- null pointers, `which`, nvec < 1),
+ * FOCK_ENOMEM, FOCK_ECUDA. */
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
                          double* y, int nvec, int on_device);
 
@@ -208,7 +217,9 @@ int fock_toeplitz_matvec_noalloc(fock_ctx* ctx, const fock_blocks* b, int which,
  * (Sec. 2.3, "structured iteration on subspace"; LOBPCG with the embedding's
  * shifted inverse as preconditioner).  evals[k] host; evecs[N_b x k]
  * (host, column-major, S-orthonormal) or NULL; iters out.  Returns
- * FOCK_ENOCONV (with the best estimates written) when maxit is reached. */
+ * FOCK_ENOCONV (with the best estimates written: Ritz values, each above
+ * the eigenvalue it approximates) when maxit is reached; FOCK_EINVAL for a
+ * periodic handle or k above the problem's k_eig; FOCK_ECUDA. */
 int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int maxit,
                  double* evals, double* evecs, int* iters);
 
@@ -247,10 +258,11 @@ int fock_profile_read(fock_ctx* ctx, int cap, char* names, int* launches, double
  * `slots` worker threads, each with a private CUDA stream, and one
  * stream-ordered device memory pool.  Submitted problems are deep-copied,
  * validated and sized, and queued in arrival order; a free worker admits
- * the queue's head problems while the device bytes of the batches already
- * in flight plus theirs stay within hbm_budget_bytes (and at most
- * max_batch of them), solves them as one batch (fock_solve's path) and
- * publishes one result per ticket.  Problems that arrive while batches
+ * the queue's head problem and, in queue order, the later problems of the
+ * same kind (periodic: one pass; box chains and defects: an iteration)
+ * while the device bytes of the batches already in flight plus theirs stay
+ * within hbm_budget_bytes (and at most max_batch of them), solves them as
+ * one batch (fock_solve's path) and publishes one result per ticket.  Problems that arrive while batches
  * run are admitted by the next free worker, so their kernels overlap with
  * the batches in flight.  Each result equals the result of solving that
  * problem alone (per-problem reduction orders and start vectors are fixed).

@@ -2006,7 +2006,7 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
 
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x, double* y,
                          int nvec, int on_device) {
-  if (!ctx || !b || !x || !y || nvec <= 0) return FOCK_EINVAL;
+  if (!ctx || !b || !x || !y || nvec <= 0 || (which != FOCK_OP_H && which != FOCK_OP_S)) return FOCK_EINVAL;
   const Batch& B = b->B;
   const HostProb& H = B.hp[0];
   if (H.kind != 1) return set_err(ctx, FOCK_EINVAL, "matvec needs a box chain");
