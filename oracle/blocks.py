@@ -14,7 +14,7 @@ FFT matvec.
 import numpy as np
 import scipy.linalg
 
-from . import dense
+from . import dense, grid
 
 
 def generators_from_dense(p, M):
@@ -71,7 +71,6 @@ def generator_block(p, kcell, forms=None, slab=None, mcell=(0, 0, 0)):
     G1[i1,m1,nu] G2.. G3.. P(i), S and A from the 1D quadratic forms.  With
     m = 0 it is the generator A_k of a periodic problem.  For problems too
     large for the dense route."""
-    from . import grid
     slab_of, slabs = slab if slab is not None else grid.potential_slabs(p)
     k1, k2, k3 = kcell
     m1, m2, m3 = mcell
@@ -118,10 +117,32 @@ def generator_block(p, kcell, forms=None, slab=None, mcell=(0, 0, 0)):
     return 0.5 * A - V, S
 
 
-def fourier_block_from_generators(p, Hk, Sk, jcell):
+def generators_direct(p):
+    """Generators A_k of H and S for every lattice offset k of a defect-free
+    periodic problem (the first block column), without the dense matrix: V
+    by the 3D grid contraction restricted to column cell 0, S and A from the
+    1D quadratic forms (Sec. 2.4).  Shapes (|L|, m0, m0) in kbar order."""
+    assert not p.defects and all(p.periodic[a] or p.L[a] == 1 for a in range(3))
+    forms = dense.axis_forms(p)
+    slab_of, slabs = grid.potential_slabs(p)
+    V = dense._contract(p, [f[0] for f in forms], slab_of, slabs, col_cells=0)
+    V = V.reshape(p.ncell, p.m0, p.m0)
+    ks, _ = dense._index(p)
+    kb = np.arange(p.ncell)
+    k1 = kb // (p.L[1] * p.L[2])
+    k2 = (kb // p.L[2]) % p.L[1]
+    k3 = kb % p.L[2]
+    sl = [forms[a][1][kk][:, :, 0, :] for a, kk in enumerate((k1, k2, k3))]
+    al = [forms[a][2][kk][:, :, 0, :] for a, kk in enumerate((k1, k2, k3))]
+    S = sl[0] * sl[1] * sl[2]
+    A = al[0] * sl[1] * sl[2] + sl[0] * al[1] * sl[2] + sl[0] * sl[1] * al[2]
+    return 0.5 * A - V, S
+
+
+def fourier_block_from_generators(p, Hk, Sk, jcell, tau=None):
     """Direct DFT (explicit sum over all lattice offsets) of given generators
-    at one Fourier index, and the block's eigenvalues after canonical
-    orthogonalisation (canonical_eigs)."""
+    at one Fourier index, and the block's eigenvalues under the dependency
+    rule (block_pencil; tau defaults to null_threshold(p))."""
     L1, L2, L3 = p.L
     j1, j2, j3 = jcell
     k = np.arange(p.ncell)
@@ -131,64 +152,133 @@ def fourier_block_from_generators(p, Hk, Sk, jcell):
     w = np.exp(-2j * np.pi * (j1 * k1 / L1 + j2 * k2 / L2 + j3 * k3 / L3))
     Hb = np.tensordot(w, Hk, axes=(0, 0))
     Sb = np.tensordot(w, Sk, axes=(0, 0))
-    return Hb, Sb, canonical_eigs(Hb, Sb)
+    if tau is None:
+        tau = null_threshold(p)
+    return Hb, Sb, block_pencil(Hb, Sb, tau)[0]
 
 
-# Canonical (Loewdin) orthogonalisation.  A Galerkin basis of Gaussians can
-# be numerically dependent (diffuse functions on a dense lattice; several
-# close exponents on one centre): the overlap then has eigenvalues at the
-# rounding level of its own assembly, and the pencil's eigenvalues in those
-# directions are not determined by the data.  The reading used here removes
-# from the variational space every eigen-direction of the overlap whose
-# eigenvalue is at most CANON_TAU times the largest eigenvalue of the same
-# matrix; on a full-rank, well-conditioned basis it is an exact change of
-# basis and changes nothing.
-CANON_TAU = 1e-8
+# ---- numerically singular overlap directions (reading G16) ----
+#
+# The problem is the Galerkin pencil H C = S C Lambda (Eqs. 2.4-2.5,
+# Eqs. 3.11-3.12, Prop. A.1).  A Gaussian basis can be dependent to the
+# rounding level of the overlap's own entries (several close exponents on one
+# centre; diffuse functions on a dense lattice): along such a direction the
+# computed overlap is zero or negative within its rounding, and the pencil's
+# value there is not determined by the data.  Only those directions are
+# removed.  The rounding level is set by the magnitudes that enter each
+# overlap entry: B[mu, nu] = sum over lattice offsets d of |S_d[mu, nu]| bounds
+# every entry of every Fourier block and every row of the lattice overlap, and
+# a direction whose overlap eigenvalue is at most
+#     tau = SINGULAR_C * u * ||B||_F        (u = 2^-53)
+# is numerically singular (an m0 x m0 block formed from entries that each
+# carry a few units of rounding relative to B has eigenvalues uncertain by
+# about m0 times that; SINGULAR_C = 64 covers m0 <= 32).  Where nothing lies
+# at or below tau the pencil is solved exactly as stated (LAPACK).
+U64 = 2.0 ** -53
+SINGULAR_C = 64
 
 
-def lowdin_basis(S, tau=CANON_TAU):
-    """X = Q_K diag(s_K)^-1/2 for the eigen-directions of the Hermitian S with
-    s > tau * max(s) (eigendecomposition by LAPACK); returns (X, s)."""
-    s, Q = np.linalg.eigh(S)
-    keep = s > tau * s.max()
-    return Q[:, keep] / np.sqrt(s[keep]), s
+def _wall_free_chain_forms(p):
+    """1D mass forms s[d] (block row cell d, column cell 0) of axis 0 on a node
+    line with no wall within reach of the functions (what a cell far from the
+    ends of a box chain sees), for every offset d with a non-zero form."""
+    rmax = np.sqrt(np.log(1.0 / p.eps_support) / np.min(p.exps))
+    pe = int(np.ceil(rmax / p.h)) + 2
+    reach = int(np.ceil((2 * pe) / p.n0)) + 1
+    Lq = 2 * reach + 1
+    q = type(p)(L=(Lq, 1, 1), periodic=(0, 0, 0), N=(Lq * p.n0 + 2 * pe, 3, 3), n0=p.n0,
+                b0=p.b0, Z=p.Z, frac=p.frac, exps=p.exps, ang=p.ang, centre=p.centre, R=p.R,
+                eps_support=p.eps_support)
+    G = grid.basis_axis(q, 0)
+    N, L, m0 = G.shape
+    S1, _ = dense.fem_1d(N, q.h, False)
+    Gf = G.reshape(N, L * m0)
+    s = (Gf.T @ S1 @ Gf).reshape(L, m0, L, m0)
+    return [s[c, :, reach, :] for c in range(L)]
 
 
-def canonical(Hb, Sb, tau=CANON_TAU):
-    """Eigenpairs of a Hermitian pencil block on the kept directions:
-    C = X^H H X (X from lowdin_basis), C y = lambda y, eigenvectors X y in
-    the original coordinates.  Returns (eigenvalues ascending followed by one
-    +inf per removed direction, eigenvectors (m, r), condition number of the
-    kept part of S)."""
-    X, s = lowdin_basis(Sb, tau)
-    C = X.conj().T @ Hb @ X
-    ev, Y = np.linalg.eigh(0.5 * (C + C.conj().T))
-    r = X.shape[1]
-    kept = s[s > tau * s.max()]
-    kappa = float(kept.max() / kept.min()) if r else 1.0
-    return np.concatenate([ev, np.full(Sb.shape[0] - r, np.inf)]), X @ Y, kappa
+def overlap_scale(p):
+    """B = sum over lattice offsets of |S_offset| (m0 x m0, entrywise), from
+    the 1D mass forms of the three axes (the overlap blocks are Hadamard
+    products of per-axis forms, Lemma 3.4, so the sum factorises): periodic
+    axis: the ring forms of the L offsets; Dirichlet axis of one cell: its
+    form with itself; Dirichlet chain axis: the wall-free forms of every
+    offset (the Toeplitz generators of Remark 3.2)."""
+    forms = dense.axis_forms(p)
+    B = np.ones((p.m0, p.m0))
+    for ax in range(3):
+        _, s, _ = forms[ax]
+        if p.periodic[ax] or p.L[ax] == 1:
+            acc = np.sum(np.abs(s[:, :, 0, :]), axis=0)
+        else:
+            acc = np.sum(np.abs(np.stack(_wall_free_chain_forms(p))), axis=0)
+        B = B * acc
+    return B
 
 
-def canonical_eigs(Hb, Sb, tau=CANON_TAU):
-    """Eigenvalues of canonical(): the kept spectrum ascending, then +inf."""
-    return canonical(Hb, Sb, tau)[0]
+def null_threshold(p):
+    """tau = SINGULAR_C u ||B||_F (see above)."""
+    return SINGULAR_C * U64 * float(np.linalg.norm(overlap_scale(p)))
 
 
-def periodic_eigs(p, H=None, S=None, tau=CANON_TAU):
-    """The periodic problem's spectrum under canonical orthogonalisation per
-    Fourier block (Prop. A.1): (all eigenvalues sorted, +inf last; per-block
-    eigenvalues (|L|, m0); per-block kept-overlap condition numbers)."""
+def block_pencil(Hb, Sb, tau, flip=()):
+    """Eigenpairs of one Hermitian pencil (Hb, Sb): eigenvalues ascending,
+    then one +inf per removed direction; eigenvectors (m, r), Sb-orthonormal;
+    r = number kept.  Directions of Sb with eigenvalue <= tau are removed:
+    with none, LAPACK's generalized Hermitian eigensolver on the pencil as it
+    stands; else the same on its restriction to the kept eigenvectors Q_K of
+    Sb (Hr = Q_K^H Hb Q_K, Sr = Q_K^H Sb Q_K), vectors Q_K y.  `flip` lists
+    indices (into the ascending eigenvalues of Sb) whose kept / removed
+    decision is reversed (the variants of a direction near the cut)."""
+    w, Q = np.linalg.eigh(Sb)
+    keep = w > tau
+    for i in flip:
+        keep[i] = not keep[i]
+    m = Sb.shape[0]
+    if keep.all():
+        ev, V = scipy.linalg.eigh(Hb, Sb)
+        return ev, V, m
+    Qk = Q[:, keep]
+    Hr = Qk.conj().T @ Hb @ Qk
+    Sr = Qk.conj().T @ Sb @ Qk
+    r = Qk.shape[1]
+    if r == 0:
+        return np.full(m, np.inf), np.zeros((m, 0), Hb.dtype), 0
+    ev, Y = scipy.linalg.eigh(0.5 * (Hr + Hr.conj().T), 0.5 * (Sr + Sr.conj().T))
+    return np.concatenate([ev, np.full(m - r, np.inf)]), Qk @ Y, r
+
+
+def block_eigs_rule(Hb, Sb, tau):
+    """Eigenvalues of block_pencil (kept spectrum ascending, then +inf)."""
+    return block_pencil(Hb, Sb, tau)[0]
+
+
+def ambiguous(w, tau, band=4.0):
+    """Indices of overlap eigenvalues w in (tau / band, band tau]: directions
+    near the cut whose kept / removed decision rounding can flip; their
+    pencil values are undetermined, and either decision is a correct reading."""
+    idx = np.nonzero((w > tau / band) & (w <= tau * band))[0]
+    return idx[np.argsort(np.abs(np.log(w[idx] / tau)))]   # nearest the cut first
+
+
+def periodic_fourier_blocks(p, H=None, S=None):
+    """(Hbar_j, Sbar_j) for every Fourier index by the direct DFT of the dense
+    matrices' generators (Lemma 3.1, Eq. A.3)."""
     if H is None:
         H, S = dense.build(p)
-    Hb = fourier_blocks(p, generators_from_dense(p, H))
-    Sb = fourier_blocks(p, generators_from_dense(p, S))
-    per, kap = [], []
-    for j in range(p.ncell):
-        ev, _, kappa = canonical(Hb[j], Sb[j], tau)
-        per.append(ev)
-        kap.append(kappa)
-    per = np.stack(per)
-    return np.sort(per.ravel()), per, np.array(kap)
+    return (fourier_blocks(p, generators_from_dense(p, H)),
+            fourier_blocks(p, generators_from_dense(p, S)))
+
+
+def periodic_eigs(p, H=None, S=None, tau=None):
+    """The periodic problem's spectrum through its Fourier blocks (Prop. A.1)
+    under the dependency rule: (all eigenvalues sorted, +inf last; per-block
+    eigenvalues (|L|, m0))."""
+    Hb, Sb = periodic_fourier_blocks(p, H, S)
+    if tau is None:
+        tau = null_threshold(p)
+    per = np.stack([block_pencil(Hb[j], Sb[j], tau)[0] for j in range(p.ncell)])
+    return np.sort(per.ravel()), per
 
 
 def bloch_phases(p, jbar):
@@ -211,20 +301,18 @@ def bloch_phases(p, jbar):
     return ph / np.sqrt(p.ncell)
 
 
-def periodic_eigvecs(p, H=None, S=None, tau=CANON_TAU):
+def periodic_eigvecs(p, H=None, S=None, tau=None):
     """Eigenpairs of a periodic problem through its Fourier blocks: each
-    block's canonical eigenpairs (kept directions only), back-transformed to
-    the lattice by bloch_phases.  Returns (eigenvalues ascending, complex
-    eigenvectors (N_b, n) in the basis order a = kbar*m0 + mu, Fourier index
-    of each); the vectors are S-orthonormal."""
-    if H is None:
-        H, S = dense.build(p)
-    Hb = fourier_blocks(p, generators_from_dense(p, H))
-    Sb = fourier_blocks(p, generators_from_dense(p, S))
+    block's eigenpairs under the dependency rule (kept directions only),
+    back-transformed to the lattice by bloch_phases.  Returns (eigenvalues
+    ascending, complex eigenvectors (N_b, n) in the basis order
+    a = kbar*m0 + mu, Fourier index of each); the vectors are S-orthonormal."""
+    Hb, Sb = periodic_fourier_blocks(p, H, S)
+    if tau is None:
+        tau = null_threshold(p)
     evs, vecs, js = [], [], []
     for j in range(p.ncell):
-        ev, Y, _ = canonical(Hb[j], Sb[j], tau)
-        r = Y.shape[1]
+        ev, Y, r = block_pencil(Hb[j], Sb[j], tau)
         f = bloch_phases(p, j)
         evs.append(ev[:r])
         vecs.append(np.kron(f[:, None], Y))          # u[(k, mu), c] = f[k] Y[mu, c]
@@ -240,7 +328,6 @@ def orbital_on_grid(p, u):
     """Real-space orbital psi(i1, i2, i3) = sum_{k, mu} u[(k, mu)]
     prod_l g_l(k_l, mu)(x_{i_l}) at the grid nodes (the separable GTO factors
     of Sec. 2.4; the P1 interpolant of psi is the Galerkin function)."""
-    from . import grid
     m0 = p.m0
     L1, L2, L3 = p.L
     Gs = [grid.basis_axis(p, a) for a in range(3)]
@@ -270,27 +357,42 @@ def cell_overlap(p):
     return s0[0, :, 0, :] * s1[0, :, 0, :] * s2[0, :, 0, :]
 
 
-def box_basis(p, tau=CANON_TAU):
-    """Block-diagonal change of basis of a chain on the structured path: the
-    canonical cell basis Xc = lowdin_basis(cell_overlap) on every cell,
-    I_L (x) Xc."""
-    Xc, _ = lowdin_basis(cell_overlap(p), tau)
-    return np.kron(np.eye(p.L[0]), Xc), Xc
+def cell_null_directions(p, tau=None):
+    """Eigen-decomposition of the cell overlap: (eigenvalues ascending,
+    eigenvectors, tau).  A cell direction v with eigenvalue <= tau spans, on
+    every cell k, vectors e_k (x) v on which the chain's overlap form is at
+    most tau: numerically singular directions of the lattice overlap."""
+    if tau is None:
+        tau = null_threshold(p)
+    s, Q = np.linalg.eigh(cell_overlap(p))
+    return s, Q, tau
 
 
-def box_eigs(p, H=None, S=None, k=None, tau=CANON_TAU, vectors=False):
+def box_eigs(p, H=None, S=None, k=None, tau=None, vectors=False, flip=()):
     """Lowest k eigenpairs of a chain on the structured path (box, or with
-    defects) in the canonical cell basis:
-    (Xb^T H Xb) y = lambda (Xb^T S Xb) y by LAPACK, eigenvectors Xb y in the
-    original coordinates.  Returns (eigenvalues, vectors or None, reduced S)."""
+    defects).  With no cell direction at or below tau: LAPACK's generalized
+    symmetric eigensolver on (H, S) as they stand.  Else the cell directions
+    at or below tau are removed from every cell: with Q_K the kept cell
+    eigenvectors and Qb = I_L (x) Q_K, the pencil (Qb^T H Qb, Qb^T S Qb) by
+    LAPACK, eigenvectors Qb y.  `flip` lists indices (into the ascending cell
+    eigenvalues) whose kept / removed decision is reversed (the ambiguous
+    variants of a direction near the cut).  Returns (eigenvalues, vectors or
+    None, number of kept cell directions)."""
     if H is None:
         H, S = dense.build(p)
     k = k or p.k_eig
-    Xb, _ = box_basis(p, tau)
-    Hr = Xb.T @ H @ Xb
-    Sr = Xb.T @ S @ Xb
-    ev, Y = scipy.linalg.eigh(Hr, Sr, subset_by_index=[0, k - 1])
-    return ev, (Xb @ Y if vectors else None), Sr
+    s, Q, tau = cell_null_directions(p, tau)
+    keep = s > tau
+    for i in flip:
+        keep[i] = not keep[i]
+    if keep.all():
+        ev, V = scipy.linalg.eigh(H, S, subset_by_index=[0, k - 1])
+        return ev, (V if vectors else None), p.m0
+    Qb = np.kron(np.eye(p.L[0]), Q[:, keep])
+    Hr = Qb.T @ H @ Qb
+    Sr = Qb.T @ S @ Qb
+    ev, Y = scipy.linalg.eigh(0.5 * (Hr + Hr.T), 0.5 * (Sr + Sr.T), subset_by_index=[0, k - 1])
+    return ev, (Qb @ Y if vectors else None), int(keep.sum())
 
 
 def structured(p):
@@ -300,10 +402,10 @@ def structured(p):
 
 
 def solve(p, box_potential="replicated"):
-    """The problem's answer under the canonical-orthogonalisation reading:
-    a periodic problem's whole spectrum (+inf for removed directions), a box
-    chain's or a defect problem's lowest k_eig eigenvalues.  box_potential
-    selects reading R1 or R2 of a box's potential (grid.potential_slabs)."""
+    """The problem's answer under the dependency rule: a periodic problem's
+    whole spectrum (+inf for removed directions), a box chain's or a defect
+    problem's lowest k_eig eigenvalues.  box_potential selects reading R1 or
+    R2 of a box's potential (grid.potential_slabs)."""
     H, S = dense.build(p, box_potential=box_potential)
     if structured(p):
         return box_eigs(p, H, S)[0]

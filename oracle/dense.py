@@ -148,6 +148,58 @@ def defect_matrix(p, forms=None):
     return D
 
 
+def chain_matrices(p, box_potential="replicated"):
+    """Dense H and S of a chain (L2 = L3 = 1, no defects) with the same
+    entries as build(), for chains too long for build()'s cell-pair tensors:
+    the sum over the 3D grid of V_ab = sum_i g_a(i) g_b(i) P(i) is grouped
+    by basis-function pair (mu, nu) -- w_{mu nu}(i1) = sum_{i2, i3} P(i)
+    g2_mu g2_nu g3_mu g3_nu (the transverse axes carry one cell), then
+    V[(k, mu), (m, nu)] = sum_{i1} G1[i1, k, mu] G1[i1, m, nu] w_{mu nu}(i1) --
+    and the 1D quadratic forms of axis 0 apply the P1 stencils to the nodal
+    vectors directly (Sec. 2.4; Lemma 2.1)."""
+    assert p.L[1] == 1 and p.L[2] == 1 and not p.defects
+    L, m0, h = p.L[0], p.m0, p.h
+    G1 = grid.basis_axis(p, 0)                                     # (N1, L, m0)
+    N1 = G1.shape[0]
+    Gf = G1.reshape(N1, L * m0)
+    per = bool(p.periodic[0])
+
+    def shift(u, s):                                              # u[i - s] (zero / wrap)
+        if per:
+            return np.roll(u, s, axis=0)
+        w = np.zeros_like(u)
+        if s == 1:
+            w[1:] = u[:-1]
+        else:
+            w[:-1] = u[1:]
+        return w
+    s0 = (Gf.T @ ((h / 6.0) * (4.0 * Gf + shift(Gf, 1) + shift(Gf, -1)))).reshape(L, m0, L, m0)
+    a0 = (Gf.T @ ((1.0 / h) * (2.0 * Gf - shift(Gf, 1) - shift(Gf, -1)))).reshape(L, m0, L, m0)
+    tr = []
+    for ax in (1, 2):
+        G = grid.basis_axis(p, ax)[:, 0, :]
+        S1, A1 = fem_1d(p.N[ax], h, bool(p.periodic[ax]))
+        tr.append((G, G.T @ S1 @ G, G.T @ A1 @ G))
+    (G2, s1, a1), (G3, s2, a2) = tr
+    S = s0 * (s1 * s2)[None, :, None, :]
+    A = a0 * (s1 * s2)[None, :, None, :] + s0 * (a1 * s2 + s1 * a2)[None, :, None, :]
+    slab_of, slabs = grid.potential_slabs(p, box_potential)
+    GG3 = G3[:, :, None] * G3[:, None, :]                         # (N3, mu, nu)
+    GG2 = G2[:, :, None] * G2[:, None, :]
+    W2 = np.zeros((slabs.shape[0], m0, m0))
+    for s in range(slabs.shape[0]):
+        W3 = np.tensordot(slabs[s], GG3, axes=(1, 0))             # (N2, mu, nu)
+        W2[s] = np.einsum("iab,iab->ab", GG2, W3)
+    w = W2[slab_of]                                               # (N1, mu, nu)
+    V = np.zeros((L, m0, L, m0))
+    for mu in range(m0):
+        for nu in range(m0):
+            V[:, mu, :, nu] = G1[:, :, mu].T @ (w[:, mu, nu, None] * G1[:, :, nu])
+    n = L * m0
+    H = (0.5 * A - V).reshape(n, n)
+    return H, S.reshape(n, n)
+
+
 def build(p, with_parts=False, box_potential="replicated"):
     """Dense (H, S) of problem p (and optionally A, V)."""
     forms = axis_forms(p)

@@ -16,6 +16,19 @@ from oracle import blocks, dense
 from tests import _cases
 
 
+def _kept_kappa(p, S):
+    """Largest condition number of the kept part of a Fourier block's
+    overlap (the rounding scale of an FP64 solve on it)."""
+    Sb = blocks.fourier_blocks(p, blocks.generators_from_dense(p, S))
+    tau = blocks.null_threshold(p)
+    k = 1.0
+    for j in range(p.ncell):
+        w = np.linalg.eigvalsh(Sb[j])
+        w = w[w > tau]
+        if len(w):
+            k = max(k, w.max() / w.min())
+    return k
+
 def _problems():
     yield _cases.periodic_chain_small(L=5, n0=6, n_perp=14, m0=8, R=12)
     yield _cases.periodic_3d_small(L=(3, 2, 2), n0=4, R=8)
@@ -35,10 +48,11 @@ def test_block_eigenvectors_solve_the_lattice_pencil(case):
     # phases times the block's kept overlap directions, orthonormal columns);
     # with nothing removed that space is everything and R itself vanishes
     Sb = blocks.fourier_blocks(p, blocks.generators_from_dense(p, S))
+    tau = blocks.null_threshold(p)
     W = []
     for j in range(p.ncell):
-        X, _ = blocks.lowdin_basis(Sb[j])
-        Q = X / np.linalg.norm(X, axis=0)
+        w, Q = np.linalg.eigh(Sb[j])
+        Q = Q[:, w > tau]                 # the kept overlap directions (orthonormal)
         W.append(np.kron(blocks.bloch_phases(p, j)[:, None], Q) * np.sqrt(p.ncell))
     W = np.concatenate(W, axis=1)
     assert W.shape[1] == len(ev)
@@ -49,9 +63,8 @@ def test_block_eigenvectors_solve_the_lattice_pencil(case):
         assert p.L[1] > 1                 # only the 3D case removes directions here
     # orthonormality to the rounding of an FP64 solve with the kept overlap:
     # about u kappa_K (the m0 = 8 recipe draws close exponents)
-    _, _, kap = blocks.periodic_eigs(p, H, S)
     G = U.conj().T @ S @ U
-    assert np.max(np.abs(G - np.eye(len(ev)))) <= 1e-12 + 16 * _cases.U64 * np.max(kap)
+    assert np.max(np.abs(G - np.eye(len(ev)))) <= 1e-12 + 16 * _cases.U64 * _kept_kappa(p, S)
     # nothing removed and S well conditioned: the dense LAPACK spectrum
     w = np.linalg.eigvalsh(S)
     if len(ev) == p.Nb and w.min() > 1e-6 * w.max():
@@ -111,7 +124,7 @@ def test_orbital_p1_norm_is_the_galerkin_norm():
     p = _cases.periodic_3d_small(L=(3, 2, 2), n0=4, R=8)
     H, S = dense.build(p)
     ev, U, jj = blocks.periodic_eigvecs(p, H, S)
-    tol = 1e-12 + 16 * _cases.U64 * np.max(blocks.periodic_eigs(p, H, S)[2])
+    tol = 1e-12 + 16 * _cases.U64 * _kept_kappa(p, S)
     S1 = [dense.fem_1d(p.N[a], p.h, bool(p.periodic[a]))[0] for a in range(3)]
     for c in (0, 5, len(ev) // 2):
         psi = blocks.orbital_on_grid(p, U[:, c])

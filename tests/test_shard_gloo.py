@@ -43,7 +43,7 @@ def _worker(rank, world, port, out, which="3d"):
     from oracle import blocks, dense
     p = _problem(which)
     H, S = dense.build(p)
-    _, per, _ = blocks.periodic_eigs(p, H, S)
+    _, per = blocks.periodic_eigs(p, H, S)
 
     def solve_range(j0, j1):
         ev = np.concatenate([per[j] for j in range(j0, j1)]) if j1 > j0 else np.zeros(0)
@@ -69,7 +69,7 @@ def test_gloo_merge_equals_unsharded(tmp_path, world, which):
     from oracle import blocks, dense
     p = _problem(which)
     H, S = dense.build(p)
-    ev, per, _ = blocks.periodic_eigs(p, H, S)
+    ev, per = blocks.periodic_eigs(p, H, S)
     bl = np.concatenate([[j] * p.m0 for j in range(p.ncell)])
     flat = np.concatenate(list(per))
     o = np.lexsort((bl, flat))
