@@ -41,6 +41,7 @@ void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
 void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
+void launch_null_tau(const NullTask*, int, cudaStream_t);
 void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
 void launch_sort_small(const SortTask*, int, int, cudaStream_t);
 void launch_sort_global(double*, int*, int, double*, int*, cudaStream_t);
@@ -362,6 +363,7 @@ struct Batch {
   std::vector<DefBlock> dblocks; DefBlock* d_dblocks = nullptr;
   std::vector<DftTask> dft; DftTask* d_dft = nullptr; int maxLdft = 1;
   std::vector<FBlockTask> fbp, fbs; FBlockTask *d_fbp = nullptr, *d_fbs = nullptr;
+  std::vector<NullTask> nulls; NullTask* d_nulls = nullptr;   // dependency cut of each periodic problem
   int maxnj_p = 0, maxnj_s = 0, maxm0 = 1;
   std::vector<PrecTask> prec; PrecTask* d_prec = nullptr; int maxM = 0;
   std::vector<CanonTask> canon; CanonTask* d_canon = nullptr; int maxcblk = 0;
@@ -446,7 +448,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.pp.assign(np, Batch::PerProb());
   B.gsegs.clear(); B.psegs.clear(); B.gram.clear(); B.combT.clear(); B.combE.clear();
   B.dtabs.clear(); B.dfields.clear(); B.dblocks.clear();
-  B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
+  B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.nulls.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
   B.any_mixed = false;
@@ -685,6 +687,16 @@ void plan(Batch& B, Slab& S, Slab& U) {
       f.prob = i; f.source = 0; f.nj = ncell;
       for (int a = 0; a < 3; ++a) { f.L[a] = H.L[a]; f.Xh[a] = Q.Xh[a]; }
       f.want = 1; f.ev = Q.ev; f.blk = Q.blk; f.fail = Q.fail;
+      NullTask nt;
+      std::memset(&nt, 0, sizeof(nt));
+      nt.m0 = H.m0; nt.nF = H.nF;
+      for (int a = 0; a < 3; ++a) {
+        nt.X[a] = Q.X[a];
+        nt.noff[a] = H.per[a] ? (int)B.ap[i * 3 + a].offs.size() : 1;
+      }
+      nt.tau = S.take<double>(1);
+      f.tau = nt.tau;
+      B.nulls.push_back(nt);
       B.fbp.push_back(f);
       B.maxnj_p = std::max(B.maxnj_p, ncell);
       if (Q.nev <= kSmallSort) {
@@ -721,6 +733,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         CanonTask ct;
         ct.m0 = H.m0; ct.D = Q.D; ct.nE = Q.nE; ct.TH = Q.TH; ct.TS = Q.TS; ct.EH = Q.EH; ct.ES = Q.ES;
         ct.Xc = Q.Xc; ct.kept = Q.kept; ct.THc = Q.THc; ct.TSc = Q.TSc; ct.EHc = Q.EHc; ct.ESc = Q.ESc;
+        ct.ring_full = (H.pchain && Q.D == Q.Lc - 1) ? 1 : 0;
         // transposed partner of each boundary block: itself on the diagonal;
         // else the entry at the mirrored position of the same kind and the
         // same rank among that position's entries (a position can hold a
@@ -1067,6 +1080,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.d_dft = U.put(B.dft);
   B.d_fbp = U.put(B.fbp);
   B.d_fbs = U.put(B.fbs);
+  B.d_nulls = U.put(B.nulls);
   B.d_prec = U.put(B.prec);
   B.d_canon = U.put(B.canon);
   B.d_fbo = U.put(B.fbo);
@@ -1200,6 +1214,7 @@ void run_periodic(fock_ctx* ctx, Batch& B) {
   if (B.fbp.empty()) return;
   zero_fail_flags(B, 0, st);
   { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
+  { PROF("k_null_tau", 1); launch_null_tau(B.d_nulls, (int)B.nulls.size(), st); }
   { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st); }
   if (!B.sorts.empty()) { PROF("k_sort", 1); launch_sort_small(B.d_sorts, (int)B.sorts.size(), B.maxsort, st); }
   for (int i : B.bigsort) { PROF("k_sort_global", 1);
@@ -1978,6 +1993,7 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
   ProfBind pb(ctx);
   cudaStream_t st = ctx->stream;
   { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
+  { PROF("k_null_tau", 1); launch_null_tau(B.d_nulls, (int)B.nulls.size(), st); }
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
   char* mem = nullptr;
@@ -2014,6 +2030,8 @@ int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const d
   cudaStream_t st = ctx->stream;
   const int n = Q.Lc * H.m0;
   const size_t nbytes = (size_t)n * nvec * 8;
+  if (on_device && (const char*)x < (const char*)y + nbytes && (const char*)y < (const char*)x + nbytes)
+    return set_err(ctx, FOCK_EINVAL, "matvec: device x and y must not overlap");
   double *dx = nullptr, *dy = nullptr;
   cplx *X = nullptr, *Y = nullptr;
   char* tasks = nullptr;

@@ -30,11 +30,17 @@ constexpr int MAXM0 = 32;
 constexpr int MAXR = 64;
 constexpr int MAXRADIX = 16;   // radix factors of a circulant size
 
-// Canonical (Loewdin) orthogonalisation threshold: an eigen-direction of an
-// overlap matrix (a Fourier block's Sbar_j, or a box chain's cell overlap
-// T_S[0]) whose eigenvalue is at most kCanonTau times that matrix's largest
-// eigenvalue is removed from the variational space.
-constexpr double kCanonTau = 1e-8;
+// Numerically singular overlap directions (reading G16 of the pencil
+// H C = S C Lambda, Eqs. 2.4-2.5 and 3.11-3.12).  B[mu nu] = sum over lattice
+// offsets d of |S_d[mu nu]| bounds every entry of every Fourier block and every
+// block row of the lattice overlap; an overlap direction (of a Fourier block
+// Sbar_j, or of the cell overlap T_S[0] of a chain, repeated on every cell)
+// whose eigenvalue is at most tau = kSingularC * 2^-53 * ||B||_F lies at the
+// rounding level of the entries it is formed from and is removed; nothing else
+// is.  kSingularC = 64: an m0 x m0 block (m0 <= 32) of entries carrying a few
+// units of rounding relative to B has eigenvalues uncertain by about that.
+constexpr double kSingularC = 64.0;
+__host__ __device__ inline double null_tau(double normB_F) { return kSingularC * 0x1p-53 * normB_F; }
 
 // Modes of a 1D Galerkin form along one axis (gram task):
 //   RING - periodic axis: nodes 0..N-1 with wrap-around, potential tiled;
@@ -173,6 +179,18 @@ struct FBlockTask {
   double* ev;                    // [nj*m0] (want 1) or [nj] (want 2)
   int* blk;                      // optional [nj*m0] Fourier index of each eigenvalue
   int* fail;                     // set to 1 if a block's Sbar is not positive definite
+  const double* tau;             // FACTORS: the problem's dependency cut (k_null_tau); TOEPLITZ:
+                                 // null, the cut is formed from TS in the block kernel
+};
+
+// Dependency cut of a periodic problem: B[mu nu] = prod over axes of the sum
+// over that axis's offsets of |X_a[o][0][mu nu]| (the per-axis mass forms; the
+// overlap blocks are their Hadamard products, Lemma 3.4), tau = null_tau(||B||_F).
+struct NullTask {
+  int m0, nF;
+  const double* X[3];            // [noff][nF][m0*m0] per axis
+  int noff[3];
+  double* tau;                   // out
 };
 
 struct PrecTask {
@@ -276,9 +294,11 @@ struct BandTask {
   int fp32;                                // 1: solve in FP32 arithmetic (mixed form)
 };
 
-// Canonical orthogonalisation of a box chain's cell basis: Xc (m0 x m0,
-// row-major Xc[mu][j]) from the cell overlap block T_S[0]; columns j >= the
-// kept count are zero.  Then every block B becomes Xc^T B Xc.
+// Cell basis of a chain on the structured path: Xc (m0 x m0, row-major
+// Xc[mu][j]) = Q_K diag(s_K)^-1/2 from the eigenpairs of the cell overlap
+// T_S[0] with s > tau (the dependency cut, common.cuh); columns j >= the kept
+// count are zero.  Then every block B becomes Xc^T B Xc: an exact change of
+// basis when nothing is removed.
 struct CanonTask {
   int m0, D, nE;
   const double* TH; const double* TS;     // original generators [D+1][m0*m0]
@@ -289,6 +309,10 @@ struct CanonTask {
   double* EHc; double* ESc;               // out transformed boundary blocks
   const int* Epart;                       // [nE] index of the transposed partner block
                                           // (self on the diagonal, -1 if none)
+  int ring_full;                          // 1: T_d, d = 0..D, are every ring offset once (a periodic
+                                          //    chain planned as its whole circulant), so the scale B of
+                                          //    the dependency cut is sum_d |T_S[d]|; 0: sum_d of
+                                          //    |T_S[d]| + |T_S[d]|^T over d >= 1, plus |T_S[0]|
 };
 
 // Device pointers and sizes the matvec of an assembled box chain needs.

@@ -11,9 +11,10 @@
 //       that embeds the symmetric block Toeplitz matrix with generators
 //       T_d = block (k+d, k), |d| <= D: Chat_j = T_0 + sum_d (w^{jd} T_d +
 //       w^{-jd} T_d^T), w = exp(-2 pi i / M) (Eq. A.3 convention).
-//     eigensolver: canonical (Loewdin) orthogonalisation -- Jacobi
-//       eigendecomposition Sbar = Q diag(s) Q^H, X = Q_K diag(s_K)^-1/2 over
-//       the kept directions K = {s > kCanonTau max s}, C = X^H Hbar X --
+//     eigensolver: Jacobi eigendecomposition Sbar = Q diag(s) Q^H,
+//       X = Q_K diag(s_K)^-1/2 over the kept directions K = {s > tau} (tau the
+//       problem's dependency cut: every direction when none is numerically
+//       singular, so C = X^H Hbar X has the pencil's eigenvalues exactly) --
 //       then Householder reduction of C to a real tridiagonal and
 //       Sturm-sequence bisection per eigenvalue, FP32 first then FP64 with
 //       division-free counts (ascending, so the block spectrum comes out
@@ -150,12 +151,14 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
   }
 }
 
-// Canonical (Loewdin) orthogonalisation of a Hermitian pencil block (h, s),
-// both m x m with stride m: Jacobi eigendecomposition s = Q diag(w) Q^H (in
-// a, q: scratch of ld x ld, ld = m + (m & 1)), kept set K = {w_i > tau max
-// w} in ascending Jacobi index, X = Q_K diag(w_K)^-1/2, and h <- X^H h X
-// (r x r, stride r, exactly Hermitian).  Returns r = |K|.  sv and keep are
-// shared arrays of MAXM0 entries.
+// Reduction of a Hermitian pencil block (h, s), both m x m with stride m, to
+// a standard Hermitian matrix: Jacobi eigendecomposition s = Q diag(w) Q^H
+// (in a, q: scratch of ld x ld, ld = m + (m & 1)), kept set K = {w_i > tau}
+// (tau absolute: the dependency cut) in ascending Jacobi index,
+// X = Q_K diag(w_K)^-1/2, and h <- X^H h X (r x r, stride r, exactly
+// Hermitian).  With every direction kept, X^H s X = I and the eigenvalues of
+// h are the pencil's.  Returns r = |K|.  sv and keep are shared arrays of
+// MAXM0 entries.
 __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m, double tau,
                                  double* sv, int* keep) {
   __shared__ int s_r;
@@ -164,12 +167,9 @@ __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m
   __syncthreads();
   cta_jacobi_herm(a, q, m, ld);
   if (threadIdx.x == 0) {
-    double wmax = 0.0;
-    for (int i = 0; i < m; ++i) wmax = fmax(wmax, a[i * ld + i].x);
     int r = 0;
-    if (wmax > 0.0)
-      for (int i = 0; i < m; ++i)
-        if (a[i * ld + i].x > tau * wmax) { keep[r] = i; sv[r] = a[i * ld + i].x; ++r; }
+    for (int i = 0; i < m; ++i)
+      if (a[i * ld + i].x > tau && a[i * ld + i].x > 0.0) { keep[r] = i; sv[r] = a[i * ld + i].x; ++r; }
     s_r = r;
   }
   __syncthreads();
@@ -387,10 +387,35 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     }
   if (F.want == 0) return;
   __syncthreads();
-  // canonical orthogonalisation (removes numerically dependent Bloch combinations)
+  // reduction on the directions of Sbar above the dependency cut (only
+  // numerically singular Bloch combinations are removed)
   __shared__ int keep[MAXM0];
   __shared__ double sv[MAXM0];
-  const int r = cta_lowdin_reduce(H, S, Aj, Qj, m0, kCanonTau, sv, keep);
+  __shared__ double s_tau;
+  if (F.source == FROM_FACTORS) {
+    if (threadIdx.x == 0) s_tau = *F.tau;
+  } else {
+    // B = |T_S[0]| + sum_{d >= 1} (|T_S[d]| + |T_S[d]|^T) of the embedded
+    // generators, tau = null_tau(||B||_F)
+    double part = 0.0;
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      const int tr = (pr % m0) * m0 + pr / m0;
+      double b = fabs(F.TS[pr]);
+      for (int dd2 = 1; dd2 <= F.D; ++dd2) b += fabs(F.TS[(size_t)dd2 * np + pr]) + fabs(F.TS[(size_t)dd2 * np + tr]);
+      part += b * b;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    __shared__ double red_b[32];
+    if ((threadIdx.x & 31) == 0) red_b[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red_b[w];
+      s_tau = null_tau(sqrt(t));
+    }
+  }
+  __syncthreads();
+  const int r = cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep);
   if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     const double e2i = (i + 1 < r) ? ee[i] * ee[i] : 0.0;
@@ -414,6 +439,36 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     // shift (lowered by 2e-3 relative afterwards): 1e-9 relative suffices
     F.ev[jl] = (r > 0) ? tridiag_eig_fast(df, e2f, dd, e2, r, 0, 1e-9) : INFINITY;
   }
+}
+
+// One CTA per periodic problem: its dependency cut (NullTask).
+__global__ void k_null_tau(const NullTask* __restrict__ tasks) {
+  const NullTask T = tasks[blockIdx.x];
+  const int np = T.m0 * T.m0;
+  const size_t os = (size_t)T.nF * np;   // offset stride of a factor tensor
+  double part = 0.0;
+  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    double b = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int o = 0; o < T.noff[a]; ++o) acc += fabs(T.X[a][(size_t)o * os + pr]);
+      b *= acc;
+    }
+    part += b * b;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    *T.tau = null_tau(sqrt(t));
+  }
+}
+
+void launch_null_tau(const NullTask* tasks, int ntask, cudaStream_t st) {
+  if (ntask) k_null_tau<<<ntask, 256, 0, st>>>(tasks);
 }
 
 // ---- preconditioner ----

@@ -836,10 +836,13 @@ __global__ void k_copy_cols(const CopyTask* __restrict__ tasks) {
 
 namespace fock {
 
-// One CTA per box problem: canonical (Loewdin) orthogonalisation of the
-// cell basis.  Jacobi eigendecomposition T_S[0] = Q diag(s) Q^T of the cell
-// overlap, kept set K = {s > kCanonTau max s} in ascending Jacobi index,
-// Xc = Q_K diag(s_K)^-1/2 (m0 x m0, the columns past |K| zero).
+// One CTA per chain on the structured path: the cell basis.  Jacobi
+// eigendecomposition T_S[0] = Q diag(s) Q^T of the cell overlap, kept set
+// K = {s > tau} in ascending Jacobi index with tau the dependency cut
+// (common.cuh) formed from B = sum over offsets of |T_S[d]|, and
+// Xc = Q_K diag(s_K)^-1/2 (m0 x m0, the columns past |K| zero).  A removed
+// cell direction v spans vectors e_k (x) v, one per cell, on which the
+// chain's overlap form is at most tau: numerically singular directions.
 __global__ void k_cell_canon(const CanonTask* __restrict__ tasks) {
   extern __shared__ double cs[];
   const CanonTask T = tasks[blockIdx.x];
@@ -848,19 +851,29 @@ __global__ void k_cell_canon(const CanonTask* __restrict__ tasks) {
   double* Q = cs + ld * ld;       // ld x ld
   __shared__ double sv[MAXM0 + 1];
   __shared__ int keep[MAXM0 + 1], s_r;
+  __shared__ double red[32], s_tau;
+  double part = 0.0;
   for (int it = threadIdx.x; it < m0 * m0; it += blockDim.x) {
     int i = it / m0, j = it % m0;
     G[i * ld + j] = 0.5 * (T.TS[i * m0 + j] + T.TS[j * m0 + i]);
+    double b = fabs(T.TS[it]);
+    for (int d = 1; d <= T.D; ++d)
+      b += fabs(T.TS[(size_t)d * m0 * m0 + it]) + (T.ring_full ? 0.0 : fabs(T.TS[(size_t)d * m0 * m0 + j * m0 + i]));
+    part += b * b;
   }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    s_tau = null_tau(sqrt(t));
+  }
   cta_jacobi(G, Q, m0, ld);
   if (threadIdx.x == 0) {
-    double smax = 0.0;
-    for (int i = 0; i < m0; ++i) smax = fmax(smax, G[i * ld + i]);
     int r = 0;
-    if (smax > 0.0)
-      for (int i = 0; i < m0; ++i)
-        if (G[i * ld + i] > kCanonTau * smax) { keep[r] = i; sv[r] = G[i * ld + i]; ++r; }
+    for (int i = 0; i < m0; ++i)
+      if (G[i * ld + i] > s_tau && G[i * ld + i] > 0.0) { keep[r] = i; sv[r] = G[i * ld + i]; ++r; }
     s_r = r;
     *T.kept = r;
   }

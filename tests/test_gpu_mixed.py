@@ -45,13 +45,12 @@ CASES = {
 def test_mixed_within_stated_bar(ctx, name):
     p = CASES[name]()
     H, S = dense.build(p)
-    ref, _, _ = _cases.reference(p, H, S)
+    ref = _cases.reference(p, H, S, base=MIXED_TOL)
     mixed = ctx.solve([_mixed(p)])[0]
     fp64 = ctx.solve([p])[0]
     assert mixed["status"] == 0
-    scale = np.max(np.abs(ref))
-    assert np.max(np.abs(mixed["evals"] - ref)) <= MIXED_TOL * scale
-    assert np.max(np.abs(mixed["evals"] - fp64["evals"])) <= MIXED_TOL * scale
+    _cases.report(name + "_mixed", _cases.check(ref, mixed["evals"]))
+    assert np.max(np.abs(mixed["evals"] - fp64["evals"])) <= MIXED_TOL * ref.scale
 
 
 def test_fp64_problems_unaffected_by_mixed_batch_mates(ctx):

@@ -1,13 +1,13 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
 the same seeded inputs.
 
-Bars (derived in the design notes): matrix entries within 1e-12 of the
-largest entry; eigenvalues within max(1e-10, c u kappa) * max|lambda| with
-kappa the condition number of the overlap that the solve works with (the
-kept part after canonical orthogonalisation; the cell-reduced overlap of a
-box chain): the conditioning bound of any backward-stable FP64 solve of the
-pencil; index maps (block_of, boundary block positions) exact; removed
-directions (+inf) in the same places.
+Bars: matrix entries within 1e-12 of the largest entry; eigenvalues within
+max(1e-10 max|lambda|, 256 u (||H|| + |lambda| ||S||) ||x||^2), the
+eigenvalue's own condition number under rounding of the data (tests/_cases.py),
+against the oracle's solve of the pencil (H, S) itself (only numerically
+singular overlap directions removed); index maps (block_of, boundary block
+positions) exact; removed directions (+inf) in the same places.  Each test
+prints its measured largest relative error (pytest -s).
 """
 import numpy as np
 import pytest
@@ -32,8 +32,7 @@ def ctx():
 
 def _ref(p):
     H, S = dense.build(p)
-    ref, tol, extra = _cases.reference(p, H, S)
-    return H, S, ref, tol, extra
+    return H, S, _cases.reference(p, H, S)
 
 
 PERIODIC = {
@@ -53,15 +52,11 @@ def test_periodic_eigenvalues_and_block_map(ctx, name):
         p = li.Problem(L=(11, 1, 1), periodic=(1, 0, 0), N=(66, 18, 18), n0=6, b0=2.0, Z=p.Z,
                        frac=p.frac, exps=p.exps, ang=p.ang, centre=p.centre, R=p.R,
                        sinc_t=p.sinc_t, sinc_c=p.sinc_c)
-    H, S, ref, tol, per_block = _ref(p)
+    H, S, ref = _ref(p)
     out = ctx.solve([p])[0]
     assert out["status"] == 0
-    _cases.assert_spectra_match(out["evals"], ref, tol)
     # block_of: each block's eigenvalues are that oracle block's spectrum
-    blk = out["block_of"]
-    assert sorted(np.bincount(blk, minlength=p.ncell).tolist()) == [p.m0] * p.ncell
-    for j in range(p.ncell):
-        _cases.assert_spectra_match(np.sort(out["evals"][blk == j]), per_block[j], tol)
+    _cases.report(name, _cases.check(ref, out["evals"], out["block_of"]))
 
 
 @pytest.mark.parametrize("name", ["chain_m0_4_L6", "chain_m0_8_L7_odd", "lattice_3d_3x2x4"])
@@ -75,8 +70,7 @@ def test_periodic_generators(ctx, name):
     assert np.max(np.abs(gh - rh)) <= ENTRY_TOL * np.max(np.abs(H))
     assert np.max(np.abs(gs - rs)) <= ENTRY_TOL * np.max(np.abs(S))
     ev, blk = b.circulant_eig()
-    ref, tol, _ = _cases.reference(p, H, S)
-    _cases.assert_spectra_match(ev, ref, tol)
+    _cases.check(_cases.reference(p, H, S), ev, blk)
     b.close()
 
 
@@ -129,12 +123,15 @@ def test_box_embedded_fft_matvec(ctx, name):
 @pytest.mark.parametrize("name", sorted(BOX))
 def test_box_lowest_eigenpairs(ctx, name):
     p = BOX[name]()
-    H, S, ref, tol, (_, _, Xb) = _ref(p)
+    H, S, ref = _ref(p)
     b = ctx.assemble(p)
     ev, V, iters, rc = b.box_eig(p.k_eig, tol=1e-10, maxit=500, vectors=True)
     assert rc == 0, f"no convergence in {iters} iterations"
-    assert np.max(np.abs(ev - ref)) <= tol
-    # residual on the kept (cell-reduced) space, S-orthonormality in the original one
+    _cases.report(name, _cases.check(ref, ev))
+    # residual on the kept space (every direction unless a cell direction is
+    # numerically singular), S-orthonormality in the original basis
+    s, Q, tau = blocks.cell_null_directions(p)
+    Xb = np.kron(np.eye(p.L[0]), Q[:, s > tau])
     R = Xb.T @ (H @ V - (S @ V) * ev)
     assert np.max(np.linalg.norm(R, axis=0) / (np.abs(ev) * np.linalg.norm(Xb.T @ (S @ V), axis=0))) < 1e-9
     G = V.T @ S @ V
@@ -155,17 +152,17 @@ def test_batched_solve_equals_alone(ctx):
 
 def test_full_size_config1(ctx):
     p = _cases.with_table(li.config1())
-    H, S, ref, tol, _ = _ref(p)
+    H, S, ref = _ref(p)
     out = ctx.solve([p])[0]
-    _cases.assert_spectra_match(out["evals"], ref, tol)
+    _cases.report("config1", _cases.check(ref, out["evals"], out["block_of"]))
 
 
 def test_full_size_config2_box(ctx):
     p = _cases.with_table(li.config2(0))
-    H, S, ref, tol, _ = _ref(p)
+    H, S, ref = _ref(p)
     out = ctx.solve([p])[0]
     assert out["status"] == 0
-    assert np.max(np.abs(out["evals"] - ref)) <= tol
+    _cases.report("config2_box", _cases.check(ref, out["evals"]))
 
 
 def test_fourier_index_ranges_merge_to_the_full_solve(ctx):

@@ -1,11 +1,11 @@
-"""Known limitation, tracked: three periodic chains with defects of the
-serving mix (requests 298, 377 and 478 of the seeded stream) ended
-unconverged (FOCK_ENOCONV) when solved inside serving batches.  Each is
-solved here alone; the outcome is recorded as an expected failure until the
-cause is fixed (a pass shows up as XPASS).  Request 478's two
-substitutions keep Z = 1, so its operator is exactly the periodic chain's:
-when it converges, its 16 lowest eigenvalues are checked against the
-oracle's Fourier-block spectrum of that chain."""
+"""Three periodic chains with defects of the serving mix (requests 298, 377
+and 478 of the seeded stream) that once ended unconverged (FOCK_ENOCONV)
+inside serving batches, each solved alone.  298 and 377 converge since only
+numerically singular overlap directions are removed.  Request 478 is tracked as a
+strict expected failure until its cause is fixed (an XPASS fails the run).
+Its two substitutions keep Z = 1, so its operator is exactly the periodic
+chain's: its 16 lowest eigenvalues are checked against the oracle's
+Fourier-block spectrum of that chain."""
 import dataclasses
 
 import numpy as np
@@ -27,8 +27,10 @@ def ctx():
     c.close()
 
 
-@pytest.mark.xfail(reason="unconverged in the serving run; cause under investigation", strict=False)
-@pytest.mark.parametrize("rid", [478, 377, 298])
+@pytest.mark.parametrize("rid", [
+    pytest.param(478, marks=pytest.mark.xfail(reason="block iteration breaks down; cause under investigation",
+                                              strict=True)),
+    377, 298])
 def test_unconverged_serving_chain_alone(ctx, rid):
     p = li.serving_stream(rid + 1, seed=3000)[rid]
     out = ctx.solve([p], check=False)[0]
@@ -38,7 +40,6 @@ def test_unconverged_serving_chain_alone(ctx, rid):
         assert all(d.newZ == p.Z[d.nucleus] for d in p.defects)
         q = _cases.with_table(dataclasses.replace(p, defects=[]))
         H, S = dense.build(q)
-        ev, _, kap = blocks.periodic_eigs(q, H, S)
+        ev, _ = blocks.periodic_eigs(q, H, S)
         ref = ev[:p.k_eig]
-        tol = max(1e-10, 16 * _cases.U64 * float(np.max(kap))) * float(np.max(np.abs(ref)))
-        assert np.max(np.abs(out["evals"] - ref)) <= tol
+        assert np.max(np.abs(out["evals"] - ref)) <= 1e-10 * float(np.max(np.abs(ev[np.isfinite(ev)])))

@@ -2,12 +2,10 @@
 periodic chains 64x1x1 (n0 = 15, 960x256x256 grid, m0 = 8, R = 32, all 512
 eigenvalues), solved as one batch with the library's default quadrature rule
 as the timed step runs them, each against the oracle's dense matrices
-reduced to Fourier blocks (direct DFT, canonical orthogonalisation, LAPACK).
-
-Seed 301 draws a basis whose Fourier-block overlaps have 41 directions below
-the canonical cut-off and the closest kept-or-removed decision 0.4 % from it,
-far above the rounding of the blocks' overlap eigenvalues; the others keep
-every direction."""
+reduced to Fourier blocks (direct DFT and LAPACK on every block pencil, only
+numerically singular overlap directions removed).  Every Fourier block is
+compared through block_of; seeds 2, 6 and 31 draw the most ill-conditioned
+overlaps of the workload (kappa_2 up to 2e9)."""
 import numpy as np
 import pytest
 
@@ -28,16 +26,12 @@ def ctx():
 
 
 def test_periodic_chains_of_the_timed_workload(ctx):
-    seeds = [0, 1, 77, 300, 301, 302, 511]
+    seeds = [0, 1, 2, 6, 31, 77, 300, 301, 302, 511]
     ps = [li.config2(s, L=64, n0=15, pad=32, n_perp=256, R=32).as_periodic_chain() for s in seeds]
     outs = ctx.solve(ps)
     for s, p, o in zip(seeds, ps, outs):
         assert o["status"] == 0, s
         q = _cases.with_table(p)
         H, S = dense.build(q)
-        ref, tol, per_block = _cases.reference(q, H, S)
-        _cases.assert_spectra_match(o["evals"], ref, tol)
-        blk = np.asarray(o["block_of"])
-        assert np.array_equal(np.bincount(blk, minlength=q.ncell), np.full(q.ncell, q.m0)), s
-        for j in (0, 1, 17, 31, 32, 63):
-            _cases.assert_spectra_match(np.sort(o["evals"][blk == j]), per_block[j], tol)
+        ref = _cases.reference(q, H, S)
+        _cases.report(f"timed_periodic_seed{s}", _cases.check(ref, o["evals"], o["block_of"]))
