@@ -191,24 +191,26 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
  * matvec plus the boundary/defect blocks (Remark 3.2, Sec. 2.3).  x, y:
  * N_b x nvec, column-major; device pointers when on_device != 0, else
  * host.  Errors: FOCK_EINVAL (a periodic handle -- its operator is applied
- * through its Fourier blocks -- null pointers, `which`, nvec < 1),
- * FOCK_ENOMEM, FOCK_ECUDA. */
+ * through its Fourier blocks -- null pointers, `which`, nvec < 1, device x
+ * and y that overlap), FOCK_ENOMEM, FOCK_ECUDA. */
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
                          double* y, int nvec, int on_device);
 
 /* Same product as fock_toeplitz_matvec (device x, y only), for callers that
- * cannot allocate device memory: code being captured into a CUDA graph,
- * real-time loops that forbid allocator calls after start-up, hosts whose
- * own allocator owns the device.  The paper has no counterpart; it is a
+ * cannot allocate device memory: real-time loops that forbid allocator calls
+ * (and the synchronisation a free implies) once running, and hosts whose own
+ * allocator owns the device.  The paper has no counterpart; it is a
  * deployment variant.  All work arrays and launch descriptors live in one
  * fixed device array of FOCK_NOALLOC_SCRATCH_BYTES per device, held until
  * the process exits; requires 2*M*m0*nvec*16 + 4096 <= that size (M =
- * circulant size from fock_blocks_info), else FOCK_EINVAL with a message.
- * The first call on a device looks the array's address up (call it before
- * any stream capture).  Calls share the array: two calls whose work
- * overlaps on the GPU race; the array keeps the last call's contents and
- * every part a call reads is written earlier in the same call.  Synchronous
- * on the context's stream. */
+ * circulant size from fock_blocks_info), else FOCK_EINVAL with a message;
+ * x and y must not overlap (FOCK_EINVAL).  The first call on a device looks
+ * the array's address up (make that first call before any stream capture);
+ * the address is kept for the life of the device's primary context.  Calls
+ * share the array: two calls whose work overlaps on the GPU race; the array
+ * keeps the last call's contents and every part a call reads is written
+ * earlier in the same call.  The caller's current device is left as it was.
+ * Synchronous on the context's stream. */
 #define FOCK_NOALLOC_SCRATCH_BYTES (16u << 20)
 int fock_toeplitz_matvec_noalloc(fock_ctx* ctx, const fock_blocks* b, int which, const double* x,
                                  double* y, int nvec);

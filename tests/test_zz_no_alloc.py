@@ -1,9 +1,9 @@
 """The no-allocation matvec entry point against the allocating one.
 
 fock_toeplitz_matvec_noalloc serves callers that cannot allocate device
-memory (work being recorded into a CUDA graph, allocator-free real-time
-loops, hosts whose allocator owns the device): its FFT work arrays live in a
-fixed per-device array inside the library.  It must return the same product
+memory (real-time loops that forbid allocator calls once running, hosts
+whose own allocator owns the device): its FFT work arrays live in a fixed
+per-device array inside the library.  It must return the same product
 as fock_toeplitz_matvec, call after call (the shared array keeps the
 previous call's contents).  This file is collected last on purpose.
 """
@@ -43,6 +43,12 @@ def test_noalloc_matvec_matches_allocating_entry_point():
         with pytest.raises(fock.FockError) as ei:
             b.matvec_noalloc(xb.data_ptr(), xb.data_ptr(), big, fock.FOCK_OP_H)
         assert ei.value.code == fock.FOCK_EINVAL
+        # x and y may not overlap (y is written before the boundary blocks read x)
+        with pytest.raises(fock.FockError) as ei:
+            b.matvec_noalloc(x.data_ptr(), x.data_ptr(), nvec, fock.FOCK_OP_H)
+        assert ei.value.code == fock.FOCK_EINVAL
+        # the caller's current device is unchanged
+        assert torch.cuda.current_device() == 0
         b.close()
     finally:
         ctx.close()
