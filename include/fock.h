@@ -80,9 +80,12 @@ typedef struct {
   int ndef;              /* number of defects */
   const fock_defect* defects;
   int k_eig;             /* box / defect solves: eigenpairs wanted (0: 16) */
-  int precision;         /* FOCK_FP64, or FOCK_MIXED: box and defect solves run the
-                            band preconditioner, and their matvecs until the residual
-                            falls below 1e-5, in FP32 (periodic solves: FP64 always) */
+  int precision;         /* FOCK_FP64, or FOCK_MIXED: the quadrature contractions of the
+                            assembly run on the tensor cores as exact split products
+                            (near-FP64 entries, fock_split_dgemm); box and defect solves
+                            run the band preconditioner, and their matvecs until the
+                            residual falls below 1e-5, in FP32; block eigensolves,
+                            Rayleigh-Ritz and Gram products stay FP64 */
 } fock_problem;
 
 /* Output slot of one problem in a batched solve. */
@@ -242,6 +245,12 @@ int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_b
 /* Sizes of problem i of a plan: N_b, circulant size M (box: M >= L + D;
  * periodic: |L|), generator reach D in cells (box) and boundary blocks. */
 int fock_plan_problem_sizes(const fock_plan* plan, int i, int* Nb, int* mcirc, int* D, int* nbound);
+/* Convergence history of problem i of a plan after its last execution: the
+ * largest relative residual of the wanted pairs at each iteration of the
+ * block iteration (box chains and problems with defects; 0 entries for
+ * periodic problems).  Writes min(n, cap) values to res (may be NULL) and
+ * returns n, or FOCK_EINVAL. */
+int fock_plan_history(const fock_plan* plan, int i, double* res, int cap);
 void fock_plan_free(fock_plan* plan);
 
 /* ---- kernel timers (CUDA events recorded on the context's stream) ----
@@ -252,6 +261,29 @@ void fock_plan_free(fock_plan* plan);
 int fock_profile_enable(fock_ctx* ctx, int on);
 int fock_profile_reset(fock_ctx* ctx);
 int fock_profile_read(fock_ctx* ctx, int cap, char* names, int* launches, double* ms);
+
+/* C = alpha A B + beta C in FP64 on the tensor cores: the exact split
+ * products (base-128 digits of the 53-bit mantissas, BF16 x BF16 -> FP32
+ * tcgen05 products, integer level sums combined in FP64) that the mixed
+ * form uses for the quadrature contractions of stage (a) (Lemma 2.1
+ * display; X_t = sum_r P_t[r] Z[r]).  A: M x K with element (m, k) at
+ * A[m*a_m + k*a_k]; B: K x N, (k, n) at B[k*b_k + n*b_n]; C: (m, n) at
+ * C[m*c_m + n*c_n]; all device pointers, strides in elements.  Each product
+ * carries a relative error below ~2^-46 of |row max of A| |column max of B|
+ * per summand.  Synchronous on the context's stream.  Errors: FOCK_EINVAL,
+ * FOCK_ETIMEOUT (a tensor-core completion wait ran out; C not written),
+ * FOCK_ECUDA. */
+int fock_split_dgemm(fock_ctx* ctx, int M, int N, int K, const double* A, long long a_m, long long a_k,
+                     const double* B, long long b_k, long long b_n, double* C, long long c_m, long long c_n,
+                     double alpha, double beta);
+
+/* Measured FP64 and FP32 fused-multiply-add throughput of CUDA device
+ * `device` in TFLOP/s (best of three timed launches of independent FMA
+ * chains on every SM, after a warm-up): the denominators of the FP64- and
+ * FP32-pipe roofline fractions.  Allocates a small output buffer; the
+ * caller's current device is left as it was.  Errors: FOCK_EINVAL,
+ * FOCK_ECUDA. */
+int fock_measure_peaks(int device, double* fp64_tflops, double* fp32_tflops);
 
 /* ---- serving: continuous batching of lattice problems on one GPU ----
  *

@@ -8,7 +8,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfock.so")
-CU = ["api.cu", "k_assemble.cu", "k_eig.cu", "k_matvec.cu", "k_lobpcg.cu", "k_band.cu", "noalloc.cu", "serve.cu"]
+CU = ["api.cu", "k_assemble.cu", "k_eig.cu", "k_matvec.cu", "k_lobpcg.cu", "k_band.cu", "noalloc.cu", "serve.cu", "peak.cu", "k_split.cu"]
 CPP = ["sinc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -41,6 +41,7 @@ void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
 void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
+void launch_split_gemm(const SplitTask*, int, int, int, int*, cudaStream_t);
 void launch_null_tau(const NullTask*, int, cudaStream_t);
 void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
 void launch_sort_small(const SortTask*, int, int, cudaStream_t);
@@ -357,6 +358,10 @@ struct Batch {
   std::vector<SegDesc> gsegs, psegs;
   SegDesc *d_gsegs = nullptr, *d_psegs = nullptr;
   std::vector<GramTask> gram; GramTask* d_gram = nullptr;
+  // mixed form: the gram tasks' potential contractions as tensor-core split products
+  std::vector<SplitTask> splits; SplitTask* d_splits = nullptr; int split_maxm = 0, split_maxn = 0;
+  int* d_split_err = nullptr;
+  long long o_split_err = -1;
   std::vector<CombineTask> combT, combE; CombineTask *d_combT = nullptr, *d_combE = nullptr;
   std::vector<DefTab> dtabs; DefTab* d_dtabs = nullptr;
   std::vector<DefField> dfields; DefField* d_dfields = nullptr;
@@ -501,7 +506,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       auto add = [&](int mode, int ca, int cb, int r0, int r1, int nfold, int foldlo) {
         GramTask t;
         t.prob = i; t.axis = a; t.mode = mode; t.a = ca; t.b = cb; t.rho0 = r0; t.rho1 = r1;
-        t.ptab = -1; t.nfold = nfold; t.foldlo = foldlo;
+        t.ptab = -1; t.nfold = nfold; t.foldlo = foldlo; t.split = 0;
         t.X = xblock ? xblock + (size_t)(nadded++) * H.nF * m2 : S.take<double>((size_t)H.nF * m2);
         zs_total += (size_t)nfold * m2;
         t.Zs = nullptr;
@@ -599,7 +604,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         g.prob = i; g.axis = a; g.mode = WALL; g.a = 0; g.b = 0;
         g.rho0 = std::max(-A.pad, A.jlo - 1); g.rho1 = std::min(H.N[a] - A.pad, A.jlo + A.W + 1);
         g.ptab = (int)B.dtabs.size() - 1;
-        g.nfold = g.rho1 - g.rho0; g.foldlo = g.rho0;
+        g.nfold = g.rho1 - g.rho0; g.foldlo = g.rho0; g.split = 0;
         g.X = S.take<double>((size_t)H.R * m2);
         g.Zs = nullptr;
         zs_total += (size_t)g.nfold * m2;
@@ -658,6 +663,31 @@ void plan(Batch& B, Slab& S, Slab& U) {
       o += (size_t)t.nfold * B.probs[t.prob].m0 * B.probs[t.prob].m0;
     }
   }
+  // mixed form: X_t[mu nu] = sum_r P_t[r] Z[r][mu nu] (T x nfold times nfold x m0^2) on the
+  // tensor cores for the gram tasks of mixed problems
+  B.splits.clear(); B.split_maxm = B.split_maxn = 0;
+  for (auto& t : B.gram) {
+    if (!B.hp[t.prob].mixed) continue;
+    const ProbDev& P = B.probs[t.prob];
+    const AxisDev& A = P.ax[t.axis];
+    const bool direct = (t.ptab >= 0);
+    const int np = P.m0 * P.m0;
+    const double* tab = direct ? B.dtabs[t.ptab].e : A.p;
+    const long long ld = direct ? B.dtabs[t.ptab].N : A.nr;
+    const long long off = direct ? (t.foldlo + B.dtabs[t.ptab].pad) : (t.foldlo - A.rlo);
+    SplitTask sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.M = direct ? P.R : P.T; sp.N = np; sp.K = t.nfold;
+    sp.A = tab + off; sp.a_m = ld; sp.a_k = 1;
+    sp.B = t.Zs; sp.b_k = np; sp.b_n = 1;
+    sp.C = t.X + (direct ? 0 : 2 * np); sp.c_m = np; sp.c_n = 1;
+    sp.alpha = 1.0; sp.beta = 0.0;
+    B.splits.push_back(sp);
+    B.split_maxm = std::max(B.split_maxm, sp.M);
+    B.split_maxn = std::max(B.split_maxn, sp.N);
+    t.split = 1;
+  }
+  if (!B.splits.empty()) B.d_split_err = S.take<int>(2);
   // ---- combine, DFT, Fourier blocks, structured operators ----
   for (int i = 0; i < np; ++i) {
     const HostProb& H = B.hp[i];
@@ -1072,6 +1102,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.d_gsegs = U.put(B.gsegs);
   B.d_psegs = U.put(B.psegs);
   B.d_gram = U.put(B.gram);
+  B.d_splits = U.put(B.splits);
   B.d_combT = U.put(B.combT);
   B.d_combE = U.put(B.combE);
   B.d_dtabs = U.put(B.dtabs);
@@ -1108,6 +1139,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       const int i = B.sidx[s2];
       B.o_ev[i] = seg(B.lob[s2].lam, 2 * (size_t)B.pp[i].nev);
     }
+    B.o_split_err = B.d_split_err ? seg(B.d_split_err, 1) : -1;
     B.ostage_words = w;
     B.d_ostage = S.take<uint32_t>(std::max<size_t>(w, 2));
     B.d_gseg = U.put(B.gseg);
@@ -1122,8 +1154,6 @@ void plan(Batch& B, Slab& S, Slab& U) {
 namespace {
 
 int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
-  const bool dbg = getenv("FOCK_DEBUG") != nullptr;
-  const auto t0 = std::chrono::steady_clock::now();
   Slab S0, U0;
   plan(B, S0, U0);
   size_t need = S0.off + 256, uneed = U0.off + 256;
@@ -1158,12 +1188,6 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
   U.stage = &B.stage;
   plan(B, S, U);
   CUDA_TRY(ctx, cudaMemcpyAsync(ub, B.stage.data(), U.off, cudaMemcpyHostToDevice, ctx->stream));
-  if (dbg) {
-    cudaStreamSynchronize(ctx->stream);
-    fprintf(stderr, "[fock dbg] plan: %d problems, slab %.1f MB, upload %.1f MB, %.2f ms host+upload\n", B.nprob,
-            S.off / 1e6, U.off / 1e6,
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
-  }
   return FOCK_OK;
 }
 
@@ -1197,6 +1221,11 @@ void run_assemble(fock_ctx* ctx, Batch& B) {
   { PROF("k_vec1d", 2); launch_vec1d(B.d_probs, B.d_gsegs, (int)B.gsegs.size(), B.d_psegs, (int)B.psegs.size(),
                                      B.d_dtabs, (int)B.dtabs.size(), B.ptab_maxT, B.ptab_maxni, st); }
   { PROF("k_gram", 2); launch_gram(B.d_probs, B.d_gram, (int)B.gram.size(), B.d_dtabs, st); }
+  if (!B.splits.empty()) {
+    cudaMemsetAsync(B.d_split_err, 0, sizeof(int), st);
+    PROF("k_split_gemm", 1);
+    launch_split_gemm(B.d_splits, (int)B.splits.size(), B.split_maxm, B.split_maxn, B.d_split_err, st);
+  }
   if (!B.combT.empty()) { PROF("k_combine", 2);
     launch_combine(B.d_probs, B.d_combT, (int)B.combT.size(), st);
     launch_combine(B.d_probs, B.d_combE, (int)B.combE.size(), st); }
@@ -1295,12 +1324,14 @@ void refresh_XP(Batch& B, cudaStream_t st) {
 }
 
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
-               std::vector<double>& resid, std::vector<int>& conv) {
+               std::vector<double>& resid, std::vector<int>& conv,
+               std::vector<std::vector<double>>* hist = nullptr) {
   cudaStream_t st = ctx->stream;
   const int ns = (int)B.sidx.size();
   iters.assign(ns, 0);
   resid.assign(ns, 0.0);
   conv.assign(ns, 0);
+  if (hist) hist->assign(ns, std::vector<double>());
   if (!ns) return FOCK_OK;
   CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, B.d_ones, ns * sizeof(int), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(ctx, cudaMemsetAsync(B.d_fail, 0, ns * sizeof(int), st));
@@ -1316,46 +1347,6 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   std::vector<double> f32_best(ns, INFINITY);
   for (int s2 = 0; s2 < ns; ++s2) mode[s2] = B.hp[B.sidx[s2]].mixed;
   CUDA_TRY(ctx, cudaMemcpyAsync(B.d_mode, mode.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
-  const bool dbg = getenv("FOCK_DEBUG") != nullptr;
-  auto dump = [&](const char* stage, int it) {
-    if (!dbg) return;
-    cudaStreamSynchronize(st);
-    const Batch::Lob& l = B.lob[0];
-    size_t nk = (size_t)l.n * l.k;
-    std::vector<double> h(9 * nk);
-    cudaMemcpy(h.data(), l.Y, 3 * nk * 8, cudaMemcpyDeviceToHost);
-    cudaMemcpy(h.data() + 3 * nk, l.HY, 3 * nk * 8, cudaMemcpyDeviceToHost);
-    cudaMemcpy(h.data() + 6 * nk, l.SY, 3 * nk * 8, cudaMemcpyDeviceToHost);
-    std::vector<double> g(2 * (size_t)l.ld3 * l.ld3), lm(l.k);
-    cudaMemcpy(g.data(), l.GH, g.size() / 2 * 8, cudaMemcpyDeviceToHost);
-    cudaMemcpy(g.data() + g.size() / 2, l.GS, g.size() / 2 * 8, cudaMemcpyDeviceToHost);
-    cudaMemcpy(lm.data(), l.lam, l.k * 8, cudaMemcpyDeviceToHost);
-    auto st3 = [&](const double* p, size_t n, double& mx, int& nan) {
-      mx = 0; nan = 0;
-      for (size_t i = 0; i < n; ++i) { if (!(p[i] == p[i])) ++nan; else mx = std::max(mx, std::fabs(p[i])); }
-    };
-    double m[6]; int nn[6];
-    for (int q = 0; q < 3; ++q) st3(h.data() + q * 3 * nk, 3 * nk, m[q], nn[q]);
-    st3(g.data(), g.size() / 2, m[3], nn[3]);
-    st3(g.data() + g.size() / 2, g.size() / 2, m[4], nn[4]);
-    st3(lm.data(), lm.size(), m[5], nn[5]);
-    if (const char* dd = getenv("FOCK_DEBUG_DIR")) {
-      auto wr = [&](const char* nm, const void* p, size_t bytes) {
-        std::string f = std::string(dd) + "/" + stage + "_" + std::to_string(it) + "_" + nm + ".bin";
-        FILE* fp = fopen(f.c_str(), "wb");
-        if (fp) { fwrite(p, 1, bytes, fp); fclose(fp); }
-      };
-      std::vector<double> cc((size_t)l.ld3 * 2 * l.k);
-      cudaMemcpy(cc.data(), l.Cc, cc.size() * 8, cudaMemcpyDeviceToHost);
-      wr("G", g.data(), g.size() * 8);
-      wr("lam", lm.data(), lm.size() * 8);
-      wr("Cc", cc.data(), cc.size() * 8);
-      wr("Y", h.data(), h.size() * 8);
-    }
-    fprintf(stderr, "[fock dbg] it %d %-6s Y %.3e/%d HY %.3e/%d SY %.3e/%d GH %.3e/%d GS %.3e/%d lam0 %.12g nan %d err %s\n",
-            it, stage, m[0], nn[0], m[1], nn[1], m[2], nn[2], m[3], nn[3], m[4], nn[4], lm[0], nn[5],
-            cudaGetErrorString(cudaGetLastError()));
-  };
   // X random, P = W = 0; Rayleigh-Ritz on X alone, then fresh images of [X | P]
   { PROF("k_init_x", 1); k_init_x<<<dim3(32, B.init.n), 256, 0, st>>>(tl<InitTask>(B.init)); }
   mv_HS(B, true, st);
@@ -1364,7 +1355,6 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   gemm_nn(B.u1, st);
   copies(B.cp2k, st);
   mv_HS(B, true, st);
-  dump("init", -1);
   std::vector<double> hres((size_t)ns * B.kmax);
   std::vector<int> active(ns, 1);
   // a residual that stops improving below kFloorTol is at the rounding floor
@@ -1399,6 +1389,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       }
       resid[s2] = bad ? INFINITY : mx;
       iters[s2] = it;
+      if (hist) (*hist)[s2].push_back(resid[s2]);
       if (mode[s2] && !bad) {   // FP32 phase of the mixed form
         ++f32_it[s2];
         if (mx < 0.5 * f32_best[s2]) { f32_best[s2] = mx; f32_stall[s2] = 0; } else ++f32_stall[s2];
@@ -1424,23 +1415,6 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
         active[s2] = 0; conv[s2] = 1; changed = true;
       }
       else any = true;
-    }
-    if (dbg) {
-      static auto t_prev = std::chrono::steady_clock::now();
-      const auto t_now = std::chrono::steady_clock::now();
-      int nact = 0;
-      for (int s2 = 0; s2 < ns; ++s2) nact += active[s2];
-      fprintf(stderr, "[fock dbg] it %d active %d dt %.3f ms res", it, nact,
-              std::chrono::duration<double, std::milli>(t_now - t_prev).count());
-      t_prev = t_now;
-      for (int s2 = 0; s2 < std::min(ns, 2); ++s2) fprintf(stderr, " %.3e", resid[s2]);
-      std::vector<double> lm(B.kmax);
-      cudaMemcpy(lm.data(), B.lob[0].lam, B.lob[0].k * 8, cudaMemcpyDeviceToHost);
-      fprintf(stderr, " lam %.14g %.14g %.14g\n", lm[0], lm[1], lm[B.lob[0].k - 1]);
-      if (getenv("FOCK_DEBUG")[0] == '2') {   // per-column residuals and Ritz values of the first problem
-        for (int c = 0; c < B.lob[0].k; ++c)
-          fprintf(stderr, "   c%-3d %.3e %.12g\n", c, hres[c], lm[c]);
-      }
     }
     if (!any || it >= maxit) break;
     if (changed) {
@@ -1468,7 +1442,6 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     // Rayleigh-Ritz on [X | P | W]
     gemm_tn(B.g3, st);
     rr(B.rr3, st);
-    if (dbg && (it < 3 || (getenv("FOCK_DEBUG_IT") && it == atoi(getenv("FOCK_DEBUG_IT"))))) dump("rr", it);
     // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
     gemm_nn(B.u3, st);
     copies(B.cp2k, st);
@@ -1489,6 +1462,7 @@ struct fock_plan {
   Batch B;
   std::vector<int> iters, conv;
   std::vector<double> resid;
+  std::vector<std::vector<double>> hist;   // per structured problem: residual of each iteration
 };
 
 namespace {
@@ -1499,7 +1473,7 @@ int plan_execute(fock_plan& P, double tol, int maxit) {
   run_assemble(ctx, B);
   run_periodic(ctx, B);
   run_struct_setup(ctx, B);
-  int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv);
+  int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
   if (rc) return rc;
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;
@@ -1510,6 +1484,7 @@ int plan_outputs(fock_plan& P, fock_output* outs, int on_device) {
   Batch& B = P.B;
   const int nprob = B.nprob;
   std::vector<int> pfail(nprob, 0);
+  int split_err = 0;
   for (int i = 0; i < nprob; ++i) {
     outs[i].n_evals = B.pp[i].nev;
     outs[i].iters = 0;
@@ -1540,6 +1515,8 @@ int plan_outputs(fock_plan& P, fock_output* outs, int on_device) {
         CUDA_TRY(ctx, cudaMemcpyAsync(outs[i].evals, B.lob[s2].lam, B.pp[i].nev * sizeof(double),
                                       cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    if (B.d_split_err)
+      CUDA_TRY(ctx, cudaMemcpyAsync(&split_err, B.d_split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   } else {           // host destinations: gather on the device, one copy to pinned memory
     const size_t nw = B.ostage_words;
@@ -1561,14 +1538,17 @@ int plan_outputs(fock_plan& P, fock_output* outs, int on_device) {
       if (outs[i].block_of && B.o_blk[i] >= 0) std::memcpy(outs[i].block_of, hs + B.o_blk[i], nev * sizeof(int));
       if (B.o_fail[i] >= 0) std::memcpy(&pfail[i], hs + B.o_fail[i], sizeof(int));
     }
+    if (B.o_split_err >= 0) std::memcpy(&split_err, hs + B.o_split_err, sizeof(int));
   }
   int first = FOCK_OK;
   for (int i = 0; i < nprob; ++i) {
+    if (split_err && B.hp[i].mixed) outs[i].status = FOCK_ETIMEOUT;   // its assembly did not complete
     if (pfail[i]) outs[i].status = FOCK_EINVAL;
     if (outs[i].status && !first) first = outs[i].status;
   }
   if (first == FOCK_EINVAL) set_err(ctx, first, "a Fourier-block mass matrix was not positive definite");
   if (first == FOCK_ENOCONV) set_err(ctx, first, "box eigensolver reached maxit");
+  if (first == FOCK_ETIMEOUT) set_err(ctx, first, "a tensor-core completion wait of the mixed assembly ran out");
   return first;
 }
 
@@ -1807,6 +1787,18 @@ int fock_plan_problem_sizes(const fock_plan* P, int i, int* Nb, int* mcirc, int*
   return FOCK_OK;
 }
 
+int fock_plan_history(const fock_plan* P, int i, double* res, int cap) {
+  if (!P || i < 0 || i >= P->B.nprob) return FOCK_EINVAL;
+  const auto& sid = P->B.sidx;
+  for (size_t s2 = 0; s2 < sid.size() && s2 < P->hist.size(); ++s2)
+    if (sid[s2] == i) {
+      const std::vector<double>& h = P->hist[s2];
+      for (int t = 0; t < std::min((int)h.size(), std::max(cap, 0)); ++t) if (res) res[t] = h[t];
+      return (int)h.size();
+    }
+  return 0;
+}
+
 void fock_plan_free(fock_plan* P) {
   if (!P) return;
   cudaStreamSynchronize(P->ctx->stream);
@@ -2018,6 +2010,34 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
   if (e != cudaSuccess) rc = set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e));
   cudaFree(mem);
   return rc;
+}
+
+int fock_split_dgemm(fock_ctx* ctx, int M, int N, int K, const double* A, long long a_m, long long a_k,
+                     const double* B, long long b_k, long long b_n, double* C, long long c_m, long long c_n,
+                     double alpha, double beta) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || (M && N && (!A || !B || !C))) return FOCK_EINVAL;
+  if (!M || !N) return FOCK_OK;
+  cudaStream_t st = ctx->stream;
+  SplitTask t;
+  std::memset(&t, 0, sizeof(t));
+  t.M = M; t.N = N; t.K = K; t.A = A; t.a_m = a_m; t.a_k = a_k; t.B = B; t.b_k = b_k; t.b_n = b_n;
+  t.C = C; t.c_m = c_m; t.c_n = c_n; t.alpha = alpha; t.beta = beta;
+  char* mem = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&mem, 256 + sizeof(SplitTask)));
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(mem, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mem + 256, &t, sizeof(t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    { ProfBind pb(ctx); PROF("k_split_gemm", 1);
+      launch_split_gemm((const SplitTask*)(mem + 256), 1, M, N, (int*)mem, st); }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, mem, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (e != cudaSuccess) return set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e));
+  if (herr) return set_err(ctx, FOCK_ETIMEOUT, "split_dgemm: a tensor-core commit did not complete in time");
+  return FOCK_OK;
 }
 
 int fock_toeplitz_matvec(fock_ctx* ctx, const fock_blocks* b, int which, const double* x, double* y,

@@ -85,6 +85,7 @@ struct GramTask {
   double* Zs;           // scratch [nfold][m0*m0] (folded pair products)
   int nfold;            // number of reduced nodes of the fold
   int foldlo;           // first reduced node
+  int split;            // 1: the potential contraction runs on the tensor cores (k_split_gemm)
 };
 
 // A defect table: single-nucleus Gaussian integrals e[q][i] on the grid of
@@ -313,6 +314,19 @@ struct CanonTask {
                                           //    chain planned as its whole circulant), so the scale B of
                                           //    the dependency cut is sum_d |T_S[d]|; 0: sum_d of
                                           //    |T_S[d]| + |T_S[d]|^T over d >= 1, plus |T_S[0]|
+};
+
+// One FP64 product C = alpha A B + beta C computed on the tensor cores by
+// exact split products (k_split.cu): A is M x K with A(m, k) at
+// A[m * a_m + k * a_k], B is K x N with B(k, n) at B[k * b_k + n * b_n],
+// C(m, n) at C[m * c_m + n * c_n].
+struct SplitTask {
+  const int* active;           // skip when *active == 0 (null: always)
+  int M, N, K;
+  const double* A; long long a_m, a_k;
+  const double* B; long long b_k, b_n;
+  double* C; long long c_m, c_n;
+  double alpha, beta;
 };
 
 // Device pointers and sizes the matvec of an assembled box chain needs.

@@ -242,6 +242,7 @@ __global__ void k_gram_fold(const ProbDev* __restrict__ probs, const GramTask* _
 __global__ void k_gram_pot(const ProbDev* __restrict__ probs, const GramTask* __restrict__ tasks,
                            const DefTab* __restrict__ dtabs) {
   const GramTask T = tasks[blockIdx.x];
+  if (T.split) return;   // mixed form: contracted by k_split_gemm
   const ProbDev& P = probs[T.prob];
   const AxisDev& A = P.ax[T.axis];
   const int np = P.m0 * P.m0;

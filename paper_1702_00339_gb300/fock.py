@@ -131,6 +131,12 @@ def lib():
         L.fock_serve_last_error.argtypes = [C.c_void_p]
         L.fock_serve_last_error.restype = C.c_char_p
         L.fock_serve_stop.argtypes = [C.c_void_p]
+        L.fock_measure_peaks.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+        L.fock_plan_history.argtypes = [C.c_void_p, C.c_int, P(C.c_double), C.c_int]
+        L.fock_split_dgemm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                       C.c_void_p, C.c_longlong, C.c_longlong,
+                                       C.c_void_p, C.c_longlong, C.c_longlong,
+                                       C.c_void_p, C.c_longlong, C.c_longlong, C.c_double, C.c_double]
         _lib = L
     return _lib
 
@@ -334,6 +340,12 @@ class Context:
     def profile_reset(self):
         self._check(lib().fock_profile_reset(self.h), "fock_profile_reset")
 
+    def split_dgemm(self, M, N, K, A, a_m, a_k, B, b_k, b_n, Cp, c_m, c_n, alpha=1.0, beta=0.0):
+        """C = alpha A B + beta C on the tensor cores (fock_split_dgemm);
+        A, B, Cp are device pointers (ints), strides in elements."""
+        self._check(lib().fock_split_dgemm(self.h, int(M), int(N), int(K), A, a_m, a_k, B, b_k, b_n,
+                                           Cp, c_m, c_n, float(alpha), float(beta)), "fock_split_dgemm")
+
     def profile_read(self, cap=64):
         names = C.create_string_buffer(32 * cap)
         nl = (C.c_int * cap)()
@@ -477,6 +489,15 @@ class Plan:
             res.append(r)
         return res
 
+    def history(self, i, cap=4096):
+        """Largest wanted-pair relative residual at each iteration of problem
+        i's block iteration in the last execution (empty for periodic)."""
+        buf = (C.c_double * cap)()
+        n = lib().fock_plan_history(self.h, int(i), buf, cap)
+        if n < 0:
+            self.ctx._check(n, "fock_plan_history")
+        return [float(buf[t]) for t in range(min(n, cap))]
+
     def close(self):
         if self.h and self.ctx.h:
             lib().fock_plan_free(self.h)
@@ -548,3 +569,13 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def measure_peaks(device=0):
+    """Measured FP64 and FP32 FMA throughput of a device (TFLOP/s), through
+    fock_measure_peaks."""
+    f64, f32 = C.c_double(), C.c_double()
+    rc = lib().fock_measure_peaks(device, C.byref(f64), C.byref(f32))
+    if rc != 0:
+        raise FockError(rc, "fock_measure_peaks failed")
+    return float(f64.value), float(f32.value)
