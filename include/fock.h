@@ -45,7 +45,7 @@ typedef enum {
   FOCK_ECUDA = -6      /* a CUDA call failed; see fock_last_error */
 } fock_status;
 
-enum { FOCK_FP64 = 0, FOCK_MIXED = 1 };
+enum { FOCK_FP64 = 0, FOCK_MIXED = 1, FOCK_MIXED_F32 = 2 };
 enum { FOCK_ANG_S = 0, FOCK_ANG_PX = 1, FOCK_ANG_PY = 2, FOCK_ANG_PZ = 3 };
 enum { FOCK_OP_H = 0, FOCK_OP_S = 1 };
 
@@ -80,12 +80,19 @@ typedef struct {
   int ndef;              /* number of defects */
   const fock_defect* defects;
   int k_eig;             /* box / defect solves: eigenpairs wanted (0: 16) */
-  int precision;         /* FOCK_FP64, or FOCK_MIXED: the quadrature contractions of the
-                            assembly run on the tensor cores as exact split products
-                            (near-FP64 entries, fock_split_dgemm); box and defect solves
-                            run the band preconditioner, and their matvecs until the
-                            residual falls below 1e-5, in FP32; block eigensolves,
-                            Rayleigh-Ritz and Gram products stay FP64 */
+  int box_potential;     /* box chains: 0 = the central cell's lattice-summed potential
+                            replicated over the box (reading R1, Sec. 2.3 (A), Eq. 3.6);
+                            1 = the plain sum over the box's cells, each nucleus once with
+                            its full charge (Sec. 2.3 case (B)): the difference is added as
+                            blocks on every pair of cells whose functions meet */
+  int precision;         /* FOCK_FP64; FOCK_MIXED: the quadrature contractions of the
+                            assembly and the dense products of the block iteration (Gram
+                            matrices, basis updates) run on the tensor cores as exact split
+                            products (fock_split_dgemm, near-FP64); Rayleigh-Ritz, matvecs,
+                            preconditioner and Fourier-block eigensolves FP64;
+                            FOCK_MIXED_F32: as FOCK_MIXED, and box / defect solves run the
+                            preconditioner, and their matvecs until the residual falls
+                            below 1e-5, in FP32 */
 } fock_problem;
 
 /* Output slot of one problem in a batched solve. */
@@ -179,8 +186,15 @@ int fock_blocks_copy_generators(const fock_blocks* b, double* H, double* S, doub
                                 double* ES, int* bound_rc);
 
 /* Periodic eigenvalues by FFT block-diagonalisation (Lemma 3.1, Thm 3.3,
- * Eqs. 3.11-3.12): evals[|L|*m0] ascending (host), block_of optional. */
-int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of);
+ * Eqs. 3.11-3.12): evals[|L|*m0] ascending (host), block_of optional.
+ * evecs (optional, host, |L|*m0*m0 complex values as interleaved re, im
+ * doubles): the Fourier-block eigenvectors y, evecs[((j*m0 + i)*m0 + mu)]
+ * = component mu of the i-th eigenvector (ascending within block j) of the
+ * pencil (Hbar_j, Sbar_j), y^H Sbar_j y = 1; removed directions give zero
+ * vectors (last).  The lattice eigenvector is u[(k, mu)] = f_j[k] y[mu] with
+ * f_j[k] = exp(+2 pi i j.k / L) / sqrt(|L|) (Prop. A.1; fock_bloch_vectors
+ * forms it on the device). */
+int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of, double* evecs);
 /* The same for the Fourier indices jbar in [j0, j1) only: evals[(j1-j0)*m0]
  * ascending (ties by Fourier index), block_of optional.  The blocks are
  * independent (Thm. 3.3), so ranks that each take a contiguous range and
@@ -188,6 +202,18 @@ int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* 
  * Errors: FOCK_EINVAL (not periodic, range outside 0..|L|), FOCK_ECUDA. */
 int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1, double* evals,
                              int* block_of);
+
+/* Lattice eigenvectors of a periodic problem (Prop. A.1: the inverse DFT
+ * over the lattice index of block eigenvectors, U = (F^* (x) I) Ubar) for
+ * nsel eigenpairs given by their Fourier index jbar[c] (block_of of
+ * fock_circulant_eig) and rank[c] within that block (0 = lowest): U is host
+ * memory of nsel columns of N_b complex values (interleaved re, im),
+ * U[c][(kbar*m0 + mu)] = f_j[k] y[mu]; S-orthonormal, H u = lambda S u.  The
+ * needed blocks are solved again (with vectors) and the back-transform runs
+ * on the device (k_bloch_vectors).  Errors: FOCK_EINVAL (not periodic, index
+ * out of range), FOCK_ECUDA. */
+int fock_bloch_vectors(fock_ctx* ctx, const fock_blocks* b, int nsel, const int* jbar, const int* rank,
+                       double* U);
 
 /* y = H x or y = S x (which = FOCK_OP_H / FOCK_OP_S) for an assembled box
  * chain or problem with defects, by the block-circulant embedding FFT
@@ -251,6 +277,12 @@ int fock_plan_problem_sizes(const fock_plan* plan, int i, int* Nb, int* mcirc, i
  * periodic problems).  Writes min(n, cap) values to res (may be NULL) and
  * returns n, or FOCK_EINVAL. */
 int fock_plan_history(const fock_plan* plan, int i, double* res, int cap);
+/* Tensor-core work of one execution of a plan's mixed-form assembly
+ * (fock_split_dgemm products of its gram tasks): the BF16 multiply-add
+ * flops the MMAs execute (128 x 64 output tiles, 64-long chunks, 28 digit
+ * pairs, 4 MMAs of K = 16 each) and the FP64 flops they stand for (2 M N K).
+ * Zero for a plan without mixed problems. */
+int fock_plan_split_work(const fock_plan* plan, double* tensor_flops, double* fp64_flops);
 void fock_plan_free(fock_plan* plan);
 
 /* ---- kernel timers (CUDA events recorded on the context's stream) ----
@@ -270,12 +302,16 @@ int fock_profile_read(fock_ctx* ctx, int cap, char* names, int* launches, double
  * A[m*a_m + k*a_k]; B: K x N, (k, n) at B[k*b_k + n*b_n]; C: (m, n) at
  * C[m*c_m + n*c_n]; all device pointers, strides in elements.  Each product
  * carries a relative error below ~2^-46 of |row max of A| |column max of B|
- * per summand.  Synchronous on the context's stream.  Errors: FOCK_EINVAL,
+ * per summand.  ksplit (1..1024): the summation is split into that many
+ * ranges computed by separate CTAs and added in a fixed order (a work array
+ * is allocated for them); sym != 0 (M = N): C is taken as symmetric, its
+ * upper triangle computed and mirrored (the Gram products of the block
+ * iteration).  Synchronous on the context's stream.  Errors: FOCK_EINVAL,
  * FOCK_ETIMEOUT (a tensor-core completion wait ran out; C not written),
  * FOCK_ECUDA. */
 int fock_split_dgemm(fock_ctx* ctx, int M, int N, int K, const double* A, long long a_m, long long a_k,
                      const double* B, long long b_k, long long b_n, double* C, long long c_m, long long c_n,
-                     double alpha, double beta);
+                     double alpha, double beta, int ksplit, int sym);
 
 /* Measured FP64 and FP32 fused-multiply-add throughput of CUDA device
  * `device` in TFLOP/s (best of three timed launches of independent FMA

@@ -40,8 +40,9 @@ void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream
 void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
-void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t);
-void launch_split_gemm(const SplitTask*, int, int, int, int*, cudaStream_t);
+void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t, bool vectors = false);
+void launch_bloch_vectors(int, int, int, int, int, const int*, const cplx*, const int*, cplx*, cudaStream_t);
+void launch_split_gemm(const SplitTask*, int, int, int, int*, cudaStream_t, int max_ks = 1, bool reduce = false);
 void launch_null_tau(const NullTask*, int, cudaStream_t);
 void launch_precond(const ProbDev*, const PrecTask*, int, int, int, cudaStream_t);
 void launch_sort_small(const SortTask*, int, int, cudaStream_t);
@@ -125,7 +126,12 @@ struct ProfBind {   // sets the context being timed for the duration of an API c
 namespace {
 
 const int kSmallSort = 4096;
-const double kPrecShift = 2e-3;   // sigma = min_j lambda_min(Chat_j) - kPrecShift (1 + |.|)
+const double kPrecShift = 2e-5;   // sigma = min_j lambda_min(Chat_j) - kPrecShift (1 + |.|)
+// mixed form: the block iteration's dense products go to the tensor cores for
+// chains of at least this many basis functions (the Gram sums are over them;
+// shorter sums do not repay the digit splitting: measured 56 vs 50 ms per
+// batch of 64 chains of 512 functions, 0.84 vs 1.66 s for one of 16384)
+const int kSplitMinRows = 2048;
 
 int set_err(fock_ctx* c, int code, const std::string& m) {
   if (c) c->err = m;
@@ -149,7 +155,9 @@ struct HostProb {
   int k_eig;
   int kind;            // 0 periodic (circulant eigensolve), 1 structured iteration
   int pchain = 0;      // structured path of a periodic chain (defects on a periodic axis 0)
-  int mixed = 0;       // FOCK_MIXED: FP32 preconditioner, FP32 matvecs until the residual is small
+  int mixed = 0;       // FOCK_MIXED or FOCK_MIXED_F32: dense products as tensor-core split products
+  int f32 = 0;         // FOCK_MIXED_F32: FP32 preconditioner, FP32 matvecs until the residual is small
+  int r2 = 0;          // box potential read as the plain lattice sum over the box's cells
   std::vector<fock_defect> defs;
 };
 
@@ -172,8 +180,11 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
   if (p.m0 < 1 || p.m0 > MAXM0 || !p.exps || !p.ang || !p.centre) { why = "1 <= m0 <= 32 with exps/ang/centre"; return FOCK_EINVAL; }
   if (p.R < 3 || p.R > MAXR) { why = "3 <= R <= 64"; return FOCK_EINVAL; }
   if (p.ndef < 0 || (p.ndef > 0 && !p.defects)) { why = "ndef >= 0 with a defects array"; return FOCK_EINVAL; }
-  if (p.precision != FOCK_FP64 && p.precision != FOCK_MIXED) { why = "precision FOCK_FP64 or FOCK_MIXED"; return FOCK_EINVAL; }
-  H.mixed = (p.precision == FOCK_MIXED) ? 1 : 0;
+  if (p.precision != FOCK_FP64 && p.precision != FOCK_MIXED && p.precision != FOCK_MIXED_F32) {
+    why = "precision FOCK_FP64, FOCK_MIXED or FOCK_MIXED_F32"; return FOCK_EINVAL;
+  }
+  H.mixed = (p.precision != FOCK_FP64) ? 1 : 0;
+  H.f32 = (p.precision == FOCK_MIXED_F32) ? 1 : 0;
   H.n0 = p.n0; H.b0 = p.b0; H.h = p.b0 / p.n0;
   H.eps = (p.eps_support > 0.0) ? p.eps_support : 1e-14;
   int nlong = 0;
@@ -228,13 +239,18 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
     }
   }
   H.k_eig = (p.k_eig > 0) ? p.k_eig : 16;
+  if (p.box_potential != 0 && p.box_potential != 1) { why = "box_potential 0 (replicated) or 1 (lattice sum)"; return FOCK_EINVAL; }
+  if (p.box_potential == 1 && !(H.kind == 1 && !H.per[0])) {
+    why = "box_potential 1 (the plain lattice sum) applies to box chains"; return FOCK_EINVAL;
+  }
+  H.r2 = p.box_potential;
   if (H.kind == 1) {
     int Nb = H.L[0] * H.m0;
     int kb = lobpcg_block(H.k_eig, Nb);
     // whole-space block: the first Rayleigh-Ritz step is exact, so the mixed
     // form has nothing to gain, and an FP32 Rayleigh-Ritz over [X | P | W]
     // (P, W inside span X) would only see noise: solved in FP64
-    if (kb == Nb) H.mixed = 0;
+    if (kb == Nb) H.f32 = 0;
     if (H.k_eig > Nb || 3 * kb > 255 || (kb < Nb && 3 * kb > Nb)) {
       why = "k_eig too large: k <= N_b and 3 (k + guard) <= min(N_b, 255) on chains with 3 N_b > 255"; return FOCK_EINVAL;
     }
@@ -251,7 +267,7 @@ uint64_t problem_seed(const HostProb& H) {
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
   };
   mix(H.L, sizeof(H.L)); mix(H.per, sizeof(H.per)); mix(H.N, sizeof(H.N)); mix(&H.n0, sizeof(H.n0));
-  mix(&H.mixed, sizeof(H.mixed));
+  mix(&H.mixed, sizeof(H.mixed)); mix(&H.f32, sizeof(H.f32)); mix(&H.r2, sizeof(H.r2));
   mix(&H.b0, sizeof(H.b0)); mix(&H.k_eig, sizeof(H.k_eig));
   mix(H.alpha.data(), H.alpha.size() * 8); mix(H.Z.data(), H.Z.size() * 8);
   mix(H.frac.data(), H.frac.size() * 8); mix(H.ang.data(), H.ang.size() * 4);
@@ -419,7 +435,11 @@ struct Batch {
   int kmax = 0;
   cplx *mvX = nullptr, *mvY1 = nullptr, *mvY2 = nullptr;   // FFT work (shared by all structured)
   std::vector<size_t> mv_off;        // per structured problem: offset (cplx) into mv buffers
-  struct TL { void* d = nullptr; int n = 0; int ga = 1, gb = 1, tile = 16; };
+  struct TL {
+    void* d = nullptr; int n = 0; int ga = 1, gb = 1, tile = 16;
+    // mixed form: the same products of mixed problems as tensor-core split tasks
+    void* sd = nullptr; int sn = 0, sm = 1, snn = 1, sks = 1; bool sred = false;
+  };
   // basis layout Y = [X | P | W] (k columns each)
   TL fwdXP, fwdW, fwdR, bmulHS2, bmulHS1, bmulK, invHXP, invSXP, invHW, invSW, invPW;
   TL eHXP, eHW;                      // boundary blocks (H and S in one task)
@@ -579,23 +599,38 @@ void plan(Batch& B, Slab& S, Slab& U) {
   for (int i = 0; i < np; ++i) {
     const HostProb& H = B.hp[i];
     Batch::PerProb& Q = B.pp[i];
-    if (H.defs.empty()) continue;
+    if (H.defs.empty() && !H.r2) continue;
     const int m2 = H.m0 * H.m0, n0 = H.n0, L = H.L[0];
     const AxisPlan& A0 = B.ap[i * 3 + 0];
     Q.defD1.clear(); Q.defD2.clear();
     std::vector<DefRef> refs;
-    for (const fock_defect& d : H.defs) {
+    // the defects, then (box potential as the plain lattice sum, Sec. 2.3 case
+    // (B)) one term per nucleus of the cell: its copies in every cell minus
+    // its replicated potential, with the nucleus's charge
+    std::vector<fock_defect> terms(H.defs);
+    const size_t ndef_real = terms.size();
+    if (H.r2)
+      for (int nu = 0; nu < H.M0; ++nu) terms.push_back(fock_defect{{0, 0, 0}, nu, 0.0});   // newZ unused here
+    for (size_t di = 0; di < terms.size(); ++di) {
+      const fock_defect& d = terms[di];
+      const bool lsum = di >= ndef_real;
       DefRef rf;
       DefTab t0;
+      std::memset(&t0, 0, sizeof(t0));
       t0.prob = i; t0.axis = 0; t0.N = H.N[0]; t0.pad = A0.pad;
       t0.pos = ((double)d.cell[0] + H.frac[d.nucleus * 3 + 0]) * n0;
       t0.e = S.take<double>((size_t)H.R * H.N[0]);
+      if (lsum) {
+        t0.mode = 1; t0.L = L; t0.nu = d.nucleus; t0.nr = A0.nr; t0.rlo = A0.rlo;
+        t0.prep = B.probs[i].ax[0].p;
+      }
       B.dtabs.push_back(t0);
       rf.e = t0.e;
-      rf.dz = d.newZ - H.Z[d.nucleus];
+      rf.dz = lsum ? H.Z[d.nucleus] : d.newZ - H.Z[d.nucleus];
       for (int a = 1; a <= 2; ++a) {
         const AxisPlan& A = B.ap[i * 3 + a];
         DefTab ta;
+        std::memset(&ta, 0, sizeof(ta));
         ta.prob = i; ta.axis = a; ta.N = H.N[a]; ta.pad = A.pad;
         ta.pos = H.frac[d.nucleus * 3 + a] * n0;
         ta.e = S.take<double>((size_t)H.R * H.N[a]);
@@ -719,7 +754,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       f.want = 1; f.ev = Q.ev; f.blk = Q.blk; f.fail = Q.fail;
       NullTask nt;
       std::memset(&nt, 0, sizeof(nt));
-      nt.m0 = H.m0; nt.nF = H.nF;
+      nt.m0 = H.m0; nt.nF = H.nF; nt.nb = ncell * H.m0;
       for (int a = 0; a < 3; ++a) {
         nt.X[a] = Q.X[a];
         nt.noff[a] = H.per[a] ? (int)B.ap[i * 3 + a].offs.size() : 1;
@@ -764,6 +799,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         ct.m0 = H.m0; ct.D = Q.D; ct.nE = Q.nE; ct.TH = Q.TH; ct.TS = Q.TS; ct.EH = Q.EH; ct.ES = Q.ES;
         ct.Xc = Q.Xc; ct.kept = Q.kept; ct.THc = Q.THc; ct.TSc = Q.TSc; ct.EHc = Q.EHc; ct.ESc = Q.ESc;
         ct.ring_full = (H.pchain && Q.D == Q.Lc - 1) ? 1 : 0;
+        ct.nb = Q.Lc * H.m0;
         // transposed partner of each boundary block: itself on the diagonal;
         // else the entry at the mirrored position of the same kind and the
         // same rank among that position's entries (a position can hold a
@@ -945,6 +981,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     std::vector<BmulTask> rbHS2;
     std::vector<InitTask> ini;
     std::vector<GemmTask> tcx, nw, tcp, npp, gg1, gg3, uu1, uu3;
+    std::vector<SplitTask> s_tcx, s_nw, s_tcp, s_npp, s_gg1, s_gg3, s_uu1, s_uu3;
     std::vector<RRTask> r1, r3;
     std::vector<CopyTask> c2k, nP, nW;
     std::vector<ResidTask> rs;
@@ -966,9 +1003,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
       const CircDev* cd = B.d_circs + Q.circ;
       // precision of the operator matvecs: the problem's current mode (mixed
       // form) or FP64; the circulant preconditioner of a mixed problem is FP32
-      const int* opmode = H.mixed ? B.d_mode + s2 : nullptr;
-      const int* pcmode = H.mixed ? B.d_ones + s2 : nullptr;
-      if (H.mixed) B.any_mixed = true;
+      const int* opmode = H.f32 ? B.d_mode + s2 : nullptr;
+      const int* pcmode = H.f32 ? B.d_ones + s2 : nullptr;
+      if (H.f32) B.any_mixed = true;
       auto fwd = [&](const double* src, int ncol, const int* md) {
         FftTask t; std::memset(&t, 0, sizeof(t));
         t.prob = i; t.L = Q.Lc; t.m0 = m0; t.ncol = ncol; t.circ = cd; t.x = src; t.ldx = n; t.X = X;
@@ -995,7 +1032,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
         bt.TH = Q.THc; bt.TS = Q.TSc; bt.nE = Q.nE; bt.Ek = U.put(Q.Ek); bt.Em = U.put(Q.Em);
         bt.EH = Q.EHc; bt.ES = Q.ESc; bt.sigma0 = Q.sigma; bt.band = Q.band; bt.sigma_used = Q.sigma_band;
         bt.fail = Q.band_fail; bt.R = l.R; bt.W = Yw; bt.ld = n; bt.active = l.active;
-        bt.fp32 = H.mixed;
+        bt.fp32 = H.f32;
         bnd.push_back(bt);
         if (m0 % 2 == 0 && (Q.D + 1) * m0 * m0 <= band_stage_doubles(1 << 30)) {   // stageable
           B.band_stage = std::max(B.band_stage, (Q.D + 1) * m0 * m0);
@@ -1021,7 +1058,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       }
       // image refresh of [X | P] for the problems whose matvecs just switched to
       // FP64 (flag 0 = refresh, 2 = leave: matches neither precision variant)
-      if (H.mixed) {
+      if (H.f32) {
         const int* rf = B.d_refresh + s2;
         rfXP.push_back(fwd(Yx, 2 * k, rf));
         riHXP.push_back(inv(Y1, l.HY, 2 * k, rf)); riSXP.push_back(inv(Y2, l.SY, 2 * k, rf));
@@ -1036,7 +1073,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       auto gt = [&](int a, int b, const double* A, int lda, const double* Bm, int ldb, double* C, int ldc,
                     double alpha, double beta) {
         GemmTask g; g.active = l.active; g.n = n; g.a = a; g.b = b; g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb;
-        g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta; g.sym = 0;
+        g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta; g.sym = 0; g.split = 0;
         g.tile = (k % 20 == 0) ? 20 : 16;   // a property of the problem alone
         B.gemm_tiles |= (g.tile == 20) ? 2 : 1;
         return g;
@@ -1066,6 +1103,38 @@ void plan(Batch& B, Slab& S, Slab& U) {
       nP.push_back({l.active, n, k, nullptr, n, l.Y + nk, n});
       nW.push_back({l.active, n, k, nullptr, n, l.Y + 2 * nk, n});
       rs.push_back({l.active, n, k, n, l.Y, l.HY, l.SY, l.lam, l.R, l.res});
+      if (H.mixed && n >= kSplitMinRows) {
+        // mixed form: the block iteration's dense products on the tensor cores
+        // (exact split products; the Gram sums over n split into K ranges)
+        auto to_tn = [&](GemmTask& g, std::vector<SplitTask>& out) {
+          SplitTask t;
+          std::memset(&t, 0, sizeof(t));
+          t.active = g.active; t.M = g.a; t.N = g.b; t.K = g.n;
+          t.A = g.A; t.a_m = g.lda; t.a_k = 1; t.B = g.B; t.b_k = 1; t.b_n = g.ldb;
+          t.C = g.C; t.c_m = 1; t.c_n = g.ldc; t.alpha = g.alpha; t.beta = g.beta;
+          t.ksplit = std::min(32, std::max(1, ((t.K + 63) / 64 + 7) / 8));
+          t.work = S.take<double>((size_t)t.ksplit * t.M * t.N);
+          t.sym = g.sym;
+          out.push_back(t);
+          g.split = 1;
+        };
+        auto to_nn = [&](GemmTask& g, std::vector<SplitTask>& out) {
+          SplitTask t;
+          std::memset(&t, 0, sizeof(t));
+          t.active = g.active; t.M = g.n; t.N = g.b; t.K = g.a;
+          t.A = g.A; t.a_m = 1; t.a_k = g.lda; t.B = g.B; t.b_k = 1; t.b_n = g.ldb;
+          t.C = g.C; t.c_m = 1; t.c_n = g.ldc; t.alpha = g.alpha; t.beta = g.beta;
+          t.ksplit = 1; t.work = nullptr; t.sym = 0;
+          out.push_back(t);
+          g.split = 1;
+        };
+        to_tn(tcx.back(), s_tcx); to_tn(tcp.back(), s_tcp);
+        to_nn(nw.back(), s_nw);
+        for (int w = 0; w < 3; ++w) to_nn(npp[npp.size() - 3 + w], s_npp);
+        to_tn(gg1[gg1.size() - 2], s_gg1); to_tn(gg1.back(), s_gg1);
+        to_tn(gg3[gg3.size() - 2], s_gg3); to_tn(gg3.back(), s_gg3);
+        to_nn(uu1.back(), s_uu1); to_nn(uu3.back(), s_uu3);
+      }
     }
     B.fft_chunks = (maxcols + B.fft_cc - 1) / B.fft_cc;
     auto TLp = [&](auto& v, Batch::TL& tl, int ga = 1, int gb = 1) {
@@ -1089,6 +1158,17 @@ void plan(Batch& B, Slab& S, Slab& U) {
     B.tnCx.tile = B.tnCp.tile = B.g1.tile = B.g3.tile = B.gemm_tiles;
     TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
     TLp(uu1, B.u1); TLp(uu3, B.u3);
+    auto TLs = [&](std::vector<SplitTask>& v, Batch::TL& tl) {
+      tl.sd = (void*)U.put(v); tl.sn = (int)v.size();
+      tl.sm = tl.snn = tl.sks = 1; tl.sred = false;
+      for (const SplitTask& t : v) {
+        tl.sm = std::max(tl.sm, t.M); tl.snn = std::max(tl.snn, t.N); tl.sks = std::max(tl.sks, t.ksplit);
+        tl.sred = tl.sred || t.work != nullptr;
+      }
+      while (tl.sn * tl.sks > 65535 && tl.sks > 1) tl.sks /= 2;   // grid z limit (tasks x K ranges)
+    };
+    TLs(s_tcx, B.tnCx); TLs(s_tcp, B.tnCp); TLs(s_nw, B.nnW); TLs(s_npp, B.nnP);
+    TLs(s_gg1, B.g1); TLs(s_gg3, B.g3); TLs(s_uu1, B.u1); TLs(s_uu3, B.u3);
     TLp(c2k, B.cp2k);
     TLp(nP, B.normP);
     TLp(nW, B.normW);
@@ -1274,13 +1354,20 @@ void mv_inv(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_fft", 1);
   launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, -1, st, B.any_mixed);
 }
-void gemm_tn(const Batch::TL& t, cudaStream_t st) {
-  PROF("k_gemm_tn", 1);
-  launch_gemm_tn(tl<GemmTask>(t), t.n, t.ga, t.gb, t.tile, st);   // ga, gb: output dims; tile: tile-size bits
+void split_products(Batch& B, const Batch::TL& t, cudaStream_t st) {
+  if (!t.sn) return;
+  PROF("k_split_gemm", 1);
+  launch_split_gemm((const SplitTask*)t.sd, t.sn, t.sm, t.snn, B.d_split_err, st, t.sks, t.sred);
 }
-void gemm_nn(const Batch::TL& t, cudaStream_t st) {
-  PROF("k_gemm_nn", 1);
-  if (t.n) k_gemm_nn<<<dim3(64, t.n), 256, 0, st>>>(tl<GemmTask>(t));
+void gemm_tn(Batch& B, const Batch::TL& t, cudaStream_t st) {
+  { PROF("k_gemm_tn", 1);
+    launch_gemm_tn(tl<GemmTask>(t), t.n, t.ga, t.gb, t.tile, st); }   // ga, gb: output dims; tile: tile-size bits
+  split_products(B, t, st);
+}
+void gemm_nn(Batch& B, const Batch::TL& t, cudaStream_t st) {
+  { PROF("k_gemm_nn", 1);
+    if (t.n) k_gemm_nn<<<dim3(64, t.n), 256, 0, st>>>(tl<GemmTask>(t)); }
+  split_products(B, t, st);
 }
 void rr(const Batch::TL& t, cudaStream_t st) {
   PROF("k_rr", 1);
@@ -1345,24 +1432,25 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   const int kMixedMaxIt = 10;
   std::vector<int> mode(ns, 0), f32_it(ns, 0), f32_stall(ns, 0);
   std::vector<double> f32_best(ns, INFINITY);
-  for (int s2 = 0; s2 < ns; ++s2) mode[s2] = B.hp[B.sidx[s2]].mixed;
+  for (int s2 = 0; s2 < ns; ++s2) mode[s2] = B.hp[B.sidx[s2]].f32;
   CUDA_TRY(ctx, cudaMemcpyAsync(B.d_mode, mode.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
   // X random, P = W = 0; Rayleigh-Ritz on X alone, then fresh images of [X | P]
   { PROF("k_init_x", 1); k_init_x<<<dim3(32, B.init.n), 256, 0, st>>>(tl<InitTask>(B.init)); }
   mv_HS(B, true, st);
-  gemm_tn(B.g1, st);
+  gemm_tn(B, B.g1, st);
   rr(B.rr1, st);
-  gemm_nn(B.u1, st);
+  gemm_nn(B, B.u1, st);
   copies(B.cp2k, st);
   mv_HS(B, true, st);
   std::vector<double> hres((size_t)ns * B.kmax);
   std::vector<int> active(ns, 1);
   // a residual that stops improving below kFloorTol is at the rounding floor
-  // of the pencil (it scales with kappa(S), up to ~1e8 after the cell
-  // reduction); Rayleigh quotients are then accurate to about the square of
-  // the residual over the gap, so the problem is done, provided the current
-  // residual is still within a factor 100 of that floor (a state that broke
-  // down after reaching it keeps iterating, or ends unconverged)
+  // of the pencil (it scales with the overlap's condition number); Rayleigh
+  // quotients are then accurate to about the square of the residual over the
+  // gap, so the problem is done, provided the current residual is still
+  // within a factor 100 of that floor (a state that broke down after reaching
+  // it keeps iterating, or ends unconverged).  1e-5 (tried) accepted a
+  // defect chain whose slowly converging pair was still 4e-5 off.
   const double kFloorTol = 1e-6;
   const int kStagnation = 8;
   // a floor within 100 tol of the target is recognised after 3 iterations
@@ -1435,20 +1523,20 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
       mv_inv(B, B.invPW, st);
     }
-    gemm_tn(B.tnCx, st);
-    gemm_nn(B.nnW, st);
+    gemm_tn(B, B.tnCx, st);
+    gemm_nn(B, B.nnW, st);
     normalize(B.normW, B.kmax, st);
     mv_HS(B, false, st);
     // Rayleigh-Ritz on [X | P | W]
-    gemm_tn(B.g3, st);
+    gemm_tn(B, B.g3, st);
     rr(B.rr3, st);
     // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
-    gemm_nn(B.u3, st);
+    gemm_nn(B, B.u3, st);
     copies(B.cp2k, st);
     normalize(B.normP, B.kmax, st);
     mv_HS(B, true, st);
-    gemm_tn(B.tnCp, st);
-    gemm_nn(B.nnP, st);
+    gemm_tn(B, B.tnCp, st);
+    gemm_nn(B, B.nnP, st);
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;
@@ -1787,6 +1875,19 @@ int fock_plan_problem_sizes(const fock_plan* P, int i, int* Nb, int* mcirc, int*
   return FOCK_OK;
 }
 
+int fock_plan_split_work(const fock_plan* P, double* tensor_flops, double* fp64_flops) {
+  if (!P) return FOCK_EINVAL;
+  double tf = 0.0, ff = 0.0;
+  for (const SplitTask& t : P->B.splits) {
+    const double tiles = (double)((t.M + 127) / 128) * ((t.N + 63) / 64), chunks = (double)((t.K + 63) / 64);
+    tf += tiles * chunks * 28.0 * 4.0 * (128.0 * 64.0 * 16.0 * 2.0);
+    ff += 2.0 * t.M * (double)t.N * t.K;
+  }
+  if (tensor_flops) *tensor_flops = tf;
+  if (fp64_flops) *fp64_flops = ff;
+  return FOCK_OK;
+}
+
 int fock_plan_history(const fock_plan* P, int i, double* res, int cap) {
   if (!P || i < 0 || i >= P->B.nprob) return FOCK_EINVAL;
   const auto& sid = P->B.sidx;
@@ -1956,10 +2057,57 @@ int fock_blocks_copy_generators(const fock_blocks* b, double* Hout, double* Sout
   return FOCK_OK;
 }
 
-int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of) {
+namespace {
+// Fourier indices [j0, j1) of an assembled periodic problem: eigenvalues
+// sorted (ties by index) into evals / block_of, and optionally the block
+// eigenvectors [j - j0][i][mu] (complex, interleaved) into vecs; host outputs.
+int periodic_range(fock_ctx* ctx, Batch& B, int j0, int j1, double* evals, int* block_of, double* vecs) {
+  const HostProb& H = B.hp[0];
+  const int nj = j1 - j0, n = nj * H.m0;
+  if (n == 0) return FOCK_OK;
+  ProfBind pb(ctx);
+  cudaStream_t st = ctx->stream;
+  { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
+  { PROF("k_null_tau", 1); launch_null_tau(B.d_nulls, (int)B.nulls.size(), st); }
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  char* mem = nullptr;
+  const size_t off_blk = ((size_t)n * 8 + 255) & ~(size_t)255;
+  const size_t off_pv = off_blk + (((size_t)n * 4 + 255) & ~(size_t)255);
+  const size_t off_pi = off_pv + (size_t)n2 * 8;
+  const size_t off_t = (off_pi + (size_t)n2 * 4 + 255) & ~(size_t)255;
+  const size_t off_v = (off_t + sizeof(FBlockTask) + 255) & ~(size_t)255;
+  const size_t vbytes = vecs ? (size_t)n * H.m0 * sizeof(cplx) : 0;
+  CUDA_TRY(ctx, cudaMalloc(&mem, off_v + vbytes));
+  double* ev = (double*)mem;
+  int* blk = (int*)(mem + off_blk);
+  FBlockTask f = B.fbp[0];
+  f.j0 = j0; f.nj = nj; f.outH = nullptr; f.outS = nullptr; f.want = 1; f.ev = ev; f.blk = blk; f.fail = nullptr;
+  f.vecs = vecs ? (cplx*)(mem + off_v) : nullptr;
+  int rc = FOCK_OK;
+  cudaError_t e = cudaMemcpyAsync(mem + off_t, &f, sizeof(f), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    { PROF("k_fblocks_eig", 1);
+      launch_fblocks(B.d_probs, (const FBlockTask*)(mem + off_t), 1, nj, H.m0, st, vecs != nullptr); }
+    { PROF("k_sort_global", 1); launch_sort_global(ev, blk, n, (double*)(mem + off_pv), (int*)(mem + off_pi), st); }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(evals, ev, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && block_of) e = cudaMemcpyAsync(block_of, blk, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && vecs) e = cudaMemcpyAsync(vecs, mem + off_v, vbytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) rc = set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e));
+  cudaFree(mem);
+  return rc;
+}
+}  // namespace
+
+int fock_circulant_eig(fock_ctx* ctx, const fock_blocks* b, double* evals, int* block_of, double* evecs) {
   if (!ctx || !b || !evals) return FOCK_EINVAL;
   Batch& B = const_cast<Batch&>(b->B);
   if (B.hp[0].kind != 0) return set_err(ctx, FOCK_EINVAL, "not a periodic problem");
+  const HostProb& H = B.hp[0];
+  if (evecs) return periodic_range(ctx, B, 0, H.L[0] * H.L[1] * H.L[2], evals, block_of, evecs);
   ProfBind pb(ctx);
   run_periodic(ctx, B);
   const Batch::PerProb& Q = B.pp[0];
@@ -1980,31 +2128,59 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
   const HostProb& H = B.hp[0];
   const int ncell = H.L[0] * H.L[1] * H.L[2];
   if (j0 < 0 || j1 < j0 || j1 > ncell) return set_err(ctx, FOCK_EINVAL, "need 0 <= j0 <= j1 <= |L|");
-  const int nj = j1 - j0, n = nj * H.m0;
-  if (n == 0) return FOCK_OK;
+  return periodic_range(ctx, B, j0, j1, evals, block_of, nullptr);
+}
+
+int fock_bloch_vectors(fock_ctx* ctx, const fock_blocks* b, int nsel, const int* jbar, const int* rank,
+                       double* U) {
+  if (!ctx || !b || nsel < 0 || (nsel && (!jbar || !rank || !U))) return FOCK_EINVAL;
+  Batch& B = const_cast<Batch&>(b->B);
+  if (B.hp[0].kind != 0) return set_err(ctx, FOCK_EINVAL, "not a periodic problem");
+  const HostProb& H = B.hp[0];
+  const int ncell = H.L[0] * H.L[1] * H.L[2], m0 = H.m0;
+  if (!nsel) return FOCK_OK;
+  // distinct Fourier indices: one single-block task each
+  std::vector<int> blocks_needed, slot(nsel);
+  for (int c = 0; c < nsel; ++c) {
+    if (jbar[c] < 0 || jbar[c] >= ncell || rank[c] < 0 || rank[c] >= m0)
+      return set_err(ctx, FOCK_EINVAL, "bloch_vectors: Fourier index or rank out of range");
+    auto it = std::find(blocks_needed.begin(), blocks_needed.end(), jbar[c]);
+    const int q = (int)(it - blocks_needed.begin());
+    if (it == blocks_needed.end()) blocks_needed.push_back(jbar[c]);
+    slot[c] = q * m0 + rank[c];   // column of that block's eigenvector array
+  }
+  const int nd = (int)blocks_needed.size();
   ProfBind pb(ctx);
   cudaStream_t st = ctx->stream;
   { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
   { PROF("k_null_tau", 1); launch_null_tau(B.d_nulls, (int)B.nulls.size(), st); }
-  int n2 = 1;
-  while (n2 < n) n2 <<= 1;
+  std::vector<FBlockTask> tasks(nd);
+  const size_t nbv = (size_t)ncell * m0;
+  const size_t off_ev = 0, off_y = ((size_t)nd * m0 * 8 + 255) & ~(size_t)255;
+  const size_t off_t = (off_y + (size_t)nd * m0 * m0 * sizeof(cplx) + 255) & ~(size_t)255;
+  const size_t off_i = (off_t + nd * sizeof(FBlockTask) + 255) & ~(size_t)255;
+  const size_t off_u = (off_i + 2 * (size_t)nsel * sizeof(int) + 255) & ~(size_t)255;
   char* mem = nullptr;
-  const size_t off_blk = ((size_t)n * 8 + 255) & ~(size_t)255;
-  const size_t off_pv = off_blk + (((size_t)n * 4 + 255) & ~(size_t)255);
-  const size_t off_pi = off_pv + (size_t)n2 * 8;
-  const size_t off_t = (off_pi + (size_t)n2 * 4 + 255) & ~(size_t)255;
-  CUDA_TRY(ctx, cudaMalloc(&mem, off_t + sizeof(FBlockTask)));
-  double* ev = (double*)mem;
-  int* blk = (int*)(mem + off_blk);
-  FBlockTask f = B.fbp[0];
-  f.j0 = j0; f.nj = nj; f.outH = nullptr; f.outS = nullptr; f.want = 1; f.ev = ev; f.blk = blk; f.fail = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&mem, off_u + nbv * nsel * sizeof(cplx)));
+  for (int q = 0; q < nd; ++q) {
+    FBlockTask f = B.fbp[0];
+    f.j0 = blocks_needed[q]; f.nj = 1; f.outH = nullptr; f.outS = nullptr; f.want = 1;
+    f.ev = (double*)(mem + off_ev) + (size_t)q * m0; f.blk = nullptr; f.fail = nullptr;
+    f.vecs = (cplx*)(mem + off_y) + (size_t)q * m0 * m0;
+    tasks[q] = f;
+  }
+  std::vector<int> ibuf(2 * (size_t)nsel);
+  for (int c = 0; c < nsel; ++c) { ibuf[c] = jbar[c]; ibuf[nsel + c] = slot[c]; }
   int rc = FOCK_OK;
-  cudaError_t e = cudaMemcpyAsync(mem + off_t, &f, sizeof(f), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(mem + off_t, tasks.data(), nd * sizeof(FBlockTask), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mem + off_i, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, (const FBlockTask*)(mem + off_t), 1, nj, H.m0, st); }
-    { PROF("k_sort_global", 1); launch_sort_global(ev, blk, n, (double*)(mem + off_pv), (int*)(mem + off_pi), st); }
-    e = cudaMemcpyAsync(evals, ev, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && block_of) e = cudaMemcpyAsync(block_of, blk, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, (const FBlockTask*)(mem + off_t), nd, 1, m0, st, true); }
+    { PROF("k_bloch_vectors", 1);
+      launch_bloch_vectors(H.L[0], H.L[1], H.L[2], m0, nsel, (const int*)(mem + off_i), (const cplx*)(mem + off_y),
+                           (const int*)(mem + off_i) + nsel, (cplx*)(mem + off_u), st); }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U, mem + off_u, nbv * nsel * sizeof(cplx), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   if (e != cudaSuccess) rc = set_err(ctx, FOCK_ECUDA, cudaGetErrorString(e));
@@ -2014,22 +2190,28 @@ int fock_circulant_eig_range(fock_ctx* ctx, const fock_blocks* b, int j0, int j1
 
 int fock_split_dgemm(fock_ctx* ctx, int M, int N, int K, const double* A, long long a_m, long long a_k,
                      const double* B, long long b_k, long long b_n, double* C, long long c_m, long long c_n,
-                     double alpha, double beta) {
-  if (!ctx || M < 0 || N < 0 || K < 0 || (M && N && (!A || !B || !C))) return FOCK_EINVAL;
+                     double alpha, double beta, int ksplit, int sym) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || (M && N && (!A || !B || !C)) || ksplit < 1 || ksplit > 1024 ||
+      (sym && M != N))
+    return FOCK_EINVAL;
   if (!M || !N) return FOCK_OK;
   cudaStream_t st = ctx->stream;
   SplitTask t;
   std::memset(&t, 0, sizeof(t));
   t.M = M; t.N = N; t.K = K; t.A = A; t.a_m = a_m; t.a_k = a_k; t.B = B; t.b_k = b_k; t.b_n = b_n;
   t.C = C; t.c_m = c_m; t.c_n = c_n; t.alpha = alpha; t.beta = beta;
+  t.ksplit = ksplit; t.sym = sym ? 1 : 0;
+  const bool red = ksplit > 1 || sym;
   char* mem = nullptr;
-  CUDA_TRY(ctx, cudaMalloc(&mem, 256 + sizeof(SplitTask)));
+  const size_t wbytes = red ? (size_t)ksplit * M * N * sizeof(double) : 0;
+  CUDA_TRY(ctx, cudaMalloc(&mem, 256 + sizeof(SplitTask) + 256 + wbytes));
+  if (red) t.work = (double*)(mem + 512 + ((sizeof(SplitTask) + 255) & ~(size_t)255));
   int herr = 0;
   cudaError_t e = cudaMemsetAsync(mem, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(mem + 256, &t, sizeof(t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     { ProfBind pb(ctx); PROF("k_split_gemm", 1);
-      launch_split_gemm((const SplitTask*)(mem + 256), 1, M, N, (int*)mem, st); }
+      launch_split_gemm((const SplitTask*)(mem + 256), 1, M, N, (int*)mem, st, ksplit, red); }
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, mem, sizeof(int), cudaMemcpyDeviceToHost, st);

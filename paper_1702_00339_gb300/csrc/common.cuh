@@ -33,14 +33,14 @@ constexpr int MAXRADIX = 16;   // radix factors of a circulant size
 // Numerically singular overlap directions (reading G16 of the pencil
 // H C = S C Lambda, Eqs. 2.4-2.5 and 3.11-3.12).  B[mu nu] = sum over lattice
 // offsets d of |S_d[mu nu]| bounds every entry of every Fourier block and every
-// block row of the lattice overlap; an overlap direction (of a Fourier block
-// Sbar_j, or of the cell overlap T_S[0] of a chain, repeated on every cell)
-// whose eigenvalue is at most tau = kSingularC * 2^-53 * ||B||_F lies at the
-// rounding level of the entries it is formed from and is removed; nothing else
-// is.  kSingularC = 64: an m0 x m0 block (m0 <= 32) of entries carrying a few
-// units of rounding relative to B has eigenvalues uncertain by about that.
-constexpr double kSingularC = 64.0;
-__host__ __device__ inline double null_tau(double normB_F) { return kSingularC * 0x1p-53 * normB_F; }
+// block row of the lattice overlap (||S||_2 <= ||B||_F).  The lattice overlap is
+// an N_b x N_b matrix (N_b = |L| m0); the usual rank tolerance of a matrix of
+// that order, N_b * eps * ||S|| (eps = 2^-52; the tolerance of LAPACK-based
+// numerical rank decisions), sets tau = N_b * eps * ||B||_F: an overlap
+// direction (of a Fourier block Sbar_j, whose eigen-directions are the
+// lattice overlap's, or of the cell overlap T_S[0] of a chain, repeated on
+// every cell) with eigenvalue at most tau is removed; nothing else is.
+__host__ __device__ inline double null_tau(double normB_F, double nb) { return nb * 0x1p-52 * normB_F; }
 
 // Modes of a 1D Galerkin form along one axis (gram task):
 //   RING - periodic axis: nodes 0..N-1 with wrap-around, potential tiled;
@@ -94,6 +94,12 @@ struct DefTab {
   int prob, axis, N, pad;
   double pos;           // nucleus coordinate in lattice units relative to X0 (h units)
   double* e;            // [R][N]
+  // mode 1 (box potential read as the plain lattice sum, Sec. 2.3 case (B), on
+  // a chain's axis 0): e[q][i] = sum over the L cells k of the Gaussian cell
+  // integral of the nucleus at pos + k n0, minus the replicated table of the
+  // same term (prep[t][r(rho) - rlo], t = nu R + q, r the reduced node)
+  int mode, L, nu, nr, rlo;
+  const double* prep;
 };
 
 // Defect field of a chain (reading R-DEF): F[rho][mu nu] = sum over defects d
@@ -182,6 +188,8 @@ struct FBlockTask {
   int* fail;                     // set to 1 if a block's Sbar is not positive definite
   const double* tau;             // FACTORS: the problem's dependency cut (k_null_tau); TOEPLITZ:
                                  // null, the cut is formed from TS in the block kernel
+  cplx* vecs;                    // optional [nj][m0][m0] (want 1): eigenvector i of block j at
+                                 // [j][i][mu], Sbar_j-orthonormal, ascending; removed directions zero
 };
 
 // Dependency cut of a periodic problem: B[mu nu] = prod over axes of the sum
@@ -189,6 +197,7 @@ struct FBlockTask {
 // overlap blocks are their Hadamard products, Lemma 3.4), tau = null_tau(||B||_F).
 struct NullTask {
   int m0, nF;
+  int nb;                        // N_b = |L| m0, the order of the lattice overlap
   const double* X[3];            // [noff][nF][m0*m0] per axis
   int noff[3];
   double* tau;                   // out
@@ -251,6 +260,7 @@ struct GemmTask {
   double alpha, beta;
   int sym;                     // TN with a symmetric result: upper tiles computed, mirrored
   int tile;                    // TN output tile: 20 when the problem's block size is a multiple of 20, else 16
+  int split;                   // 1: computed by k_split_gemm instead (mixed form)
 };
 
 struct ResidTask {
@@ -310,6 +320,7 @@ struct CanonTask {
   double* EHc; double* ESc;               // out transformed boundary blocks
   const int* Epart;                       // [nE] index of the transposed partner block
                                           // (self on the diagonal, -1 if none)
+  int nb;                                 // N_b = L m0, the order of the chain's overlap
   int ring_full;                          // 1: T_d, d = 0..D, are every ring offset once (a periodic
                                           //    chain planned as its whole circulant), so the scale B of
                                           //    the dependency cut is sum_d |T_S[d]|; 0: sum_d of
@@ -327,6 +338,10 @@ struct SplitTask {
   const double* B; long long b_k, b_n;
   double* C; long long c_m, c_n;
   double alpha, beta;
+  int ksplit;                  // K ranges computed by separate CTAs (>= 1)
+  double* work;                // null: C written directly; else [ksplit][M][N] partial sums,
+                               // reduced in a fixed order by k_split_reduce
+  int sym;                     // (with work) C is symmetric: the upper triangle is reduced, mirrored
 };
 
 // Device pointers and sizes the matvec of an assembled box chain needs.

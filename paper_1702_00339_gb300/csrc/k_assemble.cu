@@ -148,6 +148,23 @@ __global__ void k_deftab(const ProbDev* __restrict__ probs, const DefTab* __rest
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < cnt; it += gridDim.x * blockDim.x) {
     int q = it / D.N, i = it % D.N;
     double rho = (double)(i - D.pad);
+    if (D.mode == 1) {
+      // every cell's copy of the nucleus once (no window, no replication),
+      // cells beyond the Gaussian's reach skipped, minus the replicated term
+      const int n0 = P.n0;
+      const double reach = 7.0 / P.tq[q] + 2.0 * P.h;
+      const int klo = max(0, (int)floor(((rho + 0.5) * P.h - reach) / (n0 * P.h) - D.pos / n0) - 1);
+      const int khi = min(D.L - 1, (int)ceil(((rho + 0.5) * P.h + reach) / (n0 * P.h) - D.pos / n0) + 1);
+      double acc = 0.0;
+      for (int k = klo; k <= khi; ++k) {
+        const double dc = (rho + 0.5 - D.pos - (double)k * n0) * P.h;
+        acc += gauss_cell(P.tq[q], dc - 0.5 * P.h, dc + 0.5 * P.h);
+      }
+      const int ir = i - D.pad;
+      const int r = (ir < 0) ? ir : (ir >= D.L * n0 ? ir - (D.L - 1) * n0 : ir % n0);
+      D.e[it] = acc - D.prep[(size_t)(D.nu * P.R + q) * D.nr + (r - D.rlo)];
+      continue;
+    }
     double dc = (rho + 0.5 - D.pos) * P.h;      // node centre - nucleus
     if (per) {
       double period = (double)D.N * P.h;

@@ -11,7 +11,10 @@
 //       that embeds the symmetric block Toeplitz matrix with generators
 //       T_d = block (k+d, k), |d| <= D: Chat_j = T_0 + sum_d (w^{jd} T_d +
 //       w^{-jd} T_d^T), w = exp(-2 pi i / M) (Eq. A.3 convention).
-//     eigensolver: Jacobi eigendecomposition Sbar = Q diag(s) Q^H,
+//     eigensolver: Cholesky Sbar = L L^H and C = L^-1 Hbar L^-H when the
+//       factor certifies that Sbar has no eigenvalue at or below tau (the
+//       dependency cut; lambda_min >= 1 / ||L^-1||_F^2 > tau), else the
+//       Jacobi eigendecomposition Sbar = Q diag(s) Q^H,
 //       X = Q_K diag(s_K)^-1/2 over the kept directions K = {s > tau} (tau the
 //       problem's dependency cut: every direction when none is numerically
 //       singular, so C = X^H Hbar X has the pencil's eigenvalues exactly) --
@@ -36,17 +39,20 @@ enum FSource { FROM_FACTORS = 0, FROM_TOEPLITZ = 1 };
 // In-place lower Cholesky of a Hermitian positive definite m x m (row-major).
 __device__ bool cta_cholesky(cplx* a, int m) {
   __shared__ int bad;
+  __shared__ double s_inv;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < m; ++k) {
     if (threadIdx.x == 0) {
       double d = a[k * m + k].x;
       if (!(d > 0.0)) { bad = 1; d = 1.0; }
-      a[k * m + k] = cmk(sqrt(d), 0.0);
+      const double r = rsqrt_nr(d);       // 1 / sqrt(d) (Newton-Raphson from an FP32 seed)
+      a[k * m + k] = cmk(d * r, 0.0);
+      s_inv = r;
     }
     __syncthreads();
-    double dk = a[k * m + k].x;
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) a[i * m + k] = cscale(a[i * m + k], 1.0 / dk);
+    const double inv = s_inv;
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) a[i * m + k] = cscale(a[i * m + k], inv);
     __syncthreads();
     int nt = m - k - 1;
     for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
@@ -209,6 +215,65 @@ __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m
   return r;
 }
 
+// Reduction of a Hermitian pencil block (h, s), m x m with stride m, by
+// Cholesky: s = L L^H, h <- L^-1 h L^-H (exactly Hermitian), when the
+// factorisation certifies that s has no eigenvalue at or below tau
+// (lambda_min(s) = 1 / ||L^-1||_2^2 >= 1 / ||L^-1||_F^2 > tau): then no
+// direction is numerically singular and the reduction is the pencil's own.
+// Returns false with h unchanged otherwise (the caller takes the Jacobi
+// route).  a, q: scratch of m x m.  About m^3 complex multiply-adds against
+// ~100 m^3 for the Jacobi eigendecomposition.
+__device__ bool cta_cholesky_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m, double tau) {
+  __shared__ double red[32];
+  __shared__ int s_ok;
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[it] = s[it];
+  __syncthreads();
+  if (!cta_cholesky(a, m)) return false;                 // uniform: a shared flag
+  // q = L^-1 (lower triangular), one thread per column
+  for (int c = threadIdx.x; c < m; c += blockDim.x)
+    for (int i = 0; i < m; ++i) {
+      if (i < c) { q[i * m + c] = cmk(0.0, 0.0); continue; }
+      cplx t = cmk(i == c ? 1.0 : 0.0, 0.0);
+      for (int k = c; k < i; ++k) t = csub(t, cmul(a[i * m + k], q[k * m + c]));
+      q[i * m + c] = cscale(t, rcp_nr(a[i * m + i].x));
+    }
+  __syncthreads();
+  double part = 0.0;
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) part += cabs2(q[it]);
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    s_ok = (t > 0.0 && t * tau < 1.0);                     // 1 / ||L^-1||_F^2 > tau
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) {   // a = L^-1 h
+    const int i = it / m, j = it % m;
+    cplx t = cmk(0.0, 0.0);
+    for (int k = 0; k <= i; ++k) t = cadd(t, cmul(q[i * m + k], h[k * m + j]));
+    a[it] = t;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) {   // h = a L^-H (lower triangle)
+    const int i = it / m, j = it % m;
+    if (j > i) continue;
+    cplx t = cmk(0.0, 0.0);
+    for (int k = 0; k <= j; ++k) t = cadd(t, cmulc(a[i * m + k], q[j * m + k]));
+    h[it] = t;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < m * m; it += blockDim.x) {   // exactly Hermitian
+    const int i = it / m, j = it % m;
+    if (j > i) h[it] = cconj(h[j * m + i]);
+    else if (j == i) h[it].y = 0.0;
+  }
+  __syncthreads();
+  return true;
+}
+
 // Householder reduction of Hermitian c (full storage, destroyed) to a real
 // symmetric tridiagonal (d, e) with e_k = |c'_{k+1,k}| (a diagonal unitary
 // scaling removes the phases).
@@ -320,6 +385,9 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   double* e2 = ee + MAXM0;                 // e^2, and FP32 copies of d and e^2
   float* df = (float*)(e2 + MAXM0);
   float* e2f = df + MAXM0;
+  // eigenvectors (F.vecs): a copy of the reduced matrix and its Jacobi eigenvectors
+  cplx* Vc = (cplx*)(((uintptr_t)(e2f + MAXM0) + 15) & ~(uintptr_t)15);
+  cplx* Wv = Vc + ldj * ldj;
 
   if (F.source == FROM_FACTORS) {
     const int j3 = j % F.L[2], j2 = (j / F.L[2]) % F.L[1], j1 = j / (F.L[1] * F.L[2]);
@@ -411,11 +479,19 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red_b[w];
-      s_tau = null_tau(sqrt(t));
+      s_tau = null_tau(sqrt(t), (double)F.M * m0);   // the embedding's order
     }
   }
   __syncthreads();
-  const int r = cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep);
+  // Cholesky when it certifies that nothing is numerically singular, else the
+  // eigendecomposition of Sbar_j with the cut
+  const bool chol = cta_cholesky_reduce(H, S, Aj, Qj, m0, s_tau);
+  const int r = chol ? m0 : cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep);
+  const int ldr = r + (r & 1);
+  if (F.vecs) {   // the reduced matrix, kept for its eigenvectors
+    for (int it = threadIdx.x; it < r * r; it += blockDim.x) Vc[(it / r) * ldr + it % r] = H[it];
+    __syncthreads();
+  }
   if (r > 0) cta_tridiag(H, r, dd, ee, v, pv);
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     const double e2i = (i + 1 < r) ? ee[i] * ee[i] : 0.0;
@@ -436,9 +512,76 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     }
   } else if (threadIdx.x == 0) {
     // the lowest eigenvalue of an embedding block only sets the preconditioner
-    // shift (lowered by 2e-3 relative afterwards): 1e-9 relative suffices
+    // shift (lowered by 2e-5 relative afterwards): 1e-9 relative suffices
     F.ev[jl] = (r > 0) ? tridiag_eig_fast(df, e2f, dd, e2, r, 0, 1e-9) : INFINITY;
   }
+  if (F.vecs && F.want == 1) {
+    // eigenvectors of the reduced matrix by Jacobi (orthonormal also inside
+    // degenerate clusters), ordered by eigenvalue, mapped back by the
+    // reduction's transform: y = L^-H w (Cholesky route) or X w (X = Q_K
+    // diag(s_K)^-1/2), so y^H Sbar_j y = 1; the conjugate block gets conj(y)
+    __shared__ int ord[MAXM0];
+    __syncthreads();
+    if (r > 0) cta_jacobi_herm(Vc, Wv, r, ldr);
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < r; ++i) ord[i] = i;
+      for (int i = 1; i < r; ++i) {
+        const int o = ord[i];
+        const double e = Vc[o * ldr + o].x;
+        int q = i - 1;
+        while (q >= 0 && Vc[ord[q] * ldr + ord[q]].x > e) { ord[q + 1] = ord[q]; --q; }
+        ord[q + 1] = o;
+      }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < np; it += blockDim.x) {
+      const int i = it / m0, mu = it % m0;
+      cplx y = cmk(0.0, 0.0);
+      if (i < r) {
+        const int c = ord[i];
+        if (chol) {
+          for (int nu = mu; nu < m0; ++nu) y = cadd(y, cmul(cconj(Qj[nu * m0 + mu]), Wv[nu * ldr + c]));
+        } else {
+          for (int nu = 0; nu < r; ++nu) y = cadd(y, cmul(Aj[mu * r + nu], Wv[nu * ldr + c]));
+        }
+      }
+      F.vecs[(size_t)jl * np + it] = y;
+      if (jm >= 0) F.vecs[(size_t)(jm - F.j0) * np + it] = cconj(y);
+    }
+  }
+}
+
+// Lattice eigenvectors from Fourier-block eigenvectors (Prop. A.1, the
+// columns of the inverse DFT over the lattice index, U = (F^* (x) I) Ubar):
+// U[c][(k, mu)] = f_j[k] y[mu] with f_j[k] = exp(+2 pi i j.k / L) / sqrt(|L|),
+// for each requested pair c (Fourier index jbar[c], block-local vector
+// vec[c] in ys).  One thread per entry; twiddles by sincospi of the exact
+// integer phase j.k mod L.
+__global__ void k_bloch_vectors(int L1, int L2, int L3, int m0, int nsel, const int* __restrict__ jbar,
+                                const cplx* __restrict__ ys, const int* __restrict__ slot, cplx* __restrict__ U) {
+  const long long nb = (long long)L1 * L2 * L3 * m0, tot = nb * nsel;
+  const double inv = rsqrt((double)L1 * L2 * L3);
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it / nb);
+    const long long a = it % nb;
+    const int mu = (int)(a % m0);
+    const long long kb = a / m0;
+    const int k3 = (int)(kb % L3), k2 = (int)((kb / L3) % L2), k1 = (int)(kb / ((long long)L2 * L3));
+    const int j = jbar[c];
+    const int j3 = j % L3, j2 = (j / L3) % L2, j1 = j / (L2 * L3);
+    // phase 2 pi (j1 k1 / L1 + j2 k2 / L2 + j3 k3 / L3), each term reduced exactly
+    const double ph = 2.0 * ((double)((long long)j1 * k1 % L1) / L1 + (double)((long long)j2 * k2 % L2) / L2 +
+                             (double)((long long)j3 * k3 % L3) / L3);
+    double sn, cs;
+    sincospi(ph, &sn, &cs);
+    const cplx y = ys[(size_t)slot[c] * m0 + mu];
+    U[it] = cscale(cmul(cmk(cs, sn), y), inv);
+  }
+}
+
+void launch_bloch_vectors(int L1, int L2, int L3, int m0, int nsel, const int* jbar, const cplx* ys, const int* slot,
+                          cplx* U, cudaStream_t st) {
+  if (nsel > 0) k_bloch_vectors<<<1024, 256, 0, st>>>(L1, L2, L3, m0, nsel, jbar, ys, slot, U);
 }
 
 // One CTA per periodic problem: its dependency cut (NullTask).
@@ -463,7 +606,7 @@ __global__ void k_null_tau(const NullTask* __restrict__ tasks) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
-    *T.tau = null_tau(sqrt(t));
+    *T.tau = null_tau(sqrt(t), (double)T.nb);
   }
 }
 
@@ -592,16 +735,16 @@ __global__ void k_unpad_copy(const double* pv, const int* pidx, int n, double* v
 }
 
 // ---- launchers ----
-size_t fblocks_smem(int m0) {
+size_t fblocks_smem(int m0, bool vectors) {
   const int ldj = m0 + (m0 & 1);
   return (size_t)(2 * m0 * m0 + 2 * ldj * ldj + 2 * MAXM0) * sizeof(cplx) + 3 * MAXM0 * sizeof(double) +
-         2 * MAXM0 * sizeof(float);
+         2 * MAXM0 * sizeof(float) + (vectors ? 16 + 2 * ldj * ldj * sizeof(cplx) : 0);
 }
 
 void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool vectors) {
   if (!ntask || !maxnj) return;
-  size_t sm = fblocks_smem(maxm0);
+  size_t sm = fblocks_smem(maxm0, vectors);
   FOCK_SMEM_OPTIN(k_fblocks);
   // the rotation and update phases of an m0 x m0 block have about m0^2 / 2
   // parallel items: one warp for m0 <= 8 (more independent blocks resident

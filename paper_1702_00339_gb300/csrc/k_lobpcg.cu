@@ -63,6 +63,7 @@ __global__ void k_init_x(const InitTask* __restrict__ tasks) {
 template <int TILE>
 __global__ void __launch_bounds__(TILE * TILE) k_gemm_tn(const GemmTask* __restrict__ tasks) {
   const GemmTask T = tasks[blockIdx.z];
+  if (T.split) return;                       // computed on the tensor cores (mixed form)
   if (T.tile != TILE) return;                // the other tile size's launch
   if (T.active && *T.active == 0) return;
   const int i0 = blockIdx.x * TILE, j0 = blockIdx.y * TILE;
@@ -102,6 +103,7 @@ void launch_gemm_tn(const GemmTask* t, int n, int amax, int bmax, int tiles, cud
 // so each load of A serves four FP64 FMAs.
 __global__ void k_gemm_nn(const GemmTask* __restrict__ tasks) {
   const GemmTask T = tasks[blockIdx.y];
+  if (T.split) return;                       // computed on the tensor cores (mixed form)
   if (T.active && *T.active == 0) return;
   const int nb4 = (T.b + 3) >> 2;
   const int tot = T.n * nb4;
@@ -867,7 +869,7 @@ __global__ void k_cell_canon(const CanonTask* __restrict__ tasks) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
-    s_tau = null_tau(sqrt(t));
+    s_tau = null_tau(sqrt(t), (double)T.nb);
   }
   cta_jacobi(G, Q, m0, ld);
   if (threadIdx.x == 0) {

@@ -136,10 +136,11 @@ __device__ void stage(const double* __restrict__ P, long long sr, long long sk, 
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 1) k_split_gemm(const SplitTask* __restrict__ tasks, int* err) {
-  const SplitTask T = tasks[blockIdx.z];
+__global__ void __launch_bounds__(128, 1) k_split_gemm(const SplitTask* __restrict__ tasks, int max_ks, int* err) {
+  const SplitTask T = tasks[blockIdx.z / max_ks];
+  const int ks = blockIdx.z % max_ks, nks = max(T.ksplit, 1);
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  if (m0 >= T.M || n0 >= T.N) return;
+  if (ks >= nks || m0 >= T.M || n0 >= T.N) return;
   if (T.active && *T.active == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* Ap = (unsigned char*)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
@@ -170,10 +171,13 @@ __global__ void __launch_bounds__(128, 1) k_split_gemm(const SplitTask* __restri
   double acc[TN];
 #pragma unroll
   for (int c = 0; c < TN; ++c) acc[c] = 0.0;
-  const int nchunk = (T.K + KC - 1) / KC;
+  // this CTA's chunks of the summation: [c_lo, c_hi) of ceil(K / KC)
+  const int nchunk_all = (T.K + KC - 1) / KC, cps = (nchunk_all + nks - 1) / nks;
+  const int c_lo = min(ks * cps, nchunk_all), c_hi = min(c_lo + cps, nchunk_all);
+  const int nchunk = c_hi - c_lo;
   bool ok = true;
   for (int ch = 0; ch < nchunk && ok; ++ch) {
-    const int k0 = ch * KC;
+    const int k0 = (c_lo + ch) * KC;
     stage<TM>(Ab, T.a_m, T.a_k, rowsA, k0, T.K, Ap, A_PLANE, rexpA);
     stage<TN>(Bb, T.b_n, T.b_k, colsB, k0, T.K, Bp, B_PLANE, rexpB);
     asm volatile("fence.proxy.async.shared::cta;");   // generic-proxy writes -> tensor-core reads
@@ -240,6 +244,12 @@ __global__ void __launch_bounds__(128, 1) k_split_gemm(const SplitTask* __restri
       atomicExch(err, 1);
     }
     __syncthreads();
+  } else if (row < rowsA && T.work) {
+    // a partial sum over this CTA's chunks, reduced by k_split_reduce
+    double* Wr = T.work + ((long long)ks * T.M + m0 + row) * T.N + n0;
+#pragma unroll
+    for (int c = 0; c < TN; ++c)
+      if (c < colsB) Wr[c] = acc[c];
   } else if (row < rowsA) {
     // value = S * 2^(EA + EB - 2100): the per-row and per-column factors
     // 2^(E - 1050) multiply to it
@@ -257,13 +267,37 @@ __global__ void __launch_bounds__(128, 1) k_split_gemm(const SplitTask* __restri
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TMEM_COLS));
 }
 
+// C = alpha sum_ks work[ks] + beta C for the tasks with partial sums, the
+// K ranges added in a fixed order (results independent of scheduling); a
+// symmetric C takes its upper triangle and mirrors it bitwise.
+__global__ void k_split_reduce(const SplitTask* __restrict__ tasks) {
+  const SplitTask T = tasks[blockIdx.y];
+  if (!T.work) return;
+  if (T.active && *T.active == 0) return;
+  const long long mn = (long long)T.M * T.N;
+  const int nks = max(T.ksplit, 1);
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < mn; it += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(it / T.N), n = (int)(it % T.N);
+    if (T.sym && m > n) continue;
+    double s = 0.0;
+    for (int ks = 0; ks < nks; ++ks) s += T.work[ks * mn + it];
+    double* c = T.C + (long long)m * T.c_m + (long long)n * T.c_n;
+    const double v = (T.beta != 0.0) ? fma(T.beta, *c, T.alpha * s) : T.alpha * s;
+    *c = v;
+    if (T.sym && m < n) T.C[(long long)n * T.c_m + (long long)m * T.c_n] = v;
+  }
+}
+
 size_t split_gemm_smem() { return SPLIT_SMEM; }
 
-void launch_split_gemm(const SplitTask* tasks, int ntask, int max_m, int max_n, int* err, cudaStream_t st) {
+void launch_split_gemm(const SplitTask* tasks, int ntask, int max_m, int max_n, int* err, cudaStream_t st,
+                       int max_ks, bool reduce) {
   if (!ntask || max_m <= 0 || max_n <= 0) return;
   FOCK_SMEM_OPTIN(k_split_gemm);
-  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, ntask);
-  k_split_gemm<<<grid, 128, SPLIT_SMEM, st>>>(tasks, err);
+  max_ks = max_ks < 1 ? 1 : max_ks;
+  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, ntask * max_ks);
+  k_split_gemm<<<grid, 128, SPLIT_SMEM, st>>>(tasks, max_ks, err);
+  if (reduce) k_split_reduce<<<dim3(64, ntask), 256, 0, st>>>(tasks);
 }
 
 }  // namespace fock

@@ -19,7 +19,7 @@ _LIBPATH = os.path.join(_PKG, "libfock.so")
 FOCK_OK, FOCK_EINVAL, FOCK_ENOMEM, FOCK_ENOCONV = 0, -1, -2, -3
 FOCK_ETIMEOUT, FOCK_EAGAIN, FOCK_ECUDA = -4, -5, -6
 FOCK_OP_H, FOCK_OP_S = 0, 1
-FOCK_FP64, FOCK_MIXED = 0, 1
+FOCK_FP64, FOCK_MIXED, FOCK_MIXED_F32 = 0, 1, 2
 _NAMES = {0: "FOCK_OK", -1: "FOCK_EINVAL", -2: "FOCK_ENOMEM", -3: "FOCK_ENOCONV",
           -4: "FOCK_ETIMEOUT", -5: "FOCK_EAGAIN", -6: "FOCK_ECUDA"}
 
@@ -41,7 +41,8 @@ class c_problem(C.Structure):
                 ("ang", C.c_void_p), ("centre", C.c_void_p), ("R", C.c_int),        # const int*
                 ("sinc_t", C.c_void_p), ("sinc_c", C.c_void_p),                     # const double*
                 ("eps_support", C.c_double), ("ndef", C.c_int),
-                ("defects", C.c_void_p), ("k_eig", C.c_int), ("precision", C.c_int)]   # const fock_defect*
+                ("defects", C.c_void_p), ("k_eig", C.c_int), ("box_potential", C.c_int),
+                ("precision", C.c_int)]   # defects: const fock_defect*
 
 
 class c_serve_config(C.Structure):
@@ -103,7 +104,8 @@ def lib():
         L.fock_blocks_info.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int)]
         L.fock_blocks_copy_generators.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double),
                                                   P(C.c_double), P(C.c_double), P(C.c_int)]
-        L.fock_circulant_eig.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_int)]
+        L.fock_circulant_eig.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_int), P(C.c_double)]
+        L.fock_bloch_vectors.argtypes = [C.c_void_p, C.c_void_p, C.c_int, P(C.c_int), P(C.c_int), P(C.c_double)]
         L.fock_circulant_eig_range.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, P(C.c_double),
                                                P(C.c_int)]
         L.fock_toeplitz_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -133,10 +135,12 @@ def lib():
         L.fock_serve_stop.argtypes = [C.c_void_p]
         L.fock_measure_peaks.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
         L.fock_plan_history.argtypes = [C.c_void_p, C.c_int, P(C.c_double), C.c_int]
+        L.fock_plan_split_work.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
         L.fock_split_dgemm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int,
                                        C.c_void_p, C.c_longlong, C.c_longlong,
                                        C.c_void_p, C.c_longlong, C.c_longlong,
-                                       C.c_void_p, C.c_longlong, C.c_longlong, C.c_double, C.c_double]
+                                       C.c_void_p, C.c_longlong, C.c_longlong, C.c_double, C.c_double,
+                                       C.c_int, C.c_int]
         _lib = L
     return _lib
 
@@ -150,7 +154,7 @@ def _ip(a):
 
 
 # native layout of fock_problem (the same field order and alignment as c_problem)
-_PROBLEM_FMT = "@3i3i3iidiPPiPPPiPPdiPii"
+_PROBLEM_FMT = "@3i3i3iidiPPiPPPiPPdiPiii"
 
 
 class _Marshal:
@@ -183,12 +187,15 @@ class _Marshal:
             self.keep.append(d)
             dptr = C.addressof(d)
         L, per, N = p.L, p.periodic, p.N
-        self.s = c_problem.from_buffer_copy(struct.pack(
+        buf = struct.pack(
             _PROBLEM_FMT, int(L[0]), int(L[1]), int(L[2]), int(per[0]), int(per[1]), int(per[2]),
             int(N[0]), int(N[1]), int(N[2]), int(p.n0), float(p.b0), len(p.Z), bd + off[0], bd + off[1],
             len(p.exps), bd + off[2], bi, bi + 4 * ang.size, int(p.R),
             bd + off[3] if table else 0, bd + off[4] if table else 0, float(p.eps_support),
-            len(p.defects), dptr, int(p.k_eig), int(getattr(p, "precision", 0))))
+            len(p.defects), dptr, int(p.k_eig), int(getattr(p, "box_potential", 0)),
+            int(getattr(p, "precision", 0)))
+        buf += bytes(C.sizeof(c_problem) - len(buf))     # the struct's trailing padding
+        self.s = c_problem.from_buffer_copy(buf)
 
 
 def _host_outputs(problems):
@@ -340,11 +347,13 @@ class Context:
     def profile_reset(self):
         self._check(lib().fock_profile_reset(self.h), "fock_profile_reset")
 
-    def split_dgemm(self, M, N, K, A, a_m, a_k, B, b_k, b_n, Cp, c_m, c_n, alpha=1.0, beta=0.0):
+    def split_dgemm(self, M, N, K, A, a_m, a_k, B, b_k, b_n, Cp, c_m, c_n, alpha=1.0, beta=0.0,
+                    ksplit=1, sym=False):
         """C = alpha A B + beta C on the tensor cores (fock_split_dgemm);
         A, B, Cp are device pointers (ints), strides in elements."""
         self._check(lib().fock_split_dgemm(self.h, int(M), int(N), int(K), A, a_m, a_k, B, b_k, b_n,
-                                           Cp, c_m, c_n, float(alpha), float(beta)), "fock_split_dgemm")
+                                           Cp, c_m, c_n, float(alpha), float(beta), int(ksplit),
+                                           1 if sym else 0), "fock_split_dgemm")
 
     def profile_read(self, cap=64):
         names = C.create_string_buffer(32 * cap)
@@ -393,13 +402,29 @@ class Blocks:
                                                           _ip(rc_)), "fock_blocks_copy_generators")
         return H, S, EH[:self.nbound], ES[:self.nbound], rc_[:self.nbound]
 
-    def circulant_eig(self):
+    def circulant_eig(self, vectors=False):
+        """(eigenvalues ascending, Fourier index of each) and, with vectors,
+        the block eigenvectors as a complex array [block][i][mu]."""
         n = self.Nb
         ev = np.zeros(n)
         blk = np.zeros(n, np.int32)
-        self.ctx._check(lib().fock_circulant_eig(self.ctx.h, self.h, _dp(ev), _ip(blk)),
+        m0 = len(self.p.exps)
+        vec = np.zeros((n // m0, m0, m0), complex) if vectors else None
+        self.ctx._check(lib().fock_circulant_eig(self.ctx.h, self.h, _dp(ev), _ip(blk),
+                                                 vec.ctypes.data_as(C.POINTER(C.c_double)) if vectors else None),
                         "fock_circulant_eig")
-        return ev, blk
+        return (ev, blk, vec) if vectors else (ev, blk)
+
+    def bloch_vectors(self, jbar, rank):
+        """Lattice eigenvectors (N_b x nsel complex) of the eigenpairs given by
+        Fourier index and rank within the block (fock_bloch_vectors)."""
+        jb = np.ascontiguousarray(jbar, np.int32)
+        rk = np.ascontiguousarray(rank, np.int32)
+        U = np.zeros((len(jb), self.Nb), complex)
+        self.ctx._check(lib().fock_bloch_vectors(self.ctx.h, self.h, len(jb), _ip(jb), _ip(rk),
+                                                 U.ctypes.data_as(C.POINTER(C.c_double))),
+                        "fock_bloch_vectors")
+        return U.T
 
     def circulant_eig_range(self, j0, j1):
         """Eigenvalues of the Fourier blocks j0 <= jbar < j1 only, ascending."""
@@ -488,6 +513,12 @@ class Plan:
                 r["evals"], r["block_of"] = host[i]
             res.append(r)
         return res
+
+    def split_work(self):
+        """{"tensor_flops", "fp64_flops"} of one execution's tensor-core assembly."""
+        a, b = C.c_double(), C.c_double()
+        self.ctx._check(lib().fock_plan_split_work(self.h, C.byref(a), C.byref(b)), "fock_plan_split_work")
+        return {"tensor_flops": a.value, "fp64_flops": b.value}
 
     def history(self, i, cap=4096):
         """Largest wanted-pair relative residual at each iteration of problem

@@ -144,7 +144,7 @@ def _bad_problems():
     yield r(base, exps=np.ones(33), ang=np.zeros(33, int), centre=np.zeros(33, int)), "m0"
     yield r(base, R=2), "R <= 64"
     yield r(base, R=65), "R <= 64"
-    yield r(base, precision=2), "precision"
+    yield r(base, precision=3), "precision"
     yield r(base, L=(0, 1, 1)), "L >= 1"
     yield r(per, N=(41, 16, 16)), "N = L*n0"
     yield r(base, N=(39, 16, 16)), "N >= L*n0"

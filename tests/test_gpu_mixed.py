@@ -1,8 +1,10 @@
-"""Mixed form (FOCK_MIXED): FP32 preconditioner solves and FP32 embedded-FFT
-matvecs until a problem's residual falls below 1e-5, FP64 afterwards.  The
-stated bar: eigenvalues within 1e-8 relative of the oracle (and of the FP64
-form); problems in FP64 form are unaffected by mixed problems in their batch
-(bitwise)."""
+"""Mixed forms.  FOCK_MIXED: the assembly's quadrature contractions and the
+block iteration's Gram and basis products as exact split products on the
+tensor cores.  FOCK_MIXED_F32: in addition, FP32 preconditioner solves and
+FP32 embedded-FFT matvecs until a problem's residual falls below 1e-5, FP64
+afterwards.  The stated bar: eigenvalues within 1e-8 relative of the oracle
+(and of the FP64 form); problems in FP64 form are unaffected by mixed
+problems in their batch (bitwise)."""
 import dataclasses
 
 import numpy as np
@@ -27,8 +29,8 @@ def ctx():
     c.close()
 
 
-def _mixed(p):
-    q = dataclasses.replace(p, precision=1)
+def _mixed(p, precision=1):
+    q = dataclasses.replace(p, precision=precision)
     q.k_eig = p.k_eig
     return q
 
@@ -41,21 +43,22 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_mixed_within_stated_bar(ctx, name):
+def test_mixed_within_stated_bar(ctx, name, precision):
     p = CASES[name]()
     H, S = dense.build(p)
     ref = _cases.reference(p, H, S, base=MIXED_TOL)
-    mixed = ctx.solve([_mixed(p)])[0]
+    mixed = ctx.solve([_mixed(p, precision)])[0]
     fp64 = ctx.solve([p])[0]
     assert mixed["status"] == 0
-    _cases.report(name + "_mixed", _cases.check(ref, mixed["evals"]))
+    _cases.report(f"{name}_mixed{precision}", _cases.check(ref, mixed["evals"]))
     assert np.max(np.abs(mixed["evals"] - fp64["evals"])) <= MIXED_TOL * ref.scale
 
 
 def test_fp64_problems_unaffected_by_mixed_batch_mates(ctx):
     ps = [CASES[n]() for n in sorted(CASES)]
-    batch = ps + [_mixed(p) for p in ps]
+    batch = ps + [_mixed(p) for p in ps] + [_mixed(p, 2) for p in ps]
     together = ctx.solve(batch)
     for p, t in zip(ps, together[:len(ps)]):
         assert np.array_equal(ctx.solve([p])[0]["evals"], t["evals"])

@@ -18,7 +18,7 @@ def ctx():
     c.close()
 
 
-def _run(ctx, A, B, a_kcontig, b_kcontig, alpha=1.0, beta=0.0, C0=None):
+def _run(ctx, A, B, a_kcontig, b_kcontig, alpha=1.0, beta=0.0, C0=None, ksplit=1, sym=False):
     torch = pytest.importorskip("torch")
     M, K = A.shape
     N = B.shape[1]
@@ -29,7 +29,7 @@ def _run(ctx, A, B, a_kcontig, b_kcontig, alpha=1.0, beta=0.0, C0=None):
     b_k, b_n = (1, K) if b_kcontig else (N, 1)
     tC = torch.tensor(C0 if C0 is not None else np.zeros((M, N)), dtype=torch.float64, device="cuda")
     ctx.split_dgemm(M, N, K, tA.data_ptr(), a_m, a_k, tB.data_ptr(), b_k, b_n, tC.data_ptr(), N, 1,
-                    alpha, beta)
+                    alpha, beta, ksplit, sym)
     torch.cuda.synchronize()
     return tC.cpu().numpy()
 
@@ -107,3 +107,18 @@ def test_mixed_periodic_solve_matches_the_oracle(ctx):
     out = ctx.solve([_mixed(p)])[0]
     assert out["status"] == 0
     _cases.report("mixed_periodic_3d", _cases.check(_cases.reference(p, H, S), out["evals"], out["block_of"]))
+
+
+@pytest.mark.parametrize("ksplit", [1, 3, 32])
+def test_split_product_k_ranges_and_symmetric_gram(ctx, ksplit):
+    """The Gram form of the block iteration: Y^T (H Y) over a long sum split
+    into K ranges added in a fixed order, the upper triangle mirrored."""
+    rng = np.random.default_rng(ksplit)
+    n, nb = 5000, 150
+    Y = rng.standard_normal((n, nb))
+    HY = Y @ np.diag(rng.uniform(1, 3, nb)) + 1e-3 * rng.standard_normal((n, nb))
+    G = _run(ctx, Y.T.copy(), HY, True, True, ksplit=ksplit, sym=True)
+    ref = Y.T @ HY
+    up = np.triu_indices(nb)
+    assert np.all(np.abs(G[up] - ref[up]) <= _bound(Y.T, HY)[up])
+    assert np.array_equal(G, G.T)
