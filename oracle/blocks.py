@@ -161,21 +161,21 @@ def fourier_block_from_generators(p, Hk, Sk, jcell, tau=None):
 #
 # The problem is the Galerkin pencil H C = S C Lambda (Eqs. 2.4-2.5,
 # Eqs. 3.11-3.12, Prop. A.1).  A Gaussian basis can be dependent to the
-# rounding level of the overlap's own entries (several close exponents on one
-# centre; diffuse functions on a dense lattice): along such a direction the
-# computed overlap is zero or negative within its rounding, and the pencil's
-# value there is not determined by the data.  Only those directions are
-# removed.  The rounding level is set by the magnitudes that enter each
-# overlap entry: B[mu, nu] = sum over lattice offsets d of |S_d[mu, nu]| bounds
-# every entry of every Fourier block and every row of the lattice overlap, and
-# a direction whose overlap eigenvalue is at most
-#     tau = SINGULAR_C * u * ||B||_F        (u = 2^-53)
-# is numerically singular (an m0 x m0 block formed from entries that each
-# carry a few units of rounding relative to B has eigenvalues uncertain by
-# about m0 times that; SINGULAR_C = 64 covers m0 <= 32).  Where nothing lies
-# at or below tau the pencil is solved exactly as stated (LAPACK).
+# rounding level of the overlap (several close exponents on one centre;
+# diffuse functions on a dense lattice): along such a direction the computed
+# overlap is zero or negative within its rounding, and the pencil's value
+# there is not determined by the data.  Only those directions are removed.
+# B[mu, nu] = sum over lattice offsets d of |S_d[mu, nu]| bounds every entry
+# of every Fourier block and every block row of the lattice overlap
+# (||S||_2 <= ||B||_F).  The lattice overlap is of order N_b = |L| m0, and the
+# usual numerical-rank tolerance of a matrix of that order,
+#     tau = N_b * eps * ||B||_F        (eps = 2^-52),
+# is the cut: a direction whose overlap eigenvalue is at most tau is removed
+# (per Fourier block, whose eigen-directions are the lattice overlap's; per
+# cell on chains).  Where nothing lies at or below tau the pencil is solved
+# exactly as stated (LAPACK).
 U64 = 2.0 ** -53
-SINGULAR_C = 64
+EPS64 = 2.0 ** -52
 
 
 def _wall_free_chain_forms(p):
@@ -217,8 +217,8 @@ def overlap_scale(p):
 
 
 def null_threshold(p):
-    """tau = SINGULAR_C u ||B||_F (see above)."""
-    return SINGULAR_C * U64 * float(np.linalg.norm(overlap_scale(p)))
+    """tau = N_b eps ||B||_F (see above)."""
+    return p.Nb * EPS64 * float(np.linalg.norm(overlap_scale(p)))
 
 
 def block_pencil(Hb, Sb, tau, flip=()):
@@ -401,7 +401,7 @@ def structured(p):
     return bool(p.is_box or p.defects)
 
 
-def solve(p, box_potential="replicated"):
+def solve(p, box_potential=None):
     """The problem's answer under the dependency rule: a periodic problem's
     whole spectrum (+inf for removed directions), a box chain's or a defect
     problem's lowest k_eig eigenvalues.  box_potential selects reading R1 or

@@ -380,7 +380,7 @@ def test_block_pencil_reduces_to_range_of_S():
     Hh = Hh + Hh.conj().T
     A = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
     S = A @ A.conj().T + 0.1 * np.eye(m)
-    tau = blocks.SINGULAR_C * blocks.U64 * np.linalg.norm(np.abs(S))
+    tau = S.shape[0] * blocks.EPS64 * np.linalg.norm(np.abs(S))
     got = blocks.block_eigs_rule(Hh, S, tau)
     ref = scipy.linalg.eigh(Hh, S, eigvals_only=True)
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
@@ -388,7 +388,7 @@ def test_block_pencil_reduces_to_range_of_S():
     H0 = rng.standard_normal((r, r)) + 1j * rng.standard_normal((r, r))
     H0 = H0 + H0.conj().T
     S2 = F.conj().T @ F
-    tau2 = blocks.SINGULAR_C * blocks.U64 * np.linalg.norm(np.abs(S2))
+    tau2 = S2.shape[0] * blocks.EPS64 * np.linalg.norm(np.abs(S2))
     got = blocks.block_eigs_rule(F.conj().T @ H0 @ F, S2, tau2)
     assert np.sum(np.isinf(got)) == m - r
     ref = np.linalg.eigvalsh(H0)
@@ -415,7 +415,7 @@ def test_block_pencil_vectors_are_S_orthonormal_on_the_kept_directions():
     S = A @ A.conj().T + 1e-15 * np.eye(9)
     Hh = rng.standard_normal((9, 9)) + 1j * rng.standard_normal((9, 9))
     Hh = Hh + Hh.conj().T
-    tau = blocks.SINGULAR_C * blocks.U64 * np.linalg.norm(np.abs(S))
+    tau = S.shape[0] * blocks.EPS64 * np.linalg.norm(np.abs(S))
     ev, V, r = blocks.block_pencil(Hh, S, tau)
     assert r == 6 and V.shape == (9, 6) and np.sum(np.isinf(ev)) == 3
     assert np.max(np.abs(V.conj().T @ S @ V - np.eye(6))) < 1e-10
