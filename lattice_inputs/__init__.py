@@ -51,7 +51,8 @@ class Problem:
     eps_support: float = 1e-14
     defects: list = field(default_factory=list)
     k_eig: int = 0              # eigenpairs wanted by a box solve (0 = all)
-    precision: int = 0          # 0 FP64, 1 mixed (FP32 preconditioner and early matvecs)
+    precision: int = 0          # 0 FP64, 1 mixed (tensor-core split products), 2 mixed + FP32 phase
+    box_potential: int = 0      # box chains: 0 replicated central cell, 1 plain lattice sum over the cells
 
     # ---- plain derived sizes (no method arithmetic) ----
     @property

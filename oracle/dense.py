@@ -108,9 +108,19 @@ def _contract(p, Gs, slab_of, slabs, col_cells=None):
     return V
 
 
-def potential_matrix(p, forms=None, slab=None, box_potential="replicated"):
+def box_reading(p, box_potential=None):
+    """The box-potential reading of problem p: the argument when given, else
+    the problem's own field (box_potential 1 = "lattice_sum", reading R2;
+    0 = "replicated", reading R1)."""
+    if box_potential is not None:
+        return box_potential
+    return "lattice_sum" if getattr(p, "box_potential", 0) == 1 else "replicated"
+
+
+def potential_matrix(p, forms=None, slab=None, box_potential=None):
     """Dense V; box_potential selects reading R1 ("replicated") or R2
     ("lattice_sum") of the box potential (grid.potential_slabs)."""
+    box_potential = box_reading(p, box_potential)
     forms = forms or axis_forms(p)
     slab_of, slabs = slab if slab is not None else grid.potential_slabs(p, box_potential)
     V = _contract(p, [f[0] for f in forms], slab_of, slabs)
@@ -148,7 +158,7 @@ def defect_matrix(p, forms=None):
     return D
 
 
-def chain_matrices(p, box_potential="replicated"):
+def chain_matrices(p, box_potential=None):
     """Dense H and S of a chain (L2 = L3 = 1, no defects) with the same
     entries as build(), for chains too long for build()'s cell-pair tensors:
     the sum over the 3D grid of V_ab = sum_i g_a(i) g_b(i) P(i) is grouped
@@ -183,7 +193,7 @@ def chain_matrices(p, box_potential="replicated"):
     (G2, s1, a1), (G3, s2, a2) = tr
     S = s0 * (s1 * s2)[None, :, None, :]
     A = a0 * (s1 * s2)[None, :, None, :] + s0 * (a1 * s2 + s1 * a2)[None, :, None, :]
-    slab_of, slabs = grid.potential_slabs(p, box_potential)
+    slab_of, slabs = grid.potential_slabs(p, box_reading(p, box_potential))
     GG3 = G3[:, :, None] * G3[:, None, :]                         # (N3, mu, nu)
     GG2 = G2[:, :, None] * G2[:, None, :]
     W2 = np.zeros((slabs.shape[0], m0, m0))
@@ -200,7 +210,7 @@ def chain_matrices(p, box_potential="replicated"):
     return H, S.reshape(n, n)
 
 
-def build(p, with_parts=False, box_potential="replicated"):
+def build(p, with_parts=False, box_potential=None):
     """Dense (H, S) of problem p (and optionally A, V)."""
     forms = axis_forms(p)
     S, A = mass_kinetic(p, forms)
