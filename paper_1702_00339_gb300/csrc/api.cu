@@ -62,7 +62,7 @@ __global__ void k_init_x(const InitTask*);
 void launch_gemm_tn(const GemmTask*, int, int, int, int, cudaStream_t);
 __global__ void k_gemm_nn(const GemmTask*);
 __global__ void k_resid(const ResidTask*, double);
-__global__ void k_rr(const RRTask*, int);
+__global__ void k_rr(const RRTask*, int, int);
 __global__ void k_copy_cols(const CopyTask*);
 __global__ void k_colnorm(const CopyTask*);
 }  // namespace fock
@@ -132,6 +132,9 @@ const double kPrecShift = 2e-5;   // sigma = min_j lambda_min(Chat_j) - kPrecShi
 // shorter sums do not repay the digit splitting: measured 56 vs 50 ms per
 // batch of 64 chains of 512 functions, 0.84 vs 1.66 s for one of 16384)
 const int kSplitMinRows = 2048;
+// Rayleigh-Ritz working matrices (3 ld^2 doubles) up to this many bytes live in
+// shared memory
+const size_t kRRSmemCap = 160 * 1024;
 
 int set_err(fock_ctx* c, int code, const std::string& m) {
   if (c) c->err = m;
@@ -448,6 +451,8 @@ struct Batch {
   int band_stage = 0;                // doubles of a band-solve shared-memory stage
   int band_ringrow = 0;              // largest (D + 1) m0 of the staged band solves
   int gemm_tiles = 0;                // TN tile sizes in use: bit 0 = 16, bit 1 = 20
+  bool rr_small = false, rr_big = false;   // Rayleigh-Ritz launches needed (256 / 512 threads)
+  int rr_small_ld = 0;               // largest ld of the shared-memory problems
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
@@ -480,6 +485,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.band_stage = 0;
   B.band_ringrow = 0;
   B.gemm_tiles = 0;
+  B.rr_small = B.rr_big = false;
+  B.rr_small_ld = 0;
   B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
@@ -1094,8 +1101,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
       gg1.push_back(sym(gt(k, k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0)));
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
-      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
-      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode});
+      const int big = (3 * (size_t)ld3 * ld3 * sizeof(double) > kRRSmemCap) ? 1 : 0;
+      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
+      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
+      B.rr_small = B.rr_small || !big;
+      B.rr_big = B.rr_big || big;
+      if (!big) B.rr_small_ld = std::max(B.rr_small_ld, ld3);
       // [X' | P'] = Y[:, :nb] Cc, then copied over [X | P]; images recomputed by a matvec
       uu1.push_back(gt(k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
       uu3.push_back(gt(3 * k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
@@ -1369,13 +1380,17 @@ void gemm_nn(Batch& B, const Batch::TL& t, cudaStream_t st) {
     if (t.n) k_gemm_nn<<<dim3(64, t.n), 256, 0, st>>>(tl<GemmTask>(t)); }
   split_products(B, t, st);
 }
-void rr(const Batch::TL& t, cudaStream_t st) {
+void rr(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_rr", 1);
   if (!t.n) return;
   FOCK_SMEM_OPTIN(k_rr);
-  size_t sm = (size_t)3 * t.ga * t.ga * sizeof(double);
-  if (sm > 160 * 1024) sm = 0;
-  k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm);
+  // problems whose working matrices fit shared memory: 256 threads; the
+  // others (global memory, latency-bound): 512 threads, more warps in flight
+  if (B.rr_small) {
+    const size_t sm = (size_t)3 * B.rr_small_ld * B.rr_small_ld * sizeof(double);
+    k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm, 0);
+  }
+  if (B.rr_big) k_rr<<<t.n, 512, 0, st>>>(tl<RRTask>(t), 0, 1);
 }
 // unit 2-norm columns before a matvec: the FFT packs two real columns per
 // complex transform, and a column far smaller than its partner would get an
@@ -1438,7 +1453,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   { PROF("k_init_x", 1); k_init_x<<<dim3(32, B.init.n), 256, 0, st>>>(tl<InitTask>(B.init)); }
   mv_HS(B, true, st);
   gemm_tn(B, B.g1, st);
-  rr(B.rr1, st);
+  rr(B, B.rr1, st);
   gemm_nn(B, B.u1, st);
   copies(B.cp2k, st);
   mv_HS(B, true, st);
@@ -1529,7 +1544,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     mv_HS(B, false, st);
     // Rayleigh-Ritz on [X | P | W]
     gemm_tn(B, B.g3, st);
-    rr(B.rr3, st);
+    rr(B, B.rr3, st);
     // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
     gemm_nn(B, B.u3, st);
     copies(B.cp2k, st);

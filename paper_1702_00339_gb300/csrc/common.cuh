@@ -282,6 +282,9 @@ struct RRTask {
   double* Cc;             // out [nb x 2k] (ld): [C | C with the first k rows zeroed]
   int* fail;              // out: 1 if Y^T S Y was not numerically positive definite
   const int* mode;        // mixed form: 1 while the images are FP32 (coarser drop threshold)
+  int big;                // 1: the working matrices (3 ld^2 doubles) exceed shared memory; the
+                          //    problem runs in the 512-thread launch, else in the 256-thread one
+                          //    (a property of the problem alone, so results are batch-invariant)
 };
 
 struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };

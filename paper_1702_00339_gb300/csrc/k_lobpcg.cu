@@ -24,6 +24,10 @@ namespace fock {
 
 // eigenvalue given to the cell directions dropped by the canonical transform
 constexpr double kDecoupledEig = 1e6;
+// k_rr runs 256 threads when its working matrices fit shared memory, 512 when
+// they live in global memory (bases of 3 k > ~80 columns): twice the warps in
+// flight for the global loads that then bound it
+constexpr int kRRMaxThreads = 512;
 
 
 
@@ -382,7 +386,7 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
   // and keeps the sub-interval holding eigenvalue c (g + 1 times narrower).
   {
     __shared__ float s_lo[128], s_hi[128];       // kk <= 128
-    __shared__ int s_cnt[256];
+    __shared__ int s_cnt[kRRMaxThreads];
     float* df = reinterpret_cast<float*>(pv);    // pv is free here: d and e^2 in FP32
     float* e2f = df + 256;
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
@@ -620,8 +624,9 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
 // reduced matrix is C = Delta^-1/2 L^-1 (D GH D)_KK L^-T Delta^-1/2, whose k
 // lowest eigenpairs give the Ritz pairs.  Coefficients in the Y basis:
 // D P [L^-T Delta^-1/2 w; 0].
-__global__ void __launch_bounds__(256) k_rr(const RRTask* __restrict__ tasks, int smem_bytes) {
+__global__ void __launch_bounds__(kRRMaxThreads) k_rr(const RRTask* __restrict__ tasks, int smem_bytes, int big) {
   const RRTask T = tasks[blockIdx.x];
+  if (T.big != big) return;                 // the other launch's problems
   if (T.active && *T.active == 0) return;
   extern __shared__ double rr_smem[];
   // basis directions whose S-independent part is below kDropRel are dropped:
@@ -629,14 +634,14 @@ __global__ void __launch_bounds__(256) k_rr(const RRTask* __restrict__ tasks, in
   const double kDropRel = (T.mode && *T.mode) ? 1e-6 : 1e-10;
   const int ld = T.ld, k = T.k, nb = T.nb;
   // working matrices in shared memory when 3 ld^2 doubles fit, else global
-  const bool in_smem = (3 * ld * ld * (int)sizeof(double) <= smem_bytes);
+  const bool in_smem = !big && (3 * ld * ld * (int)sizeof(double) <= smem_bytes);
   double* base = in_smem ? rr_smem : T.work;
   double* C = base;                          // scaled H-Gram, then the reduced matrix (lower)
   double* V = base + (size_t)ld * ld;        // work matrix, then the eigenvectors
   double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram (lower, original indices), then L
   __shared__ double dsc[256], rl[256];
-  __shared__ long long wkey[8];
-  __shared__ int perm[256], order[256], wpos[8];
+  __shared__ long long wkey[kRRMaxThreads / 32];
+  __shared__ int perm[256], order[256], wpos[kRRMaxThreads / 32];
   __shared__ double tdd[256], tee[256], ttau[256], tpv[256], tlam[256];
   __shared__ int s_r, s_piv;
   __shared__ double s_rd;
