@@ -130,8 +130,9 @@ def potential_matrix(p, forms=None, slab=None, box_potential=None):
 def defect_matrix(p, forms=None):
     """Sum over defects of (newZ - Z_nu) <g_a g_b, P_single>, with P_single
     the rank-R kernel of the one substituted nucleus (no window, no
-    replication, minimum image on periodic axes).  Reading R-DEF of the
-    design notes: the paper only motivates defects (Sec. 1, Sec. 2.3 (B)).
+    replication, minimum image on periodic axes).  The paper only motivates
+    defects (Sec. 1, Sec. 2.3 (B)); this model of a vacancy or substitution
+    as a change of one nucleus' charge is the reading taken here.
     Pins: the single-molecule charge change, every cell of an odd periodic
     chain substituted (= a charge change of the window sum), every nucleus
     of a box vacated (= minus the box's lattice-sum potential)."""

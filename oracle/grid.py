@@ -1,7 +1,7 @@
 """Grid, nodal GTO vectors and the lattice-summed potential tensor.
 
-Readings of the paper used throughout (each listed with its reason in the
-design notes of the repository):
+Readings of the paper used throughout (where the paper leaves a choice
+open, the choice made here):
 
 * One uniform node set per axis with step h = b0/n0 (Sec. 2.3, the same h on
   all axes).  Periodic axis: N = L*n0 nodes at x_i = (i + 1/2) h, period
