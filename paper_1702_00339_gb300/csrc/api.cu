@@ -262,7 +262,8 @@ int validate(const fock_problem& p, HostProb& H, std::string& why) {
 }
 
 // FNV-1a hash of the problem's parameters: the LOBPCG start of a problem is
-// the same whatever batch it is solved in.
+// the same whatever batch it is solved in, and the same in every precision
+// form (the forms then differ by their arithmetic alone).
 uint64_t problem_seed(const HostProb& H) {
   uint64_t h = 1469598103934665603ull;
   auto mix = [&](const void* p, size_t n) {
@@ -270,7 +271,7 @@ uint64_t problem_seed(const HostProb& H) {
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
   };
   mix(H.L, sizeof(H.L)); mix(H.per, sizeof(H.per)); mix(H.N, sizeof(H.N)); mix(&H.n0, sizeof(H.n0));
-  mix(&H.mixed, sizeof(H.mixed)); mix(&H.f32, sizeof(H.f32)); mix(&H.r2, sizeof(H.r2));
+  mix(&H.r2, sizeof(H.r2));
   mix(&H.b0, sizeof(H.b0)); mix(&H.k_eig, sizeof(H.k_eig));
   mix(H.alpha.data(), H.alpha.size() * 8); mix(H.Z.data(), H.Z.size() * 8);
   mix(H.frac.data(), H.frac.size() * 8); mix(H.ang.data(), H.ang.size() * 4);
@@ -454,7 +455,7 @@ struct Batch {
   bool rr_small = false, rr_big = false;   // Rayleigh-Ritz launches needed (256 / 512 threads)
   int rr_small_ld = 0;               // largest ld of the shared-memory problems
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
-  TL init, tnCx, nnW, tnCp, nnP, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
+  TL init, tnCx, nnW, pcG, pcM, pcZ, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
   int eapply_gx = 16;
   int* d_ones = nullptr;
@@ -987,8 +988,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
     std::vector<FftTask> rfXP, riHXP, riSXP;
     std::vector<BmulTask> rbHS2;
     std::vector<InitTask> ini;
-    std::vector<GemmTask> tcx, nw, tcp, npp, gg1, gg3, uu1, uu3;
-    std::vector<SplitTask> s_tcx, s_nw, s_tcp, s_npp, s_gg1, s_gg3, s_uu1, s_uu3;
+    std::vector<GemmTask> tcx, nw, pcg, pcm, pcz, gg1, gg3, uu1, uu3;
+    std::vector<SplitTask> s_tcx, s_nw, s_gg1, s_gg3, s_uu1, s_uu3;
     std::vector<RRTask> r1, r3;
     std::vector<CopyTask> c2k, nP, nW;
     std::vector<ResidTask> rs;
@@ -1085,15 +1086,23 @@ void plan(Batch& B, Slab& S, Slab& U) {
         B.gemm_tiles |= (g.tile == 20) ? 2 : 1;
         return g;
       };
-      // W and P made S-orthogonal to X:  C = (S X)^T W,  W -= X C.  W is projected
-      // before its images are formed (fresh images of the projected vectors); P
-      // after its fresh images, which are then updated by linearity (HP, SP)
+      // W made S-orthogonal to X before its images are formed:  C = (S X)^T W,
+      // W -= X C (the images of the projected vectors are then fresh)
       tcx.push_back(gt(k, k, l.SY, n, Yw, n, l.Cx, k, 1.0, 0.0));
-      tcp.push_back(gt(k, k, l.SY, n, l.Y + nk, n, l.Cx, k, 1.0, 0.0));
       nw.push_back(gt(k, k, l.Y, n, l.Cx, k, l.Y + 2 * nk, n, -1.0, 1.0));
-      for (int w = 0; w < 3; ++w) {
-        double* base = w == 0 ? l.Y : (w == 1 ? l.HY : l.SY);
-        npp.push_back(gt(k, k, base, n, l.Cx, k, base + nk, n, -1.0, 1.0));
+      // P' made S-orthogonal to X' in the coefficients, before [X' | P'] = Y Cc is
+      // formed: with z_X, z_P the two column blocks of Cc and G_S = Y^T S Y,
+      // z_P -= z_X (z_X^T G_S z_P).  The images of [X' | P'] are computed fresh
+      // afterwards, so they match P' however much the projection cancels (images
+      // updated by linearity after a projection lose their relative accuracy in
+      // the directions it cancels, and the Rayleigh-Ritz step amplifies that)
+      {
+        auto small = [&](GemmTask g, int rows) { g.n = rows; return g; };
+        double* zX = l.Cc;
+        double* zP = l.Cc + (size_t)ld3 * k;
+        pcg.push_back(small(gt(3 * k, k, l.GS, ld3, zP, ld3, l.work, ld3, 1.0, 0.0), 3 * k));   // G_S z_P
+        pcm.push_back(small(gt(k, k, zX, ld3, l.work, ld3, l.Cx, k, 1.0, 0.0), 3 * k));        // z_X^T (G_S z_P)
+        pcz.push_back(small(gt(k, k, zX, ld3, l.Cx, k, zP, ld3, -1.0, 1.0), 3 * k));          // z_P -= z_X M
       }
       // Gram matrices Y^T H Y, Y^T S Y: symmetric, upper tiles only
       auto sym = [](GemmTask g) { g.sym = 1; return g; };
@@ -1139,9 +1148,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
           out.push_back(t);
           g.split = 1;
         };
-        to_tn(tcx.back(), s_tcx); to_tn(tcp.back(), s_tcp);
+        to_tn(tcx.back(), s_tcx);
         to_nn(nw.back(), s_nw);
-        for (int w = 0; w < 3; ++w) to_nn(npp[npp.size() - 3 + w], s_npp);
         to_tn(gg1[gg1.size() - 2], s_gg1); to_tn(gg1.back(), s_gg1);
         to_tn(gg3[gg3.size() - 2], s_gg3); to_tn(gg3.back(), s_gg3);
         to_nn(uu1.back(), s_uu1); to_nn(uu3.back(), s_uu3);
@@ -1162,11 +1170,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(rehxp, B.reHXP);
     TLp(ini, B.init);
     // TN products: ga, gb carry the largest output dimensions (tiles per launch)
-    TLp(tcx, B.tnCx, kk, kk); TLp(tcp, B.tnCp, kk, kk);
-    TLp(nw, B.nnW); TLp(npp, B.nnP);
+    TLp(tcx, B.tnCx, kk, kk);
+    TLp(nw, B.nnW);
+    TLp(pcg, B.pcG); TLp(pcm, B.pcM, kk, kk); TLp(pcz, B.pcZ);
     TLp(gg1, B.g1, kk, kk);
     TLp(gg3, B.g3, 3 * kk, 3 * kk);
-    B.tnCx.tile = B.tnCp.tile = B.g1.tile = B.g3.tile = B.gemm_tiles;
+    B.tnCx.tile = B.pcM.tile = B.g1.tile = B.g3.tile = B.gemm_tiles;
     TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
     TLp(uu1, B.u1); TLp(uu3, B.u3);
     auto TLs = [&](std::vector<SplitTask>& v, Batch::TL& tl) {
@@ -1178,7 +1187,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       }
       while (tl.sn * tl.sks > 65535 && tl.sks > 1) tl.sks /= 2;   // grid z limit (tasks x K ranges)
     };
-    TLs(s_tcx, B.tnCx); TLs(s_tcp, B.tnCp); TLs(s_nw, B.nnW); TLs(s_npp, B.nnP);
+    TLs(s_tcx, B.tnCx); TLs(s_nw, B.nnW);
     TLs(s_gg1, B.g1); TLs(s_gg3, B.g3); TLs(s_uu1, B.u1); TLs(s_uu3, B.u3);
     TLp(c2k, B.cp2k);
     TLp(nP, B.normP);
@@ -1545,13 +1554,14 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     // Rayleigh-Ritz on [X | P | W]
     gemm_tn(B, B.g3, st);
     rr(B, B.rr3, st);
-    // [X | P] <- Y Cc, fresh images, P S-orthogonal to X
+    // P' S-orthogonal to X' in the coefficients; [X | P] <- Y Cc, fresh images
+    gemm_nn(B, B.pcG, st);
+    gemm_tn(B, B.pcM, st);
+    gemm_nn(B, B.pcZ, st);
     gemm_nn(B, B.u3, st);
     copies(B.cp2k, st);
     normalize(B.normP, B.kmax, st);
     mv_HS(B, true, st);
-    gemm_tn(B, B.tnCp, st);
-    gemm_nn(B, B.nnP, st);
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;

@@ -75,16 +75,24 @@ __global__ void __launch_bounds__(TILE * TILE) k_gemm_tn(const GemmTask* __restr
   if (T.sym && j0 < i0) return;
   __shared__ double As[TILE][TILE + 1], Bs[TILE][TILE + 1];
   const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
-  double acc = 0.0;
+  // blocked summation: a partial sum over 8 tiles (128 or 160 terms) is added
+  // to the total, so the rounding error of a sum over n terms grows like
+  // (8 TILE + n / (8 TILE)) u instead of n u (n = 16384 on the 512-cell chains,
+  // where the Gram entries of nearly dependent directions decide the pivots of
+  // the Rayleigh-Ritz step)
+  double acc = 0.0, blk = 0.0;
+  int cnt = 0;
   for (int n0 = 0; n0 < T.n; n0 += TILE) {
     int r = n0 + tx;
     As[ty][tx] = (r < T.n && i0 + ty < T.a) ? T.A[(size_t)r + (size_t)T.lda * (i0 + ty)] : 0.0;
     Bs[ty][tx] = (r < T.n && j0 + ty < T.b) ? T.B[(size_t)r + (size_t)T.ldb * (j0 + ty)] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < TILE; ++q) acc += As[tx][q] * Bs[ty][q];
+    for (int q = 0; q < TILE; ++q) blk = fma(As[tx][q], Bs[ty][q], blk);
     __syncthreads();
+    if (++cnt == 8) { acc += blk; blk = 0.0; cnt = 0; }
   }
+  acc += blk;
   // thread (tx, ty) holds G[i0+tx][j0+ty]
   if (i0 + tx < T.a && j0 + ty < T.b) {
     double* g = T.C + (size_t)(i0 + tx) + (size_t)T.ldc * (j0 + ty);
