@@ -73,6 +73,11 @@ struct fock_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the structured problems' iteration runs on `hi` (greatest priority) while
+  // the periodic problems' eigensolves run on `stream`; ev_fork / ev_join
+  // order the two against `stream`
+  cudaStream_t hi = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t budget = 0;
   char* arena = nullptr;
   size_t arena_cap = 0;
@@ -1580,14 +1585,40 @@ struct fock_plan {
 
 namespace {
 
+// After the shared assembly, the periodic problems (one pass of wide launches:
+// a CTA per Fourier block) and the structured ones (a host-driven iteration of
+// narrow launches: a CTA per problem in the Rayleigh-Ritz step, which leaves
+// most SMs idle) run concurrently: the iteration on the context's
+// greatest-priority stream, whose CTAs the hardware schedules first as SMs free
+// up, the Fourier-block eigensolves on the context's stream, filling the rest.
+// Both read only the assembled generators and write disjoint buffers.  With the
+// kernel timers on, the two run one after the other on the context's stream,
+// so that each timer measures its kernel alone.
 int plan_execute(fock_plan& P, double tol, int maxit) {
   fock_ctx* ctx = P.ctx;
   Batch& B = P.B;
   run_assemble(ctx, B);
-  run_periodic(ctx, B);
-  run_struct_setup(ctx, B);
-  int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
-  if (rc) return rc;
+  const bool overlap = ctx->hi && !ctx->prof && !B.fbp.empty() && !B.fbs.empty();
+  if (!overlap) {
+    run_periodic(ctx, B);
+    run_struct_setup(ctx, B);
+    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
+    if (rc) return rc;
+  } else {
+    cudaStream_t user = ctx->stream;
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, user));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->hi, ctx->ev_fork, 0));
+    run_periodic(ctx, B);
+    ctx->stream = ctx->hi;
+    run_struct_setup(ctx, B);
+    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
+    ctx->stream = user;
+    // joined on every path: later work on the context's stream sees both
+    cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->hi);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ctx->ev_join, 0);
+    if (rc) return rc;
+    CUDA_TRY(ctx, e);
+  }
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;
 }
@@ -1767,6 +1798,19 @@ int fock_create(fock_ctx** out, int device, size_t hbm_budget_bytes, void* strea
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return FOCK_ECUDA; }
     c->own_stream = true;
   }
+  {   // the structured iteration's stream (greatest priority); without it plans run serially
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->hi) cudaStreamDestroy(c->hi);
+      if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+      if (c->ev_join) cudaEventDestroy(c->ev_join);
+      c->hi = nullptr; c->ev_fork = c->ev_join = nullptr;
+    }
+  }
   if (hbm_budget_bytes == 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
@@ -1784,6 +1828,9 @@ void fock_destroy(fock_ctx* c) {
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->arena) cudaFree(c->arena);
   if (c->hstage) cudaFreeHost(c->hstage);
+  if (c->hi) { cudaStreamSynchronize(c->hi); cudaStreamDestroy(c->hi); }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -157,10 +157,220 @@ __device__ void cta_jacobi_herm(cplx* a, cplx* v, int n, int ld) {
   }
 }
 
+// Eigendecomposition a = Q diag(w) Q^H of a Hermitian n x n matrix (row-major,
+// stride ld, n <= MAXM0), whole CTA (blockDim a multiple of 32), in about a
+// quarter of the FP64 instructions of the cyclic Jacobi method above:
+//  1. Householder reduction to tridiagonal form.  Step k maps x = a[k+1:, k]
+//     to (alpha, 0, ..., 0) with the reflector H_k = I - beta u u^H,
+//     u = (1, v_1, ...), alpha = -e^{i theta} ||x||, e^{i theta} = x_1 / |x_1|,
+//     beta = 1 + |x_1| / ||x||, v_i = x_i / (x_1 - alpha); the trailing block
+//     becomes H_k A H_k through p = beta A u, w = p - (beta / 2)(u^H p) u,
+//     A <- A - u w^H - w u^H.  The v_i stay below the subdiagonal of column k.
+//  2. The Hermitian tridiagonal T (real diagonal d, complex subdiagonal
+//     alpha_k) equals D T' D^H with T' real symmetric (subdiagonal |alpha_k|)
+//     and D = diag(phi), phi_0 = 1, phi_{k+1} = phi_k alpha_k / |alpha_k|.
+//  3. T' = Z diag(w) Z^T by the implicit QL iteration with Wilkinson's shift
+//     (Bowdler, Martin, Reinsch and Wilkinson, Numer. Math. 11 (1968)), its
+//     plane rotations accumulated into Z (the real parts of v); warp 0, each
+//     lane carrying its own copy of the tridiagonal and one row of Z.  An
+//     off-diagonal is negligible at eps ||T'||_inf (absolute accuracy, the
+//     reduction's own backward error).
+//  4. Q = H_0 ... H_{n-3} D Z, applied to v in place.
+// On return the diagonal of a holds the eigenvalues (real parts, unordered)
+// and the columns of v the orthonormal eigenvectors.  Returns false, a and v
+// then undefined, if some eigenvalue took more than 60 QL iterations.
+__device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
+  __shared__ double hb[MAXM0], hd[MAXM0], he[MAXM0];
+  __shared__ cplx hphi[MAXM0], hpw[MAXM0];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // ---- 1. tridiagonal reduction ----
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    if (warp == 0) {
+      const cplx xi = (lane < m) ? a[(k + 1 + lane) * ld + k] : cmk(0.0, 0.0);
+      double tail = (lane >= 1) ? cabs2(xi) : 0.0;
+      for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+      const cplx x1 = cmk(__shfl_sync(0xffffffffu, xi.x, 0), __shfl_sync(0xffffffffu, xi.y, 0));
+      double beta = 0.0;
+      if (tail > 0.0) {
+        const double ax1 = sqrt(cabs2(x1));
+        const double sig = sqrt(fma(ax1, ax1, tail));
+        const cplx ph = (ax1 > 0.0) ? cscale(x1, 1.0 / ax1) : cmk(1.0, 0.0);
+        beta = 1.0 + ax1 / sig;
+        const cplx inv_u1 = cscale(cconj(ph), 1.0 / (ax1 + sig));   // 1 / (x_1 - alpha)
+        if (lane >= 1 && lane < m) a[(k + 1 + lane) * ld + k] = cmul(xi, inv_u1);
+        if (lane == 0) a[(k + 1) * ld + k] = cscale(ph, -sig);        // alpha
+      }
+      if (lane == 0) hb[k] = beta;
+    }
+    __syncthreads();
+    const double beta = hb[k];
+    if (beta == 0.0) continue;                 // uniform: already reduced
+    // p = beta A u over the trailing block (4 threads per row)
+    const int tot = m * 4, totr = (tot + 31) & ~31;
+    for (int it = threadIdx.x; it < totr; it += blockDim.x) {
+      const int r = it >> 2, part = it & 3;
+      cplx acc = cmk(0.0, 0.0);
+      if (it < tot) {
+        const cplx* row = a + (size_t)(k + 1 + r) * ld + (k + 1);
+        for (int c = part; c < m; c += 4) {
+          const cplx uc = (c == 0) ? cmk(1.0, 0.0) : a[(k + 1 + c) * ld + k];
+          acc = cadd(acc, cmul(row[c], uc));
+        }
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (it < tot && part == 0) hpw[r] = cscale(acc, beta);
+    }
+    __syncthreads();
+    // w = p - (beta / 2)(u^H p) u   (u^H p real up to rounding)
+    if (warp == 0) {
+      const cplx ui = (lane == 0) ? cmk(1.0, 0.0) : ((lane < m) ? a[(k + 1 + lane) * ld + k] : cmk(0.0, 0.0));
+      const cplx pi = (lane < m) ? hpw[lane] : cmk(0.0, 0.0);
+      double up = ui.x * pi.x + ui.y * pi.y;   // Re(conj(u_i) p_i)
+      for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(0xffffffffu, up, o);
+      const double K = 0.5 * beta * up;
+      __syncwarp();
+      if (lane < m) hpw[lane] = csub(pi, cscale(ui, K));
+    }
+    __syncthreads();
+    // A <- A - u w^H - w u^H on the trailing block
+    for (int it = threadIdx.x; it < m * m; it += blockDim.x) {
+      const int i = it / m, j = it % m;
+      const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
+      const cplx uj = (j == 0) ? cmk(1.0, 0.0) : a[(k + 1 + j) * ld + k];
+      cplx* aij = a + (size_t)(k + 1 + i) * ld + (k + 1 + j);
+      *aij = csub(*aij, cadd(cmulc(ui, hpw[j]), cmulc(hpw[i], uj)));
+    }
+    __syncthreads();
+  }
+  // ---- 2. real tridiagonal T' and the phases D ----
+  if (threadIdx.x == 0) {
+    cplx phi = cmk(1.0, 0.0);
+    for (int k = 0; k < n; ++k) {
+      hd[k] = a[k * ld + k].x;
+      hphi[k] = phi;
+      if (k + 1 < n) {
+        const cplx al = a[(k + 1) * ld + k];
+        const double aa = sqrt(cabs2(al));
+        he[k] = aa;
+        if (aa > 0.0) phi = cmul(phi, cscale(al, 1.0 / aa));
+      } else {
+        he[k] = 0.0;
+      }
+    }
+    s_ok = 1;
+  }
+  for (int it = threadIdx.x; it < n * n; it += blockDim.x) {   // Z = I
+    const int i = it / n, j = it % n;
+    v[i * ld + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // ---- 3. implicit QL on warp 0 ----
+  if (warp == 0) {
+    double d[MAXM0], e[MAXM0];
+    double tn = 0.0;
+    for (int i = 0; i < n; ++i) {
+      d[i] = hd[i];
+      e[i] = he[i];
+      tn = fmax(tn, fabs(d[i]) + e[i] + (i > 0 ? e[i - 1] : 0.0));
+    }
+    const double small = 2.220446049250313e-16 * tn;   // eps ||T'||_inf
+    bool ok = true;
+    for (int l = 0; l < n && ok; ++l) {
+      for (int iter = 0;; ++iter) {
+        int m = l;
+        while (m + 1 < n && fabs(e[m]) > small) ++m;
+        if (m == l) break;                               // d[l] is an eigenvalue
+        if (iter == 60) { ok = false; break; }
+        // shift: the eigenvalue of the leading 2 x 2 of block l..m nearer d[l]
+        double g = (d[l + 1] - d[l]) * rcp_nr(2.0 * e[l]);
+        const double q1 = fma(g, g, 1.0);
+        const double r1 = q1 * rsqrt_nr(q1);
+        g = d[m] - d[l] + e[l] * rcp_nr(g + copysign(r1, g));
+        double s = 1.0, c = 1.0, p = 0.0;
+        bool split = false;
+        for (int i = m - 1; i >= l; --i) {
+          const double f = s * e[i], b = c * e[i];
+          const double q2 = fma(f, f, g * g);
+          if (q2 == 0.0) {                               // the chase stopped: restart
+            d[i + 1] -= p;
+            e[m] = 0.0;
+            split = true;
+            break;
+          }
+          const double ir = rsqrt_nr(q2);
+          e[i + 1] = q2 * ir;
+          s = f * ir;
+          c = g * ir;
+          g = d[i + 1] - p;
+          const double r = fma(d[i] - g, s, 2.0 * c * b);
+          p = s * r;
+          d[i + 1] = g + p;
+          g = fma(c, r, -b);
+          if (lane < n) {                                // rotate columns i, i + 1 of Z
+            const double zi = v[lane * ld + i].x, zj = v[lane * ld + i + 1].x;
+            v[lane * ld + i + 1].x = fma(s, zi, c * zj);
+            v[lane * ld + i].x = fma(c, zi, -s * zj);
+          }
+        }
+        if (split) continue;
+        d[l] -= p;
+        e[l] = g;
+        e[m] = 0.0;
+      }
+    }
+    if (!ok && lane == 0) s_ok = 0;
+    if (lane < n) hd[lane] = d[lane];
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  // ---- 4. Q = H_0 ... H_{n-3} D Z ----
+  for (int it = threadIdx.x; it < n * n; it += blockDim.x) {
+    const int i = it / n, j = it % n;
+    v[i * ld + j] = cscale(hphi[i], v[i * ld + j].x);
+  }
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const double beta = hb[k];
+    if (beta == 0.0) continue;
+    const int m = n - k - 1;
+    // t_j = u^H V[k+1:, j]  (4 threads per column)
+    const int tot = n * 4, totr = (tot + 31) & ~31;
+    for (int it = threadIdx.x; it < totr; it += blockDim.x) {
+      const int j = it >> 2, part = it & 3;
+      cplx acc = cmk(0.0, 0.0);
+      if (it < tot)
+        for (int i = part; i < m; i += 4) {
+          const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
+          acc = cadd(acc, cmulc(v[(k + 1 + i) * ld + j], ui));   // conj(u_i) V_ij
+        }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (it < tot && part == 0) hpw[j] = cscale(acc, beta);
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < m * n; it += blockDim.x) {
+      const int i = it / n, j = it % n;
+      const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
+      v[(k + 1 + i) * ld + j] = csub(v[(k + 1 + i) * ld + j], cmul(ui, hpw[j]));
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i * ld + i] = cmk(hd[i], 0.0);
+  __syncthreads();
+  return true;
+}
+
 // Reduction of a Hermitian pencil block (h, s), both m x m with stride m, to
-// a standard Hermitian matrix: Jacobi eigendecomposition s = Q diag(w) Q^H
-// (in a, q: scratch of ld x ld, ld = m + (m & 1)), kept set K = {w_i > tau}
-// (tau absolute: the dependency cut) in ascending Jacobi index,
+// a standard Hermitian matrix: eigendecomposition s = Q diag(w) Q^H
+// (cta_herm_eig; in a, q: scratch of ld x ld, ld = m + (m & 1)), kept set
+// K = {w_i > tau} (tau absolute: the dependency cut) in ascending index,
 // X = Q_K diag(w_K)^-1/2, and h <- X^H h X (r x r, stride r, exactly
 // Hermitian).  With every direction kept, X^H s X = I and the eigenvalues of
 // h are the pencil's.  Returns r = |K|.  sv and keep are shared arrays of
@@ -171,7 +381,11 @@ __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m
   const int ld = m + (m & 1);
   for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
   __syncthreads();
-  cta_jacobi_herm(a, q, m, ld);
+  if (!cta_herm_eig(a, q, m, ld)) {   // QL out of iterations: the Jacobi method
+    for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
+    __syncthreads();
+    cta_jacobi_herm(a, q, m, ld);
+  }
   if (threadIdx.x == 0) {
     int r = 0;
     for (int i = 0; i < m; ++i)

@@ -13,7 +13,12 @@ GPU):
   (LAPACK on 16384 x 16384);
 * box chains of the timed workload (64 cells, grid 1024x256x256), where the
   dense oracle runs in the test: a batch solved together, each against it.
+
+The mixed form (tensor-core split products in the assembly and in the block
+iteration) is checked against the same stored results with the mixed bar
+(base 1e-8).
 """
+import dataclasses
 import os
 
 import numpy as np
@@ -37,7 +42,16 @@ def ctx():
     c.close()
 
 
-def _periodic_against_golden(ctx, p, name):
+MIXED_BASE = 1e-8
+
+
+def _mixed(p):
+    q = dataclasses.replace(p, precision=1)
+    q.k_eig = p.k_eig
+    return q
+
+
+def _periodic_against_golden(ctx, p, name, base=1e-10):
     g = np.load(os.path.join(GOLD, name + ".npz"))
     b = ctx.assemble(p)
     gh, gs, _, _, _ = b.generators()
@@ -49,8 +63,8 @@ def _periodic_against_golden(ctx, p, name):
     fin = np.isfinite(ev)
     assert np.all(np.diff(ev[fin]) >= 0) and np.all(fin[:fin.sum()])   # +inf (removed) last
     assert np.all(np.bincount(blk, minlength=p.ncell) == p.m0)
-    cands, scale = _cases.golden_candidates(g)
-    _cases.report(name, _cases.check_blocks(cands, scale, ev, blk))
+    cands, scale = _cases.golden_candidates(g, base)
+    _cases.report(name + ("_mixed" if base != 1e-10 else ""), _cases.check_blocks(cands, scale, ev, blk))
 
 
 def test_periodic_16cubed_m0_16(ctx):
@@ -62,11 +76,25 @@ def test_periodic_32cubed_m0_32(ctx):
                              "config5_periodic_32cubed_seed0")
 
 
-def test_box_512_m0_32_lowest_64(ctx):
+def test_periodic_32cubed_m0_32_mixed(ctx):
+    _periodic_against_golden(ctx, _mixed(_cases.with_table(li.config5_periodic(0))),
+                             "config5_periodic_32cubed_seed0", base=MIXED_BASE)
+
+
+def test_periodic_16cubed_m0_16_mixed(ctx):
+    _periodic_against_golden(ctx, _mixed(_cases.with_table(li.config3(0))),
+                             "config3_periodic_16cubed_seed0", base=MIXED_BASE)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_box_512_m0_32_lowest_64(ctx, precision):
     from paper_1702_00339_gb300 import fock
     name = "config5_box_512_seed0"
     g = np.load(os.path.join(GOLD, name + ".npz"))
     p = _cases.with_table(li.config5_box(0))
+    if precision:
+        p = _mixed(p)
+    base = MIXED_BASE if precision else 1e-10
     b = ctx.assemble(p)
     TH, TS, EH, ES, rc = b.generators()
     D = (TH.shape[0] - 1) // 2
@@ -85,11 +113,11 @@ def test_box_512_m0_32_lowest_64(ctx):
     scale = float(np.max(np.abs(g["ev"][0])))
     cands = []
     for evv, vn in zip(g["ev"], g["vn2"]):
-        tol = np.maximum(1e-10 * scale, _cases.EPS_DATA * (float(g["Hn"]) + np.abs(evv) * float(g["Sn"])) * vn)
+        tol = np.maximum(base * scale, _cases.EPS_DATA * (float(g["Hn"]) + np.abs(evv) * float(g["Sn"])) * vn)
         cands.append((evv, tol))
     e = _cases._match(np.asarray(ev), cands)
     assert e is not None, f"lowest {k} off every variant: max |d| {np.max(np.abs(ev - g['ev'][0])):.3e}"
-    _cases.report(name, e / scale)
+    _cases.report(name + ("_mixed" if precision else ""), e / scale)
 
 
 def test_box_chains_of_the_timed_workload(ctx):
