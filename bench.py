@@ -117,21 +117,49 @@ def _poll_all(srv, tickets, deadline):
     return out
 
 
-def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plain_s=4.0,
-                limit_s=300.0):
-    """Continuous-batching leg: capacity from a burst of n_warm requests, then
-    n_stream requests with Poisson arrivals at 80 % of that capacity; latency
-    = done - submit per request (server clock).  Also the plain per-lattice
-    FP64 path (one fock_solve per request, sequential) on the same mix."""
-    srv = fock.Server(dev, slots=slots, max_batch=max_batch)
-    warm = serving_requests(n_warm, seed=3100)
-    t0 = time.perf_counter()
-    tk = [srv.submit(p) for p in warm]
-    rw = _poll_all(srv, tk, t0 + limit_s)
-    cap = n_warm / (time.perf_counter() - t0)
-    stream = serving_requests(n_stream, seed=3000)
-    rate = 0.8 * cap
+def serving_run(fock, dev, n_stream=512, n_burst=128, slots=2, max_batch=64, limit_s=300.0):
+    """Continuous batching (fock_serve_*) against the plain per-lattice FP64
+    path (one fock_solve per request, one after the other), both on the same
+    burst of n_burst requests of the serving mix: solves/s of each.  The
+    server solves the burst in the FP64 form and in the mixed form; the
+    mixed results are compared with the plain FP64 ones request by request
+    (largest |difference| / max |lambda| over each request's eigenvalues), and
+    the batched FP64 results must equal the plain ones bit for bit (a result
+    does not depend on its batch).  Then n_stream requests with Poisson
+    arrivals at 80 % of the mixed burst capacity, in the mixed form: p50 / p99
+    latency (done - submit, server clock) and the stream's throughput."""
+    burst = serving_requests(n_burst, seed=3100)
+    mburst = mixed_of(burst)
+
+    def batched(ps):
+        srv = fock.Server(dev, slots=slots, max_batch=max_batch)
+        _poll_all(srv, [srv.submit(p) for p in ps[:8]], time.perf_counter() + limit_s)   # warm-up
+        t0 = time.perf_counter()
+        res = _poll_all(srv, [srv.submit(p) for p in ps], t0 + limit_s)
+        rate = len(ps) / (time.perf_counter() - t0)
+        srv.stop()
+        return rate, res
+
+    cap64, r64 = batched(burst)
+    capm, rm = batched(mburst)
+    ctx = fock.Context(dev)
+    ctx.solve([burst[0]], check=False)
+    t1 = time.perf_counter()
+    rp = [ctx.solve([p], check=False)[0] for p in burst]
+    plain = len(burst) / (time.perf_counter() - t1)
+    ctx.close()
+    same = all(np.array_equal(a["evals"], b["evals"]) for a, b in zip(r64, rp))
+    diff = 0.0
+    for a, b in zip(rm, rp):
+        x, y = np.asarray(a["evals"]), np.asarray(b["evals"])
+        f = np.isfinite(x) & np.isfinite(y)
+        if f.any():
+            diff = max(diff, float(np.max(np.abs(x[f] - y[f])) / np.max(np.abs(y[f]))))
+
+    stream = mixed_of(serving_requests(n_stream, seed=3000))
+    rate = 0.8 * capm
     gaps = np.random.default_rng(7).exponential(1.0 / rate, size=n_stream)
+    srv = fock.Server(dev, slots=slots, max_batch=max_batch)
     tickets = []
     t0 = time.perf_counter()
     nxt = t0
@@ -146,30 +174,25 @@ def serving_run(fock, dev, n_stream=512, n_warm=128, slots=2, max_batch=64, plai
     st = srv.stats()
     srv.stop()
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res])
-    ok = sum(r["status"] == 0 for r in res + rw)
-    fails = [{"stream": nm, "i": i, "status": r["status"], "L": list(p.L), "periodic": list(p.periodic),
-              "m0": len(p.exps), "k": p.k_eig, "iters": r["iters"], "resid": r["resid"],
-              "batch_size": r["batch_size"]}
-             for nm, ps_, rs_ in (("warm", warm, rw), ("stream", stream, res))
-             for i, (p, r) in enumerate(zip(ps_, rs_)) if r["status"] != 0][:8]
-    # plain per-lattice FP64 path on the same mix, bounded by time
-    ctx = fock.Context(dev)
-    ctx.solve([stream[0]], check=False)
-    n_plain, t1 = 0, time.perf_counter()
-    while time.perf_counter() - t1 < plain_s and n_plain < len(stream):
-        ctx.solve([stream[n_plain]], check=False)
-        n_plain += 1
-    plain = n_plain / (time.perf_counter() - t1)
-    ctx.close()
-    out = {"requests": n_stream, "arrival": f"Poisson at 80% of the burst capacity ({rate:.1f}/s)",
-           "throughput": n_stream / wall, "unit": UNIT}
+    runs = (("burst_fp64", burst, r64), ("burst_mixed", mburst, rm), ("plain_fp64", burst, rp),
+            ("stream_mixed", stream, res))
+    ok = sum(r["status"] == 0 for _, _, rs_ in runs for r in rs_)
+    total = sum(len(rs_) for _, _, rs_ in runs)
+    fails = [{"run": nm, "i": i, "status": r["status"], "L": list(p.L), "periodic": list(p.periodic),
+              "m0": len(p.exps), "k": p.k_eig, "iters": r["iters"], "resid": r["resid"]}
+             for nm, ps_, rs_ in runs for i, (p, r) in enumerate(zip(ps_, rs_)) if r["status"] != 0][:8]
+    out = {"burst_requests": n_burst, "batched_fp64": cap64, "batched_mixed": capm,
+           "plain_per_lattice_fp64": plain, "unit": UNIT,
+           "mixed_vs_plain": capm / plain, "fp64_batched_vs_plain": cap64 / plain,
+           "batched_fp64_equals_plain_bitwise": bool(same),
+           "max_rel_eig_diff_mixed_vs_plain_fp64": diff,
+           "requests": n_stream, "arrival": f"Poisson at 80% of the mixed burst capacity ({rate:.1f}/s)",
+           "throughput": n_stream / wall}
     out.update(latency_summary(lat, [bool(p.is_box or p.defects) for p in stream]))
-    out.update({"burst_capacity": cap,
-                "plain_per_lattice_fp64": plain, "plain_sample": n_plain, "slots": slots,
-                "max_batch": max_batch, "batches": int(st["batches"]),
+    out.update({"slots": slots, "max_batch": max_batch, "batches": int(st["batches"]),
                 "max_inflight": int(st["max_inflight"]),
                 "peak_reserved_bytes": int(st["peak_reserved_bytes"]), "status_ok": int(ok),
-                "failures": fails,
+                "status_total": int(total), "failures": fails,
                 "mix": "chains 4..256 cells x1x1 (box or periodic) and periodic cubes 8,12,16,24^3; "
                        "m0 4/8/16; n0 16, N_perp 256, R 32; 0-4 defects per chain",
                 "admission": "head of the queue, then later requests of the same kind "
@@ -482,7 +505,7 @@ def load_peaks():
 
 
 # --------------------------------------------------------------- timing
-def timed_plan(ctx, stream, problems, steps, warmup, flush, maxit=400, profile=False):
+def timed_plan(ctx, stream, problems, steps, warmup, flush, maxit=1000, profile=False):
     """W untimed executions, then K executions timed with CUDA events on the
     context's stream, L2 flushed before each.  With `profile`, K more
     executions with the library's kernel timers on (the periodic and the
@@ -580,7 +603,7 @@ def main():
     ap.add_argument("--profile-json", default="")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
-    ap.add_argument("--maxit", type=int, default=600)
+    ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:   # child of cpu_baseline: time the oracle only, print one JSON line

@@ -158,7 +158,10 @@ int fock_problem_layout(const fock_problem* p, int* Nb, int* mcirc, int* D, int*
  * FOCK_EINVAL (no problems, a malformed problem: see fock_problem_check),
  * FOCK_ENOMEM (the batch exceeds the context's budget), FOCK_ECUDA; per
  * problem, out->status FOCK_ENOCONV when the block iteration hit its cap
- * (best estimates written). */
+ * (best estimates written).  The block iteration stops at a relative
+ * residual of 1e-10 (or its rounding floor) or after FOCK_DEFAULT_MAXIT
+ * iterations. */
+#define FOCK_DEFAULT_MAXIT 1000
 int fock_solve(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_output* outs,
                int outputs_on_device);
 
@@ -263,11 +266,21 @@ int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int max
  * destinations).  A plan may be executed any number of times. */
 typedef struct fock_plan fock_plan;
 int fock_plan_create(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_plan** out);
+/* tol <= 0: 1e-10; maxit <= 0: FOCK_DEFAULT_MAXIT */
 int fock_plan_execute(fock_plan* plan, double tol, int maxit);
 int fock_plan_outputs(fock_plan* plan, fock_output* outs, int outputs_on_device);
 /* bytes uploaded by fock_plan_create, bytes of device memory held, and the
  * number of eigenvalues the plan returns in total */
 int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_bytes, size_t* n_evals);
+/* Launch machinery of a plan (no counterpart in the paper; its batching):
+ * fft_cc = columns per CTA of the embedded FFT chosen by the plan's tuner
+ * (timed on the first execution, once per largest embedding size and column
+ * count per context; 0 before), graph_nodes = kernels of the block iteration's
+ * body captured as one CUDA graph and replayed from its second pass on (0: not
+ * captured -- before the second pass, with the kernel timers on, or when the
+ * capture was refused and the launches stayed eager).  Either pointer may be
+ * NULL.  FOCK_EINVAL for a NULL plan. */
+int fock_plan_tuning(const fock_plan* plan, int* fft_cc, int* graph_nodes);
 /* Sizes of problem i of a plan: N_b, circulant size M (box: M >= L + D;
  * periodic: |L|), generator reach D in cells (box) and boundary blocks. */
 int fock_plan_problem_sizes(const fock_plan* plan, int i, int* Nb, int* mcirc, int* D, int* nbound);
@@ -343,7 +356,7 @@ typedef struct {
   int max_batch;            /* problems per batch; 0: 256 */
   size_t hbm_budget_bytes;  /* device bytes for all batches in flight; 0: 80% of free memory */
   double tol;               /* box eigensolver relative residual; <= 0: 1e-10 */
-  int maxit;                /* box eigensolver iteration cap; <= 0: 400 */
+  int maxit;                /* box eigensolver iteration cap; <= 0: FOCK_DEFAULT_MAXIT */
 } fock_serve_config;
 /* One request's result.  evals/block_of point into library-owned host
  * memory that stays valid until fock_result_release(ticket) or

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -49,6 +50,8 @@ void launch_sort_small(const SortTask*, int, int, cudaStream_t);
 void launch_sort_global(double*, int*, int, double*, int*, cudaStream_t);
 void launch_twiddles(CircDev*, int, cudaStream_t);
 void launch_fft(const FftTask*, int, int, int, int, int, cudaStream_t, bool);
+void launch_fft_cc(const FftTask*, int, int, int, int, int, cudaStream_t, bool);
+int fft_max_cc(int);
 void launch_blockmul(const BmulTask*, int, int, int, cudaStream_t, bool);
 void launch_eapply(const EApplyTask*, int, int, cudaStream_t);
 int eapply_grid(long long items);
@@ -78,6 +81,8 @@ struct fock_ctx {
   // order the two against `stream`
   cudaStream_t hi = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // tuner results: FFT columns per CTA by (largest embedding M, largest column count)
+  std::map<std::pair<int, int>, int> fft_tune;
   size_t budget = 0;
   char* arena = nullptr;
   size_t arena_cap = 0;
@@ -462,6 +467,13 @@ struct Batch {
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, pcG, pcM, pcZ, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
+  int fft_maxcols = 0;               // largest transform column count of a launch
+  bool tuned = false;                // fft_cc chosen by the tuner (first execution)
+  // the block iteration's body as a CUDA graph (captured on its second pass,
+  // replayed afterwards); graph_failed: capture refused, launches stay eager
+  cudaGraphExec_t iter_graph = nullptr;
+  bool graph_failed = false;
+  int graph_nodes = 0;
   int eapply_gx = 16;
   int* d_ones = nullptr;
   int* d_active = nullptr;
@@ -1161,6 +1173,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       }
     }
     B.fft_chunks = (maxcols + B.fft_cc - 1) / B.fft_cc;
+    B.fft_maxcols = maxcols;
     auto TLp = [&](auto& v, Batch::TL& tl, int ga = 1, int gb = 1) {
       tl.d = (void*)U.put(v); tl.n = (int)v.size(); tl.ga = ga; tl.gb = gb;
     };
@@ -1297,6 +1310,8 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
 }
 
 void free_batch(Batch& B) {
+  if (B.iter_graph) cudaGraphExecDestroy(B.iter_graph);
+  B.iter_graph = nullptr;
   if (B.pooled) {
     cudaFreeAsync(B.base, B.pooled);
     cudaFreeAsync(B.ubase, B.pooled);
@@ -1373,11 +1388,53 @@ template <class T> const T* tl(const Batch::TL& t) { return reinterpret_cast<con
 
 void mv_fwd(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_fft", 1);
-  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, +1, st, B.any_mixed);
+  launch_fft_cc(tl<FftTask>(t), t.n, (B.fft_maxcols + B.fft_cc - 1) / B.fft_cc, B.maxM, B.fft_cc, +1, st,
+                B.any_mixed);
 }
 void mv_inv(Batch& B, const Batch::TL& t, cudaStream_t st) {
   PROF("k_fft", 1);
-  launch_fft(tl<FftTask>(t), t.n, B.fft_chunks, B.maxM, B.fft_cc, -1, st, B.any_mixed);
+  launch_fft_cc(tl<FftTask>(t), t.n, (B.fft_maxcols + B.fft_cc - 1) / B.fft_cc, B.maxM, B.fft_cc, -1, st,
+                B.any_mixed);
+}
+
+// Tuner of the embedded FFT's launch shape: columns per CTA trade shared memory
+// per CTA (two M-point buffers per column) against CTAs per SM.  Timed once per
+// (largest M, largest column count) on the plan's own forward transform of
+// [X | P] (1, 2, 4, ... columns, three launches each after a warm-up, CUDA
+// events on the plan's stream), cached in the context.  The width does not
+// change any column's arithmetic, so results do not depend on the choice.
+void tune_fft(fock_ctx* ctx, Batch& B, cudaStream_t st) {
+  B.tuned = true;
+  if (!B.fwdXP.n || B.fft_maxcols <= 0) return;
+  const auto key = std::make_pair(B.maxM, B.fft_maxcols);
+  const auto f = ctx->fft_tune.find(key);
+  if (f != ctx->fft_tune.end()) { B.fft_cc = f->second; return; }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return;
+  }
+  const int top = std::min(16, fft_max_cc(B.maxM));
+  float best = INFINITY;
+  int bc = B.fft_cc;
+  for (int cc = 1; cc <= top; cc *= 2) {
+    const int ch = (B.fft_maxcols + cc - 1) / cc;
+    launch_fft_cc(tl<FftTask>(B.fwdXP), B.fwdXP.n, ch, B.maxM, cc, +1, st, B.any_mixed);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) launch_fft_cc(tl<FftTask>(B.fwdXP), B.fwdXP.n, ch, B.maxM, cc, +1, st, B.any_mixed);
+    cudaEventRecord(e1, st);
+    float ms = INFINITY;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      bc = cc;
+    }
+  }
+  cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B.fft_cc = bc;
+  ctx->fft_tune[key] = bc;
 }
 void split_products(Batch& B, const Batch::TL& t, cudaStream_t st) {
   if (!t.sn) return;
@@ -1439,6 +1496,35 @@ void refresh_XP(Batch& B, cudaStream_t st) {
   if (B.reHXP.n) { PROF("k_eapply", 1); launch_eapply(tl<EApplyTask>(B.reHXP), B.reHXP.n, B.eapply_gx, st); }
 }
 
+// One block-iteration step after the convergence test: W = K R (the shifted
+// inverse of the embedding's Fourier blocks, or the banded factor)
+// S-orthogonal to X, fresh images of W, Rayleigh-Ritz on [X | P | W], P'
+// S-orthogonal to X' in the coefficients, [X | P] <- Y Cc and their fresh
+// images.  Launches only.
+void lobpcg_body(Batch& B, cudaStream_t st) {
+  if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, B.band_ringrow, st, B.any_mixed); }
+  if (B.fwdR.n) {
+    mv_fwd(B, B.fwdR, st);
+    { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
+    mv_inv(B, B.invPW, st);
+  }
+  gemm_tn(B, B.tnCx, st);
+  gemm_nn(B, B.nnW, st);
+  normalize(B.normW, B.kmax, st);
+  mv_HS(B, false, st);
+  // Rayleigh-Ritz on [X | P | W]
+  gemm_tn(B, B.g3, st);
+  rr(B, B.rr3, st);
+  // P' S-orthogonal to X' in the coefficients; [X | P] <- Y Cc, fresh images
+  gemm_nn(B, B.pcG, st);
+  gemm_tn(B, B.pcM, st);
+  gemm_nn(B, B.pcZ, st);
+  gemm_nn(B, B.u3, st);
+  copies(B.cp2k, st);
+  normalize(B.normP, B.kmax, st);
+  mv_HS(B, true, st);
+}
+
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
                std::vector<double>& resid, std::vector<int>& conv,
                std::vector<std::vector<double>>* hist = nullptr) {
@@ -1465,6 +1551,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
   CUDA_TRY(ctx, cudaMemcpyAsync(B.d_mode, mode.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
   // X random, P = W = 0; Rayleigh-Ritz on X alone, then fresh images of [X | P]
   { PROF("k_init_x", 1); k_init_x<<<dim3(32, B.init.n), 256, 0, st>>>(tl<InitTask>(B.init)); }
+  if (!B.tuned) tune_fft(ctx, B, st);
   mv_HS(B, true, st);
   gemm_tn(B, B.g1, st);
   rr(B, B.rr1, st);
@@ -1545,28 +1632,30 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
       refresh_XP(B, st);
       CUDA_TRY(ctx, cudaStreamSynchronize(st));   // rf is a host temporary
     }
-    // W = K R  (Fourier-block shifted inverse of the embedding), S-orthogonal to X
-    if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, B.band_ringrow, st, B.any_mixed); }
-    if (B.fwdR.n) {
-      mv_fwd(B, B.fwdR, st);
-      { PROF("k_blockmul", 1); launch_blockmul(tl<BmulTask>(B.bmulK), B.bmulK.n, B.maxM, B.maxm0, st, B.any_mixed); }
-      mv_inv(B, B.invPW, st);
+    // the iteration's body: launches only (converged problems are skipped by
+    // every kernel through their device-side flags), so from the second pass
+    // on it is replayed as one CUDA graph captured on that pass; with the
+    // kernel timers on it stays eager
+    if (!ctx->prof && it >= 1 && !B.iter_graph && !B.graph_failed) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        lobpcg_body(B, st);
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (ce == cudaSuccess && g && cudaGraphInstantiate(&B.iter_graph, g, 0) == cudaSuccess) {
+          size_t nn = 0;
+          if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) B.graph_nodes = (int)nn;
+        } else {
+          B.iter_graph = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!B.iter_graph) { B.graph_failed = true; cudaGetLastError(); }
     }
-    gemm_tn(B, B.tnCx, st);
-    gemm_nn(B, B.nnW, st);
-    normalize(B.normW, B.kmax, st);
-    mv_HS(B, false, st);
-    // Rayleigh-Ritz on [X | P | W]
-    gemm_tn(B, B.g3, st);
-    rr(B, B.rr3, st);
-    // P' S-orthogonal to X' in the coefficients; [X | P] <- Y Cc, fresh images
-    gemm_nn(B, B.pcG, st);
-    gemm_tn(B, B.pcM, st);
-    gemm_nn(B, B.pcZ, st);
-    gemm_nn(B, B.u3, st);
-    copies(B.cp2k, st);
-    normalize(B.normP, B.kmax, st);
-    mv_HS(B, true, st);
+    if (B.iter_graph && !ctx->prof) {
+      CUDA_TRY(ctx, cudaGraphLaunch(B.iter_graph, st));
+    } else {
+      lobpcg_body(B, st);
+    }
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;
@@ -1893,7 +1982,7 @@ int fock_solve(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_output*
   P.ctx = ctx;
   int rc = build_batch(ctx, nprob, probs, P.B, false);
   if (rc) return rc;
-  rc = plan_execute(P, 1e-10, 400);
+  rc = plan_execute(P, 1e-10, FOCK_DEFAULT_MAXIT);
   if (rc) return rc;
   return plan_outputs(P, outs, on_device);
 }
@@ -1915,7 +2004,7 @@ int fock_plan_create(fock_ctx* ctx, int nprob, const fock_problem* probs, fock_p
 int fock_plan_execute(fock_plan* P, double tol, int maxit) {
   if (!P) return FOCK_EINVAL;
   ProfBind pb(P->ctx);
-  return plan_execute(*P, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : 400);
+  return plan_execute(*P, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : FOCK_DEFAULT_MAXIT);
 }
 
 int fock_plan_outputs(fock_plan* P, fock_output* outs, int on_device) {
@@ -1932,6 +2021,13 @@ int fock_plan_info(const fock_plan* P, size_t* upload_bytes, size_t* device_byte
     for (const auto& Q : P->B.pp) n += Q.nev;
     *n_evals = n;
   }
+  return FOCK_OK;
+}
+
+int fock_plan_tuning(const fock_plan* P, int* fft_cc, int* graph_nodes) {
+  if (!P) return FOCK_EINVAL;
+  if (fft_cc) *fft_cc = P->B.tuned ? P->B.fft_cc : 0;
+  if (graph_nodes) *graph_nodes = P->B.iter_graph ? P->B.graph_nodes : 0;
   return FOCK_OK;
 }
 
@@ -2356,7 +2452,7 @@ int fock_box_eig(fock_ctx* ctx, const fock_blocks* b, int k, double tol, int max
   ProfBind pb(ctx);
   std::vector<int> it, conv;
   std::vector<double> res;
-  int rc = run_lobpcg(ctx, B, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : 400, it, res, conv);
+  int rc = run_lobpcg(ctx, B, tol > 0 ? tol : 1e-10, maxit > 0 ? maxit : FOCK_DEFAULT_MAXIT, it, res, conv);
   if (rc) return rc;
   const Batch::Lob& l = B.lob[0];
   CUDA_TRY(ctx, cudaMemcpyAsync(evals, l.lam, (size_t)k * 8, cudaMemcpyDeviceToHost, ctx->stream));

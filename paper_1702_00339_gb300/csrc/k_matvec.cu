@@ -49,16 +49,18 @@ template <typename R> __device__ inline bool mode_match(const int* mode) {
 }
 
 // dir = +1 forward (w), -1 inverse (conj w); R = double (FP64 form) or float
-// (early iterations of the mixed form).
+// (early iterations of the mixed form).  cc_arg > 0: columns per CTA for every
+// task of the launch (a tuned width), else each task's own cc.  The arithmetic
+// of a column does not depend on the width.
 template <int DIR, typename R>
-__global__ void k_fft(const FftTask* __restrict__ tasks) {
+__global__ void k_fft(const FftTask* __restrict__ tasks, int cc_arg) {
   using C = typename CT<R>::T;
   extern __shared__ __align__(16) unsigned char fft_sbuf[];
   const FftTask T = tasks[blockIdx.y];
   if (!mode_match<R>(T.mode)) return;
   if (T.active && *T.active == 0) return;
   const CircDev Cd = *T.circ;
-  const int M = Cd.M, CC = T.cc;
+  const int M = Cd.M, CC = (cc_arg > 0) ? cc_arg : T.cc;
   const int npair = (T.ncol + 1) >> 1;    // two real columns per complex transform
   const int ncols = T.m0 * npair;
   const int c0 = blockIdx.x * CC;
@@ -249,25 +251,49 @@ size_t fft_smem(int M, int cc) { return (size_t)2 * M * cc * sizeof(cplx); }
 
 // mixed: the batch has problems in the mixed form; their FP32 variant is
 // launched too (each variant skips the tasks of the other precision).
-void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
-                cudaStream_t st, bool mixed) {
+static void fft_launch(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
+                       cudaStream_t st, bool mixed, int cc_arg) {
   if (!ntask) return;
   size_t sm = fft_smem(maxM, cc);
   if (dir > 0) {
     FOCK_SMEM_OPTIN((k_fft<1, double>));
-    k_fft<1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    k_fft<1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks, cc_arg);
     if (mixed) {
       FOCK_SMEM_OPTIN((k_fft<1, float>));
-      k_fft<1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
+      k_fft<1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks, cc_arg);
     }
   } else {
     FOCK_SMEM_OPTIN((k_fft<-1, double>));
-    k_fft<-1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks);
+    k_fft<-1, double><<<dim3(maxchunks, ntask), 256, sm, st>>>(tasks, cc_arg);
     if (mixed) {
       FOCK_SMEM_OPTIN((k_fft<-1, float>));
-      k_fft<-1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks);
+      k_fft<-1, float><<<dim3(maxchunks, ntask), 256, sm / 2, st>>>(tasks, cc_arg);
     }
   }
+}
+
+// columns per CTA from each task (cc: the largest, for the shared-memory size)
+void launch_fft(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
+                cudaStream_t st, bool mixed) {
+  fft_launch(tasks, ntask, maxchunks, maxM, cc, dir, st, mixed, 0);
+}
+
+// every task with cc columns per CTA (the width chosen by the plan's tuner)
+void launch_fft_cc(const FftTask* tasks, int ntask, int maxchunks, int maxM, int cc, int dir,
+                   cudaStream_t st, bool mixed) {
+  fft_launch(tasks, ntask, maxchunks, maxM, cc, dir, st, mixed, cc);
+}
+
+// largest columns per CTA whose two M-point buffers fit the opt-in shared memory
+int fft_max_cc(int maxM) {
+  int dev = 0, mx = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_fft<1, double>) == cudaSuccess) mx -= (int)fa.sharedSizeBytes;
+  int cc = 1;
+  while (cc < 32 && fft_smem(maxM, 2 * cc) <= (size_t)mx) cc *= 2;
+  return cc;
 }
 
 void launch_blockmul(const BmulTask* tasks, int ntask, int maxM, int maxm0, cudaStream_t st, bool mixed) {

@@ -211,7 +211,7 @@ int fock_serve_start(int device, const fock_serve_config* cfg, fock_server** out
   if (S->cfg.slots <= 0) S->cfg.slots = 2;
   if (S->cfg.slots > 16) S->cfg.slots = 16;
   if (!(S->cfg.tol > 0.0)) S->cfg.tol = 1e-10;
-  if (S->cfg.maxit <= 0) S->cfg.maxit = 400;
+  if (S->cfg.maxit <= 0) S->cfg.maxit = FOCK_DEFAULT_MAXIT;
   if (S->cfg.hbm_budget_bytes == 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);

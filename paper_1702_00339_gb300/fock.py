@@ -20,6 +20,7 @@ FOCK_OK, FOCK_EINVAL, FOCK_ENOMEM, FOCK_ENOCONV = 0, -1, -2, -3
 FOCK_ETIMEOUT, FOCK_EAGAIN, FOCK_ECUDA = -4, -5, -6
 FOCK_OP_H, FOCK_OP_S = 0, 1
 FOCK_FP64, FOCK_MIXED, FOCK_MIXED_F32 = 0, 1, 2
+FOCK_DEFAULT_MAXIT = 1000   # the block iteration's default cap (include/fock.h)
 _NAMES = {0: "FOCK_OK", -1: "FOCK_EINVAL", -2: "FOCK_ENOMEM", -3: "FOCK_ENOCONV",
           -4: "FOCK_ETIMEOUT", -5: "FOCK_EAGAIN", -6: "FOCK_ECUDA"}
 
@@ -118,6 +119,7 @@ def lib():
         L.fock_plan_execute.argtypes = [C.c_void_p, C.c_double, C.c_int]
         L.fock_plan_outputs.argtypes = [C.c_void_p, P(c_output), C.c_int]
         L.fock_plan_info.argtypes = [C.c_void_p, P(C.c_size_t), P(C.c_size_t), P(C.c_size_t)]
+        L.fock_plan_tuning.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int)]
         L.fock_plan_problem_sizes.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int),
                                               P(C.c_int)]
         L.fock_plan_free.argtypes = [C.c_void_p]
@@ -453,7 +455,7 @@ class Blocks:
                                                            y_ptr, int(nvec)),
                         "fock_toeplitz_matvec_noalloc")
 
-    def box_eig(self, k, tol=1e-10, maxit=400, vectors=False):
+    def box_eig(self, k, tol=1e-10, maxit=FOCK_DEFAULT_MAXIT, vectors=False):
         ev = np.zeros(k)
         V = np.zeros((self.Nb, k), order="F") if vectors else None
         it = C.c_int()
@@ -480,6 +482,14 @@ class Plan:
         lib().fock_plan_info(self.h, C.byref(a), C.byref(b), C.byref(c))
         self.upload_bytes, self.device_bytes, self.n_evals = a.value, b.value, c.value
 
+    def tuning(self):
+        """{"fft_cc": FFT columns per CTA chosen by the tuner (0 before the
+        first execution), "graph_nodes": kernels of the block iteration's
+        body replayed as one CUDA graph (0 when not captured)}."""
+        a, b = C.c_int(), C.c_int()
+        self.ctx._check(lib().fock_plan_tuning(self.h, C.byref(a), C.byref(b)), "fock_plan_tuning")
+        return {"fft_cc": a.value, "graph_nodes": b.value}
+
     def sizes(self, i):
         """(N_b, circulant size M, generator reach D, boundary blocks) of problem i."""
         a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
@@ -487,7 +497,7 @@ class Plan:
                                                       C.byref(d)), "fock_plan_problem_sizes")
         return a.value, b.value, c.value, d.value
 
-    def execute(self, tol=1e-10, maxit=400):
+    def execute(self, tol=1e-10, maxit=FOCK_DEFAULT_MAXIT):
         rc = lib().fock_plan_execute(self.h, float(tol), int(maxit))
         if rc:
             self.ctx._check(rc, "fock_plan_execute")
@@ -541,7 +551,7 @@ class Server:
     """Continuous-batching server (fock_serve_*): submit problems from any
     thread, poll tickets for results."""
 
-    def __init__(self, device=0, slots=2, max_batch=256, budget_bytes=0, tol=1e-10, maxit=400):
+    def __init__(self, device=0, slots=2, max_batch=256, budget_bytes=0, tol=1e-10, maxit=FOCK_DEFAULT_MAXIT):
         cfg = c_serve_config(int(slots), int(max_batch), C.c_size_t(budget_bytes), float(tol), int(maxit))
         self.h = C.c_void_p()
         rc = lib().fock_serve_start(int(device), C.byref(cfg), C.byref(self.h))
