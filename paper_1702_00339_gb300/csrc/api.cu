@@ -464,6 +464,7 @@ struct Batch {
   int gemm_tiles = 0;                // TN tile sizes in use: bit 0 = 16, bit 1 = 20
   bool rr_small = false, rr_big = false;   // Rayleigh-Ritz launches needed (256 / 512 threads)
   int rr_small_ld = 0;               // largest ld of the shared-memory problems
+  int rr_big_ld = 0;                 // largest ld of the others
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, pcG, pcM, pcZ, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
@@ -504,7 +505,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.band_ringrow = 0;
   B.gemm_tiles = 0;
   B.rr_small = B.rr_big = false;
-  B.rr_small_ld = 0;
+  B.rr_small_ld = B.rr_big_ld = 0;
   B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
@@ -1133,6 +1134,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
       B.rr_small = B.rr_small || !big;
       B.rr_big = B.rr_big || big;
       if (!big) B.rr_small_ld = std::max(B.rr_small_ld, ld3);
+      else B.rr_big_ld = std::max(B.rr_big_ld, ld3);
       // [X' | P'] = Y[:, :nb] Cc, then copied over [X | P]; images recomputed by a matvec
       uu1.push_back(gt(k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
       uu3.push_back(gt(3 * k, 2 * k, l.Y, n, l.Cc, ld3, l.T1, n, 1.0, 0.0));
@@ -1458,10 +1460,14 @@ void rr(Batch& B, const Batch::TL& t, cudaStream_t st) {
   // problems whose working matrices fit shared memory: 256 threads; the
   // others (global memory, latency-bound): 512 threads, more warps in flight
   if (B.rr_small) {
-    const size_t sm = (size_t)3 * B.rr_small_ld * B.rr_small_ld * sizeof(double);
+    const int ld = B.rr_small_ld;
+    const size_t sm = ((size_t)3 * ld * ld + (size_t)rr_stage_extra(ld)) * sizeof(double);
     k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm, 0);
   }
-  if (B.rr_big) k_rr<<<t.n, 512, 0, st>>>(tl<RRTask>(t), 0, 1);
+  if (B.rr_big) {
+    const size_t sm = (size_t)2 * kRRBlock * B.rr_big_ld * sizeof(double);
+    k_rr<<<t.n, 512, sm, st>>>(tl<RRTask>(t), (int)sm, 1);
+  }
 }
 // unit 2-norm columns before a matvec: the FFT packs two real columns per
 // complex transform, and a column far smaller than its partner would get an

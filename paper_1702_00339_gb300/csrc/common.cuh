@@ -272,6 +272,13 @@ struct ResidTask {
   double* res;        // [k] relative residual
 };
 
+// pivot columns per block of the Rayleigh-Ritz step's triangular substitutions
+// (its shared-memory staging: 2 kRRBlock ld doubles)
+constexpr int kRRBlock = 8;
+// extra doubles of staging a shared-memory Rayleigh-Ritz step needs beyond its
+// 3 ld^2 (none when its first working matrix, ld^2 doubles, can hold it)
+__host__ __device__ inline int rr_stage_extra(int ld) { return (ld * ld >= 2 * kRRBlock * ld) ? 0 : 2 * kRRBlock * ld; }
+
 struct RRTask {
   const int* active;
   int nb, k, ld;          // current basis size, wanted pairs, leading dim of G / C

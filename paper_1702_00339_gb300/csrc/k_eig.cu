@@ -609,7 +609,14 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     const cplx* x0 = F.Xh[0] + (size_t)j1 * nfe;
     const cplx* x1 = F.Xh[1] + (size_t)j2 * nfe;
     const cplx* x2 = F.Xh[2] + (size_t)j3 * nfe;
-    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+    // H and S are Hermitian (each axis factor is, and so is a Hadamard product
+    // of Hermitian matrices): the upper triangle, enumerated compactly so that
+    // whole warps share the work, is formed and mirrored; the diagonal is real
+    const int nup = m0 * (m0 + 1) / 2;
+    for (int u = threadIdx.x; u < nup; u += blockDim.x) {
+      int mu = 0, rem = u;
+      while (rem >= m0 - mu) { rem -= m0 - mu; ++mu; }
+      const int nu = mu + rem, pr = mu * m0 + nu, tr = nu * m0 + mu;
       cplx s0 = x0[pr], s1 = x1[pr], s2 = x2[pr];
       cplx a0 = x0[np + pr], a1 = x1[np + pr], a2 = x2[np + pr];
       cplx s12 = cmul(s1, s2);
@@ -621,8 +628,10 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
         cplx pr3 = cmul(cmul(x0[(2 + t) * np + pr], x1[(2 + t) * np + pr]), x2[(2 + t) * np + pr]);
         vv = cadd(vv, cscale(pr3, w));
       }
-      H[pr] = csub(hk, vv);
-      S[pr] = cmul(s0, s12);
+      cplx h = csub(hk, vv), s = cmul(s0, s12);
+      if (mu == nu) { h.y = 0.0; s.y = 0.0; }
+      H[pr] = h; S[pr] = s;
+      H[tr] = cconj(h); S[tr] = cconj(s);
     }
   } else {
     // twiddles exp(-2 pi i j d / M), d = 1..D, once per block (in the Jacobi
@@ -649,19 +658,22 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
     }
   }
   __syncthreads();
-  // exact Hermitian symmetrisation of the formed pair (removes rounding asymmetry)
-  for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
-    int mu = pr / m0, nu = pr % m0;
-    if (mu < nu) {
-      cplx h1 = H[pr], h2 = H[nu * m0 + mu], s1 = S[pr], s2 = S[nu * m0 + mu];
-      cplx hm = cscale(cadd(h1, cconj(h2)), 0.5), sm2 = cscale(cadd(s1, cconj(s2)), 0.5);
-      H[pr] = hm; H[nu * m0 + mu] = cconj(hm);
-      S[pr] = sm2; S[nu * m0 + mu] = cconj(sm2);
-    } else if (mu == nu) {
-      H[pr].y = 0.0; S[pr].y = 0.0;
+  // exact Hermitian symmetrisation of the formed pair (removes rounding
+  // asymmetry; the factor route forms Hermitian blocks directly)
+  if (F.source != FROM_FACTORS) {
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      int mu = pr / m0, nu = pr % m0;
+      if (mu < nu) {
+        cplx h1 = H[pr], h2 = H[nu * m0 + mu], s1 = S[pr], s2 = S[nu * m0 + mu];
+        cplx hm = cscale(cadd(h1, cconj(h2)), 0.5), sm2 = cscale(cadd(s1, cconj(s2)), 0.5);
+        H[pr] = hm; H[nu * m0 + mu] = cconj(hm);
+        S[pr] = sm2; S[nu * m0 + mu] = cconj(sm2);
+      } else if (mu == nu) {
+        H[pr].y = 0.0; S[pr].y = 0.0;
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (F.outH)
     for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
       F.outH[(size_t)jl * np + pr] = H[pr];

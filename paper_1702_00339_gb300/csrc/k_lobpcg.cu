@@ -641,9 +641,15 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr(const RRTask* __restrict__
   // 1e-10 with FP64 images, 1e-6 while the images are FP32 (their noise level)
   const double kDropRel = (T.mode && *T.mode) ? 1e-6 : 1e-10;
   const int ld = T.ld, k = T.k, nb = T.nb;
-  // working matrices in shared memory when 3 ld^2 doubles fit, else global
-  const bool in_smem = !big && (3 * ld * ld * (int)sizeof(double) <= smem_bytes);
+  // working matrices in shared memory when 3 ld^2 doubles fit, else global.
+  // The substitutions' staging (2 kRRBlock ld doubles) is shared memory: the
+  // first ld^2 of the working matrices (C, free while they run) when those are
+  // in shared memory and large enough, else dynamic shared memory of its own
+  // (after the matrices, or all of it for matrices in global memory)
+  const int xs = rr_stage_extra(ld);
+  const bool in_smem = !big && ((3 * ld * ld + xs) * (int)sizeof(double) <= smem_bytes);
   double* base = in_smem ? rr_smem : T.work;
+  double* rr_blk = !in_smem ? rr_smem : (xs ? rr_smem + (size_t)3 * ld * ld : rr_smem);
   double* C = base;                          // scaled H-Gram, then the reduced matrix (lower)
   double* V = base + (size_t)ld * ld;        // work matrix, then the eigenvectors
   double* G = base + (size_t)2 * ld * ld;    // scaled S-Gram (lower, original indices), then L
@@ -739,23 +745,81 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr(const RRTask* __restrict__
   }
   __syncthreads();
   auto Lp = [&](int aa, int bb) -> double { return GP(perm[aa], perm[bb]); };   // unit lower factor, aa > bb
-  // V <- L^-1 V (right-looking over rows), then the lower triangle of V L^-T
-  for (int i = 0; i + 1 < r; ++i) {
-    const int n = r - i - 1;
-    for (int it = threadIdx.x; it < n * r; it += blockDim.x) {
-      const int aa = i + 1 + it / r, col = it % r;
-      V[aa * ld + col] = fma(-Lp(aa, i), V[i * ld + col], V[aa * ld + col]);
+  // V <- L^-1 V (right-looking over rows), then the lower triangle of V L^-T,
+  // both blocked by kRRBlock pivot columns: the block's columns of L and its
+  // finished rows (columns) of V are staged in shared memory, then every entry
+  // outside the block takes the block's updates in one pass.  Each entry gets
+  // the same fma sequence, in the same order, as in the unblocked
+  // substitution; global traffic per fma falls from three accesses to about
+  // two per block.
+  constexpr int RB = kRRBlock;
+  double* sL = rr_blk;                         // sL[q ld + a] = L(a, i0 + q), a > i0 + q
+  double* sV = rr_blk + (size_t)RB * ld;       // the block's finished rows / columns of V
+  for (int i0 = 0; i0 < r; i0 += RB) {
+    const int nbk = min(RB, r - i0);
+    for (int it = threadIdx.x; it < nbk * r; it += blockDim.x) {
+      const int q = it / r, aa = it % r;
+      sL[q * ld + aa] = (aa > i0 + q) ? Lp(aa, i0 + q) : 0.0;
+    }
+    __syncthreads();
+    for (int col = threadIdx.x; col < r; col += blockDim.x) {   // the block's rows
+      double v[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        if (q < nbk) {
+          double t = V[(i0 + q) * ld + col];
+#pragma unroll
+          for (int p = 0; p < q; ++p) t = fma(-sL[p * ld + i0 + q], v[p], t);
+          v[q] = t;
+          V[(i0 + q) * ld + col] = t;
+          sV[q * ld + col] = t;
+        }
+      }
+    }
+    __syncthreads();
+    const int a0 = i0 + nbk, na = r - a0;
+    for (int it = threadIdx.x; it < na * r; it += blockDim.x) {   // rows below the block
+      const int aa = a0 + it / r, col = it % r;
+      double t = V[aa * ld + col];
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (q < nbk) t = fma(-sL[q * ld + aa], sV[q * ld + col], t);
+      V[aa * ld + col] = t;
     }
     __syncthreads();
   }
-  for (int i = 0; i + 1 < r; ++i) {            // columns a > i, rows x >= a
-    const int n = r - i - 1, nt = n * (n + 1) / 2;
-    for (int it = threadIdx.x; it < nt; it += blockDim.x) {
-      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
-      while (ii * (ii + 1) / 2 > it) --ii;
-      const int x = i + 1 + ii, aa = i + 1 + (it - ii * (ii + 1) / 2);
-      V[x * ld + aa] = fma(-Lp(aa, i), V[x * ld + i], V[x * ld + aa]);
+  for (int i0 = 0; i0 < r; i0 += RB) {         // columns a > i, rows x >= a
+    const int nbk = min(RB, r - i0);
+    for (int it = threadIdx.x; it < nbk * r; it += blockDim.x) {
+      const int q = it / r, aa = it % r;
+      sL[q * ld + aa] = (aa > i0 + q) ? Lp(aa, i0 + q) : 0.0;
+    }
+    __syncthreads();
+    for (int x = i0 + threadIdx.x; x < r; x += blockDim.x) {   // the block's columns, rows x >= column
+      double w[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int c = i0 + q;
+        if (q < nbk && x >= c) {
+          double t = V[x * ld + c];
+#pragma unroll
+          for (int p = 0; p < q; ++p) t = fma(-sL[p * ld + c], w[p], t);
+          w[q] = t;
+          V[x * ld + c] = t;
+          sV[q * ld + x] = t;
+        }
+      }
+    }
+    __syncthreads();
+    const int a0 = i0 + nbk, na = r - a0;
+    for (int it = threadIdx.x; it < na * na; it += blockDim.x) {   // columns right of the block
+      const int x = a0 + it / na, aa = a0 + it % na;
+      if (aa > x) continue;
+      double t = V[x * ld + aa];
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (q < nbk) t = fma(-sL[q * ld + aa], sV[q * ld + x], t);
+      V[x * ld + aa] = t;
     }
     __syncthreads();
   }
