@@ -443,11 +443,16 @@ def fp64_flops_per_step(problems, outs):
             rr = lambda b: 3 * b ** 3 + 3 * b * b * kb + 6 * b * kb * kb
             w["k_rr"] = w.get("k_rr", 0) + it * rr(nb) + rr(kb)
             # Gram products: the two symmetric nb x nb products of the basis
-            # (n nb (nb + 1) flops each) and the two kb x kb projections onto X;
-            # the start: the two symmetric kb x kb products
-            w["k_gemm_tn"] = (w.get("k_gemm_tn", 0) + it * (2 * n * nb * (nb + 1) + 2 * 2 * n * kb * kb)
+            # (n nb (nb + 1) flops each), the kb x kb projection of W onto X and the
+            # coefficient projection's z_X^T (G_S z_P) (nb rows); the start: the two
+            # symmetric kb x kb products
+            w["k_gemm_tn"] = (w.get("k_gemm_tn", 0) + it * (2 * n * nb * (nb + 1) + 2 * n * kb * kb
+                                                            + 2 * nb * kb * kb)
                               + 2 * n * kb * (kb + 1))
-            w["k_gemm_nn"] = w.get("k_gemm_nn", 0) + it * (2 * n * nb * 2 * kb + 6 * 2 * n * kb * kb)
+            # basis update [X|P] = Y Cc, W -= X C, and the coefficient projection
+            # G_S z_P (nb x nb x kb) and z_P -= z_X M (nb x kb x kb)
+            w["k_gemm_nn"] = (w.get("k_gemm_nn", 0)
+                              + it * (2 * n * nb * 2 * kb + 2 * n * kb * kb + 2 * nb * nb * kb + 2 * nb * kb * kb))
             # banded preconditioner: forward and backward block substitution over
             # L cells with D + 1 blocks of m0 x m0 per block row, kb columns
             D = o.get("D")
