@@ -41,7 +41,8 @@ void launch_gram(const ProbDev*, const GramTask*, int, const DefTab*, cudaStream
 void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
-void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t, bool vectors = false);
+void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t, bool vectors = false,
+                    int x0 = 0, int nx = -1);
 void launch_bloch_vectors(int, int, int, int, int, const int*, const cplx*, const int*, cplx*, cudaStream_t);
 void launch_split_gemm(const SplitTask*, int, int, int, int*, cudaStream_t, int max_ks = 1, bool reduce = false);
 void launch_null_tau(const NullTask*, int, cudaStream_t);
@@ -80,7 +81,10 @@ struct fock_ctx {
   // the periodic problems' eigensolves run on `stream`; ev_fork / ev_join
   // order the two against `stream`
   cudaStream_t hi = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_chunk = nullptr;
+  // while a plan's iteration runs on hi: the stream its periodic problems'
+  // Fourier-block pieces go to (nullptr otherwise)
+  cudaStream_t pstream = nullptr;
   // tuner results: FFT columns per CTA by (largest embedding M, largest column count)
   std::map<std::pair<int, int>, int> fft_tune;
   size_t budget = 0;
@@ -145,6 +149,10 @@ const int kSplitMinRows = 2048;
 // Rayleigh-Ritz working matrices (3 ld^2 doubles) up to this many bytes live in
 // shared memory
 const size_t kRRSmemCap = 160 * 1024;
+// Fourier blocks (CTAs, of which about half are conjugates that return at
+// once) per piece launched beside a Rayleigh-Ritz launch: about three waves of
+// the 32 x 32 block kernel on the SMs the iteration leaves free, ~10 ms
+const int kPeriodicPieceCTAs = 3072;
 
 int set_err(fock_ctx* c, int code, const std::string& m) {
   if (c) c->err = m;
@@ -470,11 +478,14 @@ struct Batch {
   int fft_cc = 1, fft_chunks = 1;
   int fft_maxcols = 0;               // largest transform column count of a launch
   bool tuned = false;                // fft_cc chosen by the tuner (first execution)
-  // the block iteration's body as a CUDA graph (captured on its second pass,
-  // replayed afterwards); graph_failed: capture refused, launches stay eager
-  cudaGraphExec_t iter_graph = nullptr;
+  // the block iteration's body as two CUDA graphs, before and from the
+  // Rayleigh-Ritz launch (captured on its second pass, replayed afterwards);
+  // graph_failed: capture refused, launches stay eager
+  cudaGraphExec_t iter_graph = nullptr, iter_graph_b = nullptr;
   bool graph_failed = false;
   int graph_nodes = 0;
+  // periodic Fourier blocks issued in pieces: next local index, piece width
+  int pchunk_next = 0, pchunk_w = 0;
   int eapply_gx = 16;
   int* d_ones = nullptr;
   int* d_active = nullptr;
@@ -1313,7 +1324,8 @@ int alloc_and_plan(fock_ctx* ctx, Batch& B, bool own) {
 
 void free_batch(Batch& B) {
   if (B.iter_graph) cudaGraphExecDestroy(B.iter_graph);
-  B.iter_graph = nullptr;
+  if (B.iter_graph_b) cudaGraphExecDestroy(B.iter_graph_b);
+  B.iter_graph = B.iter_graph_b = nullptr;
   if (B.pooled) {
     cudaFreeAsync(B.base, B.pooled);
     cudaFreeAsync(B.ubase, B.pooled);
@@ -1360,16 +1372,34 @@ void zero_fail_flags(Batch& B, int kind, cudaStream_t st) {
     if (B.hp[i].kind == kind && B.pp[i].fail) cudaMemsetAsync(B.pp[i].fail, 0, sizeof(int), st);
 }
 
-void run_periodic(fock_ctx* ctx, Batch& B) {
-  cudaStream_t st = ctx->stream;
+// Periodic problems: per-axis DFTs and the dependency cuts (head), the
+// Fourier-block eigensolves (in pieces of local indices when they share the
+// GPU with a block iteration), then the sort of each spectrum (tail).
+void run_periodic_head(fock_ctx* ctx, Batch& B, cudaStream_t st) {
+  B.pchunk_next = 0;
   if (B.fbp.empty()) return;
   zero_fail_flags(B, 0, st);
   { PROF("k_axis_dft", 1); launch_axis_dft(B.d_probs, B.d_dft, (int)B.dft.size(), B.maxLdft, st); }
   { PROF("k_null_tau", 1); launch_null_tau(B.d_nulls, (int)B.nulls.size(), st); }
-  { PROF("k_fblocks_eig", 1); launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st); }
+}
+// the next nx local indices of every periodic task (nx < 0: all that remain)
+void run_periodic_piece(fock_ctx* ctx, Batch& B, int nx, cudaStream_t st) {
+  if (B.fbp.empty() || B.pchunk_next >= B.maxnj_p) return;
+  const int w = (nx < 0) ? B.maxnj_p - B.pchunk_next : std::min(nx, B.maxnj_p - B.pchunk_next);
+  { PROF("k_fblocks_eig", 1);
+    launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st, false, B.pchunk_next, w); }
+  B.pchunk_next += w;
+}
+void run_periodic_tail(fock_ctx* ctx, Batch& B, cudaStream_t st) {
+  if (B.fbp.empty()) return;
+  run_periodic_piece(ctx, B, -1, st);
   if (!B.sorts.empty()) { PROF("k_sort", 1); launch_sort_small(B.d_sorts, (int)B.sorts.size(), B.maxsort, st); }
   for (int i : B.bigsort) { PROF("k_sort_global", 1);
     launch_sort_global(B.pp[i].ev, B.pp[i].blk, B.pp[i].nev, B.sort_pv, B.sort_pi, st); }
+}
+void run_periodic(fock_ctx* ctx, Batch& B) {
+  run_periodic_head(ctx, B, ctx->stream);
+  run_periodic_tail(ctx, B, ctx->stream);
 }
 
 void run_struct_setup(fock_ctx* ctx, Batch& B) {
@@ -1502,12 +1532,12 @@ void refresh_XP(Batch& B, cudaStream_t st) {
   if (B.reHXP.n) { PROF("k_eapply", 1); launch_eapply(tl<EApplyTask>(B.reHXP), B.reHXP.n, B.eapply_gx, st); }
 }
 
-// One block-iteration step after the convergence test: W = K R (the shifted
-// inverse of the embedding's Fourier blocks, or the banded factor)
-// S-orthogonal to X, fresh images of W, Rayleigh-Ritz on [X | P | W], P'
-// S-orthogonal to X' in the coefficients, [X | P] <- Y Cc and their fresh
-// images.  Launches only.
-void lobpcg_body(Batch& B, cudaStream_t st) {
+// One block-iteration step after the convergence test, in two parts.  A: W = K R
+// (the shifted inverse of the embedding's Fourier blocks, or the banded factor)
+// S-orthogonal to X, fresh images of W, the Gram matrices of [X | P | W].  B:
+// Rayleigh-Ritz, P' S-orthogonal to X' in the coefficients, [X | P] <- Y Cc and
+// their fresh images.  Launches only.
+void lobpcg_body_a(Batch& B, cudaStream_t st) {
   if (B.bandS.n) { PROF("k_band_solve", 1); launch_band_solve(tl<BandTask>(B.bandS), B.bandS.n, B.kmax, B.band_stage, B.band_ringrow, st, B.any_mixed); }
   if (B.fwdR.n) {
     mv_fwd(B, B.fwdR, st);
@@ -1520,6 +1550,8 @@ void lobpcg_body(Batch& B, cudaStream_t st) {
   mv_HS(B, false, st);
   // Rayleigh-Ritz on [X | P | W]
   gemm_tn(B, B.g3, st);
+}
+void lobpcg_body_b(Batch& B, cudaStream_t st) {
   rr(B, B.rr3, st);
   // P' S-orthogonal to X' in the coefficients; [X | P] <- Y Cc, fresh images
   gemm_nn(B, B.pcG, st);
@@ -1640,28 +1672,47 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     }
     // the iteration's body: launches only (converged problems are skipped by
     // every kernel through their device-side flags), so from the second pass
-    // on it is replayed as one CUDA graph captured on that pass; with the
+    // on it is replayed as two CUDA graphs captured on that pass; with the
     // kernel timers on it stays eager
     if (!ctx->prof && it >= 1 && !B.iter_graph && !B.graph_failed) {
-      cudaGraph_t g = nullptr;
-      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        lobpcg_body(B, st);
+      B.graph_nodes = 0;
+      auto capture = [&](void (*body)(Batch&, cudaStream_t), cudaGraphExec_t* out) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+        body(B, st);
         const cudaError_t ce = cudaStreamEndCapture(st, &g);
-        if (ce == cudaSuccess && g && cudaGraphInstantiate(&B.iter_graph, g, 0) == cudaSuccess) {
+        bool ok = (ce == cudaSuccess && g && cudaGraphInstantiate(out, g, 0) == cudaSuccess);
+        if (ok) {
           size_t nn = 0;
-          if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) B.graph_nodes = (int)nn;
+          if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) B.graph_nodes += (int)nn;
         } else {
-          B.iter_graph = nullptr;
+          *out = nullptr;
         }
         if (g) cudaGraphDestroy(g);
+        return ok;
+      };
+      if (!capture(lobpcg_body_a, &B.iter_graph) || !capture(lobpcg_body_b, &B.iter_graph_b)) {
+        if (B.iter_graph) cudaGraphExecDestroy(B.iter_graph);
+        if (B.iter_graph_b) cudaGraphExecDestroy(B.iter_graph_b);
+        B.iter_graph = B.iter_graph_b = nullptr;
+        B.graph_failed = true;
+        cudaGetLastError();
       }
-      if (!B.iter_graph) { B.graph_failed = true; cudaGetLastError(); }
     }
-    if (B.iter_graph && !ctx->prof) {
-      CUDA_TRY(ctx, cudaGraphLaunch(B.iter_graph, st));
-    } else {
-      lobpcg_body(B, st);
+    const bool graphs = B.iter_graph && !ctx->prof;
+    if (graphs) CUDA_TRY(ctx, cudaGraphLaunch(B.iter_graph, st));
+    else lobpcg_body_a(B, st);
+    // a piece of the periodic problems' Fourier-block eigensolves on their own
+    // (lower-priority) stream, started when this stream reaches the
+    // Rayleigh-Ritz launch, which occupies one SM per box chain: the piece fills
+    // the other SMs meanwhile and is sized to end about when it does
+    if (ctx->pstream && B.pchunk_next < B.maxnj_p) {
+      CUDA_TRY(ctx, cudaEventRecord(ctx->ev_chunk, st));
+      CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->pstream, ctx->ev_chunk, 0));
+      run_periodic_piece(ctx, B, B.pchunk_w, ctx->pstream);
     }
+    if (graphs) CUDA_TRY(ctx, cudaGraphLaunch(B.iter_graph_b, st));
+    else lobpcg_body_b(B, st);
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return FOCK_OK;
@@ -1703,11 +1754,17 @@ int plan_execute(fock_plan& P, double tol, int maxit) {
     cudaStream_t user = ctx->stream;
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, user));
     CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->hi, ctx->ev_fork, 0));
-    run_periodic(ctx, B);
+    run_periodic_head(ctx, B, user);
+    // pieces of about kPeriodicPieceCTAs Fourier blocks ride along with the
+    // iteration's Rayleigh-Ritz launches; the rest, and the sorts, follow it
+    B.pchunk_w = std::max(1, kPeriodicPieceCTAs / std::max(1, (int)B.fbp.size()));
+    ctx->pstream = user;
     ctx->stream = ctx->hi;
     run_struct_setup(ctx, B);
     int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
     ctx->stream = user;
+    ctx->pstream = nullptr;
+    run_periodic_tail(ctx, B, user);
     // joined on every path: later work on the context's stream sees both
     cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->hi);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ctx->ev_join, 0);
@@ -1898,12 +1955,14 @@ int fock_create(fock_ctx** out, int device, size_t hbm_budget_bytes, void* strea
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_chunk, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       if (c->hi) cudaStreamDestroy(c->hi);
       if (c->ev_fork) cudaEventDestroy(c->ev_fork);
       if (c->ev_join) cudaEventDestroy(c->ev_join);
-      c->hi = nullptr; c->ev_fork = c->ev_join = nullptr;
+      if (c->ev_chunk) cudaEventDestroy(c->ev_chunk);
+      c->hi = nullptr; c->ev_fork = c->ev_join = c->ev_chunk = nullptr;
     }
   }
   if (hbm_budget_bytes == 0) {
@@ -1926,6 +1985,7 @@ void fock_destroy(fock_ctx* c) {
   if (c->hi) { cudaStreamSynchronize(c->hi); cudaStreamDestroy(c->hi); }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_chunk) cudaEventDestroy(c->ev_chunk);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -2033,7 +2093,7 @@ int fock_plan_info(const fock_plan* P, size_t* upload_bytes, size_t* device_byte
 int fock_plan_tuning(const fock_plan* P, int* fft_cc, int* graph_nodes) {
   if (!P) return FOCK_EINVAL;
   if (fft_cc) *fft_cc = P->B.tuned ? P->B.fft_cc : 0;
-  if (graph_nodes) *graph_nodes = P->B.iter_graph ? P->B.graph_nodes : 0;
+  if (graph_nodes) *graph_nodes = (P->B.iter_graph && P->B.iter_graph_b) ? P->B.graph_nodes : 0;
   return FOCK_OK;
 }
 

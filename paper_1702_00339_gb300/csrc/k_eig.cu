@@ -28,6 +28,8 @@
 //  k_precond    K_j = (Chat_H,j - sigma Chat_S,j)^-1 per Fourier index.
 //  k_sort_*     ascending sort of (eigenvalue, Fourier index) pairs.
 #include <float.h>
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fock {
@@ -567,10 +569,10 @@ __device__ inline cplx twiddle(long long num, int M) {   // exp(-2 pi i num / M)
   return cmk(c, s);
 }
 
-__global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* __restrict__ tasks) {
+__global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* __restrict__ tasks, int x0) {
   extern __shared__ cplx sm[];
   const FBlockTask F = tasks[blockIdx.y];
-  const int jl = blockIdx.x;      // local output index
+  const int jl = x0 + blockIdx.x; // local output index (a launch may cover a range of them)
   if (jl >= F.nj) return;
   const int j = F.j0 + jl;        // Fourier index
   // Real generators: the block at -j (componentwise mod L) is the complex
@@ -967,16 +969,19 @@ size_t fblocks_smem(int m0, bool vectors) {
          2 * MAXM0 * sizeof(float) + (vectors ? 16 + 2 * ldj * ldj * sizeof(cplx) : 0);
 }
 
+// x0, nx: the launch covers local indices x0 .. x0 + nx - 1 of every task
+// (nx < 0: up to maxnj), so that a large solve can be issued in pieces
 void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,
-                    cudaStream_t st, bool vectors) {
-  if (!ntask || !maxnj) return;
+                    cudaStream_t st, bool vectors, int x0, int nx) {
+  const int gx = (nx < 0) ? maxnj - x0 : std::min(nx, maxnj - x0);
+  if (!ntask || gx <= 0) return;
   size_t sm = fblocks_smem(maxm0, vectors);
   FOCK_SMEM_OPTIN(k_fblocks);
   // the rotation and update phases of an m0 x m0 block have about m0^2 / 2
   // parallel items: one warp for m0 <= 8 (more independent blocks resident
   // per SM keep the FP64 pipe busy), up to four warps for m0 = 32
   const int threads = (maxm0 <= 8) ? 32 : (maxm0 <= 16) ? 64 : 128;
-  k_fblocks<<<dim3(maxnj, ntask), threads, sm, st>>>(probs, tasks);
+  k_fblocks<<<dim3(gx, ntask), threads, sm, st>>>(probs, tasks, x0);
 }
 
 void launch_precond(const ProbDev* probs, const PrecTask* tasks, int ntask, int maxM, int maxm0,
