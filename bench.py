@@ -436,7 +436,7 @@ def fp64_flops_per_step(problems, outs):
             n = p.L[0] * m0
             it = max(o["iters"], 1)
             # block size kb (k wanted + guards, or the whole space) and basis 3 kb
-            kb = n if 3 * n <= 255 else k + max(2, k // 4)
+            kb = n if 3 * n <= 255 else k + max(4, k // 8)
             nb = 3 * kb
             # Rayleigh-Ritz per launch: pivoted LDL^T nb^3/3, the two triangular
             # solves 4 nb^3/3, Householder tridiagonal 4 nb^3/3, back-transformation
@@ -491,7 +491,7 @@ def matvec_bytes_per_step(problems, outs):
             continue
         m0 = len(p.exps)
         n = p.L[0] * m0
-        kb = n if 3 * n <= 255 else p.k_eig + max(2, p.k_eig // 4)
+        kb = n if 3 * n <= 255 else p.k_eig + max(4, p.k_eig // 8)
         M, nE = o["M"], o.get("nE", 0)
         per_app = lambda ncol: 2 * M * m0 * m0 * 16 + 2 * nE * m0 * m0 * 8 + 3 * n * ncol * 8
         it = max(o["iters"], 1)

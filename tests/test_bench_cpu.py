@@ -39,7 +39,7 @@ def test_work_models_scale_with_iterations_and_batch():
         assert np.isclose(w4[k], 2 * w2[k])
     # the band solve model: 4 L (D+1) m0^2 kb flops per application
     box = ps[0]
-    kb = box.k_eig + max(2, box.k_eig // 4)
+    kb = box.k_eig + max(4, box.k_eig // 8)
     one = bench.fp64_flops_per_step([box], [{"iters": 1, "M": 128, "D": 20}])
     assert one["k_band_solve"] == 4 * box.L[0] * 21 * 64 * kb
 
