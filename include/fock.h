@@ -276,7 +276,8 @@ int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_b
  * fft_cc = columns per CTA of the embedded FFT chosen by the plan's tuner
  * (timed on the first execution, once per largest embedding size and column
  * count per context; 0 before), graph_nodes = kernels of the block iteration's
- * body captured as one CUDA graph and replayed from its second pass on (0: not
+ * body captured as two CUDA graphs (split at the Rayleigh-Ritz launch) and
+ * replayed from its second pass on (0: not
  * captured -- before the second pass, with the kernel timers on, or when the
  * capture was refused and the launches stayed eager).  Either pointer may be
  * NULL.  FOCK_EINVAL for a NULL plan. */
