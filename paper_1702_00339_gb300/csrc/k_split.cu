@@ -99,36 +99,65 @@ __device__ void stage(const double* __restrict__ P, long long sr, long long sk, 
                       unsigned char* planes, uint32_t plane_bytes, int* rexp) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (sk == 1) {
-    // rows contiguous along k: one warp per row, lanes along k
-    for (int r = warp; r < TR; r += 4) {
-      double x0 = 0.0, x1 = 0.0;
-      if (r < rows) {
-        if (k0 + lane < K) x0 = P[r * sr + (k0 + lane)];
-        if (k0 + lane + 32 < K) x1 = P[r * sr + (k0 + lane + 32)];
+    // rows contiguous along k: one warp per row, lanes along k; the loads of
+    // SU rows are issued before any of them is converted (their latency
+    // overlaps instead of adding up row after row)
+    constexpr int SU = 4;
+    for (int r0 = warp; r0 < TR; r0 += 4 * SU) {
+      double x0[SU], x1[SU];
+#pragma unroll
+      for (int u = 0; u < SU; ++u) {
+        const int r = r0 + 4 * u;
+        x0[u] = 0.0; x1[u] = 0.0;
+        if (r < rows) {
+          if (k0 + lane < K) x0[u] = P[r * sr + (k0 + lane)];
+          if (k0 + lane + 32 < K) x1[u] = P[r * sr + (k0 + lane + 32)];
+        }
       }
-      const int E = __reduce_max_sync(0xffffffffu, max(exp_field(x0), exp_field(x1)));
-      if (lane == 0) rexp[r] = E;
-      __nv_bfloat16 q[NDIG];
-      digits(x0, E, q);
 #pragma unroll
-      for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, lane)) = q[j];
-      digits(x1, E, q);
+      for (int u = 0; u < SU; ++u) {
+        const int r = r0 + 4 * u;
+        if (r >= TR) break;
+        const int E = __reduce_max_sync(0xffffffffu, max(exp_field(x0[u]), exp_field(x1[u])));
+        if (lane == 0) rexp[r] = E;
+        __nv_bfloat16 q[NDIG];
+        digits(x0[u], E, q);
 #pragma unroll
-      for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, lane + 32)) = q[j];
+        for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, lane)) = q[j];
+        digits(x1[u], E, q);
+#pragma unroll
+        for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, lane + 32)) = q[j];
+      }
     }
   } else {
     // lanes along the rows (coalesced when rows are contiguous), loop along k
+    // in groups of SK independent loads (the exponent pass and the digit pass
+    // each keep SK loads in flight)
+    constexpr int SK = 8;
     for (int r = threadIdx.x; r < TR; r += blockDim.x) {
+      const bool live = (r < rows);
       int E = 1;
-      if (r < rows)
-        for (int k = 0; k < KC && k0 + k < K; ++k) E = max(E, exp_field(P[r * sr + (long long)(k0 + k) * sk]));
-      rexp[r] = E;
-      for (int k = 0; k < KC; ++k) {
-        const double x = (r < rows && k0 + k < K) ? P[r * sr + (long long)(k0 + k) * sk] : 0.0;
-        __nv_bfloat16 q[NDIG];
-        digits(x, E, q);
+      for (int kb = 0; kb < KC; kb += SK) {
+        double x[SK];
 #pragma unroll
-        for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, k)) = q[j];
+        for (int u = 0; u < SK; ++u)
+          x[u] = (live && k0 + kb + u < K) ? P[r * sr + (long long)(k0 + kb + u) * sk] : 0.0;
+#pragma unroll
+        for (int u = 0; u < SK; ++u) E = max(E, exp_field(x[u]));
+      }
+      rexp[r] = E;
+      for (int kb = 0; kb < KC; kb += SK) {
+        double x[SK];
+#pragma unroll
+        for (int u = 0; u < SK; ++u)
+          x[u] = (live && k0 + kb + u < K) ? P[r * sr + (long long)(k0 + kb + u) * sk] : 0.0;
+#pragma unroll
+        for (int u = 0; u < SK; ++u) {
+          __nv_bfloat16 q[NDIG];
+          digits(x[u], E, q);
+#pragma unroll
+          for (int j = 0; j < NDIG; ++j) *(__nv_bfloat16*)(planes + j * plane_bytes + core_off(r, kb + u)) = q[j];
+        }
       }
     }
   }
