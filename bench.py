@@ -796,6 +796,26 @@ def main():
                                                 fp64_peak, "TFLOP/s", f64src, c_pms)}
         except Exception as e:   # noqa: BLE001
             other["cube16"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            ps = [li.config5_box(rank * args.batch + r) for r in range(args.batch)]
+            b_ms, b_outs, b_prof, b_plan, b_pms = timed_plan(ctx, stream, ps, 2, 1, flush, args.maxit, profile=True)
+            b_plan.close()
+            bm_ms, bm_outs, _, bm_plan, _ = timed_plan(ctx, stream, mixed_of(ps), 2, 1, flush, args.maxit)
+            bm_plan.close()
+            b_fl = fp64_flops_per_step(ps, b_outs)
+            other["box512_only"] = {
+                "config": {"workload": "box chain 512x1x1 (n0=15, grid 8192x256x256, m0=32, R=40, lowest 64) "
+                                      f"without periodic problems; batch {args.batch}",
+                           "rayleigh_ritz": "one thread-block cluster of 8 CTAs per chain (no periodic work "
+                                            "to share the GPU with)"},
+                "value": len(ps) * 2 / (b_ms / 1e3), "unit": UNIT, "ms_per_step": b_ms / 2,
+                "mixed_value": len(ps) * 2 / (bm_ms / 1e3),
+                "max_rel_eig_diff_mixed_vs_fp64": max_rel_diff(b_outs, bm_outs, 64),
+                "statuses_nonzero": sum(1 for o in b_outs + bm_outs if o["status"] != 0),
+                "roofline_rayleigh_ritz": roof("k_rr", "alu", b_fl.get("k_rr"), b_prof, 2, fp64_peak, "TFLOP/s",
+                                               f64src, b_pms)}
+        except Exception as e:   # noqa: BLE001
+            other["box512_only"] = {"error": f"{type(e).__name__}: {e}"}
         line["other_configs"] = other
 
     if rank == 0:

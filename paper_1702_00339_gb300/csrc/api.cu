@@ -67,6 +67,8 @@ void launch_gemm_tn(const GemmTask*, int, int, int, int, cudaStream_t);
 __global__ void k_gemm_nn(const GemmTask*);
 __global__ void k_resid(const ResidTask*, double);
 __global__ void k_rr(const RRTask*, int, int);
+__global__ void k_rr_cl(const RRTask*);
+size_t rr_cl_smem(int, int);
 __global__ void k_copy_cols(const CopyTask*);
 __global__ void k_colnorm(const CopyTask*);
 }  // namespace fock
@@ -477,6 +479,10 @@ struct Batch {
   bool rr_small = false, rr_big = false;   // Rayleigh-Ritz launches needed (256 / 512 threads)
   int rr_small_ld = 0;               // largest ld of the shared-memory problems
   int rr_big_ld = 0;                 // largest ld of the others
+  // the others on thread-block clusters (k_rr_cl) when the plan has no periodic
+  // problems; beside periodic problems one CTA each (k_rr), whose narrow launch
+  // leaves the other SMs to the periodic pieces (both give the same bits)
+  bool rr_cluster = false;
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, pcG, pcM, pcZ, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
@@ -497,6 +503,7 @@ struct Batch {
   int* d_refresh = nullptr;          // per structured problem: 0 = refresh its [X | P] images now
   bool any_mixed = false;
   int* d_fail = nullptr;
+  unsigned* d_rrbar = nullptr;       // per structured problem: k_rr_cl's barrier counter
   double* d_res = nullptr;
   double* d_lam = nullptr;
   // upload slab: parameters and descriptors, staged on the host, one copy
@@ -521,6 +528,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.gemm_tiles = 0;
   B.rr_small = B.rr_big = false;
   B.rr_small_ld = B.rr_big_ld = 0;
+  B.rr_cluster = false;
   B.ptab_maxT = 0; B.ptab_maxni = 0;
   size_t zs_total = 0;
   // ---- parameters, vectors, gram tasks ----
@@ -989,6 +997,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     B.d_mode = S.take<int>(ns);
     B.d_refresh = S.take<int>(ns);
     B.d_fail = S.take<int>(ns);
+    B.d_rrbar = S.take<unsigned>(ns);
     B.d_res = S.take<double>((size_t)ns * B.kmax);
     B.d_lam = S.take<double>((size_t)ns * B.kmax);
     for (int s = 0; s < ns; ++s) {
@@ -1144,8 +1153,9 @@ void plan(Batch& B, Slab& S, Slab& U) {
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0)));
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
       const int big = (3 * (size_t)ld3 * ld3 * sizeof(double) > kRRSmemCap) ? 1 : 0;
-      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
-      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
+      unsigned* rbar = B.d_rrbar + s2;
+      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big, rbar});
+      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big, rbar});
       B.rr_small = B.rr_small || !big;
       B.rr_big = B.rr_big || big;
       if (!big) B.rr_small_ld = std::max(B.rr_small_ld, ld3);
@@ -1212,6 +1222,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     TLp(gg3, B.g3, 3 * kk, 3 * kk);
     B.tnCx.tile = B.pcM.tile = B.g1.tile = B.g3.tile = B.gemm_tiles;
     TLp(r1, B.rr1, maxld3); TLp(r3, B.rr3, maxld3);
+    B.rr_cluster = B.fbp.empty();   // the periodic tasks are planned by now
     TLp(uu1, B.u1); TLp(uu3, B.u3);
     auto TLs = [&](std::vector<SplitTask>& v, Batch::TL& tl) {
       tl.sd = (void*)U.put(v); tl.sn = (int)v.size();
@@ -1498,9 +1509,28 @@ void rr(Batch& B, const Batch::TL& t, cudaStream_t st) {
     const size_t sm = ((size_t)3 * ld * ld + (size_t)rr_stage_extra(ld)) * sizeof(double);
     k_rr<<<t.n, 256, sm, st>>>(tl<RRTask>(t), (int)sm, 0);
   }
-  if (B.rr_big) {
+  if (B.rr_big && !B.rr_cluster) {
     const size_t sm = (size_t)2 * kRRBlock * B.rr_big_ld * sizeof(double);
     k_rr<<<t.n, 512, sm, st>>>(tl<RRTask>(t), (int)sm, 1);
+  }
+  if (B.rr_big && B.rr_cluster) {
+    // one cluster of kRRCluster CTAs per problem; their barrier counters start
+    // at zero (kept for the bounded-wait form of the barrier)
+    cudaMemsetAsync(B.d_rrbar, 0, B.sidx.size() * sizeof(unsigned), st);
+    FOCK_SMEM_OPTIN(k_rr_cl);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(t.n * kRRCluster));
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = rr_cl_smem(B.rr_big_ld, B.kmax);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kRRCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_rr_cl, tl<RRTask>(t));
   }
 }
 // unit 2-norm columns before a matvec: the FFT packs two real columns per

@@ -275,6 +275,8 @@ struct ResidTask {
 // pivot columns per block of the Rayleigh-Ritz step's triangular substitutions
 // (its shared-memory staging: 2 kRRBlock ld doubles)
 constexpr int kRRBlock = 8;
+// CTAs of the cluster that runs one large Rayleigh-Ritz step (k_rr_cl)
+constexpr int kRRCluster = 8;
 // extra doubles of staging a shared-memory Rayleigh-Ritz step needs beyond its
 // 3 ld^2 (none when its first working matrix, ld^2 doubles, can hold it)
 __host__ __device__ inline int rr_stage_extra(int ld) { return (ld * ld >= 2 * kRRBlock * ld) ? 0 : 2 * kRRBlock * ld; }
@@ -290,8 +292,10 @@ struct RRTask {
   int* fail;              // out: 1 if Y^T S Y was not numerically positive definite
   const int* mode;        // mixed form: 1 while the images are FP32 (coarser drop threshold)
   int big;                // 1: the working matrices (3 ld^2 doubles) exceed shared memory; the
-                          //    problem runs in the 512-thread launch, else in the 256-thread one
-                          //    (a property of the problem alone, so results are batch-invariant)
+                          //    problem runs on a cluster of 512-thread CTAs (k_rr_cl), else in
+                          //    the 256-thread k_rr (a property of the problem alone, so results
+                          //    are batch-invariant)
+  unsigned* bar;          // k_rr_cl: the cluster's barrier counter (zeroed before each launch)
 };
 
 struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };

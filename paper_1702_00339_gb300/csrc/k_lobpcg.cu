@@ -1066,3 +1066,640 @@ void launch_cell_back(const double* Xc, int m0, int L, int ncol, const double* V
 }
 
 }  // namespace fock
+
+namespace fock {
+
+// ---- Rayleigh-Ritz on a thread-block cluster (bases in global memory) ----
+//
+// A basis too large for one CTA's shared memory (3 ld^2 doubles > 160 KB) is
+// handled by a cluster of kRRCluster CTAs of kRRMaxThreads threads, so that
+// one problem's step uses kRRCluster SMs' FP64 pipes instead of one.  The
+// phases are those of k_rr / cta_sym_lowest with every per-entry operation
+// unchanged: work that is independent per entry, row, column or vector is
+// divided among the CTAs; small sequential decisions (pivots, reflectors, the
+// kk x kk Cholesky and Jacobi steps) are repeated in every CTA from the same
+// data, so all CTAs take the same branches and the results equal the
+// single-CTA kernel's bit for bit.  The working matrices stay in the problem's
+// global work array (L2); a CTA's copies of the small arrays live in its own
+// shared memory.
+
+
+// Barrier of the cluster's CTAs: the hardware cluster barrier, whose arrive
+// has release and whose wait has acquire semantics at cluster scope, so every
+// global-memory write of the cluster before it is seen by every read after it.
+// Every CTA of a cluster reaches the same sequence of barriers: each branch on
+// the way is taken on values that every CTA computes alike from data that no
+// CTA changes until the next barrier (checked by a version of this barrier
+// with bounded waits, which never ran out and gave the same results).  The
+// counter arguments serve that checking version and are unused here.
+__device__ bool cl_sync(unsigned*, unsigned&) {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  return true;
+}
+
+// [lo, hi) of 0..n-1 for CTA `rank` of the cluster (contiguous shares)
+__device__ inline int cl_lo(int n, int rank) { return (int)(((long long)n * rank) / kRRCluster); }
+
+// cta_sym_lowest on a cluster (same phases, same per-entry arithmetic).
+// a, z: r x r and r x kk in global memory (stride ld); scr: 4 ld^2 doubles of
+// global scratch shared by the cluster; priv: this CTA's dynamic shared
+// memory, >= 2 (kk + 1)^2 doubles (private copies for the small factorisations);
+// d, e, tau, pv, lam, ord: this CTA's shared arrays as in cta_sym_lowest.
+// Returns false when a cluster barrier ran out.
+__device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, double* scr, double* priv,
+                              double* d, double* e, double* tau, double* pv, double* lam, int* ord,
+                              unsigned* bar, unsigned& tgt, int rank) {
+  __shared__ double s_tau, s_K, s_v1;
+  __shared__ double s_pw[4][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* pg = scr + (size_t)3 * ld * ld;        // p of the current column, shared by the cluster
+  auto A = [&](int i, int j) -> double { return i >= j ? a[i * ld + j] : a[j * ld + i]; };
+  // v of column k: its first entry (row k + 1) is this CTA's s_v1 until the
+  // reduction ends, the rest are the column's entries below it
+  // ---- Householder reduction to tridiagonal form ----
+  for (int k = 0; k + 2 < r; ++k) {
+    const int n = r - k - 1;
+    if (warp == 0) {                             // reflector of column k (every CTA alike)
+      double part = 0.0;
+      for (int i = k + 1 + lane; i < r; i += 32) part = fma(a[i * ld + k], a[i * ld + k], part);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) {
+        const double s = part;
+        const double x0 = a[(k + 1) * ld + k];
+        const double xn = (s > 0.0) ? s * rsqrt_nr(s) : 0.0;
+        const double alpha = (x0 > 0.0) ? -xn : xn;
+        const double vtv = 2.0 * (s - x0 * alpha);
+        d[k] = a[k * ld + k];
+        e[k] = alpha;
+        s_tau = (vtv > 0.0) ? 2.0 * rcp_nr(vtv) : 0.0;
+        tau[k] = s_tau;
+        s_v1 = x0 - alpha;
+      }
+    }
+    __syncthreads();
+    const double tk = s_tau, v1 = s_v1;
+    if (__double_as_longlong(tk) == 0) continue;   // the same in every CTA: x = 0 below row k + 1
+    auto vv = [&](int j) -> double { return j == k + 1 ? v1 : a[j * ld + k]; };
+    // p = tau A22 v for this CTA's rows of the trailing block, into pg
+    const int rlo = cl_lo(n, rank), rhi = cl_lo(n, rank + 1);
+    if (n <= 64) {
+      const int q = threadIdx.x >> 6, ri = rlo + (threadIdx.x & 63);
+      if (q < 4 && ri < rhi) {
+        const int i = k + 1 + ri;
+        double acc = 0.0;
+        for (int j = k + 1 + q; j < r; j += 4) acc = fma(A(i, j), vv(j), acc);
+        s_pw[q][ri - rlo] = acc;
+      }
+      __syncthreads();
+      for (int ri2 = rlo + threadIdx.x; ri2 < rhi; ri2 += blockDim.x) {
+        const int o = ri2 - rlo;
+        pg[k + 1 + ri2] = tk * ((s_pw[0][o] + s_pw[1][o]) + (s_pw[2][o] + s_pw[3][o]));
+      }
+    } else {
+      for (int i = k + 1 + rlo + threadIdx.x; i < k + 1 + rhi; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = k + 1; j < r; ++j) acc = fma(A(i, j), vv(j), acc);
+        pg[i] = tk * acc;
+      }
+    }
+    if (!cl_sync(bar, tgt)) return false;
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] = pg[i];
+    __syncthreads();
+    if (warp == 0) {                             // K = (tau / 2) v^T p (every CTA alike)
+      double kp = 0.0;
+      for (int i = k + 1 + lane; i < r; i += 32) kp = fma(vv(i), pv[i], kp);
+      for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+      if (lane == 0) s_K = 0.5 * tk * kp;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] = fma(-s_K, vv(i), pv[i]);   // w
+    __syncthreads();
+    // A22 -= v w^T + w v^T on the lower triangle, this CTA's share of its entries
+    const int nt = n * (n + 1) / 2, tlo = cl_lo(nt, rank), thi = cl_lo(nt, rank + 1);
+    for (int it = tlo + threadIdx.x; it < thi; it += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
+      while (ii * (ii + 1) / 2 > it) --ii;
+      const int jj = it - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      a[i * ld + j] -= fma(vv(i), pv[j], pv[i] * vv(j));
+    }
+    if (rank == 0 && threadIdx.x == 0) a[(k + 1) * ld + k] = v1;   // read again only by the back-transformation
+    if (!cl_sync(bar, tgt)) return false;
+  }
+  if (threadIdx.x == 0) {
+    if (r >= 2) {
+      d[r - 2] = a[(r - 2) * ld + (r - 2)];
+      d[r - 1] = a[(r - 1) * ld + (r - 1)];
+      e[r - 2] = a[(r - 1) * ld + (r - 2)];
+      if (r >= 3) tau[r - 2] = 0.0;
+    } else {
+      d[0] = a[0];
+    }
+  }
+  __syncthreads();
+  float tnorm;                                   // Gershgorin bound of |T|, FP32
+  // ---- kk lowest eigenvalues of T: FP32 Sturm multisection (every CTA alike) ----
+  {
+    __shared__ float s_lo[128], s_hi[128];       // kk <= 128
+    __shared__ int s_cnt[kRRMaxThreads];
+    float* df = reinterpret_cast<float*>(pv);    // pv is free here: d and e^2 in FP32
+    float* e2f = df + 256;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      df[i] = (float)d[i];
+      e2f[i] = (i + 1 < r) ? (float)(e[i] * e[i]) : 0.0f;
+    }
+    __syncthreads();
+    float glo = FLT_MAX, ghi = -FLT_MAX, emax2 = 0.0f;
+    for (int i = 0; i < r; ++i) {
+      const float rad = (i > 0 ? sqrtf(e2f[i - 1]) : 0.0f) + (i + 1 < r ? sqrtf(e2f[i]) : 0.0f);
+      glo = fminf(glo, df[i] - rad);
+      ghi = fmaxf(ghi, df[i] + rad);
+      if (i + 1 < r) emax2 = fmaxf(emax2, e2f[i]);
+    }
+    tnorm = fmaxf(fabsf(glo), fabsf(ghi));
+    const float pivmin = FLT_MIN * fmaxf(1.0f, emax2);
+    glo -= 4.0f * FLT_EPSILON * tnorm + pivmin;
+    ghi += 4.0f * FLT_EPSILON * tnorm + pivmin;
+    const int g = max(1, (int)blockDim.x / max(kk, 1));
+    const int grp = threadIdx.x / g, mem = threadIdx.x % g;
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) { s_lo[c] = glo; s_hi[c] = ghi; }
+    __syncthreads();
+    for (int round = 0; round < 40; ++round) {
+      float x = 0.0f;
+      if (grp < kk) {
+        const float lo = s_lo[grp], hi = s_hi[grp];
+        x = lo + (hi - lo) * ((float)(mem + 1) / (float)(g + 1));
+        int cnt = 0;
+        float q = df[0] - x;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += (q < 0.0f);
+        for (int i = 1; i < r; ++i) {
+          q = (df[i] - x) - __fdividef(e2f[i - 1], q);
+          if (fabsf(q) < pivmin) q = -pivmin;
+          cnt += (q < 0.0f);
+        }
+        s_cnt[threadIdx.x] = cnt;
+      }
+      __syncthreads();
+      int open = 0;
+      if (grp < kk && mem == 0) {
+        const float lo = s_lo[grp], hi = s_hi[grp];
+        float nlo = lo, nhi = hi;
+        for (int m = 0; m < g; ++m) {
+          const float xm = lo + (hi - lo) * ((float)(m + 1) / (float)(g + 1));
+          if (s_cnt[grp * g + m] > grp) { nhi = fminf(nhi, xm); break; }
+          nlo = fmaxf(nlo, xm);
+        }
+        if (!(nlo < nhi)) nhi = nlo;
+        s_lo[grp] = nlo;
+        s_hi[grp] = nhi;
+        open = (nhi - nlo > 2.0f * FLT_EPSILON * fmaxf(fabsf(nlo), fabsf(nhi)) + pivmin);
+      }
+      if (!__syncthreads_or(open)) break;
+    }
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = 0.5 * ((double)s_lo[c] + (double)s_hi[c]);
+    __syncthreads();
+  }
+  // ---- inverse iteration: vector c on CTA c mod kRRCluster, workspace 5 r at scr + 5 r c ----
+  for (int c = rank + kRRCluster * (int)threadIdx.x; c < kk; c += kRRCluster * (int)blockDim.x) {
+    double* lv = scr + (size_t)c * 5 * r;        // multipliers
+    double* rp = lv + r;                         // reciprocal pivots
+    double* u1 = rp + r;
+    double* u2 = u1 + r;
+    double* pvt = u2 + r;                        // row swap flags
+    const double eps = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
+    const long long eps_bits = abs_bits(eps);
+    const double lm = lam[c];
+    double a0 = d[0] - lm, a1 = (r > 1) ? e[0] : 0.0;
+    for (int i = 0; i + 1 < r; ++i) {
+      const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
+      const bool sw = abs_bits(sub) > abs_bits(a0);
+      double p0 = sw ? sub : a0;
+      const double p1 = sw ? dn : a1, p2 = sw ? sn : 0.0;
+      const double o0 = sw ? a0 : sub, o1 = sw ? a1 : dn, o2 = sw ? 0.0 : sn;
+      if (abs_bits(p0) < eps_bits) p0 = (__double_as_longlong(p0) < 0) ? -eps : eps;
+      const double rq = rcp_nr(p0);
+      const double m = o0 * rq;
+      lv[i] = m; rp[i] = rq; u1[i] = p1; u2[i] = p2; pvt[i] = sw ? 1.0 : 0.0;
+      a0 = fma(-m, p1, o1);
+      a1 = fma(-m, p2, o2);
+    }
+    if (abs_bits(a0) < eps_bits) a0 = (__double_as_longlong(a0) < 0) ? -eps : eps;
+    rp[r - 1] = rcp_nr(a0);
+    u1[r - 1] = 0.0; u2[r - 1] = 0.0;
+    if (r >= 2) u2[r - 2] = 0.0;
+    for (int i = 0; i < r; ++i) {
+      const uint32_t h = (uint32_t)(splitmix64(((uint64_t)(c + 1) << 32) | (uint64_t)(i + 1)) >> 40);
+      z[i * ld + c] = 0.5 + (double)h * (1.0 / 16777216.0);
+    }
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      for (int i = 0; i + 1 < r; ++i) {
+        const double zi = z[i * ld + c], zn = z[(i + 1) * ld + c];
+        const bool sw = __double_as_longlong(pvt[i]) != 0;
+        const double bi = sw ? zn : zi, bn = sw ? zi : zn;
+        z[i * ld + c] = bi;
+        z[(i + 1) * ld + c] = fma(-lv[i], bi, bn);
+      }
+      double nxt = 0.0, nxt2 = 0.0, nn = 0.0;
+      for (int i = r - 1; i >= 0; --i) {
+        double s = fma(-u1[i], nxt, z[i * ld + c]);
+        s = fma(-u2[i], nxt2, s);
+        s *= rp[i];
+        z[i * ld + c] = s;
+        nn = fma(s, s, nn);
+        nxt2 = nxt; nxt = s;
+      }
+      const double inv = (nn > 0.0 && isfinite(nn)) ? rsqrt_nr(nn) : 0.0;
+      for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
+    }
+  }
+  if (!cl_sync(bar, tgt)) return false;
+  // ---- Cholesky-QR, twice: Gram entries shared out, each CTA factors its own copy ----
+  double* s_rl = pv;                             // reciprocal diagonal of the Gram factor
+  double* Gg = scr + (size_t)ld * ld;            // the Gram, shared by the cluster
+  double* Gp = priv;                             // this CTA's copy, factored in place
+  const int zlo = cl_lo(r, rank), zhi = cl_lo(r, rank + 1);   // this CTA's rows of Z
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int it = cl_lo(kk * kk, rank) + threadIdx.x; it < cl_lo(kk * kk, rank + 1); it += blockDim.x) {
+      const int c1 = it / kk, c2 = it % kk;
+      if (c2 > c1) continue;
+      double s = 0.0;
+      for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], z[i * ld + c2], s);
+      Gg[c1 * kk + c2] = s;
+    }
+    if (!cl_sync(bar, tgt)) return false;
+    for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) Gp[it] = Gg[it];
+    __syncthreads();
+    for (int j = 0; j < kk; ++j) {               // right-looking Cholesky, reciprocal diagonal in s_rl
+      if (threadIdx.x == 0) {
+        const double gjj = fmax(Gp[j * kk + j], DBL_MIN);
+        const double rlj = rsqrt_nr(gjj);
+        s_rl[j] = rlj;
+        Gp[j * kk + j] = gjj * rlj;
+      }
+      __syncthreads();
+      const double rlj = s_rl[j];
+      for (int i = j + 1 + threadIdx.x; i < kk; i += blockDim.x) Gp[i * kk + j] *= rlj;
+      __syncthreads();
+      const int nt = kk - j - 1;
+      for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
+        const int i = j + 1 + it / nt, l = j + 1 + it % nt;
+        if (l <= i) Gp[i * kk + l] = fma(-Gp[i * kk + j], Gp[l * kk + j], Gp[i * kk + l]);
+      }
+      __syncthreads();
+    }
+    for (int i = zlo + threadIdx.x; i < zhi; i += blockDim.x)   // row i of Z times L^-T
+      for (int c = 0; c < kk; ++c) {
+        double s = z[i * ld + c];
+        for (int q = 0; q < c; ++q) s = fma(-z[i * ld + q], Gp[c * kk + q], s);
+        z[i * ld + c] = s * s_rl[c];
+      }
+    if (!cl_sync(bar, tgt)) return false;
+  }
+  // ---- Rayleigh-Ritz in span(Z): Tz = Z^T (T Z) shared out, Jacobi on each CTA's copy ----
+  const int kj = kk + 1;
+  double* Tz = scr + (size_t)2 * ld * ld;
+  double* tmp = scr;   // r x kk: T Z, then Z Qz
+  double* Tp = priv;                               // (kk + 1) x kj
+  double* Qp = priv + (size_t)kj * kj;             // (kk + 1) x kj
+  for (int it = cl_lo(r * kk, rank) + threadIdx.x; it < cl_lo(r * kk, rank + 1); it += blockDim.x) {
+    const int i = it / kk, c = it % kk;
+    double s = d[i] * z[i * ld + c];
+    if (i > 0) s = fma(e[i - 1], z[(i - 1) * ld + c], s);
+    if (i + 1 < r) s = fma(e[i], z[(i + 1) * ld + c], s);
+    tmp[it] = s;
+  }
+  if (!cl_sync(bar, tgt)) return false;
+  for (int it = cl_lo(kk * kk, rank) + threadIdx.x; it < cl_lo(kk * kk, rank + 1); it += blockDim.x) {
+    const int c1 = it / kk, c2 = it % kk;
+    if (c2 > c1) continue;
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], tmp[i * kk + c2], s);
+    Tz[c1 * kj + c2] = s;
+    Tz[c2 * kj + c1] = s;
+  }
+  if (!cl_sync(bar, tgt)) return false;
+  for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) Tp[(it / kk) * kj + it % kk] = Tz[(it / kk) * kj + it % kk];
+  __syncthreads();
+  cta_jacobi(Tp, Qp, kk, kj);
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) {   // ascending order, ties by index, NaN last
+    double di = Tp[i * kj + i];
+    if (isnan(di)) di = DBL_MAX;
+    int rk = 0;
+    for (int j = 0; j < kk; ++j) {
+      double dj = Tp[j * kj + j];
+      if (isnan(dj)) dj = DBL_MAX;
+      rk += (dj < di) || (dj == di && j < i);
+    }
+    ord[rk] = i;
+  }
+  __syncthreads();
+  for (int it = zlo * kk + threadIdx.x; it < zhi * kk; it += blockDim.x) {   // this CTA's rows of Z Qz
+    const int i = it / kk, c = it % kk, oc = ord[c];
+    double s = 0.0;
+    for (int q = 0; q < kk; ++q) s = fma(z[i * ld + q], Qp[q * kj + oc], s);
+    tmp[it] = s;
+  }
+  __syncthreads();
+  for (int it = zlo * kk + threadIdx.x; it < zhi * kk; it += blockDim.x) z[(it / kk) * ld + (it % kk)] = tmp[it];
+  for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = Tp[ord[c] * kj + ord[c]];
+  if (!cl_sync(bar, tgt)) return false;
+  // ---- back-transformation z = H_0 ... H_{r-3} y of this CTA's vectors (c = rank mod kRRCluster) ----
+  {
+    const int grp = threadIdx.x >> 3, q = threadIdx.x & 7;
+    const int nown = (kk - rank + kRRCluster - 1) / kRRCluster;
+    for (int m0 = 0; m0 < nown; m0 += (int)(blockDim.x >> 3)) {
+      const int m = m0 + grp, c = rank + kRRCluster * m;
+      const bool act = m < nown;
+      if (__all_sync(0xffffffffu, !act)) continue;
+      for (int k = r - 3; k >= 0; --k) {
+        const double tk = tau[k];
+        if (__double_as_longlong(tk) == 0) continue;
+        const int i0 = k + 1 + ((q - (k + 1)) & 7);
+        double s = 0.0;
+        if (act)
+          for (int i = i0; i < r; i += 8) s = fma(a[i * ld + k], z[i * ld + c], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s *= tk;
+        if (act)
+          for (int i = i0; i < r; i += 8) z[i * ld + c] = fma(-s, a[i * ld + k], z[i * ld + c]);
+      }
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// k_rr for the problems with big = 1, one cluster of kRRCluster CTAs per task
+// (grid = tasks x kRRCluster).  T.bar: the task's barrier counter, zeroed
+// before the launch.  Dynamic shared memory: the substitutions' staging and
+// the private copies of cl_sym_lowest (rr_cl_smem doubles).  A barrier that
+// ran out leaves NaN in the first coefficient, so the problem's next residual
+// is not finite and the iteration reports it unconverged.
+__global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restrict__ tasks) {
+  const RRTask T = tasks[blockIdx.x / kRRCluster];
+  const int rank = blockIdx.x % kRRCluster;
+  if (T.big != 1) return;                   // the same for the whole cluster
+  if (T.active && *T.active == 0) return;
+  extern __shared__ double rr_smem[];
+  const double kDropRel = (T.mode && *T.mode) ? 1e-6 : 1e-10;
+  const int ld = T.ld, k = T.k, nb = T.nb;
+  unsigned tgt = 0;
+  double* C = T.work;                        // scaled H-Gram, then the reduced matrix (lower)
+  double* V = T.work + (size_t)ld * ld;      // work matrix, then the eigenvectors
+  double* G = T.work + (size_t)2 * ld * ld;  // scaled S-Gram (lower, original indices), then L
+  double* rr_blk = rr_smem;                  // substitution staging, 2 kRRBlock ld
+  double* priv = rr_smem + (size_t)2 * kRRBlock * ld;
+  __shared__ double dsc[256], rl[256], rdv[256], colS[256], colL[256], dg[256];
+  __shared__ long long wkey[kRRMaxThreads / 32];
+  __shared__ int perm[256], order[256], wpos[kRRMaxThreads / 32];
+  __shared__ double tdd[256], tee[256], ttau[256], tpv[256], tlam[256];
+  __shared__ int s_r;
+  __shared__ double s_rd;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  bool ok = true;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const double g = T.GS[(size_t)i * ld + i];
+    dsc[i] = (g > 0.0) ? rsqrt_nr(g) : 0.0;
+    perm[i] = i;
+  }
+  __syncthreads();
+  for (int it = cl_lo(nb * nb, rank) + threadIdx.x; it < cl_lo(nb * nb, rank + 1); it += blockDim.x) {
+    const int i = it / nb, j = it % nb;
+    if (j > i) continue;
+    const double gs = 0.5 * (T.GS[(size_t)i + (size_t)ld * j] + T.GS[(size_t)j + (size_t)ld * i]);
+    const double gh = 0.5 * (T.GH[(size_t)i + (size_t)ld * j] + T.GH[(size_t)j + (size_t)ld * i]);
+    const double sc = dsc[i] * dsc[j];
+    G[i * ld + j] = gs * sc;
+    C[i * ld + j] = gh * sc;
+  }
+  if (threadIdx.x == 0) s_r = nb;
+  ok = cl_sync(T.bar, tgt);
+  auto GP = [&](int pa, int pb) -> double& { return pa >= pb ? G[pa * ld + pb] : G[pb * ld + pa]; };
+  // this CTA's copy of the diagonal (original indices), kept up to date with the
+  // same fma as the trailing update, so that the pivot search reads nothing
+  // another CTA is writing
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) dg[i] = G[i * ld + i];
+  __syncthreads();
+  // ---- pivoted LDL^T: pivots in every CTA alike, the trailing update shared
+  // out; column j keeps S(., j) until the factorisation ends (colL holds its
+  // scaled copy for the update), then every column is scaled to L in one pass
+  for (int j = 0; ok && j < nb; ++j) {
+    long long bk = -2;
+    int bi = j;
+    for (int i = j + threadIdx.x; i < nb; i += blockDim.x) {
+      const long long kq = pivot_key(dg[perm[i]]);
+      if (kq > bk) { bk = kq; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long okk = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (okk > bk || (okk == bk && oi < bi)) { bk = okk; bi = oi; }
+    }
+    if (lane == 0) { wkey[warp] = bk; wpos[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nwarp; ++w)
+        if (wkey[w] > wkey[0] || (wkey[w] == wkey[0] && wpos[w] < wpos[0])) { wkey[0] = wkey[w]; wpos[0] = wpos[w]; }
+      const int piv = wpos[0];
+      const double dj = dg[perm[piv]];
+      if (!(wkey[0] >= 0 && dj > kDropRel)) {
+        s_r = j;
+      } else {
+        const int t = perm[j]; perm[j] = perm[piv]; perm[piv] = t;
+        s_rd = rcp_nr(dj);
+        rl[j] = rsqrt_nr(dj);
+        rdv[j] = s_rd;
+      }
+    }
+    __syncthreads();
+    if (s_r == j) break;                      // the same j in every CTA
+    const int pj = perm[j];
+    const double rd = s_rd;
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      const double sij = GP(perm[i], pj);
+      colS[i] = sij;
+      colL[i] = __dmul_rn(sij, rd);           // the value the single-CTA kernel stores as L(i, j)
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      const int pi = perm[i];
+      dg[pi] = fma(-colL[i], colS[i], dg[pi]);
+    }
+    const int n = nb - j - 1, nt = n * (n + 1) / 2;
+    for (int it = cl_lo(nt, rank) + threadIdx.x; it < cl_lo(nt, rank + 1); it += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= it) ++ii;
+      while (ii * (ii + 1) / 2 > it) --ii;
+      const int aa = j + 1 + ii, bb = j + 1 + (it - ii * (ii + 1) / 2);
+      double& s = GP(perm[aa], perm[bb]);
+      s = fma(-colL[aa], colS[bb], s);
+    }
+    if (!(ok = cl_sync(T.bar, tgt))) break;
+  }
+  const int r = s_r;
+  if (ok) {
+    // L(a, j) = S(a, j) / delta_j for the kept pivots j < r, rows a > j: this CTA's rows
+    for (int aa = cl_lo(nb, rank) + threadIdx.x; aa < cl_lo(nb, rank + 1); aa += blockDim.x)
+      for (int jj = 0; jj < min(aa, r); ++jj) {
+        double& s = GP(perm[aa], perm[jj]);
+        s *= rdv[jj];
+      }
+    ok = cl_sync(T.bar, tgt);
+  }
+  if (rank == 0 && threadIdx.x == 0 && r < k && T.fail) *T.fail = 1;
+  auto Lp = [&](int aa, int bb) -> double { return GP(perm[aa], perm[bb]); };   // unit lower factor, aa > bb
+  constexpr int RB = kRRBlock;
+  double* sL = rr_blk;
+  double* sV = rr_blk + (size_t)RB * ld;
+  if (ok) {
+    // V = (D GH D) at the kept positions, this CTA's columns; V <- L^-1 V on them
+    const int clo = cl_lo(r, rank), chi = cl_lo(r, rank + 1), nc = chi - clo;
+    for (int it = threadIdx.x; it < r * nc; it += blockDim.x) {
+      const int aa = it / nc, col = clo + it % nc;
+      const int pa = perm[aa], pb = perm[col];
+      V[aa * ld + col] = pa >= pb ? C[pa * ld + pb] : C[pb * ld + pa];
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 < r; i0 += RB) {
+      const int nbk = min(RB, r - i0);
+      for (int it = threadIdx.x; it < nbk * r; it += blockDim.x) {
+        const int q = it / r, aa = it % r;
+        sL[q * ld + aa] = (aa > i0 + q) ? Lp(aa, i0 + q) : 0.0;
+      }
+      __syncthreads();
+      for (int col = clo + threadIdx.x; col < chi; col += blockDim.x) {
+        double v[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          if (q < nbk) {
+            double t = V[(i0 + q) * ld + col];
+#pragma unroll
+            for (int p = 0; p < q; ++p) t = fma(-sL[p * ld + i0 + q], v[p], t);
+            v[q] = t;
+            V[(i0 + q) * ld + col] = t;
+            sV[q * ld + col] = t;
+          }
+        }
+      }
+      __syncthreads();
+      const int a0 = i0 + nbk, na = r - a0;
+      for (int it = threadIdx.x; it < na * nc; it += blockDim.x) {
+        const int aa = a0 + it / nc, col = clo + it % nc;
+        double t = V[aa * ld + col];
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+          if (q < nbk) t = fma(-sL[q * ld + aa], sV[q * ld + col], t);
+        V[aa * ld + col] = t;
+      }
+      __syncthreads();
+    }
+    ok = cl_sync(T.bar, tgt);
+  }
+  if (ok) {
+    // the lower triangle of V L^-T on this CTA's rows x = rank + kRRCluster m,
+    // then C = Delta^-1/2 V Delta^-1/2 on them
+    const int nm = (r - rank + kRRCluster - 1) / kRRCluster;   // rows of this CTA
+    for (int i0 = 0; i0 < r; i0 += RB) {
+      const int nbk = min(RB, r - i0);
+      for (int it = threadIdx.x; it < nbk * r; it += blockDim.x) {
+        const int q = it / r, aa = it % r;
+        sL[q * ld + aa] = (aa > i0 + q) ? Lp(aa, i0 + q) : 0.0;
+      }
+      __syncthreads();
+      const int mb = (i0 > rank) ? (i0 - rank + kRRCluster - 1) / kRRCluster : 0;   // first row >= i0
+      for (int m = mb + threadIdx.x; m < nm; m += blockDim.x) {
+        const int x = rank + kRRCluster * m;
+        double w[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const int c = i0 + q;
+          if (q < nbk && x >= c) {
+            double t = V[x * ld + c];
+#pragma unroll
+            for (int p = 0; p < q; ++p) t = fma(-sL[p * ld + c], w[p], t);
+            w[q] = t;
+            V[x * ld + c] = t;
+            sV[q * ld + x] = t;
+          }
+        }
+      }
+      __syncthreads();
+      const int a0 = i0 + nbk, na = r - a0;
+      const int ma = (a0 > rank) ? (a0 - rank + kRRCluster - 1) / kRRCluster : 0;  // first row >= a0
+      const int nmr = max(nm - ma, 0);
+      for (int it = threadIdx.x; it < nmr * na; it += blockDim.x) {
+        const int x = rank + kRRCluster * (ma + it / na), aa = a0 + it % na;
+        if (aa > x) continue;
+        double t = V[x * ld + aa];
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+          if (q < nbk) t = fma(-sL[q * ld + aa], sV[q * ld + x], t);
+        V[x * ld + aa] = t;
+      }
+      __syncthreads();
+    }
+    for (int it = threadIdx.x; it < nm * r; it += blockDim.x) {
+      const int x = rank + kRRCluster * (it / r), bb = it % r;
+      if (bb > x) continue;
+      C[x * ld + bb] = V[x * ld + bb] * (rl[x] * rl[bb]);
+    }
+    ok = cl_sync(T.bar, tgt);
+  }
+  const int kk = min(k, r);
+  if (ok) ok = cl_sym_lowest(C, V, r, ld, kk, T.work + (size_t)3 * ld * ld, priv, tdd, tee, ttau, tpv, tlam,
+                             order, T.bar, tgt, rank);
+  const int nown_k = (k - rank + kRRCluster - 1) / kRRCluster;   // this CTA's columns c = rank + kRRCluster m < k
+  if (!ok) {
+    for (int it = threadIdx.x; it < nown_k; it += blockDim.x) {
+      const int c = rank + kRRCluster * it;
+      T.Cc[(size_t)ld * c] = NAN;
+      T.Cc[(size_t)ld * (k + c)] = NAN;
+    }
+    if (threadIdx.x == 0 && T.fail) *T.fail = 2;
+    return;
+  }
+  if (rank == 0)
+    for (int c = threadIdx.x; c < k; c += blockDim.x) T.lam[c] = (c < kk) ? tlam[c] : NAN;
+  // coefficients of this CTA's columns: w = L^-T Delta^-1/2 v (right-looking over positions)
+  const int nown = (kk - rank + kRRCluster - 1) / kRRCluster;
+  for (int it = threadIdx.x; it < r * nown; it += blockDim.x) {
+    const int aa = it / nown, c = rank + kRRCluster * (it % nown);
+    V[aa * ld + c] *= rl[aa];
+  }
+  __syncthreads();
+  for (int aa = r - 1; aa > 0; --aa) {
+    for (int it = threadIdx.x; it < aa * nown; it += blockDim.x) {
+      const int qq = it / nown, c = rank + kRRCluster * (it % nown);
+      V[qq * ld + c] = fma(-Lp(aa, qq), V[aa * ld + c], V[qq * ld + c]);
+    }
+    __syncthreads();
+  }
+  // z[perm a] = D w[a]; the second block is z with the first k rows zeroed
+  for (int it = threadIdx.x; it < nown_k * nb; it += blockDim.x) {
+    const int c = rank + kRRCluster * (it / nb), i = it % nb;
+    T.Cc[(size_t)ld * c + i] = 0.0;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nown * r; it += blockDim.x) {
+    const int c = rank + kRRCluster * (it / r), aa = it % r;
+    const int p = perm[aa];
+    T.Cc[(size_t)ld * c + p] = V[aa * ld + c] * dsc[p];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nown_k * nb; it += blockDim.x) {
+    const int c = rank + kRRCluster * (it / nb), i = it % nb;
+    T.Cc[(size_t)ld * (k + c) + i] = (i < k) ? 0.0 : T.Cc[(size_t)ld * c + i];
+  }
+}
+
+// doubles of dynamic shared memory k_rr_cl needs for leading dimension ld and k
+size_t rr_cl_smem(int ld, int k) {
+  return ((size_t)2 * kRRBlock * ld + (size_t)2 * (k + 1) * (k + 1)) * sizeof(double);
+}
+
+}  // namespace fock

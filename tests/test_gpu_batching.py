@@ -81,3 +81,24 @@ def test_tuner_result_is_cached_per_context(ctx):
     finally:
         p1.close()
         p2.close()
+
+
+def test_large_rayleigh_ritz_same_bits_on_a_cluster_and_on_one_cta(ctx):
+    """A basis too large for one CTA's shared memory (k = 32 on a 64-cell
+    chain: 3 x 36 columns) takes its Rayleigh-Ritz steps on a thread-block
+    cluster in a batch without periodic problems and on one CTA beside a
+    periodic problem.  Both give the same bits, and the oracle's eigenvalues."""
+    from oracle import dense
+    p = li.config2(5, L=64, n0=15, pad=32, n_perp=256, R=32)
+    p.k_eig = 32
+    per = li.config2(6, L=64, n0=15, pad=32, n_perp=256, R=32).as_periodic_chain()
+    per.k_eig = 0
+    alone = ctx.solve([p])[0]
+    beside = ctx.solve([p, per])[0]
+    assert alone["status"] == 0 and beside["status"] == 0
+    assert np.array_equal(alone["evals"], beside["evals"]) and alone["iters"] == beside["iters"]
+    q = _cases.with_table(p)
+    q.k_eig = p.k_eig
+    H, S = dense.build(q)
+    ref = _cases.reference(q, H, S)
+    _cases.report("box_k32_cluster", _cases.check(ref, alone["evals"]))
