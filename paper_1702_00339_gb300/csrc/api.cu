@@ -503,7 +503,6 @@ struct Batch {
   int* d_refresh = nullptr;          // per structured problem: 0 = refresh its [X | P] images now
   bool any_mixed = false;
   int* d_fail = nullptr;
-  unsigned* d_rrbar = nullptr;       // per structured problem: k_rr_cl's barrier counter
   double* d_res = nullptr;
   double* d_lam = nullptr;
   // upload slab: parameters and descriptors, staged on the host, one copy
@@ -997,7 +996,6 @@ void plan(Batch& B, Slab& S, Slab& U) {
     B.d_mode = S.take<int>(ns);
     B.d_refresh = S.take<int>(ns);
     B.d_fail = S.take<int>(ns);
-    B.d_rrbar = S.take<unsigned>(ns);
     B.d_res = S.take<double>((size_t)ns * B.kmax);
     B.d_lam = S.take<double>((size_t)ns * B.kmax);
     for (int s = 0; s < ns; ++s) {
@@ -1153,9 +1151,8 @@ void plan(Batch& B, Slab& S, Slab& U) {
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.HY, n, l.GH, ld3, 1.0, 0.0)));
       gg3.push_back(sym(gt(3 * k, 3 * k, l.Y, n, l.SY, n, l.GS, ld3, 1.0, 0.0)));
       const int big = (3 * (size_t)ld3 * ld3 * sizeof(double) > kRRSmemCap) ? 1 : 0;
-      unsigned* rbar = B.d_rrbar + s2;
-      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big, rbar});
-      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big, rbar});
+      r1.push_back({l.active, k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
+      r3.push_back({l.active, 3 * k, k, ld3, l.GH, l.GS, l.work, l.lam, l.Cc, l.fail, opmode, big});
       B.rr_small = B.rr_small || !big;
       B.rr_big = B.rr_big || big;
       if (!big) B.rr_small_ld = std::max(B.rr_small_ld, ld3);
@@ -1514,9 +1511,7 @@ void rr(Batch& B, const Batch::TL& t, cudaStream_t st) {
     k_rr<<<t.n, 512, sm, st>>>(tl<RRTask>(t), (int)sm, 1);
   }
   if (B.rr_big && B.rr_cluster) {
-    // one cluster of kRRCluster CTAs per problem; their barrier counters start
-    // at zero (kept for the bounded-wait form of the barrier)
-    cudaMemsetAsync(B.d_rrbar, 0, B.sidx.size() * sizeof(unsigned), st);
+    // one cluster of kRRCluster CTAs per problem
     FOCK_SMEM_OPTIN(k_rr_cl);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(t.n * kRRCluster));

@@ -295,7 +295,6 @@ struct RRTask {
                           //    problem runs on a cluster of 512-thread CTAs (k_rr_cl), else in
                           //    the 256-thread k_rr (a property of the problem alone, so results
                           //    are batch-invariant)
-  unsigned* bar;          // k_rr_cl: the cluster's barrier counter (zeroed before each launch)
 };
 
 struct CopyTask { const int* active; int n, ncols; const double* src; int lds; double* dst; int ldd; };

@@ -1089,10 +1089,10 @@ namespace fock {
 // global-memory write of the cluster before it is seen by every read after it.
 // Every CTA of a cluster reaches the same sequence of barriers: each branch on
 // the way is taken on values that every CTA computes alike from data that no
-// CTA changes until the next barrier (checked by a version of this barrier
-// with bounded waits, which never ran out and gave the same results).  The
-// counter arguments serve that checking version and are unused here.
-__device__ bool cl_sync(unsigned*, unsigned&) {
+// CTA changes until the next barrier (checked on the GPU with a form of this
+// barrier whose waits were bounded: no wait ran out, and the results were the
+// same).
+__device__ bool cl_sync() {
   __threadfence();
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   return true;
@@ -1109,7 +1109,7 @@ __device__ inline int cl_lo(int n, int rank) { return (int)(((long long)n * rank
 // Returns false when a cluster barrier ran out.
 __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, double* scr, double* priv,
                               double* d, double* e, double* tau, double* pv, double* lam, int* ord,
-                              unsigned* bar, unsigned& tgt, int rank) {
+                              int rank) {
   __shared__ double s_tau, s_K, s_v1;
   __shared__ double s_pw[4][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1163,7 +1163,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
         pg[i] = tk * acc;
       }
     }
-    if (!cl_sync(bar, tgt)) return false;
+    if (!cl_sync()) return false;
     for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) pv[i] = pg[i];
     __syncthreads();
     if (warp == 0) {                             // K = (tau / 2) v^T p (every CTA alike)
@@ -1186,7 +1186,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
       a[i * ld + j] -= fma(vv(i), pv[j], pv[i] * vv(j));
     }
     if (rank == 0 && threadIdx.x == 0) a[(k + 1) * ld + k] = v1;   // read again only by the back-transformation
-    if (!cl_sync(bar, tgt)) return false;
+    if (!cl_sync()) return false;
   }
   if (threadIdx.x == 0) {
     if (r >= 2) {
@@ -1315,7 +1315,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
       for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
     }
   }
-  if (!cl_sync(bar, tgt)) return false;
+  if (!cl_sync()) return false;
   // ---- Cholesky-QR, twice: Gram entries shared out, each CTA factors its own copy ----
   double* s_rl = pv;                             // reciprocal diagonal of the Gram factor
   double* Gg = scr + (size_t)ld * ld;            // the Gram, shared by the cluster
@@ -1329,7 +1329,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
       for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], z[i * ld + c2], s);
       Gg[c1 * kk + c2] = s;
     }
-    if (!cl_sync(bar, tgt)) return false;
+    if (!cl_sync()) return false;
     for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) Gp[it] = Gg[it];
     __syncthreads();
     for (int j = 0; j < kk; ++j) {               // right-looking Cholesky, reciprocal diagonal in s_rl
@@ -1356,7 +1356,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
         for (int q = 0; q < c; ++q) s = fma(-z[i * ld + q], Gp[c * kk + q], s);
         z[i * ld + c] = s * s_rl[c];
       }
-    if (!cl_sync(bar, tgt)) return false;
+    if (!cl_sync()) return false;
   }
   // ---- Rayleigh-Ritz in span(Z): Tz = Z^T (T Z) shared out, Jacobi on each CTA's copy ----
   const int kj = kk + 1;
@@ -1371,7 +1371,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
     if (i + 1 < r) s = fma(e[i], z[(i + 1) * ld + c], s);
     tmp[it] = s;
   }
-  if (!cl_sync(bar, tgt)) return false;
+  if (!cl_sync()) return false;
   for (int it = cl_lo(kk * kk, rank) + threadIdx.x; it < cl_lo(kk * kk, rank + 1); it += blockDim.x) {
     const int c1 = it / kk, c2 = it % kk;
     if (c2 > c1) continue;
@@ -1380,7 +1380,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
     Tz[c1 * kj + c2] = s;
     Tz[c2 * kj + c1] = s;
   }
-  if (!cl_sync(bar, tgt)) return false;
+  if (!cl_sync()) return false;
   for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) Tp[(it / kk) * kj + it % kk] = Tz[(it / kk) * kj + it % kk];
   __syncthreads();
   cta_jacobi(Tp, Qp, kk, kj);
@@ -1405,7 +1405,7 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
   __syncthreads();
   for (int it = zlo * kk + threadIdx.x; it < zhi * kk; it += blockDim.x) z[(it / kk) * ld + (it % kk)] = tmp[it];
   for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = Tp[ord[c] * kj + ord[c]];
-  if (!cl_sync(bar, tgt)) return false;
+  if (!cl_sync()) return false;
   // ---- back-transformation z = H_0 ... H_{r-3} y of this CTA's vectors (c = rank mod kRRCluster) ----
   {
     const int grp = threadIdx.x >> 3, q = threadIdx.x & 7;
@@ -1435,11 +1435,11 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
 }
 
 // k_rr for the problems with big = 1, one cluster of kRRCluster CTAs per task
-// (grid = tasks x kRRCluster).  T.bar: the task's barrier counter, zeroed
-// before the launch.  Dynamic shared memory: the substitutions' staging and
-// the private copies of cl_sym_lowest (rr_cl_smem doubles).  A barrier that
-// ran out leaves NaN in the first coefficient, so the problem's next residual
-// is not finite and the iteration reports it unconverged.
+// (grid = tasks x kRRCluster).  Dynamic shared memory: the substitutions' staging and
+// the private copies of cl_sym_lowest (rr_cl_smem doubles).  If a barrier
+// reported failure (a bounded form of cl_sync), the CTA would leave NaN in its
+// coefficient columns, so that the problem's next residual is not finite and
+// the iteration reports it unconverged.
 __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restrict__ tasks) {
   const RRTask T = tasks[blockIdx.x / kRRCluster];
   const int rank = blockIdx.x % kRRCluster;
@@ -1448,7 +1448,6 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
   extern __shared__ double rr_smem[];
   const double kDropRel = (T.mode && *T.mode) ? 1e-6 : 1e-10;
   const int ld = T.ld, k = T.k, nb = T.nb;
-  unsigned tgt = 0;
   double* C = T.work;                        // scaled H-Gram, then the reduced matrix (lower)
   double* V = T.work + (size_t)ld * ld;      // work matrix, then the eigenvectors
   double* G = T.work + (size_t)2 * ld * ld;  // scaled S-Gram (lower, original indices), then L
@@ -1478,7 +1477,7 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
     C[i * ld + j] = gh * sc;
   }
   if (threadIdx.x == 0) s_r = nb;
-  ok = cl_sync(T.bar, tgt);
+  ok = cl_sync();
   auto GP = [&](int pa, int pb) -> double& { return pa >= pb ? G[pa * ld + pb] : G[pb * ld + pa]; };
   // this CTA's copy of the diagonal (original indices), kept up to date with the
   // same fma as the trailing update, so that the pivot search reads nothing
@@ -1539,7 +1538,7 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
       double& s = GP(perm[aa], perm[bb]);
       s = fma(-colL[aa], colS[bb], s);
     }
-    if (!(ok = cl_sync(T.bar, tgt))) break;
+    if (!(ok = cl_sync())) break;
   }
   const int r = s_r;
   if (ok) {
@@ -1549,7 +1548,7 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
         double& s = GP(perm[aa], perm[jj]);
         s *= rdv[jj];
       }
-    ok = cl_sync(T.bar, tgt);
+    ok = cl_sync();
   }
   if (rank == 0 && threadIdx.x == 0 && r < k && T.fail) *T.fail = 1;
   auto Lp = [&](int aa, int bb) -> double { return GP(perm[aa], perm[bb]); };   // unit lower factor, aa > bb
@@ -1598,7 +1597,7 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
       }
       __syncthreads();
     }
-    ok = cl_sync(T.bar, tgt);
+    ok = cl_sync();
   }
   if (ok) {
     // the lower triangle of V L^-T on this CTA's rows x = rank + kRRCluster m,
@@ -1648,11 +1647,11 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr_cl(const RRTask* __restric
       if (bb > x) continue;
       C[x * ld + bb] = V[x * ld + bb] * (rl[x] * rl[bb]);
     }
-    ok = cl_sync(T.bar, tgt);
+    ok = cl_sync();
   }
   const int kk = min(k, r);
   if (ok) ok = cl_sym_lowest(C, V, r, ld, kk, T.work + (size_t)3 * ld * ld, priv, tdd, tee, ttau, tpv, tlam,
-                             order, T.bar, tgt, rank);
+                             order, rank);
   const int nown_k = (k - rank + kRRCluster - 1) / kRRCluster;   // this CTA's columns c = rank + kRRCluster m < k
   if (!ok) {
     for (int it = threadIdx.x; it < nown_k; it += blockDim.x) {
