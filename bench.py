@@ -470,11 +470,19 @@ def fp64_flops_per_step(problems, outs):
             T = len(p.Z) * p.R
             # per Fourier block solved (conjugate pairs once): Hadamard combine over
             # T+3 factor terms on the upper triangle (complex, ~20 flops per entry
-            # and term), Cholesky reduction C = L^-1 Hbar L^-H (~m0^3 complex
-            # multiply-adds = 8 m0^3), Householder tridiagonal (16/3 m0^3),
-            # Sturm bisection (m0 eigenvalues x 55 steps x 3 m0)
-            per = (T + 3) * m0 * (m0 + 1) // 2 * 20 + (8 + 16 / 3) * m0 ** 3 + 55 * 3 * m0 * m0
-            w["k_fblocks_eig"] = w.get("k_fblocks_eig", 0) + _conjugate_classes(p.L) * per
+            # and term), then by the route the block took.  Cholesky route:
+            # reduction C = L^-1 Hbar L^-H (~m0^3 complex multiply-adds = 8 m0^3).
+            # Eigendecomposition route (a direction at the dependency cut): complex
+            # Householder tridiagonal of Sbar (16/3 m0^3), QL with its rotations
+            # accumulated (~6 m0^3), back-transformation (8 m0^3), C = X^H Hbar X
+            # (16 m0^3).  Both: Householder tridiagonal of C (16/3 m0^3), Sturm
+            # bisection (m0 eigenvalues x 55 steps x 3 m0)
+            form = (T + 3) * m0 * (m0 + 1) // 2 * 20 + 16 / 3 * m0 ** 3 + 55 * 3 * m0 * m0
+            chol = form + 8 * m0 ** 3
+            eig = form + (16 / 3 + 6 + 8 + 16) * m0 ** 3
+            ncls = _conjugate_classes(p.L)
+            neig = min(int(o.get("n_eig", 0)), ncls)
+            w["k_fblocks_eig"] = w.get("k_fblocks_eig", 0) + neig * eig + (ncls - neig) * chol
     return w
 
 
@@ -525,6 +533,7 @@ def timed_plan(ctx, stream, problems, steps, warmup, flush, maxit=1000, profile=
     outs = plan.outputs(check=False)
     for i, o in enumerate(outs):
         _, o["M"], o["D"], o["nE"] = plan.sizes(i)
+        o["n_eig"] = plan.block_routes(i)
 
     def run():
         torch.cuda.synchronize()

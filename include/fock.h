@@ -282,6 +282,13 @@ int fock_plan_info(const fock_plan* plan, size_t* upload_bytes, size_t* device_b
  * capture was refused and the launches stayed eager).  Either pointer may be
  * NULL.  FOCK_EINVAL for a NULL plan. */
 int fock_plan_tuning(const fock_plan* plan, int* fft_cc, int* graph_nodes);
+/* Periodic problem i of a plan, after an execution: n_eig = the Fourier blocks
+ * (conjugate pairs once) whose overlap had a direction at or below the
+ * dependency cut, or could not be certified free of one, and so were solved
+ * through the overlap's eigendecomposition instead of its Cholesky factor
+ * (Prop. A.1; the cut of reading G16).  0 for other problems.  Synchronous.
+ * FOCK_EINVAL for a NULL plan or pointer or i out of range. */
+int fock_plan_block_routes(const fock_plan* plan, int i, int* n_eig);
 /* Sizes of problem i of a plan: N_b, circulant size M (box: M >= L + D;
  * periodic: |L|), generator reach D in cells (box) and boundary blocks. */
 int fock_plan_problem_sizes(const fock_plan* plan, int i, int* Nb, int* mcirc, int* D, int* nbound);

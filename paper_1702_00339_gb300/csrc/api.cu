@@ -794,12 +794,12 @@ void plan(Batch& B, Slab& S, Slab& U) {
       Q.nev = ncell * H.m0;
       Q.ev = S.take<double>(Q.nev);
       Q.blk = S.take<int>(Q.nev);
-      Q.fail = S.take<int>(1);
+      Q.fail = S.take<int>(2);   // [0]: a block's Sbar not positive definite; [1]: blocks cut
       FBlockTask f;
       std::memset(&f, 0, sizeof(f));
       f.prob = i; f.source = 0; f.nj = ncell;
       for (int a = 0; a < 3; ++a) { f.L[a] = H.L[a]; f.Xh[a] = Q.Xh[a]; }
-      f.want = 1; f.ev = Q.ev; f.blk = Q.blk; f.fail = Q.fail;
+      f.want = 1; f.ev = Q.ev; f.blk = Q.blk; f.fail = Q.fail; f.neig = Q.fail + 1;
       NullTask nt;
       std::memset(&nt, 0, sizeof(nt));
       nt.m0 = H.m0; nt.nF = H.nF; nt.nb = ncell * H.m0;
@@ -1380,8 +1380,10 @@ void run_assemble(fock_ctx* ctx, Batch& B) {
 }
 
 void zero_fail_flags(Batch& B, int kind, cudaStream_t st) {
+  // periodic problems: the flag and the count of blocks taking the eigendecomposition route
   for (int i = 0; i < B.nprob; ++i)
-    if (B.hp[i].kind == kind && B.pp[i].fail) cudaMemsetAsync(B.pp[i].fail, 0, sizeof(int), st);
+    if (B.hp[i].kind == kind && B.pp[i].fail)
+      cudaMemsetAsync(B.pp[i].fail, 0, (kind == 0 ? 2 : 1) * sizeof(int), st);
 }
 
 // Periodic problems: per-axis DFTs and the dependency cuts (head), the
@@ -2123,6 +2125,17 @@ int fock_plan_tuning(const fock_plan* P, int* fft_cc, int* graph_nodes) {
   if (!P) return FOCK_EINVAL;
   if (fft_cc) *fft_cc = P->B.tuned ? P->B.fft_cc : 0;
   if (graph_nodes) *graph_nodes = (P->B.iter_graph && P->B.iter_graph_b) ? P->B.graph_nodes : 0;
+  return FOCK_OK;
+}
+
+int fock_plan_block_routes(const fock_plan* P, int i, int* n_eig) {
+  if (!P || !n_eig || i < 0 || i >= P->B.nprob) return FOCK_EINVAL;
+  *n_eig = 0;
+  const Batch& B = P->B;
+  if (B.hp[i].kind != 0 || !B.pp[i].fail) return FOCK_OK;
+  fock_ctx* ctx = P->ctx;
+  CUDA_TRY(ctx, cudaMemcpyAsync(n_eig, B.pp[i].fail + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return FOCK_OK;
 }
 

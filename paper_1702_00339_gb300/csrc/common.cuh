@@ -190,6 +190,8 @@ struct FBlockTask {
                                  // null, the cut is formed from TS in the block kernel
   cplx* vecs;                    // optional [nj][m0][m0] (want 1): eigenvector i of block j at
                                  // [j][i][mu], Sbar_j-orthonormal, ascending; removed directions zero
+  int* neig;                     // optional: counts the blocks solved by the overlap's
+                                 // eigendecomposition (the Cholesky certificate failed)
 };
 
 // Dependency cut of a periodic problem: B[mu nu] = prod over axes of the sum

@@ -715,6 +715,7 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   // eigendecomposition of Sbar_j with the cut
   const bool chol = cta_cholesky_reduce(H, S, Aj, Qj, m0, s_tau);
   const int r = chol ? m0 : cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep);
+  if (!chol && F.neig && threadIdx.x == 0) atomicAdd(F.neig, 1);
   const int ldr = r + (r & 1);
   if (F.vecs) {   // the reduced matrix, kept for its eigenvectors
     for (int it = threadIdx.x; it < r * r; it += blockDim.x) Vc[(it / r) * ldr + it % r] = H[it];

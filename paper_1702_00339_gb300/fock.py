@@ -120,6 +120,7 @@ def lib():
         L.fock_plan_outputs.argtypes = [C.c_void_p, P(c_output), C.c_int]
         L.fock_plan_info.argtypes = [C.c_void_p, P(C.c_size_t), P(C.c_size_t), P(C.c_size_t)]
         L.fock_plan_tuning.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int)]
+        L.fock_plan_block_routes.argtypes = [C.c_void_p, C.c_int, P(C.c_int)]
         L.fock_plan_problem_sizes.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int),
                                               P(C.c_int)]
         L.fock_plan_free.argtypes = [C.c_void_p]
@@ -489,6 +490,13 @@ class Plan:
         a, b = C.c_int(), C.c_int()
         self.ctx._check(lib().fock_plan_tuning(self.h, C.byref(a), C.byref(b)), "fock_plan_tuning")
         return {"fft_cc": a.value, "graph_nodes": b.value}
+
+    def block_routes(self, i):
+        """Fourier blocks of periodic problem i (conjugate pairs once) solved
+        through the overlap's eigendecomposition at the last execution."""
+        a = C.c_int()
+        self.ctx._check(lib().fock_plan_block_routes(self.h, int(i), C.byref(a)), "fock_plan_block_routes")
+        return a.value
 
     def sizes(self, i):
         """(N_b, circulant size M, generator reach D, boundary blocks) of problem i."""

@@ -102,3 +102,25 @@ def test_large_rayleigh_ritz_same_bits_on_a_cluster_and_on_one_cta(ctx):
     H, S = dense.build(q)
     ref = _cases.reference(q, H, S)
     _cases.report("box_k32_cluster", _cases.check(ref, alone["evals"]))
+
+
+def test_block_route_count(ctx):
+    """fock_plan_block_routes counts the Fourier blocks solved through the
+    overlap's eigendecomposition: every block when a Gaussian is listed twice
+    (each overlap block is then singular), conjugate pairs once."""
+    import dataclasses
+    p = _cases.periodic_chain_small(L=6, seed=3)
+    p.k_eig = 0
+    dup = dataclasses.replace(p, exps=np.concatenate([p.exps, p.exps[:1]]),
+                              ang=np.concatenate([p.ang, p.ang[:1]]),
+                              centre=np.concatenate([p.centre, p.centre[:1]]))
+    dup.k_eig = 0
+    plan = ctx.plan([dup])
+    try:
+        plan.execute()
+        o = plan.outputs()[0]
+        assert o["status"] == 0
+        assert plan.block_routes(0) == 4          # j = 0, 3 and the pairs (1, 5), (2, 4)
+        assert int(np.sum(~np.isfinite(o["evals"]))) == 6   # one direction removed per block
+    finally:
+        plan.close()
