@@ -117,7 +117,28 @@ def _poll_all(srv, tickets, deadline):
     return out
 
 
-def serving_run(fock, dev, n_stream=512, n_burst=128, slots=2, max_batch=64, limit_s=300.0):
+def _poisson_stream(fock, dev, reqs, rate, seed, slots, max_batch, limit_s):
+    """Submit `reqs` with exponential gaps at `rate` per second to a fresh
+    server; (results, wall seconds from the first submit, server stats)."""
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(reqs))
+    srv = fock.Server(dev, slots=slots, max_batch=max_batch)
+    tickets = []
+    t0 = time.perf_counter()
+    nxt = t0
+    for p, g in zip(reqs, gaps):
+        nxt += g
+        d = nxt - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(p))
+    res = _poll_all(srv, tickets, time.perf_counter() + limit_s)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.stop()
+    return res, wall, st
+
+
+def serving_run(fock, dev, n_stream=512, n_burst=128, n_sweep=128, slots=2, max_batch=64, limit_s=300.0):
     """Continuous batching (fock_serve_*) against the plain per-lattice FP64
     path (one fock_solve per request, one after the other), both on the same
     burst of n_burst requests of the serving mix: solves/s of each.  The
@@ -153,24 +174,21 @@ def serving_run(fock, dev, n_stream=512, n_burst=128, slots=2, max_batch=64, lim
 
     stream = mixed_of(serving_requests(n_stream, seed=3000))
     rate = 0.8 * capm
-    gaps = np.random.default_rng(7).exponential(1.0 / rate, size=n_stream)
-    srv = fock.Server(dev, slots=slots, max_batch=max_batch)
-    tickets = []
-    t0 = time.perf_counter()
-    nxt = t0
-    for p, g in zip(stream, gaps):
-        nxt += g
-        d = nxt - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        tickets.append(srv.submit(p))
-    res = _poll_all(srv, tickets, time.perf_counter() + limit_s)
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.stop()
+    res, wall, st = _poisson_stream(fock, dev, stream, rate, 7, slots, max_batch, limit_s)
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res])
+    # arrival-rate sweep: n_sweep requests at 0.5, 1 and 1.5 times the mixed capacity
+    sweep = []
+    sweep_runs = []
+    for f in (0.5, 1.0, 1.5):
+        reqs = mixed_of(serving_requests(n_sweep, seed=3300 + int(10 * f)))
+        sr, sw, _ = _poisson_stream(fock, dev, reqs, f * capm, 11, slots, max_batch, limit_s)
+        sl = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in sr])
+        sweep.append({"rate_over_capacity": f, "arrival_per_s": f * capm, "throughput": len(reqs) / sw,
+                      "p50_ms": float(np.percentile(sl, 50)), "p99_ms": float(np.percentile(sl, 99)),
+                      "status_ok": int(sum(r["status"] == 0 for r in sr))})
+        sweep_runs.append((f"sweep_{f}", reqs, sr))
     runs = (("burst_fp64", burst, r64), ("burst_mixed", mburst, rm), ("plain_fp64", burst, rp),
-            ("stream_mixed", stream, res))
+            ("stream_mixed", stream, res)) + tuple(sweep_runs)
     ok = sum(r["status"] == 0 for _, _, rs_ in runs for r in rs_)
     total = sum(len(rs_) for _, _, rs_ in runs)
     fails = [{"run": nm, "i": i, "status": r["status"], "L": list(p.L), "periodic": list(p.periodic),
@@ -188,7 +206,7 @@ def serving_run(fock, dev, n_stream=512, n_burst=128, slots=2, max_batch=64, lim
                         "per-eigenvalue bar within which tests/test_gpu_large.py checks both forms against "
                         "the oracle's stored 16^3 and 32^3 spectra",
            "requests": n_stream, "arrival": f"Poisson at 80% of the mixed burst capacity ({rate:.1f}/s)",
-           "throughput": n_stream / wall}
+           "throughput": n_stream / wall, "arrival_sweep": sweep}
     out.update(latency_summary(lat, [bool(p.is_box or p.defects) for p in stream]))
     out.update({"slots": slots, "max_batch": max_batch, "batches": int(st["batches"]),
                 "max_inflight": int(st["max_inflight"]),
@@ -458,7 +476,9 @@ def fp64_flops_per_step(problems, outs):
             # banded preconditioner: forward and backward block substitution over
             # L cells with D + 1 blocks of m0 x m0 per block row, kb columns
             D = o.get("D")
-            if D is not None and o.get("band", True):
+            # the library's rule: the banded factor when 2 L D^2 m0^3 <= 4e9
+            band = D is not None and 2.0 * p.L[0] * D * D * m0 ** 3 <= 4e9
+            if band:
                 w["k_band_solve"] = w.get("k_band_solve", 0) + it * 4 * p.L[0] * (D + 1) * m0 * m0 * kb
             # circulant-embedding FFTs: per iteration 9 kb m0 column transforms (forward of W
             # and [X|P], inverse of their H and S images), 12 kb m0 at start; conventional
@@ -466,6 +486,15 @@ def fp64_flops_per_step(problems, outs):
             M = o.get("M")
             if M:
                 w["k_fft"] = w.get("k_fft", 0) + (it * 9 + 12) * kb * m0 * 5 * M * math.log2(M)
+                # block products at every frequency: a complex m0 x m0 block times
+                # ncol / 2 packed columns (8 m0^2 flops per packed column), H and S on
+                # W (kb columns) and on [X | P] (2 kb) per iteration, twice on [X | P]
+                # at start; the circulant preconditioner (one operator on kb) when
+                # the chain has no band factor
+                bm = lambda ncol, nop: nop * 8 * M * m0 * m0 * (ncol / 2)
+                pre = 0 if band else bm(kb, 1)
+                w["k_blockmul"] = (w.get("k_blockmul", 0) + it * (bm(kb, 2) + bm(2 * kb, 2) + pre)
+                                   + 2 * bm(2 * kb, 2))
         else:
             T = len(p.Z) * p.R
             # per Fourier block solved (conjugate pairs once): Hadamard combine over
@@ -728,6 +757,8 @@ def main():
                                       "TFLOP/s", f64src, pms)
     stages["c4_gram_products"] = roof("k_gemm_tn", "alu", flops.get("k_gemm_tn"), prof, args.steps, fp64_peak,
                                       "TFLOP/s", f64src, pms)
+    stages["c3_block_products"] = roof("k_blockmul", "alu", flops.get("k_blockmul"), prof, args.steps, fp64_peak,
+                                       "TFLOP/s", f64src, pms)
     mv_ms = sum(prof[k][1] for k in ("k_fft", "k_blockmul", "k_eapply") if k in prof)
     mvb = matvec_bytes_per_step(problems, outs)
     if mv_ms > 0 and mvb:
