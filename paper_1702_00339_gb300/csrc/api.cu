@@ -42,7 +42,7 @@ void launch_combine(const ProbDev*, const CombineTask*, int, cudaStream_t);
 void launch_defects(const ProbDev*, const DefField*, int, const DefBlock*, int, cudaStream_t);
 void launch_axis_dft(const ProbDev*, const DftTask*, int, int, cudaStream_t);
 void launch_fblocks(const ProbDev*, const FBlockTask*, int, int, int, cudaStream_t, bool vectors = false,
-                    int x0 = 0, int nx = -1);
+                    int x0 = 0, int nx = -1, bool any_odd = true);
 void launch_bloch_vectors(int, int, int, int, int, const int*, const cplx*, const int*, cplx*, cudaStream_t);
 void launch_split_gemm(const SplitTask*, int, int, int, int*, cudaStream_t, int max_ks = 1, bool reduce = false);
 void launch_null_tau(const NullTask*, int, cudaStream_t);
@@ -483,6 +483,7 @@ struct Batch {
   // problems; beside periodic problems one CTA each (k_rr), whose narrow launch
   // leaves the other SMs to the periodic pieces (both give the same bits)
   bool rr_cluster = false;
+  bool odd_m0 = true;                // some problem has odd m0 (Fourier-block layout, k_fblocks)
   int ptab_maxT = 0, ptab_maxni = 0; // potential tables: largest term count, endpoint count
   TL init, tnCx, nnW, pcG, pcM, pcZ, g1, g3, rr1, rr3, u1, u3, cp2k, resid, normP, normW;
   int fft_cc = 1, fft_chunks = 1;
@@ -521,6 +522,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
   B.dft.clear(); B.fbp.clear(); B.fbs.clear(); B.nulls.clear(); B.prec.clear(); B.canon.clear(); B.fbo.clear(); B.maxcblk = 0; B.sorts.clear(); B.bigsort.clear();
   B.circs.clear(); B.lob.clear(); B.sidx.clear(); B.mv_off.clear();
   B.maxnj_p = B.maxnj_s = 0; B.maxm0 = 1; B.maxM = 0; B.maxsort = 0; B.kmax = 0; B.maxLdft = 1;
+  B.odd_m0 = false;
   B.any_mixed = false;
   B.band_stage = 0;
   B.band_ringrow = 0;
@@ -538,6 +540,7 @@ void plan(Batch& B, Slab& S, Slab& U) {
     P.m0 = H.m0; P.M0 = H.M0; P.R = H.R; P.T = H.T; P.nF = H.nF; P.n0 = H.n0;
     P.b0 = H.b0; P.h = H.h; P.eps = H.eps;
     B.maxm0 = std::max(B.maxm0, H.m0);
+    B.odd_m0 = B.odd_m0 || (H.m0 & 1);
     std::vector<double> hpar;
     hpar.insert(hpar.end(), H.alpha.begin(), H.alpha.end());
     hpar.insert(hpar.end(), H.Z.begin(), H.Z.end());
@@ -1401,7 +1404,8 @@ void run_periodic_piece(fock_ctx* ctx, Batch& B, int nx, cudaStream_t st) {
   if (B.fbp.empty() || B.pchunk_next >= B.maxnj_p) return;
   const int w = (nx < 0) ? B.maxnj_p - B.pchunk_next : std::min(nx, B.maxnj_p - B.pchunk_next);
   { PROF("k_fblocks_eig", 1);
-    launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st, false, B.pchunk_next, w); }
+    launch_fblocks(B.d_probs, B.d_fbp, (int)B.fbp.size(), B.maxnj_p, B.maxm0, st, false, B.pchunk_next, w,
+                   B.odd_m0); }
   B.pchunk_next += w;
 }
 void run_periodic_tail(fock_ctx* ctx, Batch& B, cudaStream_t st) {
@@ -1422,7 +1426,8 @@ void run_struct_setup(fock_ctx* ctx, Batch& B) {
   zero_fail_flags(B, 1, st);
   { PROF("k_cell_canon", 2); launch_cell_canon(B.d_canon, (int)B.canon.size(), B.maxm0, B.maxcblk, st); }
   { PROF("k_twiddle", 1); launch_twiddles(B.d_circs, (int)B.circs.size(), st); }
-  { PROF("k_fblocks_embed", 1); launch_fblocks(B.d_probs, B.d_fbs, (int)B.fbs.size(), B.maxnj_s, B.maxm0, st); }
+  { PROF("k_fblocks_embed", 1);
+    launch_fblocks(B.d_probs, B.d_fbs, (int)B.fbs.size(), B.maxnj_s, B.maxm0, st, false, 0, -1, B.odd_m0); }
   { PROF("k_precond", 2); launch_precond(B.d_probs, B.d_prec, (int)B.prec.size(), B.maxM, B.maxm0, st); }
   for (auto& Q : B.pp)
     if (Q.band_fail) cudaMemsetAsync(Q.band_fail, 0, sizeof(int), st);

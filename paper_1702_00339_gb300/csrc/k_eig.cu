@@ -377,15 +377,24 @@ __device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
 // Hermitian).  With every direction kept, X^H s X = I and the eigenvalues of
 // h are the pencil's.  Returns r = |K|.  sv and keep are shared arrays of
 // MAXM0 entries.
+// a may be s itself (even m: the same layout); the copy is then skipped and,
+// should QL run out of iterations, -1 is returned (s is overwritten) so that the
+// caller forms s again and calls back with jacobi = true.
 __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m, double tau,
-                                 double* sv, int* keep) {
+                                 double* sv, int* keep, bool jacobi) {
   __shared__ int s_r;
   const int ld = m + (m & 1);
-  for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
-  __syncthreads();
-  if (!cta_herm_eig(a, q, m, ld)) {   // QL out of iterations: the Jacobi method
+  const bool inplace = ((const void*)a == (const void*)s);
+  if (!inplace) {
     for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
     __syncthreads();
+  }
+  if (jacobi || !cta_herm_eig(a, q, m, ld)) {   // QL out of iterations: the Jacobi method
+    if (!jacobi && inplace) return -1;
+    if (!inplace) {
+      for (int it = threadIdx.x; it < m * m; it += blockDim.x) a[(it / m) * ld + (it % m)] = s[it];
+      __syncthreads();
+    }
     cta_jacobi_herm(a, q, m, ld);
   }
   if (threadIdx.x == 0) {
@@ -569,6 +578,59 @@ __device__ inline cplx twiddle(long long num, int M) {   // exp(-2 pi i num / M)
   return cmk(c, s);
 }
 
+// Sbar_j of a block formed again, with the arithmetic of the formation in
+// k_fblocks (used where the block's eigendecomposition works in Sbar's own
+// storage and a route that overwrote it fell through).  tw: ldj^2 entries of
+// scratch for the Toeplitz twiddles.
+__device__ void reform_S(const FBlockTask& F, const ProbDev& P, int j, int m0, cplx* S, cplx* tw, int ldj) {
+  const int np = m0 * m0;
+  if (F.source == FROM_FACTORS) {
+    const int j3 = j % F.L[2], j2 = (j / F.L[2]) % F.L[1], j1 = j / (F.L[1] * F.L[2]);
+    const int nfe = P.nF * np;
+    const cplx* x0 = F.Xh[0] + (size_t)j1 * nfe;
+    const cplx* x1 = F.Xh[1] + (size_t)j2 * nfe;
+    const cplx* x2 = F.Xh[2] + (size_t)j3 * nfe;
+    const int nup = m0 * (m0 + 1) / 2;
+    for (int u = threadIdx.x; u < nup; u += blockDim.x) {
+      int mu = 0, rem = u;
+      while (rem >= m0 - mu) { rem -= m0 - mu; ++mu; }
+      const int nu = mu + rem, pr = mu * m0 + nu, tr = nu * m0 + mu;
+      cplx s = cmul(x0[pr], cmul(x1[pr], x2[pr]));
+      if (mu == nu) s.y = 0.0;
+      S[pr] = s;
+      S[tr] = cconj(s);
+    }
+    __syncthreads();
+  } else {
+    const bool tab = (F.D <= ldj * ldj);
+    if (tab) {
+      for (int dd2 = 1 + threadIdx.x; dd2 <= F.D; dd2 += blockDim.x) tw[dd2 - 1] = twiddle((long long)j * dd2, F.M);
+      __syncthreads();
+    }
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      const int mu = pr / m0, nu = pr % m0, tr = nu * m0 + mu;
+      cplx s = cmk(F.TS[pr], 0.0);
+      for (int dd2 = 1; dd2 <= F.D; ++dd2) {
+        const cplx w = tab ? tw[dd2 - 1] : twiddle((long long)j * dd2, F.M);
+        const double* ts = F.TS + (size_t)dd2 * np;
+        s = cadd(s, cmk(w.x * (ts[pr] + ts[tr]), w.y * (ts[pr] - ts[tr])));
+      }
+      S[pr] = s;
+    }
+    __syncthreads();
+    for (int pr = threadIdx.x; pr < np; pr += blockDim.x) {
+      const int mu = pr / m0, nu = pr % m0;
+      if (mu < nu) {
+        const cplx sm2 = cscale(cadd(S[pr], cconj(S[nu * m0 + mu])), 0.5);
+        S[pr] = sm2; S[nu * m0 + mu] = cconj(sm2);
+      } else if (mu == nu) {
+        S[pr].y = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* __restrict__ tasks, int x0) {
   extern __shared__ cplx sm[];
   const FBlockTask F = tasks[blockIdx.y];
@@ -590,10 +652,14 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   const ProbDev& P = probs[F.prob];
   const int m0 = P.m0, np = m0 * m0;
   const int ldj = m0 + (m0 & 1);
+  // even m0: the overlap's eigendecomposition works in Sbar's own storage (the
+  // same m0 x m0 layout), so a block needs three m0^2 arrays and 32 x 32 blocks
+  // fit four CTAs per SM; odd m0 keeps a padded work array of its own
+  const bool alias = !(m0 & 1);
   cplx* H = sm;
   cplx* S = sm + np;
-  cplx* Aj = S + np;            // Jacobi work, ldj x ldj
-  cplx* Qj = Aj + ldj * ldj;    // Jacobi eigenvectors, ldj x ldj
+  cplx* Aj = alias ? S : S + np;                       // eigendecomposition work, ldj x ldj
+  cplx* Qj = alias ? S + np : Aj + ldj * ldj;          // its eigenvectors, ldj x ldj
   cplx* v = Qj + ldj * ldj;
   cplx* pv = v + MAXM0;
   double* dd = (double*)(pv + MAXM0);
@@ -636,10 +702,10 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
       H[tr] = cconj(h); S[tr] = cconj(s);
     }
   } else {
-    // twiddles exp(-2 pi i j d / M), d = 1..D, once per block (in the Jacobi
-    // scratch, free until the canonical reduction) when they fit
-    cplx* tw = Aj;
-    const bool tab = (F.D <= 2 * ldj * ldj);
+    // twiddles exp(-2 pi i j d / M), d = 1..D, once per block (in the
+    // eigenvector scratch, free until the reduction) when they fit
+    cplx* tw = Qj;
+    const bool tab = (F.D <= ldj * ldj);
     if (tab) {
       for (int dd2 = 1 + threadIdx.x; dd2 <= F.D; dd2 += blockDim.x) tw[dd2 - 1] = twiddle((long long)j * dd2, F.M);
       __syncthreads();
@@ -714,7 +780,12 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
   // Cholesky when it certifies that nothing is numerically singular, else the
   // eigendecomposition of Sbar_j with the cut
   const bool chol = cta_cholesky_reduce(H, S, Aj, Qj, m0, s_tau);
-  const int r = chol ? m0 : cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep);
+  if (!chol && alias) reform_S(F, P, j, m0, S, Qj, ldj);   // the attempt factored Sbar in place
+  int r = chol ? m0 : cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep, false);
+  if (r < 0) {                                             // QL ran out on Sbar in place
+    reform_S(F, P, j, m0, S, Qj, ldj);
+    r = cta_lowdin_reduce(H, S, Aj, Qj, m0, s_tau, sv, keep, true);
+  }
   if (!chol && F.neig && threadIdx.x == 0) atomicAdd(F.neig, 1);
   const int ldr = r + (r & 1);
   if (F.vecs) {   // the reduced matrix, kept for its eigenvectors
@@ -964,20 +1035,28 @@ __global__ void k_unpad_copy(const double* pv, const int* pidx, int n, double* v
 }
 
 // ---- launchers ----
-size_t fblocks_smem(int m0, bool vectors) {
+// m0: the launch's largest block order; any_odd: some block of the launch has
+// odd m0 (its layout keeps a padded work array of its own)
+size_t fblocks_smem(int m0, bool vectors, bool any_odd) {
   const int ldj = m0 + (m0 & 1);
-  return (size_t)(2 * m0 * m0 + 2 * ldj * ldj + 2 * MAXM0) * sizeof(cplx) + 3 * MAXM0 * sizeof(double) +
-         2 * MAXM0 * sizeof(float) + (vectors ? 16 + 2 * ldj * ldj * sizeof(cplx) : 0);
+  const size_t mats = (!any_odd && !(m0 & 1)) ? (size_t)2 * m0 * m0 + (size_t)ldj * ldj
+                                              : (size_t)2 * m0 * m0 + (size_t)2 * ldj * ldj;
+  return (mats + 2 * MAXM0) * sizeof(cplx) + 3 * MAXM0 * sizeof(double) + 2 * MAXM0 * sizeof(float) +
+         (vectors ? 16 + 2 * ldj * ldj * sizeof(cplx) : 0);
 }
 
 // x0, nx: the launch covers local indices x0 .. x0 + nx - 1 of every task
 // (nx < 0: up to maxnj), so that a large solve can be issued in pieces
 void launch_fblocks(const ProbDev* probs, const FBlockTask* tasks, int ntask, int maxnj, int maxm0,
-                    cudaStream_t st, bool vectors, int x0, int nx) {
+                    cudaStream_t st, bool vectors, int x0, int nx, bool any_odd) {
   const int gx = (nx < 0) ? maxnj - x0 : std::min(nx, maxnj - x0);
   if (!ntask || gx <= 0) return;
-  size_t sm = fblocks_smem(maxm0, vectors);
+  size_t sm = fblocks_smem(maxm0, vectors, any_odd);
   FOCK_SMEM_OPTIN(k_fblocks);
+  {   // the largest shared-memory carveout: four 32 x 32 blocks (~54 KB each) per SM
+    static std::once_flag carve;
+    std::call_once(carve, [] { cudaFuncSetAttribute(k_fblocks, cudaFuncAttributePreferredSharedMemoryCarveout, 100); });
+  }
   // the rotation and update phases of an m0 x m0 block have about m0^2 / 2
   // parallel items: one warp for m0 <= 8 (more independent blocks resident
   // per SM keep the FP64 pipe busy), up to four warps for m0 = 32
