@@ -218,7 +218,7 @@ __device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
         const cplx* row = a + (size_t)(k + 1 + r) * ld + (k + 1);
         for (int c = part; c < m; c += 4) {
           const cplx uc = (c == 0) ? cmk(1.0, 0.0) : a[(k + 1 + c) * ld + k];
-          acc = cadd(acc, cmul(row[c], uc));
+          acc = cfma(row[c], uc, acc);
         }
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
@@ -245,7 +245,7 @@ __device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
       const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
       const cplx uj = (j == 0) ? cmk(1.0, 0.0) : a[(k + 1 + j) * ld + k];
       cplx* aij = a + (size_t)(k + 1 + i) * ld + (k + 1 + j);
-      *aij = csub(*aij, cadd(cmulc(ui, hpw[j]), cmulc(hpw[i], uj)));
+      *aij = crank2(*aij, ui, hpw[j], hpw[i], uj);
     }
     __syncthreads();
   }
@@ -348,7 +348,7 @@ __device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
       if (it < tot)
         for (int i = part; i < m; i += 4) {
           const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
-          acc = cadd(acc, cmulc(v[(k + 1 + i) * ld + j], ui));   // conj(u_i) V_ij
+          acc = cfmac(v[(k + 1 + i) * ld + j], ui, acc);         // conj(u_i) V_ij
         }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -360,7 +360,7 @@ __device__ bool cta_herm_eig(cplx* a, cplx* v, int n, int ld) {
     for (int it = threadIdx.x; it < m * n; it += blockDim.x) {
       const int i = it / n, j = it % n;
       const cplx ui = (i == 0) ? cmk(1.0, 0.0) : a[(k + 1 + i) * ld + k];
-      v[(k + 1 + i) * ld + j] = csub(v[(k + 1 + i) * ld + j], cmul(ui, hpw[j]));
+      v[(k + 1 + i) * ld + j] = cfma(cmk(-ui.x, -ui.y), hpw[j], v[(k + 1 + i) * ld + j]);
     }
     __syncthreads();
   }
@@ -415,14 +415,14 @@ __device__ int cta_lowdin_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, int m
   for (int it = threadIdx.x; it < m * r; it += blockDim.x) {
     int mu = it / r, c = it % r;
     cplx acc = cmk(0.0, 0.0);
-    for (int nu = 0; nu < m; ++nu) acc = cadd(acc, cmul(h[mu * m + nu], X[nu * r + c]));
+    for (int nu = 0; nu < m; ++nu) acc = cfma(h[mu * m + nu], X[nu * r + c], acc);
     Y[it] = acc;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < r * r; it += blockDim.x) {   // h = X^H Y
     int ia = it / r, ib = it % r;
     cplx acc = cmk(0.0, 0.0);
-    for (int mu = 0; mu < m; ++mu) acc = cadd(acc, cmulc(Y[mu * r + ib], X[mu * r + ia]));
+    for (int mu = 0; mu < m; ++mu) acc = cfmac(Y[mu * r + ib], X[mu * r + ia], acc);
     h[it] = acc;
   }
   __syncthreads();
@@ -478,7 +478,7 @@ __device__ bool cta_cholesky_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, in
   for (int it = threadIdx.x; it < m * m; it += blockDim.x) {   // a = L^-1 h
     const int i = it / m, j = it % m;
     cplx t = cmk(0.0, 0.0);
-    for (int k = 0; k <= i; ++k) t = cadd(t, cmul(q[i * m + k], h[k * m + j]));
+    for (int k = 0; k <= i; ++k) t = cfma(q[i * m + k], h[k * m + j], t);
     a[it] = t;
   }
   __syncthreads();
@@ -486,7 +486,7 @@ __device__ bool cta_cholesky_reduce(cplx* h, const cplx* s, cplx* a, cplx* q, in
     const int i = it / m, j = it % m;
     if (j > i) continue;
     cplx t = cmk(0.0, 0.0);
-    for (int k = 0; k <= j; ++k) t = cadd(t, cmulc(a[i * m + k], q[j * m + k]));
+    for (int k = 0; k <= j; ++k) t = cfmac(a[i * m + k], q[j * m + k], t);
     h[it] = t;
   }
   __syncthreads();
@@ -537,7 +537,7 @@ __device__ void cta_tridiag(cplx* c, int m, double* d, double* e, cplx* v, cplx*
     if (tau != 0.0) {
       for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) {
         cplx s = cmk(0.0, 0.0);
-        for (int j = k + 1; j < m; ++j) s = cadd(s, cmul(c[i * m + j], v[j]));
+        for (int j = k + 1; j < m; ++j) s = cfma(c[i * m + j], v[j], s);
         p[i] = cscale(s, tau);
       }
       __syncthreads();
@@ -554,8 +554,7 @@ __device__ void cta_tridiag(cplx* c, int m, double* d, double* e, cplx* v, cplx*
       for (int it = threadIdx.x; it < nt * nt; it += blockDim.x) {
         int i = k + 1 + it / nt, j = k + 1 + it % nt;
         // c -= v w^H + w v^H   (w stored in p)
-        cplx u = cadd(cmulc(v[i], p[j]), cmulc(p[i], v[j]));
-        c[i * m + j] = csub(c[i * m + j], u);
+        c[i * m + j] = crank2(c[i * m + j], v[i], p[j], p[i], v[j]);
       }
     }
     __syncthreads();
@@ -694,7 +693,8 @@ __global__ void k_fblocks(const ProbDev* __restrict__ probs, const FBlockTask* _
       for (int t = 0; t < P.T; ++t) {
         double w = P.Z[t / P.R] * P.cq[t % P.R];
         cplx pr3 = cmul(cmul(x0[(2 + t) * np + pr], x1[(2 + t) * np + pr]), x2[(2 + t) * np + pr]);
-        vv = cadd(vv, cscale(pr3, w));
+        vv.x = fma(pr3.x, w, vv.x);
+        vv.y = fma(pr3.y, w, vv.y);
       }
       cplx h = csub(hk, vv), s = cmul(s0, s12);
       if (mu == nu) { h.y = 0.0; s.y = 0.0; }
