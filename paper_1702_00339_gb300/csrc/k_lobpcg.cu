@@ -295,14 +295,116 @@ __device__ void cta_jacobi(double* a, double* v, int n, int ld) {
 // roots by Newton-Raphson from FP32 seeds, and locate eigenvalues by FP32
 // multisection.
 //
+// Shifts closer than kShiftCluster ||T|| form a cluster.  The FP32
+// multisection places a shift within a few FP32 units of ||T|| of its
+// eigenvalue, so two shifts in one such window can both lie much nearer one
+// of the two eigenvalues; inverse iteration then turns both vectors into that
+// one eigenvector, the Cholesky-QR below meets a singular Gram matrix, and
+// the Ritz basis built from it loses rank.  Exactly degenerate pairs (a ring
+// with two identical, distant defects) split, as the block iteration
+// converges, by about lambda res^2, which crosses that window.  A cluster's
+// vectors are therefore computed by one thread in turn, each orthogonalised
+// against the cluster's earlier vectors after every solve (the
+// reorthogonalisation of LAPACK's inverse iteration, dstein).
+constexpr double kShiftCluster = 32.0 * FLT_EPSILON;
+// The multisection's own resolution is far finer than that bound wherever
+// ||T|| is far above the wanted eigenvalues (the Rayleigh-Ritz matrices of
+// box chains), and clusters of the bound's width there chain long runs of
+// well separated shifts into one thread.  So clusters are first tight
+// (shifts whose final brackets lie within twice their widths: the ones the
+// multisection could not tell apart), and the wide clusters are taken only
+// when the first Cholesky factor of the vectors' Gram matrix meets a pivot
+// below kDepPivot (a unit vector within 1e-5 of the span of the earlier ones).
+constexpr double kDepPivot = 1e-10;
+
+// Whether shift q (> 0) joins the cluster of shift q - 1: tight (brackets lo,
+// hi of the multisection) or wide (kShiftCluster ||T||, tnorm = ||T||).
+__device__ inline bool shift_clustered(const double* lam, const float* lo, const float* hi, int q,
+                                       float tnorm, bool wide) {
+  const double gap = lam[q] - lam[q - 1];
+  if (wide) return gap <= kShiftCluster * (double)tnorm;
+  const double w = (double)(hi[q] - lo[q]) + (double)(hi[q - 1] - lo[q - 1]);
+  return gap <= 2.0 * w + 4.0 * FLT_EPSILON * fmax(fabs(lam[q]), fabs(lam[q - 1]));
+}
+
+// One inverse-iteration vector of the symmetric tridiagonal (d, e) of order r
+// for the shift lm into column c of z (rows 0..r-1, stride ld): LU with
+// partial pivoting of T - lm I (pivots below eps raised to eps; ws: 5 r
+// doubles of workspace), start vector from a counter hash of (row, c), three
+// sweeps of solve and normalisation.  Columns c0..c-1 (the earlier vectors
+// of c's cluster, orthonormal) are projected out after every solve; with
+// c0 == c the vector is the plain inverse iteration.
+__device__ void inverse_iteration(const double* d, const double* e, int r, double lm, double eps,
+                                  double* ws, double* z, int ld, int c, int c0) {
+  double* lv = ws;                                   // multipliers
+  double* rp = lv + r;                               // reciprocal pivots
+  double* u1 = rp + r;
+  double* u2 = u1 + r;
+  double* pvt = u2 + r;                              // row swap flags (bit pattern tested)
+  const long long eps_bits = abs_bits(eps);
+  // LU of T - lm I with partial pivoting between rows i and i+1, branch-free
+  double a0 = d[0] - lm, a1 = (r > 1) ? e[0] : 0.0;
+  for (int i = 0; i + 1 < r; ++i) {
+    const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
+    const bool sw = abs_bits(sub) > abs_bits(a0);
+    double p0 = sw ? sub : a0;
+    const double p1 = sw ? dn : a1, p2 = sw ? sn : 0.0;
+    const double o0 = sw ? a0 : sub, o1 = sw ? a1 : dn, o2 = sw ? 0.0 : sn;
+    if (abs_bits(p0) < eps_bits) p0 = (__double_as_longlong(p0) < 0) ? -eps : eps;   // tiny pivot raised to eps
+    const double rq = rcp_nr(p0);
+    const double m = o0 * rq;
+    lv[i] = m; rp[i] = rq; u1[i] = p1; u2[i] = p2; pvt[i] = sw ? 1.0 : 0.0;
+    a0 = fma(-m, p1, o1);
+    a1 = fma(-m, p2, o2);
+  }
+  if (abs_bits(a0) < eps_bits) a0 = (__double_as_longlong(a0) < 0) ? -eps : eps;
+  rp[r - 1] = rcp_nr(a0);
+  u1[r - 1] = 0.0; u2[r - 1] = 0.0;
+  if (r >= 2) u2[r - 2] = 0.0;
+  // start vector: counter hash of (row, vector), uniform in [0.5, 1.5)
+  for (int i = 0; i < r; ++i) {
+    const uint32_t h = (uint32_t)(splitmix64(((uint64_t)(c + 1) << 32) | (uint64_t)(i + 1)) >> 40);
+    z[i * ld + c] = 0.5 + (double)h * (1.0 / 16777216.0);
+  }
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int i = 0; i + 1 < r; ++i) {                // P and L^-1
+      const double zi = z[i * ld + c], zn = z[(i + 1) * ld + c];
+      const bool sw = __double_as_longlong(pvt[i]) != 0;
+      const double bi = sw ? zn : zi, bn = sw ? zi : zn;
+      z[i * ld + c] = bi;
+      z[(i + 1) * ld + c] = fma(-lv[i], bi, bn);
+    }
+    double nxt = 0.0, nxt2 = 0.0, nn = 0.0;          // U^-1, and the squared norm
+    for (int i = r - 1; i >= 0; --i) {
+      double s = fma(-u1[i], nxt, z[i * ld + c]);
+      s = fma(-u2[i], nxt2, s);
+      s *= rp[i];
+      z[i * ld + c] = s;
+      nn = fma(s, s, nn);
+      nxt2 = nxt; nxt = s;
+    }
+    if (c0 < c) {                                    // the cluster's earlier vectors projected out
+      for (int p = c0; p < c; ++p) {
+        double dp = 0.0;
+        for (int i = 0; i < r; ++i) dp = fma(z[i * ld + p], z[i * ld + c], dp);
+        for (int i = 0; i < r; ++i) z[i * ld + c] = fma(-dp, z[i * ld + p], z[i * ld + c]);
+      }
+      nn = 0.0;
+      for (int i = 0; i < r; ++i) nn = fma(z[i * ld + c], z[i * ld + c], nn);
+    }
+    const double inv = (nn > 0.0 && isfinite(nn)) ? rsqrt_nr(nn) : 0.0;
+    for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
+  }
+}
+
 // Householder reduction to a tridiagonal T = Q^T A Q (A symmetric, only its
 // lower triangle is read or kept; reflectors stay below the subdiagonal of
 // a); the kk lowest eigenvalues of T by FP32 Sturm multisection; one FP64
-// inverse-iteration vector per eigenvalue (LU with partial pivoting of
-// T - lambda I, three sweeps, one thread per vector); Cholesky-QR applied
-// twice to those vectors and a Rayleigh-Ritz step in their span (Jacobi of
-// the kk x kk projection of T), which restores orthogonality inside
-// clusters of close eigenvalues; z = Q y (groups of 8 lanes per vector).
+// inverse-iteration vector per eigenvalue (one thread per cluster of shifts,
+// see kShiftCluster); Cholesky-QR applied twice to those vectors and a
+// Rayleigh-Ritz step in their span (Jacobi of the kk x kk projection of T),
+// which restores orthogonality between clusters of close eigenvalues; z = Q y
+// (groups of 8 lanes per vector).
 // Eigenvector c lands in column c of z (rows 0..r-1, stride ld), eigenvalue
 // c in lam[c], ascending.  scr: 4 ld^2 doubles of scratch.  d, e, tau, pv:
 // shared arrays of >= 256 entries; ord: shared ints, >= kk + 1 entries.
@@ -388,12 +490,12 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
   }
   __syncthreads();
   float tnorm;                                   // Gershgorin bound of |T|, FP32
+  __shared__ float s_lo[128], s_hi[128];         // final multisection brackets (kk <= 128)
   // ---- kk lowest eigenvalues of T: FP32 Sturm multisection ----
   // Eigenvalue c is assigned a group of g = blockDim / kk threads; each round
   // the group counts the eigenvalues below g interior points of its bracket
   // and keeps the sub-interval holding eigenvalue c (g + 1 times narrower).
   {
-    __shared__ float s_lo[128], s_hi[128];       // kk <= 128
     __shared__ int s_cnt[kRRMaxThreads];
     float* df = reinterpret_cast<float*>(pv);    // pv is free here: d and e^2 in FP32
     float* e2f = df + 256;
@@ -453,69 +555,29 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
     for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = 0.5 * ((double)s_lo[c] + (double)s_hi[c]);
     __syncthreads();
   }
-  // ---- inverse iteration, one thread per vector (workspace 5 r per thread in scr) ----
+  // ---- inverse iteration: one thread per cluster of shifts (workspace 5 r per thread in scr),
+  // tight clusters first, wide ones when the Gram factor below finds a dependent vector ----
   const int nw = max(1, min(kk, min((4 * ld * ld) / (5 * r), (int)blockDim.x)));
-  if (threadIdx.x < nw) {
-    double* lv = scr + (size_t)threadIdx.x * 5 * r;   // multipliers
-    double* rp = lv + r;                               // reciprocal pivots
-    double* u1 = rp + r;
-    double* u2 = u1 + r;
-    double* pvt = u2 + r;                              // row swap flags (bit pattern tested)
-    const double eps = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
-    const long long eps_bits = abs_bits(eps);
-    for (int c = threadIdx.x; c < kk; c += nw) {
-      const double lm = lam[c];
-      // LU of T - lm I with partial pivoting between rows i and i+1, branch-free
-      double a0 = d[0] - lm, a1 = (r > 1) ? e[0] : 0.0;
-      for (int i = 0; i + 1 < r; ++i) {
-        const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
-        const bool sw = abs_bits(sub) > abs_bits(a0);
-        double p0 = sw ? sub : a0;
-        const double p1 = sw ? dn : a1, p2 = sw ? sn : 0.0;
-        const double o0 = sw ? a0 : sub, o1 = sw ? a1 : dn, o2 = sw ? 0.0 : sn;
-        if (abs_bits(p0) < eps_bits) p0 = (__double_as_longlong(p0) < 0) ? -eps : eps;   // tiny pivot raised to eps
-        const double rq = rcp_nr(p0);
-        const double m = o0 * rq;
-        lv[i] = m; rp[i] = rq; u1[i] = p1; u2[i] = p2; pvt[i] = sw ? 1.0 : 0.0;
-        a0 = fma(-m, p1, o1);
-        a1 = fma(-m, p2, o2);
-      }
-      if (abs_bits(a0) < eps_bits) a0 = (__double_as_longlong(a0) < 0) ? -eps : eps;
-      rp[r - 1] = rcp_nr(a0);
-      u1[r - 1] = 0.0; u2[r - 1] = 0.0;
-      if (r >= 2) u2[r - 2] = 0.0;
-      // start vector: counter hash of (row, vector), uniform in [0.5, 1.5)
-      for (int i = 0; i < r; ++i) {
-        const uint32_t h = (uint32_t)(splitmix64(((uint64_t)(c + 1) << 32) | (uint64_t)(i + 1)) >> 40);
-        z[i * ld + c] = 0.5 + (double)h * (1.0 / 16777216.0);
-      }
-      for (int sweep = 0; sweep < 3; ++sweep) {
-        for (int i = 0; i + 1 < r; ++i) {              // P and L^-1
-          const double zi = z[i * ld + c], zn = z[(i + 1) * ld + c];
-          const bool sw = __double_as_longlong(pvt[i]) != 0;
-          const double bi = sw ? zn : zi, bn = sw ? zi : zn;
-          z[i * ld + c] = bi;
-          z[(i + 1) * ld + c] = fma(-lv[i], bi, bn);
-        }
-        double nxt = 0.0, nxt2 = 0.0, nn = 0.0;        // U^-1, and the squared norm
-        for (int i = r - 1; i >= 0; --i) {
-          double s = fma(-u1[i], nxt, z[i * ld + c]);
-          s = fma(-u2[i], nxt2, s);
-          s *= rp[i];
-          z[i * ld + c] = s;
-          nn = fma(s, s, nn);
-          nxt2 = nxt; nxt = s;
-        }
-        const double inv = (nn > 0.0 && isfinite(nn)) ? rsqrt_nr(nn) : 0.0;
-        for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
+  auto vectors = [&](bool wide) {
+    if (threadIdx.x < nw) {
+      double* ws = scr + (size_t)threadIdx.x * 5 * r;
+      const double eps = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
+      for (int c = threadIdx.x; c < kk; c += nw) {
+        if (c > 0 && shift_clustered(lam, s_lo, s_hi, c, tnorm, wide)) continue;   // its cluster's first thread
+        for (int q = c; q < kk && (q == c || shift_clustered(lam, s_lo, s_hi, q, tnorm, wide)); ++q)
+          inverse_iteration(d, e, r, lam[q], eps, ws, z, ld, q, c);
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
+  };
   // ---- Cholesky-QR, twice: Z <- Z L^-T with Z^T Z = L L^T (G in scr[ld^2, 2 ld^2)) ----
   double* s_rl = pv;                             // reciprocal diagonal of the Gram factor
   double* G = scr + (size_t)ld * ld;
-  for (int pass = 0; pass < 2; ++pass) {
+  __shared__ int s_dep;
+  // the Gram of the (unit) vectors and its Cholesky factor; with `track`, s_dep
+  // = 1 when a pivot falls below kDepPivot (a vector nearly in the span of the
+  // earlier ones)
+  auto gram_factor = [&](bool track) {
     for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) {
       const int c1 = it / kk, c2 = it % kk;
       if (c2 > c1) continue;
@@ -523,9 +585,11 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
       for (int i = 0; i < r; ++i) s = fma(z[i * ld + c1], z[i * ld + c2], s);
       G[c1 * kk + c2] = s;
     }
+    if (threadIdx.x == 0) s_dep = 0;
     __syncthreads();
     for (int j = 0; j < kk; ++j) {               // right-looking Cholesky, reciprocal diagonal in s_rl
       if (threadIdx.x == 0) {
+        if (track && !(G[j * kk + j] >= kDepPivot)) s_dep = 1;
         const double gjj = fmax(G[j * kk + j], DBL_MIN);
         const double rl = rsqrt_nr(gjj);
         s_rl[j] = rl;
@@ -542,6 +606,8 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
       }
       __syncthreads();
     }
+  };
+  auto apply = [&]() {
     for (int i = threadIdx.x; i < r; i += blockDim.x)   // row i of Z times L^-T
       for (int c = 0; c < kk; ++c) {
         double s = z[i * ld + c];
@@ -549,7 +615,16 @@ __device__ void cta_sym_lowest(double* a, double* z, int r, int ld, int kk, doub
         z[i * ld + c] = s * s_rl[c];
       }
     __syncthreads();
+  };
+  vectors(false);
+  gram_factor(true);
+  if (s_dep) {                                   // uniform: read after the factor's last barrier
+    vectors(true);
+    gram_factor(false);
   }
+  apply();
+  gram_factor(false);
+  apply();
   // ---- Rayleigh-Ritz in span(Z): Tz = Z^T (T Z), Jacobi (stride kj = kk + 1) ----
   const int kj = kk + 1;
   double* Tz = scr + (size_t)2 * ld * ld;
@@ -657,7 +732,7 @@ __global__ void __launch_bounds__(kRRMaxThreads) k_rr(const RRTask* __restrict__
   __shared__ long long wkey[kRRMaxThreads / 32];
   __shared__ int perm[256], order[256], wpos[kRRMaxThreads / 32];
   __shared__ double tdd[256], tee[256], ttau[256], tpv[256], tlam[256];
-  __shared__ int s_r, s_piv;
+  __shared__ int s_r;
   __shared__ double s_rd;
   double* colS = tlam;                       // column of the Schur complement (until the eigensolver)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
@@ -1200,9 +1275,9 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
   }
   __syncthreads();
   float tnorm;                                   // Gershgorin bound of |T|, FP32
+  __shared__ float s_lo[128], s_hi[128];         // final multisection brackets (kk <= 128)
   // ---- kk lowest eigenvalues of T: FP32 Sturm multisection (every CTA alike) ----
   {
-    __shared__ float s_lo[128], s_hi[128];       // kk <= 128
     __shared__ int s_cnt[kRRMaxThreads];
     float* df = reinterpret_cast<float*>(pv);    // pv is free here: d and e^2 in FP32
     float* e2f = df + 256;
@@ -1262,66 +1337,26 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
     for (int c = threadIdx.x; c < kk; c += blockDim.x) lam[c] = 0.5 * ((double)s_lo[c] + (double)s_hi[c]);
     __syncthreads();
   }
-  // ---- inverse iteration: vector c on CTA c mod kRRCluster, workspace 5 r at scr + 5 r c ----
-  for (int c = rank + kRRCluster * (int)threadIdx.x; c < kk; c += kRRCluster * (int)blockDim.x) {
-    double* lv = scr + (size_t)c * 5 * r;        // multipliers
-    double* rp = lv + r;                         // reciprocal pivots
-    double* u1 = rp + r;
-    double* u2 = u1 + r;
-    double* pvt = u2 + r;                        // row swap flags
-    const double eps = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
-    const long long eps_bits = abs_bits(eps);
-    const double lm = lam[c];
-    double a0 = d[0] - lm, a1 = (r > 1) ? e[0] : 0.0;
-    for (int i = 0; i + 1 < r; ++i) {
-      const double sub = e[i], dn = d[i + 1] - lm, sn = (i + 2 < r) ? e[i + 1] : 0.0;
-      const bool sw = abs_bits(sub) > abs_bits(a0);
-      double p0 = sw ? sub : a0;
-      const double p1 = sw ? dn : a1, p2 = sw ? sn : 0.0;
-      const double o0 = sw ? a0 : sub, o1 = sw ? a1 : dn, o2 = sw ? 0.0 : sn;
-      if (abs_bits(p0) < eps_bits) p0 = (__double_as_longlong(p0) < 0) ? -eps : eps;
-      const double rq = rcp_nr(p0);
-      const double m = o0 * rq;
-      lv[i] = m; rp[i] = rq; u1[i] = p1; u2[i] = p2; pvt[i] = sw ? 1.0 : 0.0;
-      a0 = fma(-m, p1, o1);
-      a1 = fma(-m, p2, o2);
+  // ---- inverse iteration: the cluster of shifts led by vector c on CTA c mod kRRCluster,
+  // workspace 5 r at scr + 5 r c; tight clusters first, wide ones when the Gram
+  // factor below finds a dependent vector (every CTA decides alike: the copies
+  // it factors are equal) ----
+  const double eps_ii = DBL_EPSILON * fmax((double)tnorm, DBL_MIN);
+  auto vectors = [&](bool wide) -> bool {
+    for (int c = rank + kRRCluster * (int)threadIdx.x; c < kk; c += kRRCluster * (int)blockDim.x) {
+      if (c > 0 && shift_clustered(lam, s_lo, s_hi, c, tnorm, wide)) continue;   // its cluster's first thread
+      for (int q = c; q < kk && (q == c || shift_clustered(lam, s_lo, s_hi, q, tnorm, wide)); ++q)
+        inverse_iteration(d, e, r, lam[q], eps_ii, scr + (size_t)q * 5 * r, z, ld, q, c);
     }
-    if (abs_bits(a0) < eps_bits) a0 = (__double_as_longlong(a0) < 0) ? -eps : eps;
-    rp[r - 1] = rcp_nr(a0);
-    u1[r - 1] = 0.0; u2[r - 1] = 0.0;
-    if (r >= 2) u2[r - 2] = 0.0;
-    for (int i = 0; i < r; ++i) {
-      const uint32_t h = (uint32_t)(splitmix64(((uint64_t)(c + 1) << 32) | (uint64_t)(i + 1)) >> 40);
-      z[i * ld + c] = 0.5 + (double)h * (1.0 / 16777216.0);
-    }
-    for (int sweep = 0; sweep < 3; ++sweep) {
-      for (int i = 0; i + 1 < r; ++i) {
-        const double zi = z[i * ld + c], zn = z[(i + 1) * ld + c];
-        const bool sw = __double_as_longlong(pvt[i]) != 0;
-        const double bi = sw ? zn : zi, bn = sw ? zi : zn;
-        z[i * ld + c] = bi;
-        z[(i + 1) * ld + c] = fma(-lv[i], bi, bn);
-      }
-      double nxt = 0.0, nxt2 = 0.0, nn = 0.0;
-      for (int i = r - 1; i >= 0; --i) {
-        double s = fma(-u1[i], nxt, z[i * ld + c]);
-        s = fma(-u2[i], nxt2, s);
-        s *= rp[i];
-        z[i * ld + c] = s;
-        nn = fma(s, s, nn);
-        nxt2 = nxt; nxt = s;
-      }
-      const double inv = (nn > 0.0 && isfinite(nn)) ? rsqrt_nr(nn) : 0.0;
-      for (int i = 0; i < r; ++i) z[i * ld + c] *= inv;
-    }
-  }
-  if (!cl_sync()) return false;
+    return cl_sync();
+  };
   // ---- Cholesky-QR, twice: Gram entries shared out, each CTA factors its own copy ----
   double* s_rl = pv;                             // reciprocal diagonal of the Gram factor
   double* Gg = scr + (size_t)ld * ld;            // the Gram, shared by the cluster
   double* Gp = priv;                             // this CTA's copy, factored in place
   const int zlo = cl_lo(r, rank), zhi = cl_lo(r, rank + 1);   // this CTA's rows of Z
-  for (int pass = 0; pass < 2; ++pass) {
+  __shared__ int s_dep;
+  auto gram_factor = [&](bool track) -> bool {
     for (int it = cl_lo(kk * kk, rank) + threadIdx.x; it < cl_lo(kk * kk, rank + 1); it += blockDim.x) {
       const int c1 = it / kk, c2 = it % kk;
       if (c2 > c1) continue;
@@ -1331,9 +1366,11 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
     }
     if (!cl_sync()) return false;
     for (int it = threadIdx.x; it < kk * kk; it += blockDim.x) Gp[it] = Gg[it];
+    if (threadIdx.x == 0) s_dep = 0;
     __syncthreads();
     for (int j = 0; j < kk; ++j) {               // right-looking Cholesky, reciprocal diagonal in s_rl
       if (threadIdx.x == 0) {
+        if (track && !(Gp[j * kk + j] >= kDepPivot)) s_dep = 1;
         const double gjj = fmax(Gp[j * kk + j], DBL_MIN);
         const double rlj = rsqrt_nr(gjj);
         s_rl[j] = rlj;
@@ -1350,14 +1387,23 @@ __device__ bool cl_sym_lowest(double* a, double* z, int r, int ld, int kk, doubl
       }
       __syncthreads();
     }
+    return true;
+  };
+  auto apply = [&]() -> bool {
     for (int i = zlo + threadIdx.x; i < zhi; i += blockDim.x)   // row i of Z times L^-T
       for (int c = 0; c < kk; ++c) {
         double s = z[i * ld + c];
         for (int q = 0; q < c; ++q) s = fma(-z[i * ld + q], Gp[c * kk + q], s);
         z[i * ld + c] = s * s_rl[c];
       }
-    if (!cl_sync()) return false;
+    return cl_sync();
+  };
+  if (!vectors(false) || !gram_factor(true)) return false;
+  if (s_dep) {                                   // the workspace overlays the shared Gram: every
+    if (!cl_sync()) return false;                // CTA has copied it before the vectors are redone
+    if (!vectors(true) || !gram_factor(false)) return false;
   }
+  if (!apply() || !gram_factor(false) || !apply()) return false;
   // ---- Rayleigh-Ritz in span(Z): Tz = Z^T (T Z) shared out, Jacobi on each CTA's copy ----
   const int kj = kk + 1;
   double* Tz = scr + (size_t)2 * ld * ld;

@@ -15,9 +15,13 @@ here comes from the CUDA path.  Each file holds, for one seeded problem:
   .dense.chain_matrices), the lowest 64 eigenpairs by LAPACK under the
   dependency rule (each variant of a cell direction near the cut), and
   sampled blocks: Toeplitz generators at an interior cell and the corner
-  block of the first cell.
+  block of the first cell;
+* ring 202 x 1 x 1 (m0 = 4, periodic, substitutions Z = 1 -> 3 at cells 92
+  and 171; lowest 16): every level is a pair, exactly degenerate in double
+  precision (two identical, distant defects on a ring).  The dense H and S
+  (oracle.dense.build), the lowest 16 by LAPACK under the dependency rule.
 
-Run: python tests/golden/make_golden.py [c3] [c5p] [c5box]   (minutes each;
+Run: python tests/golden/make_golden.py [c3] [c5p] [c5box] [ring]   (minutes each;
 the box chain needs ~20 GB of host memory).
 """
 import os
@@ -102,8 +106,34 @@ def box(p, name):
                         ev=np.array(evs), vn2=np.array(vns), kept=np.array(kept))
 
 
+def ring(p, name):
+    t0 = time.time()
+    H, S = dense.build(p)
+    print(f"{name}: matrices {time.time() - t0:.0f} s", flush=True)
+    Hn = float(np.max(np.sum(np.abs(H), axis=1)))
+    Sn = float(np.max(np.sum(np.abs(S), axis=1)))
+    tau = blocks.null_threshold(p)
+    s, _, _ = blocks.cell_null_directions(p, tau)
+    evs, vns = [], []
+    for f in _flips(blocks.ambiguous(s, tau)):
+        ev, V, _ = blocks.box_eigs(p, H, S, tau=tau, vectors=True, flip=f)
+        evs.append(ev); vns.append(np.sum(V * V, axis=0))
+    np.savez_compressed(os.path.join(HERE, name + ".npz"), k=p.k_eig, Hn=Hn, Sn=Sn,
+                        ev=np.array(evs), vn2=np.array(vns))
+
+
+def ring_two_defects():
+    """The ring 202 x 1 x 1 of the serving mix (request 328 of its stream
+    with seed 3000: m0 = 4, two Z = 3 substitutions 79 cells apart)."""
+    p = li.serving_stream(512, seed=3000)[328]
+    assert p.L == (202, 1, 1) and p.periodic == (1, 0, 0) and len(p.defects) == 2
+    q = _tab(p)
+    q.k_eig = p.k_eig
+    return q
+
+
 if __name__ == "__main__":
-    which = set(sys.argv[1:]) or {"c3", "c5p", "c5box"}
+    which = set(sys.argv[1:]) or {"c3", "c5p", "c5box", "ring"}
     rng = np.random.default_rng(20170201)
     if "c3" in which:
         p = _tab(li.config3(0))
@@ -117,3 +147,5 @@ if __name__ == "__main__":
                  sorted(set([0, 1, 1057, corner] + list(rng.choice(p.ncell, 28, replace=False)))))
     if "c5box" in which:
         box(_tab(li.config5_box(0)), "config5_box_512_seed0")
+    if "ring" in which:
+        ring(ring_two_defects(), "ring_202_two_defects")

@@ -12,7 +12,10 @@ GPU):
   the first cell, and the lowest 64 eigenvalues of the dense pencil
   (LAPACK on 16384 x 16384);
 * box chains of the timed workload (64 cells, grid 1024x256x256), where the
-  dense oracle runs in the test: a batch solved together, each against it.
+  dense oracle runs in the test: a batch solved together, each against it;
+* a ring of 202 cells with two identical, distant substitutions, whose
+  levels are all exactly degenerate pairs: the lowest 16 against the dense
+  pencil's.
 
 The mixed form (tensor-core split products in the assembly and in the block
 iteration) is checked against the same stored results with the mixed bar
@@ -142,3 +145,36 @@ def test_box_chains_of_the_timed_workload(ctx):
         ref = _cases.reference(q, H, S)
         assert o["status"] == 0, s
         _cases.report(f"timed_box_seed{s}", _cases.check(ref, o["evals"]))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ring_with_degenerate_pairs(ctx, precision):
+    """Ring 202 x 1 x 1 (m0 = 4) with Z = 3 substitutions at cells 92 and 171:
+    every level is a pair, exactly degenerate in double precision, and the
+    Ritz values of each pair split by about lambda res^2 as the block
+    iteration converges.  When such a split fell inside one FP32 multisection
+    bracket of the Rayleigh-Ritz eigensolver, both inverse-iteration vectors
+    converged to one eigenvector, the Ritz basis lost rank and the solve
+    ended without convergence (FP64 form after 30 iterations, mixed after 50);
+    the vectors of a cluster of shifts are now orthogonalised against each
+    other."""
+    g = np.load(os.path.join(GOLD, "ring_202_two_defects.npz"))
+    p = li.serving_stream(512, seed=3000)[328]
+    assert p.L == (202, 1, 1) and p.periodic == (1, 0, 0) and len(p.defects) == 2
+    q = _cases.with_table(p)
+    q.k_eig = p.k_eig
+    if precision:
+        q = _mixed(q)
+    o = ctx.solve([q], check=False)[0]
+    assert o["status"] == 0, f"status {o['status']} after {o['iters']} iterations"
+    k = int(g["k"])
+    ev = np.asarray(o["evals"][:k])
+    base = MIXED_BASE if precision else 1e-10
+    scale = float(np.max(np.abs(g["ev"][0])))
+    cands = []
+    for evv, vn in zip(g["ev"], g["vn2"]):
+        tol = np.maximum(base * scale, _cases.EPS_DATA * (float(g["Hn"]) + np.abs(evv) * float(g["Sn"])) * vn)
+        cands.append((evv, tol))
+    e = _cases._match(ev, cands)
+    assert e is not None, f"lowest {k} off the oracle: max |d| {np.max(np.abs(ev - g['ev'][0])):.3e}"
+    _cases.report("ring_202_two_defects" + ("_mixed" if precision else ""), e / scale)
