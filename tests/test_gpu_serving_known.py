@@ -1,12 +1,15 @@
-"""Three periodic chains with defects of the serving mix (requests 298, 377
-and 478 of the seeded stream) that once ended unconverged (FOCK_ENOCONV)
+"""Four periodic chains with defects of the serving mix (requests 298, 328,
+377 and 478 of the seeded stream) that once ended unconverged (FOCK_ENOCONV)
 inside serving batches, each solved alone.  377 and 478 converge since only
 numerically singular overlap directions are removed (rank tolerance) and the
 circulant preconditioner's shift sits 2e-5 (relative) below the embedding's
 spectrum.  298 (194 cells, m0 = 16, three defects) converges slowly, in
 300-500 iterations depending on its start vector (its residual falls by
-~1.5 % per iteration near 1e-6), so the cap here is 1000 iterations (the
-serving default is 400).  Request 478's
+~1.5 % per iteration near 1e-6), within the default cap of 1000 iterations.
+328 (a ring of 202 cells whose levels are all exactly degenerate pairs)
+broke down when both vectors of a pair converged to one eigenvector in the
+Rayleigh-Ritz eigensolver; its eigenvalues are checked against the dense
+oracle in test_gpu_large.py.  Request 478's
 two substitutions keep Z = 1, so its operator is exactly the periodic
 chain's: its 16 lowest eigenvalues are checked against the oracle's
 Fourier-block spectrum of that chain."""
@@ -33,7 +36,7 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("rid", [478, 377, 298])
+@pytest.mark.parametrize("rid", [478, 377, 328, 298])
 def test_unconverged_serving_chain_alone(ctx, rid):
     p = li.serving_stream(rid + 1, seed=3000)[rid]
     plan = ctx.plan([p])
