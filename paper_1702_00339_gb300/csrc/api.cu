@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1599,9 +1600,13 @@ void lobpcg_body_b(Batch& B, cudaStream_t st) {
   mv_HS(B, true, st);
 }
 
+// on_left (optional): called after each convergence test with the problems
+// (indices into B.sidx) that left the iteration in it, converged or broken down;
+// no later launch touches their outputs, and the stream is idle at the call.
 int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>& iters,
                std::vector<double>& resid, std::vector<int>& conv,
-               std::vector<std::vector<double>>* hist = nullptr) {
+               std::vector<std::vector<double>>* hist = nullptr,
+               const std::function<void(const std::vector<int>&)>* on_left = nullptr) {
   cudaStream_t st = ctx->stream;
   const int ns = (int)B.sidx.size();
   iters.assign(ns, 0);
@@ -1656,7 +1661,7 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
     CUDA_TRY(ctx, cudaMemcpyAsync(hres.data(), B.d_res, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     bool any = false, changed = false, switched = false;
-    std::vector<int> just(ns, 0);
+    std::vector<int> just(ns, 0), left;
     for (int s2 = 0; s2 < ns; ++s2) {
       if (!active[s2]) continue;
       double mx = 0.0;
@@ -1693,7 +1698,9 @@ int run_lobpcg(fock_ctx* ctx, Batch& B, double tol, int maxit, std::vector<int>&
         active[s2] = 0; conv[s2] = 1; changed = true;
       }
       else any = true;
+      if (!active[s2]) left.push_back(s2);
     }
+    if (on_left && *on_left && !left.empty()) (*on_left)(left);
     if (!any || it >= maxit) break;
     if (changed) {
       CUDA_TRY(ctx, cudaMemcpyAsync(B.d_active, active.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1763,6 +1770,7 @@ struct fock_plan {
   std::vector<int> iters, conv;
   std::vector<double> resid;
   std::vector<std::vector<double>> hist;   // per structured problem: residual of each iteration
+  std::function<void(const std::vector<int>&)> on_left;   // see run_lobpcg (serving's early release)
 };
 
 namespace {
@@ -1784,7 +1792,7 @@ int plan_execute(fock_plan& P, double tol, int maxit) {
   if (!overlap) {
     run_periodic(ctx, B);
     run_struct_setup(ctx, B);
-    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
+    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist, &P.on_left);
     if (rc) return rc;
   } else {
     cudaStream_t user = ctx->stream;
@@ -1797,7 +1805,7 @@ int plan_execute(fock_plan& P, double tol, int maxit) {
     ctx->pstream = user;
     ctx->stream = ctx->hi;
     run_struct_setup(ctx, B);
-    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist);
+    int rc = run_lobpcg(ctx, B, tol, maxit, P.iters, P.resid, P.conv, &P.hist, &P.on_left);
     ctx->stream = user;
     ctx->pstream = nullptr;
     run_periodic_tail(ctx, B, user);
@@ -1959,9 +1967,48 @@ fock_ctx* detail_worker_ctx(int device, cudaMemPool_t pool, size_t budget) {
 const char* detail_ctx_error(const fock_ctx* c) { return c->err.c_str(); }
 cudaStream_t detail_ctx_stream(const fock_ctx* c) { return c->stream; }
 
-int detail_solve(fock_ctx* w, int n, const fock_problem* probs, fock_output* outs, double tol, int maxit) {
+// release (optional): called for each structured problem as soon as it leaves
+// the block iteration, with its output (eigenvalues already in outs[i].evals on
+// the host, n_evals, status, iters, resid); that problem's outs[i].evals is then
+// set to null, so the batch's final outputs leave the caller's buffer alone (the
+// caller may hand it back to its owner at once).  A mixed problem is released
+// early only while the batch's tensor-core completion flag is clear; else its
+// status (FOCK_ETIMEOUT) is decided with the batch's.
+int detail_solve(fock_ctx* w, int n, const fock_problem* probs, fock_output* outs, double tol, int maxit,
+                 const std::function<void(int, const fock_output&)>* release) {
   fock_plan P;
   P.ctx = w;
+  if (release && *release) {
+    P.on_left = [&P, outs, release](const std::vector<int>& left) {
+      Batch& B = P.B;
+      fock_ctx* c = P.ctx;
+      int split_err = 0;
+      std::vector<int> go;
+      if (B.d_split_err &&
+          cudaMemcpyAsync(&split_err, B.d_split_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return;
+      for (int s2 : left) {
+        const int i = B.sidx[s2];
+        if (!outs[i].evals) continue;
+        if (cudaMemcpyAsync(outs[i].evals, B.lob[s2].lam, B.pp[i].nev * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess)
+          return;
+        go.push_back(s2);
+      }
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;   // left to the batch's end
+      for (int s2 : go) {
+        const int i = B.sidx[s2];
+        if (split_err && B.hp[i].mixed) continue;
+        fock_output o = outs[i];
+        o.n_evals = B.pp[i].nev;
+        o.iters = P.iters[s2];
+        o.resid = P.resid[s2];
+        o.status = P.conv[s2] ? FOCK_OK : FOCK_ENOCONV;
+        outs[i].evals = nullptr;
+        (*release)(i, o);
+      }
+    };
+  }
   int rc = build_batch(w, n, probs, P.B, false);
   if (rc == FOCK_OK) rc = plan_execute(P, tol, maxit);
   if (rc == FOCK_OK || rc == FOCK_ENOCONV) rc = plan_outputs(P, outs, 0);

@@ -8,8 +8,10 @@
 // structured (an iteration: box chains and defects) -- while they fit the
 // server's HBM budget (bytes reserved by the batches already on the device
 // are subtracted) and the batch cap, solves them as one batch, publishes
-// the per-request results and releases its reservation.  A batch ends with
-// its slowest problem, so one-pass problems are not batched with iterated
+// the per-request results and releases its reservation.  A structured
+// request is published as soon as it leaves the block iteration, not when
+// its batch's slowest problem does.  A batch holds its reservation until its
+// slowest problem ends, so one-pass problems are not batched with iterated
 // ones; the head of the queue is always admitted first, so neither kind
 // waits more than the batches ahead of it.  Requests arriving
 // while batches run are admitted by the next free worker, so their work
@@ -25,6 +27,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -40,7 +43,8 @@ int detail_estimate(const fock_problem& p, size_t* bytes, int* n_evals, std::str
 fock_ctx* detail_worker_ctx(int device, cudaMemPool_t pool, size_t budget);
 const char* detail_ctx_error(const fock_ctx* c);
 cudaStream_t detail_ctx_stream(const fock_ctx* c);
-int detail_solve(fock_ctx* w, int n, const fock_problem* probs, fock_output* outs, double tol, int maxit);
+int detail_solve(fock_ctx* w, int n, const fock_problem* probs, fock_output* outs, double tol, int maxit,
+                 const std::function<void(int, const fock_output&)>* release);
 }  // namespace fock
 
 namespace {
@@ -176,11 +180,31 @@ void fock_server::worker(int slot) {
       outs[i].block_of = r->blk.empty() ? nullptr : r->blk.data();
       outs[i].status = FOCK_EAGAIN;
     }
-    int rc = fock::detail_solve(w, n, probs.data(), outs.data(), cfg.tol, cfg.maxit);
+    // a structured request is published as soon as it leaves the block
+    // iteration (its result is final then); the batch's end publishes the rest.
+    // A published request may be released by its client at once, so nothing
+    // below touches it again.
+    std::vector<char> published(n, 0);
+    int n_published = 0;
+    const std::function<void(int, const fock_output&)> publish = [&](int i, const fock_output& o) {
+      std::lock_guard<std::mutex> lk(m);
+      Req* r = batch[i];
+      r->status = o.status;
+      r->iters = o.iters;
+      r->resid = o.resid;
+      r->t_done = now_ns();
+      r->done = true;
+      published[i] = 1;
+      ++n_published;
+      ++completed;
+      cv_done.notify_all();
+    };
+    int rc = fock::detail_solve(w, n, probs.data(), outs.data(), cfg.tol, cfg.maxit, &publish);
     {
       std::lock_guard<std::mutex> lk(m);
       const int64_t td = now_ns();
       for (int i = 0; i < n; ++i) {
+        if (published[i]) continue;
         Req* r = batch[i];
         r->status = (outs[i].status == FOCK_EAGAIN) ? (rc ? rc : FOCK_ECUDA) : outs[i].status;
         r->iters = outs[i].iters;
@@ -191,7 +215,7 @@ void fock_server::worker(int slot) {
       if (rc && rc != FOCK_ENOCONV && rc != FOCK_EINVAL) err = fock::detail_ctx_error(w);
       reserved -= bytes;
       --inflight;
-      completed += n;
+      completed += n - n_published;
     }
     cv_done.notify_all();
     cv_work.notify_all();

@@ -112,3 +112,35 @@ def test_refusals(fock):
         srv.submit(bad)
     assert e.value.code == fock.FOCK_EINVAL
     srv.stop()
+
+
+def test_structured_request_published_when_it_leaves_the_iteration(fock):
+    """A box chain that converges in tens of iterations and a ring of 194
+    cells with three defects that needs hundreds share one batch (one slot,
+    both queued behind a 16^3 lattice).  The chain's result is published when
+    it converges, before the batch ends, and the client frees it at once
+    while the batch still runs; both results equal a solve alone bit for
+    bit."""
+    fast = _cases.box_chain_small(L=12, n0=5, pad=6, n_perp=20, seed=0, R=16, k=6)
+    slow = li.serving_stream(299, seed=3000)[298]
+    ctx = fock.Context(0)
+    alone = [ctx.solve([q], check=False)[0] for q in (fast, slow)]
+    ctx.close()
+    assert alone[0]["iters"] < alone[1]["iters"]
+    srv = fock.Server(0, slots=1, max_batch=8)
+    tb = srv.submit(_cases.with_table(li.config3(0)))
+    tf = srv.submit(fast)
+    ts = srv.submit(slow)
+    rf = srv.poll(tf, timeout_ms=300000)
+    rs = srv.poll(ts, timeout_ms=300000)
+    rb = srv.poll(tb, timeout_ms=300000)
+    st = srv.stats()
+    srv.stop()
+    assert rb["status"] == 0 and rb["batch_id"] < rf["batch_id"]
+    assert rf["batch_id"] == rs["batch_id"] and rf["batch_size"] == 2
+    assert rf["t_done_ns"] < rs["t_done_ns"]
+    assert st["completed"] == 3
+    for r, a in zip((rf, rs), alone):
+        assert r["status"] == a["status"] == 0
+        assert r["iters"] == a["iters"]
+        assert np.array_equal(r["evals"], a["evals"])
