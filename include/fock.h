@@ -394,10 +394,15 @@ int fock_serve_start(int device, const fock_serve_config* cfg, fock_server** out
  * Thread-safe. */
 int fock_serve_submit(fock_server* s, const fock_problem* p, uint64_t* ticket);
 /* Waits up to timeout_ms (< 0: no limit, 0: no wait) for the ticket's result.
+ * A periodic request's result is ready when its batch ends; a structured
+ * request's (box chains, defects) as soon as it leaves the block iteration,
+ * while the rest of its batch may still run (the values are the same either
+ * way; t_done_ns records which).
  * FOCK_OK: *out filled (the problem's own status in out->status);
  * FOCK_EAGAIN: not finished yet; FOCK_EINVAL: unknown ticket.  Thread-safe. */
 int fock_serve_poll(fock_server* s, uint64_t ticket, fock_result* out, int timeout_ms);
-/* Frees a finished ticket's result (FOCK_EAGAIN if it is still running). */
+/* Frees a finished ticket's result (FOCK_EAGAIN if it is still running); a
+ * finished structured request may be freed while its batch still runs. */
 int fock_result_release(fock_server* s, uint64_t ticket);
 int fock_serve_stats(fock_server* s, fock_serve_stats_t* out);
 const char* fock_serve_last_error(const fock_server* s);

@@ -10,8 +10,9 @@
 //  k_resid      R = HX - SX diag(lambda), relative residual norms, soft locking
 //  k_rr         Rayleigh-Ritz: diagonal scaling, pivoted LDL^T of Y^T S Y (rank-revealing),
 //               C = Delta^-1/2 L^-1 (Y^T H Y) L^-T Delta^-1/2, Householder tridiagonal,
-//               FP32 multisection shifts, FP64 inverse iteration, Cholesky-QR twice and a
-//               Rayleigh-Ritz step in their span, back-transformation; lowest k
+//               FP32 multisection shifts, FP64 inverse iteration (clusters of shifts in turn),
+//               Cholesky-QR twice and a Rayleigh-Ritz step in their span, back-transformation;
+//               lowest k
 //  k_colnorm    unit 2-norm columns (non-finite ones zeroed)
 //  k_copy_cols  column-block copies
 //  k_gather     results of a batch into one staging buffer
