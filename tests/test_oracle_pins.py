@@ -536,6 +536,37 @@ def test_defects_on_every_cell_equal_a_charge_change_periodic_odd_chain():
     assert np.array_equal(Sq, S)
 
 
+@pytest.mark.parametrize("maker", [
+    lambda: _cases.periodic_chain_small(L=9, n0=6, n_perp=14, m0=4, R=12),
+    lambda: _cases.box_chain_small(L=10, n0=5, pad=5, n_perp=14, seed=1, R=12, k=4),
+])
+def test_defect_contributions_add_and_scale_with_the_charge_change(maker):
+    """The nuclear potential is linear in the charges, so substitutions enter
+    H as independent terms proportional to their charge change: two defects
+    give the sum of their separate changes of H, halving the charge change
+    halves the term, a substitution Z -> Z changes nothing, and S is never
+    touched.  (A charge change is not local: the second defect's Coulomb tail
+    shifts the first one's bound levels, so the pin is on H, not on the
+    spectrum.)"""
+    p = maker()
+    H0, S0 = dense.build(p)
+
+    def build(defects):
+        return dense.build(_chain_with_defects(p, defects))
+
+    Ha, Sa = build([li.Defect((2, 0, 0), 0, 3.0)])
+    Hb, _ = build([li.Defect((6, 0, 0), 0, 3.0)])
+    Hab, Sab = build([li.Defect((2, 0, 0), 0, 3.0), li.Defect((6, 0, 0), 0, 3.0)])
+    Hh, _ = build([li.Defect((2, 0, 0), 0, 2.0)])
+    Hn, _ = build([li.Defect((2, 0, 0), 0, float(p.Z[0]))])
+    scale = np.max(np.abs(Ha - H0))
+    assert scale > 0.1
+    assert np.max(np.abs((Hab - H0) - (Ha - H0) - (Hb - H0))) <= 1e-12 * scale
+    assert np.max(np.abs(2.0 * (Hh - H0) - (Ha - H0))) <= 1e-12 * scale
+    assert np.max(np.abs(Hn - H0)) <= 1e-12 * scale
+    assert np.array_equal(Sa, S0) and np.array_equal(Sab, S0)
+
+
 def test_defect_matrix_translation_covariance():
     """A defect moved by one cell moves its matrix by one cell: cyclically on
     a periodic chain (exact symmetry of the ring), and in the interior of a
