@@ -580,7 +580,9 @@ class Server:
     def poll(self, ticket, timeout_ms=-1, release=True):
         """The ticket's result as a dict, or None if not finished within
         timeout_ms.  Copies the eigenvalues out and (by default) releases the
-        library's buffers."""
+        library's buffers.  A structured request (box chain, defects) is ready
+        as soon as it leaves the block iteration, while its batch may still
+        run; a periodic one when its batch ends."""
         r = c_result()
         rc = lib().fock_serve_poll(self.h, C.c_uint64(ticket), C.byref(r), int(timeout_ms))
         if rc == FOCK_EAGAIN:
